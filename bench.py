@@ -1,0 +1,336 @@
+"""Throughput benchmark of the BML lattice step on B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Workload: one 32768 x 32768 periodic lattice per GPU (1.07 G cells, 256 MB
+of bitplanes), density 0.38 split evenly LR/TB, seeded placement (seed 1 on
+rank 0, 1 + rank elsewhere), moved counts recorded every step.  One bench
+step is bml_step(sim, 8): eight full lattice steps, so the default 1250
+steps are 10^4 lattice steps.  Metric: cell-updates/s over the whole job.
+
+The bitplane state (2 x 256 MB, ping-pong) is larger than the 126 MB L2, so
+no flush is needed between timed steps.  With --gpus N > 1 (torchrun) each
+rank runs an independent replica (weak scaling); there is no data-path
+collective.
+
+--impl reference times the CPU oracle (test infrastructure) on the host
+cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+M_ROWS = N_COLS = 32768
+DENSITY = 0.38
+STEPS_PER_BENCH_STEP = 8
+BYTES_PER_CELL_STEP = 0.5  # 2 bits read + 2 bits written per cell per step
+WORKLOAD = "bml_32768x32768_rho0.38"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.tmp = None
+
+    def start(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.tmp.flush()
+        with open(self.tmp.name) as fh:
+            rows = [r for r in csv.reader(io.StringIO(fh.read())) if len(r) >= 9]
+        os.unlink(self.tmp.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4)
+                          if r[5 + k].strip().lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _cpu_sample(budget_s: float, threads: int):
+    """Time the oracle, as it stands, on a band of rows of the workload
+    (periodic R x 32768 lattice, same density and placement rule).  Returns
+    (cell-updates/s, description)."""
+    import oracle
+    rows = 256
+    g = oracle.init(rows, N_COLS, 1, DENSITY / 2, DENSITY / 2)
+    t0 = time.perf_counter()
+    oracle.run(g, 1, threads=threads)
+    per = max(time.perf_counter() - t0, 1e-6)  # seconds per step for `rows` rows
+    rows = int(min(M_ROWS, max(64, rows * budget_s / (per * STEPS_PER_BENCH_STEP))))
+    g = oracle.init(rows, N_COLS, 1, DENSITY / 2, DENSITY / 2)
+    t0 = time.perf_counter()
+    oracle.run(g, STEPS_PER_BENCH_STEP, threads=threads)
+    dt = time.perf_counter() - t0
+    rate = rows * N_COLS * STEPS_PER_BENCH_STEP / dt
+    desc = ("oracle (C, OpenMP rows, %d threads) on a %d x %d periodic lattice at "
+            "density %.2f, %d steps, %.1f s" % (threads, rows, N_COLS, DENSITY,
+                                               STEPS_PER_BENCH_STEP, dt))
+    return rate, desc, dt
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    threads = os.cpu_count() or 1
+    # size each reference step so that warmup + steps take ~2 minutes
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    rows = 64
+    g = oracle.init(rows, N_COLS, 1, DENSITY / 2, DENSITY / 2)
+    t0 = time.perf_counter()
+    oracle.run(g, 1, threads=threads)
+    per_row_step = max(time.perf_counter() - t0, 1e-6) / rows
+    rows = int(min(M_ROWS, max(8, budget / (per_row_step * STEPS_PER_BENCH_STEP))))
+    g = oracle.init(rows, N_COLS, 1, DENSITY / 2, DENSITY / 2)
+    for _ in range(args.warmup):
+        g, _, _ = oracle.run(g, STEPS_PER_BENCH_STEP, threads=threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        g, _, _ = oracle.run(g, STEPS_PER_BENCH_STEP, threads=threads)
+    dt = time.perf_counter() - t0
+    value = rows * N_COLS * STEPS_PER_BENCH_STEP * args.steps / dt
+    sample = ("each step: %d lattice steps of a %d x %d periodic band of the workload "
+              "(density %.2f)" % (STEPS_PER_BENCH_STEP, rows, N_COLS, DENSITY))
+    line = {
+        "impl": "reference", "metric": "cell-updates/s", "value": value,
+        "unit": "cell-updates/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt * 1e3 / max(1, args.steps),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "M": M_ROWS, "N": N_COLS, "density": DENSITY,
+                   "lattice_steps_per_step": STEPS_PER_BENCH_STEP, "impl": "cpu oracle"},
+        "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": threads,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(local)
+    from paper_1804_07981_b300 import bml
+
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.Stream(device=dev)
+    seed = 1 + rank
+    M, N = args.M, args.N
+    cells = M * N
+    K, W = args.steps, args.warmup
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---------------- device-resident run (value, roofline) ----------------
+    sim = bml.Lattice(M, N, seed=seed, p_lr=DENSITY / 2, p_tb=DENSITY / 2, kernel=args.kernel,
+                      block_k=args.block_k, stream=stream,
+                      reserve_steps=(K + W) * STEPS_PER_BENCH_STEP)
+    kernel_id, block_k, band_rows = sim.config
+    for _ in range(W):
+        sim.step(STEPS_PER_BENCH_STEP)
+    sim.synchronize()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(K):
+        sim.step(STEPS_PER_BENCH_STEP)
+    e1.record(stream)
+    e1.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    ms_max = max_over_ranks(ms)
+    lattice_steps = K * STEPS_PER_BENCH_STEP
+    value = world * cells * lattice_steps / (ms_max / 1e3)
+    # counts of the timed steps must be complete and plausible
+    tot, _, _ = sim.moved_counts(W * STEPS_PER_BENCH_STEP, lattice_steps)
+    assert (tot >= 0).all() and (tot <= cells).all()
+
+    # dominant kernel: every launch in the timed region is the same kernel
+    if kernel_id in (bml.BML_KERNEL_TBLOCK, bml.BML_KERNEL_FUSED):
+        launches_per_step = STEPS_PER_BENCH_STEP // max(1, block_k)
+        kname = "stream_kernel<%d>" % max(1, block_k)
+        depth = max(1, block_k)
+        bytes_per_launch = BYTES_PER_CELL_STEP * cells  # one pass over both planes
+    elif kernel_id == bml.BML_KERNEL_BITPLANE:
+        launches_per_step = 2 * STEPS_PER_BENCH_STEP
+        kname, depth = "plane_h/plane_v", 1
+        bytes_per_launch = 0.4375 * cells
+    else:
+        launches_per_step = 2 * STEPS_PER_BENCH_STEP
+        kname, depth = "byte_h/byte_v", 1
+        bytes_per_launch = 2.0 * cells
+    launch_ms = ms / (K * launches_per_step)
+    hbm_peak, peak_kind = _peaks()
+    achieved = bytes_per_launch / (launch_ms / 1e3) / 1e9
+    effective = BYTES_PER_CELL_STEP * cells * lattice_steps / (ms / 1e3) / 1e9
+    roofline = {
+        "bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm_peak,
+        "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+        "peak_kind": peak_kind, "launch_ms": launch_ms, "temporal_depth": depth,
+        "effective_GBps": effective, "effective_frac": effective / hbm_peak,
+    }
+    gpu_launches = K * launches_per_step
+
+    # ---------------- end to end through the C ABI with host buffers -------
+    import numpy as np
+    e2e = None
+    if not args.no_e2e:
+        host_in = torch.empty((M, N), dtype=torch.uint8, pin_memory=True)
+        host_out = torch.empty((M, N), dtype=torch.uint8, pin_memory=True)
+        sim.synchronize()
+        hin = host_in.numpy()  # the seeded lattice, as a user's host input
+        bml.bml_read_lattice(sim.handle, M, N, out=hin)
+        hout = host_out.numpy()
+        counts_host = np.zeros((K, 3, STEPS_PER_BENCH_STEP), dtype=np.int64)
+        barrier()
+        t0 = time.perf_counter()
+        bml.bml_write_lattice(sim.handle, hin)  # H2D + pack, restarts the trajectory
+        for s in range(K):
+            bml.bml_step(sim.handle, STEPS_PER_BENCH_STEP)
+            a, b, c = bml.bml_moved_counts(sim.handle, s * STEPS_PER_BENCH_STEP,
+                                           STEPS_PER_BENCH_STEP)
+            counts_host[s, 0], counts_host[s, 1], counts_host[s, 2] = a, b, c
+        bml.bml_read_lattice(sim.handle, M, N, out=hout)
+        dt = time.perf_counter() - t0
+        dt = max_over_ranks(dt)
+        e2e = {"value": world * cells * lattice_steps / dt, "unit": "cell-updates/s",
+               "h2d_bytes_per_step": cells / K,
+               "d2h_bytes_per_step": cells / K + STEPS_PER_BENCH_STEP * 3 * 8,
+               "seconds": dt}
+    sim.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        threads = os.cpu_count() or 1
+        rate, desc, _ = _cpu_sample(args.cpu_seconds, threads)
+        cpu = {"value": rate, "unit": "cell-updates/s", "cores": threads, "kind": "oracle",
+               "sample": desc}
+
+    if rank == 0:
+        line = {
+            "metric": "cell-updates/s", "value": value, "unit": "cell-updates/s",
+            "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": ms_max / K,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u64 bitplanes" if kernel_id != bml.BML_KERNEL_BYTE else "u8",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "M": M, "N": N, "density": DENSITY,
+                       "seed": 1, "lattice_steps_per_step": STEPS_PER_BENCH_STEP,
+                       "kernel": {0: "auto", 1: "byte", 2: "bitplane", 3: "fused",
+                                  4: "tblock"}[kernel_id],
+                       "temporal_depth": block_k, "band_rows": band_rows,
+                       "l2": "inputs larger than L2 (2 x 256 MB bitplanes)",
+                       "parallelism": "replicas x%d" % world},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": gpu_launches, "clocks": clk,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1250)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--kernel", default="auto")
+    ap.add_argument("--block-k", type=int, default=0)
+    ap.add_argument("--M", type=int, default=M_ROWS)
+    ap.add_argument("--N", type=int, default=N_COLS)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.impl == "ours":
+        args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

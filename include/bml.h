@@ -1,0 +1,152 @@
+/*
+ * bml.h -- C ABI of the B300 (sm_103a) Biham-Middleton-Levine traffic CA.
+ *
+ * The automaton (Marzolla 2018, "Parallel Implementations of Cellular
+ * Automata for Traffic Models", Sec. 2): a periodic lattice of M rows and
+ * N columns; each cell is EMPTY (0), LR (1, moves one column right) or
+ * TB (2, moves one row down).  One step is a horizontal phase (every LR car
+ * whose right neighbour is EMPTY moves into it) followed by a vertical phase
+ * (every TB car whose lower neighbour is EMPTY moves into it), both applied
+ * synchronously with wrap-around.  The paper states the model for square
+ * N x N lattices; this library takes any M x N.
+ *
+ * Lattice format at the boundary (Sec. 3): one byte per cell, values 0/1/2,
+ * row-major, cell (i, j) at byte i*N + j, no padding.
+ *
+ * Moved counts (not defined in the paper): for step t (1-based), moved_lr[t-1]
+ * is the number of LR cars that moved in its horizontal phase and
+ * moved_tb[t-1] the number of TB cars that moved in its vertical phase;
+ * total = lr + tb.  Counts are exact int64.
+ *
+ * Seeded placement (Sec. 2 says only that cars are placed at random): cell
+ * (i, j) takes u = SplitMix64 output number i*N + j + 1 from state `seed`
+ * (Steele, Lea, Flood 2014); with t_x = floor(p_x * 2^64) (clamped to
+ * 2^64 - 1) the cell is LR if u < t_lr, else TB if u - t_lr < t_tb, else
+ * EMPTY.  bml_create's `density` means p_lr = p_tb = density / 2.
+ *
+ * Conventions for every call:
+ *   - the return value is a status code (BML_OK or a negative BML_E*);
+ *     on failure the object is left unchanged and bml_last_error() returns a
+ *     message (thread-local, valid until the next call on that thread);
+ *   - host buffers are owned by the caller and only read/written during the
+ *     call; device memory is owned by the library (or by the allocator that
+ *     bml_set_allocator installed);
+ *   - work is enqueued on the simulation's CUDA stream (the caller's stream
+ *     given at creation, or the legacy default stream); calls that return
+ *     host data synchronise that stream first;
+ *   - a bml_sim is not thread-safe: one thread at a time per object.
+ */
+#ifndef BML_H
+#define BML_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define BML_OK 0
+#define BML_EINVAL (-1)   /* invalid argument                                  */
+#define BML_ENOMEM (-2)   /* device or host allocation failed                  */
+#define BML_ECUDA (-3)    /* a CUDA runtime call or kernel launch failed       */
+#define BML_ETIMEOUT (-4) /* a bounded device-side wait gave up               */
+#define BML_ESTATE (-5)   /* call not valid in the object's state (e.g. count
+                             capacity exhausted)                              */
+
+/* Step kernels. */
+#define BML_KERNEL_AUTO 0     /* autotuned: streaming bitplane kernel with the
+                                 fastest (temporal depth k, band height)      */
+#define BML_KERNEL_BYTE 1     /* one byte per cell; one horizontal and one
+                                 vertical launch per step (the plain GPU form
+                                 of Sec. 6)                                   */
+#define BML_KERNEL_BITPLANE 2 /* two uint64 bitplanes; one horizontal and one
+                                 vertical launch per step                     */
+#define BML_KERNEL_FUSED 3    /* two bitplanes; one launch per step (both
+                                 phases in one streaming pass)                */
+#define BML_KERNEL_TBLOCK 4   /* two bitplanes; k full steps per launch       */
+
+typedef struct bml_sim bml_sim;
+
+/* Optional device allocator (e.g. a framework's caching allocator).
+ * alloc returns a device pointer of at least `bytes` bytes usable on
+ * `stream`, or NULL; free releases it.  Pointers must be 256-byte aligned. */
+typedef void *(*bml_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*bml_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
+
+/* Install (or, with NULLs, remove) the process-wide device allocator used by
+ * objects created afterwards.  Objects remember the allocator they were
+ * created with.  Returns BML_EINVAL if exactly one of alloc/free is NULL. */
+int bml_set_allocator(bml_alloc_fn alloc, bml_free_fn free_fn, void *ctx);
+
+/* Create an M x N lattice with the seeded placement above at `density`
+ * (p_lr = p_tb = density/2), kernel BML_KERNEL_AUTO, legacy default stream.
+ * M, N >= 1, M*N <= 2^37; 0 <= density <= 1.  *out receives the object. */
+int bml_create(int64_t M, int64_t N, uint64_t seed, double density, bml_sim **out);
+
+/* Full form.  p_lr, p_tb >= 0, p_lr + p_tb <= 1.  kernel is a BML_KERNEL_*.
+ * block_k is the temporal depth for BML_KERNEL_TBLOCK (1, 2, 4 or 8; 0 picks
+ * 4) and is ignored otherwise.  stream is a cudaStream_t (NULL = legacy
+ * default stream).  reserve_steps preallocates the moved-count history (0
+ * picks 4096; it grows on demand in bml_step).  With BML_KERNEL_AUTO the call
+ * times the candidate configurations on this lattice (the lattice itself is
+ * not advanced) and keeps the fastest; results are cached per (M, N, device)
+ * for the process. */
+int bml_create_ex(int64_t M, int64_t N, uint64_t seed, double p_lr, double p_tb,
+                  int kernel, int block_k, void *stream, int64_t reserve_steps,
+                  bml_sim **out);
+
+/* Ensure room for the moved counts of at least K steps in total. */
+int bml_reserve_steps(bml_sim *sim, int64_t K);
+
+/* Enqueue k >= 0 full steps (horizontal then vertical phase each) on the
+ * object's stream; asynchronous.  Grows the count history if needed. */
+int bml_step(bml_sim *sim, int64_t k);
+
+/* Copy the moved counts of steps first+1 .. first+n (0-based entries
+ * first .. first+n-1) to host arrays of n int64 each.  Any of the three
+ * outputs may be NULL.  Requires 0 <= first, first + n <= bml_steps_done().
+ * Synchronises the stream. */
+int bml_moved_counts(bml_sim *sim, int64_t first, int64_t n, int64_t *out_total,
+                     int64_t *out_lr, int64_t *out_tb);
+
+/* Copy the current lattice (M*N bytes, format above) to host memory `out`.
+ * Synchronises the stream. */
+int bml_read_lattice(bml_sim *sim, uint8_t *out);
+
+/* Replace the lattice with M*N bytes from host memory `in` (values 0, 1, 2;
+ * any other value gives BML_EINVAL and leaves the object unchanged).  This
+ * starts a new trajectory: bml_steps_done() becomes 0 and the count history
+ * is cleared.  Synchronises the stream. */
+int bml_write_lattice(bml_sim *sim, const uint8_t *in);
+
+/* Device-memory forms of the two calls above: `d_out` / `d_in` are device
+ * pointers to M*N bytes (for example a framework tensor); enqueued on the
+ * object's stream without synchronising.  bml_write_lattice_device checks
+ * the values on the device and synchronises to report BML_EINVAL. */
+int bml_read_lattice_device(bml_sim *sim, uint8_t *d_out);
+int bml_write_lattice_device(bml_sim *sim, const uint8_t *d_in);
+
+/* Number of steps taken since creation (or the last bml_write_lattice). */
+int64_t bml_steps_done(const bml_sim *sim);
+
+/* Kernel actually used (BML_KERNEL_*), its temporal depth and band height
+ * (rows per warp tile; 0 for kernels without bands). */
+int bml_get_config(const bml_sim *sim, int *kernel, int *block_k, int64_t *band_rows);
+
+/* Wait for all work enqueued by the object. */
+int bml_synchronize(bml_sim *sim);
+
+/* Release the object and its device memory (synchronises first).  NULL is
+ * allowed. */
+void bml_destroy(bml_sim *sim);
+
+/* Message describing the last failure on this thread ("" if none). */
+const char *bml_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BML_H */

@@ -1,0 +1,263 @@
+"""Thin ctypes binding of libbml (include/bml.h): same names, argument
+marshalling only.  Every step of the automaton runs in the CUDA library; if
+the library is missing this module raises at import time -- there is no CPU
+fallback.
+
+PyTorch's role is limited to device memory and streams: `use_torch_allocator`
+routes the library's device allocations through torch's caching allocator,
+and `stream=` arguments take a torch.cuda.Stream (or a raw cudaStream_t).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbml.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        "libbml.so is not built (%s); run `python -m paper_1804_07981_b300.build`" % LIB_PATH)
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+BML_OK = 0
+BML_EINVAL = -1
+BML_ENOMEM = -2
+BML_ECUDA = -3
+BML_ETIMEOUT = -4
+BML_ESTATE = -5
+
+BML_KERNEL_AUTO = 0
+BML_KERNEL_BYTE = 1
+BML_KERNEL_BITPLANE = 2
+BML_KERNEL_FUSED = 3
+BML_KERNEL_TBLOCK = 4
+
+KERNELS = {"auto": BML_KERNEL_AUTO, "byte": BML_KERNEL_BYTE, "bitplane": BML_KERNEL_BITPLANE,
+           "fused": BML_KERNEL_FUSED, "tblock": BML_KERNEL_TBLOCK}
+
+_i64, _u64, _dbl, _int, _vp = (ctypes.c_int64, ctypes.c_uint64, ctypes.c_double,
+                               ctypes.c_int, ctypes.c_void_p)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+
+
+class BMLError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("bml error %d: %s" % (code, msg))
+        self.code = code
+
+
+def _sig(name, args, res=_int):
+    f = getattr(_lib, name)
+    f.argtypes = args
+    f.restype = res
+    return f
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(_vp, ctypes.c_size_t, _vp, _vp)
+FREE_FN = ctypes.CFUNCTYPE(None, _vp, ctypes.c_size_t, _vp, _vp)
+
+_lib_set_allocator = _sig("bml_set_allocator", [ALLOC_FN, FREE_FN, _vp])
+_lib_create = _sig("bml_create", [_i64, _i64, _u64, _dbl, ctypes.POINTER(_vp)])
+_lib_create_ex = _sig("bml_create_ex", [_i64, _i64, _u64, _dbl, _dbl, _int, _int, _vp, _i64,
+                                        ctypes.POINTER(_vp)])
+_lib_reserve = _sig("bml_reserve_steps", [_vp, _i64])
+_lib_step = _sig("bml_step", [_vp, _i64])
+_lib_counts = _sig("bml_moved_counts", [_vp, _i64, _i64, _vp, _vp, _vp])
+_lib_read = _sig("bml_read_lattice", [_vp, _vp])
+_lib_write = _sig("bml_write_lattice", [_vp, _vp])
+_lib_read_dev = _sig("bml_read_lattice_device", [_vp, _vp])
+_lib_write_dev = _sig("bml_write_lattice_device", [_vp, _vp])
+_lib_steps_done = _sig("bml_steps_done", [_vp], _i64)
+_lib_get_config = _sig("bml_get_config", [_vp, ctypes.POINTER(_int), ctypes.POINTER(_int), _i64p])
+_lib_sync = _sig("bml_synchronize", [_vp])
+_lib_destroy = _sig("bml_destroy", [_vp], None)
+_lib_last_error = _sig("bml_last_error", [], ctypes.c_char_p)
+
+
+def bml_last_error() -> str:
+    return (_lib_last_error() or b"").decode()
+
+
+def _check(rc: int) -> None:
+    if rc != BML_OK:
+        raise BMLError(rc, bml_last_error())
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+def _host_ptr(a: np.ndarray):
+    return a.ctypes.data_as(_vp)
+
+
+# ---------------------------------------------------------------- allocator --
+_torch_alloc_refs = None
+
+
+def use_torch_allocator(enable: bool = True) -> None:
+    """Route the library's device allocations through torch's caching
+    allocator (objects created afterwards)."""
+    global _torch_alloc_refs
+    if not enable:
+        _check(_lib_set_allocator(ALLOC_FN(), FREE_FN(), None))
+        _torch_alloc_refs = None
+        return
+    import torch
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            dev = torch.cuda.current_device()
+            return torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream or 0)
+        except Exception:  # out of memory -> NULL -> BML_ENOMEM
+            return None
+
+    def _free(ptr, nbytes, stream, ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    refs = (ALLOC_FN(_alloc), FREE_FN(_free))
+    _check(_lib_set_allocator(refs[0], refs[1], None))
+    _torch_alloc_refs = refs  # keep the callbacks alive
+
+
+# ---------------------------------------------------------------- functions --
+def bml_create(M: int, N: int, seed: int, density: float) -> int:
+    out = _vp()
+    _check(_lib_create(M, N, seed, density, ctypes.byref(out)))
+    return out.value
+
+
+def bml_create_ex(M: int, N: int, seed: int, p_lr: float, p_tb: float, kernel: int = 0,
+                  block_k: int = 0, stream=None, reserve_steps: int = 0) -> int:
+    out = _vp()
+    _check(_lib_create_ex(M, N, seed, p_lr, p_tb, kernel, block_k, _stream_handle(stream),
+                          reserve_steps, ctypes.byref(out)))
+    return out.value
+
+
+def bml_reserve_steps(sim: int, K: int) -> None:
+    _check(_lib_reserve(sim, K))
+
+
+def bml_step(sim: int, k: int) -> None:
+    _check(_lib_step(sim, k))
+
+
+def bml_moved_counts(sim: int, first: int, n: int):
+    """Returns (total, lr, tb), each int64[n]."""
+    tot = np.zeros(n, dtype=np.int64)
+    lr = np.zeros(n, dtype=np.int64)
+    tb = np.zeros(n, dtype=np.int64)
+    _check(_lib_counts(sim, first, n, _host_ptr(tot), _host_ptr(lr), _host_ptr(tb)))
+    return tot, lr, tb
+
+
+def bml_read_lattice(sim: int, M: int, N: int, out: np.ndarray | None = None) -> np.ndarray:
+    if out is None:
+        out = np.empty((M, N), dtype=np.uint8)
+    assert out.dtype == np.uint8 and out.flags.c_contiguous and out.size == M * N
+    _check(_lib_read(sim, _host_ptr(out)))
+    return out
+
+
+def bml_write_lattice(sim: int, lattice: np.ndarray) -> None:
+    a = np.ascontiguousarray(lattice, dtype=np.uint8)
+    _check(_lib_write(sim, _host_ptr(a)))
+
+
+def bml_read_lattice_device(sim: int, d_out: int) -> None:
+    _check(_lib_read_dev(sim, d_out))
+
+
+def bml_write_lattice_device(sim: int, d_in: int) -> None:
+    _check(_lib_write_dev(sim, d_in))
+
+
+def bml_steps_done(sim: int) -> int:
+    return int(_lib_steps_done(sim))
+
+
+def bml_get_config(sim: int):
+    k, bk, br = _int(), _int(), _i64()
+    _check(_lib_get_config(sim, ctypes.byref(k), ctypes.byref(bk), ctypes.byref(br)))
+    return k.value, bk.value, br.value
+
+
+def bml_synchronize(sim: int) -> None:
+    _check(_lib_sync(sim))
+
+
+def bml_destroy(sim: int) -> None:
+    _lib_destroy(sim)
+
+
+# ----------------------------------------------------------- convenience --
+class Lattice:
+    """Owning wrapper of a bml_sim handle."""
+
+    def __init__(self, M: int, N: int, seed: int = 1, density: float | None = None,
+                 p_lr: float | None = None, p_tb: float | None = None, kernel="auto",
+                 block_k: int = 0, stream=None, reserve_steps: int = 0):
+        if density is not None:
+            p_lr = p_tb = density / 2
+        if p_lr is None or p_tb is None:
+            raise ValueError("give density or both p_lr and p_tb")
+        kid = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+        self.M, self.N = M, N
+        self._h = bml_create_ex(M, N, seed, p_lr, p_tb, kid, block_k, stream, reserve_steps)
+
+    @property
+    def handle(self) -> int:
+        return self._h
+
+    def step(self, k: int = 1) -> None:
+        bml_step(self._h, k)
+
+    def moved_counts(self, first: int = 0, n: int | None = None):
+        if n is None:
+            n = self.steps_done - first
+        return bml_moved_counts(self._h, first, n)
+
+    def read(self) -> np.ndarray:
+        return bml_read_lattice(self._h, self.M, self.N)
+
+    def write(self, lattice: np.ndarray) -> None:
+        if lattice.shape != (self.M, self.N):
+            raise ValueError("shape mismatch")
+        bml_write_lattice(self._h, lattice)
+
+    @property
+    def steps_done(self) -> int:
+        return bml_steps_done(self._h)
+
+    @property
+    def config(self):
+        return bml_get_config(self._h)
+
+    def synchronize(self) -> None:
+        bml_synchronize(self._h)
+
+    def close(self) -> None:
+        if self._h:
+            bml_destroy(self._h)
+            self._h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

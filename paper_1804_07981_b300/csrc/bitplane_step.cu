@@ -1,0 +1,139 @@
+// Two-phase bitplane step: one horizontal-phase launch and one vertical-phase
+// launch per step, on the two uint64 bitplanes L (LR) and T (TB).
+//
+// Horizontal phase (Sec. 2, first rule), on 64 cells of a row at a time:
+//   E  = ~(L | T)              empty cells (tail bits masked)
+//   Er = E shifted one cell toward lower columns: Er[j] = E[j+1 mod N]
+//   Ll = L shifted one cell toward higher columns: Ll[j] = L[j-1 mod N]
+//   moved = L & Er,  L' = (L & ~Er) | (Ll & E)
+// Vertical phase (Sec. 2, second rule), row i against rows i-1 and i+1 of
+// the horizontally updated lattice:
+//   E_i = ~(L'_i | T_i),  moved = T_i & E_{i+1},
+//   T'_i = (T_i & ~E_{i+1}) | (T_{i-1} & E_i)
+// The cross-word shifts are 32-bit funnel shifts; the word holding column
+// N-1 takes its right neighbour from bit 0 of word 0 and word 0 takes its
+// left neighbour from column N-1, whatever N mod 64 is.
+#include "device_common.cuh"
+
+namespace bml {
+
+namespace {
+
+int sm_count() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    sms = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  return sms;
+}
+
+// One thread per (row, pair of words): 128-bit loads of L and T.
+__global__ void __launch_bounds__(256) plane_h_kernel(const u64 *__restrict__ L,
+                                                      const u64 *__restrict__ T,
+                                                      u64 *__restrict__ Lh, Geom g, u64 *moved) {
+  const int64_t np = g.P / 2, total = g.M * np;
+  uint32_t cnt = 0;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx / np, p = idx - i * np;
+    const int64_t a = 2 * p, b = a + 1;
+    const u64 *Lr = L + i * g.P, *Tr = T + i * g.P;
+    u64 La, Lb, Ta, Tb;
+    ld2(Lr + a, La, Lb);
+    ld2(Tr + a, Ta, Tb);
+    const u64 Ea = ~(La | Ta) & word_valid(a, g);
+    const u64 Eb = ~(Lb | Tb) & word_valid(b, g);
+    // left neighbour of column 64a: the last cell of word a-1 (or of word W-1)
+    const int64_t wl = a == 0 ? g.W - 1 : a - 1;
+    const u64 lbit = (__ldg(Lr + wl) >> word_top(wl, g)) & 1ull;
+    u64 Era, Erb, Llb;
+    if (b < g.W) {
+      // right neighbour of word b: bit 0 of word b+1, or of word 0 after N-1
+      const int64_t wr = b == g.W - 1 ? 0 : b + 1;
+      const u64 e0 = ~(__ldg(Lr + wr) | __ldg(Tr + wr)) & 1ull;
+      Era = funnel_r1(Ea, Eb);
+      Erb = (Eb >> 1) | (e0 << word_top(b, g));
+      Llb = funnel_l1(La, Lb);
+    } else {
+      // word a is the last word of the row; b is padding
+      const u64 e0 = ~(__ldg(Lr) | __ldg(Tr)) & 1ull;
+      Era = (Ea >> 1) | (e0 << word_top(a, g));
+      Erb = 0;
+      Llb = 0;
+    }
+    const u64 Lla = (La << 1) | lbit;
+    const u64 mva = La & Era, mvb = Lb & Erb;
+    st2(Lh + i * g.P + a, (La & ~Era) | (Lla & Ea), (Lb & ~Erb) | (Llb & Eb));
+    cnt += (uint32_t)(__popcll(mva) + __popcll(mvb));
+  }
+  block_count_add(cnt, moved);
+}
+
+// One thread per (band of rows, pair of words): marches down the band with
+// the previous row's T and the current row's E in registers.
+__global__ void __launch_bounds__(256) plane_v_kernel(const u64 *__restrict__ Lh,
+                                                      const u64 *__restrict__ T,
+                                                      u64 *__restrict__ Tv, Geom g,
+                                                      int64_t band, u64 *moved) {
+  const int64_t np = g.P / 2, nbands = (g.M + band - 1) / band, total = nbands * np;
+  uint32_t cnt = 0;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t bnd = idx / np, p = idx - bnd * np;
+    const int64_t a = 2 * p;
+    const u64 va = word_valid(a, g), vb = word_valid(a + 1, g);
+    const int64_t r0 = bnd * band, r1 = r0 + band < g.M ? r0 + band : g.M;
+    u64 Tpa, Tpb, x0, x1, Ta, Tb;
+    ld2(T + (r0 > 0 ? r0 - 1 : g.M - 1) * g.P + a, Tpa, Tpb);
+    ld2(Lh + r0 * g.P + a, x0, x1);
+    ld2(T + r0 * g.P + a, Ta, Tb);
+    u64 Ea = ~(x0 | Ta) & va, Eb = ~(x1 | Tb) & vb;
+    for (int64_t i = r0; i < r1; ++i) {
+      const int64_t n = i + 1 < g.M ? i + 1 : 0;
+      u64 Lna, Lnb, Tna, Tnb;
+      ld2(Lh + n * g.P + a, Lna, Lnb);
+      ld2(T + n * g.P + a, Tna, Tnb);
+      const u64 Ena = ~(Lna | Tna) & va, Enb = ~(Lnb | Tnb) & vb;
+      const u64 mva = Ta & Ena, mvb = Tb & Enb;
+      st2(Tv + i * g.P + a, (Ta & ~Ena) | (Tpa & Ea), (Tb & ~Enb) | (Tpb & Eb));
+      cnt += (uint32_t)(__popcll(mva) + __popcll(mvb));
+      Tpa = Ta;
+      Tpb = Tb;
+      Ta = Tna;
+      Tb = Tnb;
+      Ea = Ena;
+      Eb = Enb;
+    }
+  }
+  block_count_add(cnt, moved);
+}
+
+int grid_cap(int64_t items, int threads, int per_sm) {
+  int64_t blocks = (items + threads - 1) / threads;
+  const int64_t cap = (int64_t)sm_count() * per_sm;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  return (int)blocks;
+}
+
+}  // namespace
+
+cudaError_t launch_plane_h(const u64 *L, const u64 *T, u64 *Lh, const Geom &g, u64 *moved,
+                           cudaStream_t st) {
+  const int64_t items = g.M * (g.P / 2);
+  plane_h_kernel<<<grid_cap(items, 256, 8), 256, 0, st>>>(L, T, Lh, g, moved);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_plane_v(const u64 *Lh, const u64 *T, u64 *Tv, const Geom &g, u64 *moved,
+                           cudaStream_t st) {
+  const int64_t band = 16;
+  const int64_t items = ((g.M + band - 1) / band) * (g.P / 2);
+  plane_v_kernel<<<grid_cap(items, 256, 8), 256, 0, st>>>(Lh, T, Tv, g, band, moved);
+  return cudaGetLastError();
+}
+
+}  // namespace bml

@@ -1,0 +1,540 @@
+// C ABI of the single-lattice simulator (declared in include/bml.h).
+//
+// Host-side logic only: argument checks, device memory, the count history,
+// dispatch of the step kernels and the autotuner.  Every step of the
+// automaton runs in the kernels of the other translation units.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/bml.h"
+#include "bml_internal.cuh"
+
+using namespace bml;
+
+// ---------------------------------------------------------------- errors --
+static thread_local std::string g_last_error;
+
+static int fail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+#define CUDA_TRY(expr)                                                                       \
+  do {                                                                                       \
+    cudaError_t e_ = (expr);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      return fail(BML_ECUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__,    \
+                  __LINE__);                                                                 \
+  } while (0)
+
+extern "C" const char *bml_last_error(void) { return g_last_error.c_str(); }
+
+// ------------------------------------------------------------- allocator --
+namespace {
+
+struct Allocator {
+  bml_alloc_fn alloc = nullptr;
+  bml_free_fn free_fn = nullptr;
+  void *ctx = nullptr;
+};
+
+std::mutex g_alloc_mu;
+Allocator g_alloc;
+
+struct DevBuf {
+  void *ptr = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+extern "C" int bml_set_allocator(bml_alloc_fn alloc, bml_free_fn free_fn, void *ctx) {
+  if ((alloc == nullptr) != (free_fn == nullptr))
+    return fail(BML_EINVAL, "bml_set_allocator: alloc and free must both be set or both NULL");
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  g_alloc.alloc = alloc;
+  g_alloc.free_fn = free_fn;
+  g_alloc.ctx = ctx;
+  return BML_OK;
+}
+
+// ------------------------------------------------------------------ sim --
+struct bml_sim {
+  Geom g;
+  int kernel = BML_KERNEL_AUTO;
+  int block_k = 1;
+  int64_t band_rows = 0;
+  cudaStream_t st = nullptr;
+  Allocator alloc;
+  // state: bitplane kernels use L[cur], T[cur]; the byte kernel uses c[0]
+  // (c[1] holds the lattice between the two phases of a step)
+  DevBuf planes[2];  // each: L then T, M*P words apiece
+  DevBuf bytes[2];
+  int cur = 0;
+  DevBuf counts;  // cap u64 LR counts, then cap u64 TB counts
+  int64_t cap = 0;
+  int64_t steps_done = 0;
+  DevBuf flag;     // one int for value checks
+  DevBuf scratch;  // 16 u64 of counts for autotuning launches
+};
+
+namespace {
+
+int dev_alloc(bml_sim *s, DevBuf &b, size_t bytes) {
+  b.bytes = bytes;
+  b.ptr = nullptr;
+  if (bytes == 0) return BML_OK;
+  if (s->alloc.alloc) {
+    b.ptr = s->alloc.alloc(bytes, (void *)s->st, s->alloc.ctx);
+    if (!b.ptr) return fail(BML_ENOMEM, "allocator returned NULL for %zu bytes", bytes);
+    if ((uintptr_t)b.ptr % 256)
+      return fail(BML_EINVAL, "allocator returned a pointer not aligned to 256 bytes");
+  } else {
+    cudaError_t e = cudaMalloc(&b.ptr, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      b.ptr = nullptr;
+      return fail(BML_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    }
+  }
+  cudaError_t e = cudaMemsetAsync(b.ptr, 0, bytes, s->st);
+  if (e != cudaSuccess) return fail(BML_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+  return BML_OK;
+}
+
+void dev_free(bml_sim *s, DevBuf &b) {
+  if (!b.ptr) return;
+  if (s->alloc.free_fn)
+    s->alloc.free_fn(b.ptr, b.bytes, (void *)s->st, s->alloc.ctx);
+  else
+    cudaFree(b.ptr);
+  b.ptr = nullptr;
+  b.bytes = 0;
+}
+
+void free_all(bml_sim *s) {
+  cudaStreamSynchronize(s->st);
+  for (int i = 0; i < 2; ++i) {
+    dev_free(s, s->planes[i]);
+    dev_free(s, s->bytes[i]);
+  }
+  dev_free(s, s->counts);
+  dev_free(s, s->flag);
+  dev_free(s, s->scratch);
+}
+
+inline u64 *plane_L(bml_sim *s, int i) { return (u64 *)s->planes[i].ptr; }
+inline u64 *plane_T(bml_sim *s, int i) { return (u64 *)s->planes[i].ptr + s->g.M * s->g.P; }
+inline u64 *cnt_lr(bml_sim *s) { return (u64 *)s->counts.ptr; }
+inline u64 *cnt_tb(bml_sim *s) { return (u64 *)s->counts.ptr + s->cap; }
+
+bool uses_planes(int kernel) { return kernel != BML_KERNEL_BYTE; }
+
+int check_shape(int64_t M, int64_t N) {
+  if (M < 1 || N < 1) return fail(BML_EINVAL, "M and N must be >= 1 (got %lld x %lld)",
+                                  (long long)M, (long long)N);
+  if (M > INT32_MAX || N > INT32_MAX || (double)M * (double)N > 137438953472.0)
+    return fail(BML_EINVAL, "lattice %lld x %lld too large (M, N < 2^31, M*N <= 2^37)",
+                (long long)M, (long long)N);
+  return BML_OK;
+}
+
+int grow_counts(bml_sim *s, int64_t need) {
+  if (need <= s->cap) return BML_OK;
+  int64_t ncap = s->cap > 0 ? s->cap : 4096;
+  while (ncap < need) ncap *= 2;
+  DevBuf nb;
+  int rc = dev_alloc(s, nb, (size_t)ncap * 2 * sizeof(u64));
+  if (rc) return rc;
+  if (s->counts.ptr && s->steps_done > 0) {
+    const size_t n = (size_t)s->steps_done * sizeof(u64);
+    CUDA_TRY(cudaMemcpyAsync(nb.ptr, cnt_lr(s), n, cudaMemcpyDeviceToDevice, s->st));
+    CUDA_TRY(cudaMemcpyAsync((u64 *)nb.ptr + ncap, cnt_tb(s), n, cudaMemcpyDeviceToDevice, s->st));
+  }
+  dev_free(s, s->counts);
+  s->counts = nb;
+  s->cap = ncap;
+  return BML_OK;
+}
+
+// Enqueue `k` steps with the configured kernel.  lr/tb point at the count
+// slots of the first step.
+int enqueue_steps(bml_sim *s, int64_t k, u64 *lr, u64 *tb, bool commit) {
+  const Geom &g = s->g;
+  if (s->kernel == BML_KERNEL_BYTE) {
+    uint8_t *c0 = (uint8_t *)s->bytes[0].ptr, *c1 = (uint8_t *)s->bytes[1].ptr;
+    for (int64_t t = 0; t < k; ++t) {
+      CUDA_TRY(launch_byte_h(c0, c1, g, lr + t, s->st));
+      CUDA_TRY(launch_byte_v(c1, c0, g, tb + t, s->st));
+    }
+    return BML_OK;
+  }
+  if (s->kernel == BML_KERNEL_BITPLANE) {
+    for (int64_t t = 0; t < k; ++t) {
+      const int a = s->cur, b = 1 - s->cur;
+      CUDA_TRY(launch_plane_h(plane_L(s, a), plane_T(s, a), plane_L(s, b), g, lr + t, s->st));
+      CUDA_TRY(launch_plane_v(plane_L(s, b), plane_T(s, a), plane_T(s, b), g, tb + t, s->st));
+      if (commit) s->cur = b;
+    }
+    return BML_OK;
+  }
+  // streaming kernels: depth block_k, remainder by powers of two
+  int64_t done = 0;
+  while (done < k) {
+    int d = s->block_k;
+    while (d > k - done) d >>= 1;
+    const int a = s->cur, b = 1 - s->cur;
+    CUDA_TRY(launch_stream(plane_L(s, a), plane_T(s, a), plane_L(s, b), plane_T(s, b), g, d,
+                           s->band_rows, lr + done, tb + done, s->st));
+    if (commit) s->cur = b;
+    done += d;
+  }
+  return BML_OK;
+}
+
+// ------------------------------------------------------------ autotuner --
+struct TuneKey {
+  int64_t M, N;
+  int dev;
+  bool operator<(const TuneKey &o) const {
+    return std::tie(M, N, dev) < std::tie(o.M, o.N, o.dev);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, int64_t>> g_tune_cache;
+
+int autotune(bml_sim *s) {
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  const TuneKey key{s->g.M, s->g.N, dev};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      s->block_k = it->second.first;
+      s->band_rows = it->second.second;
+      return BML_OK;
+    }
+  }
+  const int ks[] = {1, 2, 4, 8};
+  std::vector<int64_t> bands;
+  for (int64_t b : {16, 32, 64, 128, 256, 512, 1024}) {
+    if (b >= s->g.M) {
+      bands.push_back(s->g.M);
+      break;
+    }
+    bands.push_back(b);
+  }
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  const int saved_k = s->block_k;
+  const int64_t saved_b = s->band_rows;
+  double best = 1e30;
+  int best_k = 1;
+  int64_t best_b = bands[0];
+  const double cells = (double)s->g.M * (double)s->g.N;
+  const int reps = cells > 1e8 ? 3 : (cells > 1e6 ? 10 : 20);
+  int rc = BML_OK;
+  for (int k : ks) {
+    for (int64_t b : bands) {
+      s->block_k = k;
+      s->band_rows = b;
+      u64 *lr = (u64 *)s->scratch.ptr, *tb = lr + 8;
+      // warm-up (non-committing: reads cur, writes the other buffer)
+      if ((rc = enqueue_steps(s, k, lr, tb, false))) goto done;
+      cudaEventRecord(e0, s->st);
+      for (int r = 0; r < reps; ++r)
+        if ((rc = enqueue_steps(s, k, lr, tb, false))) goto done;
+      cudaEventRecord(e1, s->st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        rc = fail(BML_ECUDA, "autotune: %s", cudaGetErrorString(cudaGetLastError()));
+        goto done;
+      }
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      const double per_step = (double)ms / (reps * k);
+      if (per_step < best) {
+        best = per_step;
+        best_k = k;
+        best_b = b;
+      }
+    }
+  }
+done:
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) {
+    s->block_k = saved_k;
+    s->band_rows = saved_b;
+    return rc;
+  }
+  s->block_k = best_k;
+  s->band_rows = best_b;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[key] = {best_k, best_b};
+  return BML_OK;
+}
+
+int64_t default_band(const Geom &g) { return g.M < 128 ? g.M : 128; }
+
+}  // namespace
+
+// ------------------------------------------------------------- creation --
+extern "C" int bml_create_ex(int64_t M, int64_t N, uint64_t seed, double p_lr, double p_tb,
+                             int kernel, int block_k, void *stream, int64_t reserve_steps,
+                             bml_sim **out) {
+  if (!out) return fail(BML_EINVAL, "out is NULL");
+  int rc = check_shape(M, N);
+  if (rc) return rc;
+  if (!(p_lr >= 0.0 && p_tb >= 0.0 && p_lr + p_tb <= 1.0))
+    return fail(BML_EINVAL, "need p_lr >= 0, p_tb >= 0, p_lr + p_tb <= 1 (got %g, %g)", p_lr,
+                p_tb);
+  if (kernel < BML_KERNEL_AUTO || kernel > BML_KERNEL_TBLOCK)
+    return fail(BML_EINVAL, "unknown kernel %d", kernel);
+  if (kernel == BML_KERNEL_TBLOCK) {
+    if (block_k == 0) block_k = 4;
+    if (block_k != 1 && block_k != 2 && block_k != 4 && block_k != 8)
+      return fail(BML_EINVAL, "block_k must be 1, 2, 4 or 8 (got %d)", block_k);
+  }
+  if (reserve_steps < 0) return fail(BML_EINVAL, "reserve_steps < 0");
+
+  bml_sim *s = new (std::nothrow) bml_sim;
+  if (!s) return fail(BML_ENOMEM, "host allocation failed");
+  s->g = make_geom(M, N);
+  s->kernel = kernel;
+  s->block_k = kernel == BML_KERNEL_TBLOCK ? block_k : 1;
+  s->band_rows = default_band(s->g);
+  s->st = (cudaStream_t)stream;
+  {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    s->alloc = g_alloc;
+  }
+  const Geom &g = s->g;
+  const u64 t_lr = placement_threshold(p_lr), t_tb = placement_threshold(p_tb);
+  if (uses_planes(kernel)) {
+    for (int i = 0; i < 2; ++i)
+      if ((rc = dev_alloc(s, s->planes[i], (size_t)(2 * g.M * g.P) * sizeof(u64)))) goto fail_;
+    if (launch_init_planes(plane_L(s, 0), plane_T(s, 0), g, seed, t_lr, t_tb, s->st) !=
+        cudaSuccess) {
+      rc = fail(BML_ECUDA, "init kernel: %s", cudaGetErrorString(cudaGetLastError()));
+      goto fail_;
+    }
+  } else {
+    for (int i = 0; i < 2; ++i)
+      if ((rc = dev_alloc(s, s->bytes[i], (size_t)(g.M * g.PB)))) goto fail_;
+    if (launch_init_bytes((uint8_t *)s->bytes[0].ptr, g, seed, t_lr, t_tb, s->st) !=
+        cudaSuccess) {
+      rc = fail(BML_ECUDA, "init kernel: %s", cudaGetErrorString(cudaGetLastError()));
+      goto fail_;
+    }
+  }
+  if ((rc = dev_alloc(s, s->flag, 256))) goto fail_;
+  if ((rc = dev_alloc(s, s->scratch, 16 * sizeof(u64)))) goto fail_;
+  if ((rc = grow_counts(s, reserve_steps > 0 ? reserve_steps : 4096))) goto fail_;
+  if (kernel == BML_KERNEL_AUTO) {
+    if ((rc = autotune(s))) goto fail_;
+  }
+  if (cudaStreamSynchronize(s->st) != cudaSuccess) {
+    rc = fail(BML_ECUDA, "create: %s", cudaGetErrorString(cudaGetLastError()));
+    goto fail_;
+  }
+  *out = s;
+  return BML_OK;
+fail_:
+  free_all(s);
+  delete s;
+  return rc;
+}
+
+extern "C" int bml_create(int64_t M, int64_t N, uint64_t seed, double density, bml_sim **out) {
+  if (!(density >= 0.0 && density <= 1.0))
+    return fail(BML_EINVAL, "density must be in [0, 1] (got %g)", density);
+  return bml_create_ex(M, N, seed, density / 2, density / 2, BML_KERNEL_AUTO, 0, nullptr, 0,
+                       out);
+}
+
+extern "C" void bml_destroy(bml_sim *s) {
+  if (!s) return;
+  free_all(s);
+  delete s;
+}
+
+// ---------------------------------------------------------------- steps --
+extern "C" int bml_reserve_steps(bml_sim *s, int64_t K) {
+  if (!s) return fail(BML_EINVAL, "sim is NULL");
+  if (K < 0) return fail(BML_EINVAL, "K < 0");
+  return grow_counts(s, K);
+}
+
+extern "C" int bml_step(bml_sim *s, int64_t k) {
+  if (!s) return fail(BML_EINVAL, "sim is NULL");
+  if (k < 0) return fail(BML_EINVAL, "k < 0");
+  if (k == 0) return BML_OK;
+  int rc = grow_counts(s, s->steps_done + k);
+  if (rc) return rc;
+  rc = enqueue_steps(s, k, cnt_lr(s) + s->steps_done, cnt_tb(s) + s->steps_done, true);
+  if (rc) return rc;
+  s->steps_done += k;
+  return BML_OK;
+}
+
+extern "C" int64_t bml_steps_done(const bml_sim *s) { return s ? s->steps_done : -1; }
+
+extern "C" int bml_get_config(const bml_sim *s, int *kernel, int *block_k, int64_t *band_rows) {
+  if (!s) return fail(BML_EINVAL, "sim is NULL");
+  if (kernel) *kernel = s->kernel == BML_KERNEL_AUTO ? BML_KERNEL_TBLOCK : s->kernel;
+  if (block_k) *block_k = s->block_k;
+  if (band_rows)
+    *band_rows = (s->kernel == BML_KERNEL_BYTE || s->kernel == BML_KERNEL_BITPLANE)
+                     ? 0
+                     : s->band_rows;
+  return BML_OK;
+}
+
+extern "C" int bml_synchronize(bml_sim *s) {
+  if (!s) return fail(BML_EINVAL, "sim is NULL");
+  CUDA_TRY(cudaStreamSynchronize(s->st));
+  return BML_OK;
+}
+
+extern "C" int bml_moved_counts(bml_sim *s, int64_t first, int64_t n, int64_t *out_total,
+                                int64_t *out_lr, int64_t *out_tb) {
+  if (!s) return fail(BML_EINVAL, "sim is NULL");
+  if (first < 0 || n < 0 || first + n > s->steps_done)
+    return fail(BML_EINVAL, "count range [%lld, %lld) outside [0, %lld)", (long long)first,
+                (long long)(first + n), (long long)s->steps_done);
+  if (n == 0) return BML_OK;
+  std::vector<int64_t> lr((size_t)n), tb((size_t)n);
+  CUDA_TRY(cudaMemcpyAsync(lr.data(), cnt_lr(s) + first, (size_t)n * 8, cudaMemcpyDeviceToHost,
+                           s->st));
+  CUDA_TRY(cudaMemcpyAsync(tb.data(), cnt_tb(s) + first, (size_t)n * 8, cudaMemcpyDeviceToHost,
+                           s->st));
+  CUDA_TRY(cudaStreamSynchronize(s->st));
+  for (int64_t t = 0; t < n; ++t) {
+    if (out_lr) out_lr[t] = lr[(size_t)t];
+    if (out_tb) out_tb[t] = tb[(size_t)t];
+    if (out_total) out_total[t] = lr[(size_t)t] + tb[(size_t)t];
+  }
+  return BML_OK;
+}
+
+// -------------------------------------------------------- lattice I/O --
+namespace {
+
+// Enqueue: current state -> bytes with pitch PB in `dst` (device).
+int state_to_pitched(bml_sim *s, uint8_t *dst) {
+  if (uses_planes(s->kernel)) {
+    CUDA_TRY(launch_unpack(plane_L(s, s->cur), plane_T(s, s->cur), dst, s->g, s->st));
+  } else {
+    CUDA_TRY(cudaMemcpyAsync(dst, s->bytes[0].ptr, (size_t)(s->g.M * s->g.PB),
+                             cudaMemcpyDeviceToDevice, s->st));
+  }
+  return BML_OK;
+}
+
+int read_impl(bml_sim *s, uint8_t *out, cudaMemcpyKind kind) {
+  const Geom &g = s->g;
+  const uint8_t *src = nullptr;
+  DevBuf stage;
+  int rc;
+  if (uses_planes(s->kernel)) {
+    if ((rc = dev_alloc(s, stage, (size_t)(g.M * g.PB)))) return rc;
+    if ((rc = state_to_pitched(s, (uint8_t *)stage.ptr))) {
+      dev_free(s, stage);
+      return rc;
+    }
+    src = (const uint8_t *)stage.ptr;
+  } else {
+    src = (const uint8_t *)s->bytes[0].ptr;
+  }
+  cudaError_t e = cudaMemcpy2DAsync(out, (size_t)g.N, src, (size_t)g.PB, (size_t)g.N,
+                                    (size_t)g.M, kind, s->st);
+  if (kind == cudaMemcpyDeviceToHost && e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+  dev_free(s, stage);  // stream-ordered for allocator frees; cudaFree syncs
+  if (e != cudaSuccess) return fail(BML_ECUDA, "read lattice: %s", cudaGetErrorString(e));
+  return BML_OK;
+}
+
+int write_impl(bml_sim *s, const uint8_t *in, cudaMemcpyKind kind) {
+  const Geom &g = s->g;
+  int rc;
+  DevBuf stage;
+  uint8_t *dst;
+  const int other = 1 - s->cur;
+  if (uses_planes(s->kernel)) {
+    if ((rc = dev_alloc(s, stage, (size_t)(g.M * g.PB)))) return rc;  // zeroed padding
+    dst = (uint8_t *)stage.ptr;
+  } else {
+    dst = (uint8_t *)s->bytes[1].ptr;  // padding bytes of the byte buffers stay 0
+  }
+  int *bad = (int *)s->flag.ptr;
+  int hbad = 0;
+  cudaError_t e = cudaMemcpy2DAsync(dst, (size_t)g.PB, in, (size_t)g.N, (size_t)g.N,
+                                    (size_t)g.M, kind, s->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(int), s->st);
+  if (e == cudaSuccess) {
+    if (uses_planes(s->kernel))
+      e = launch_pack(dst, plane_L(s, other), plane_T(s, other), g, bad, s->st);
+    else
+      e = launch_check_bytes(dst, g, bad, s->st);
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+  dev_free(s, stage);
+  if (e != cudaSuccess) return fail(BML_ECUDA, "write lattice: %s", cudaGetErrorString(e));
+  if (hbad) {
+    if (!uses_planes(s->kernel)) {
+      // the rejected bytes sit in the scratch half of the byte state; the
+      // lattice itself (bytes[0]) is untouched
+    }
+    return fail(BML_EINVAL, "lattice holds a value other than 0, 1, 2");
+  }
+  if (uses_planes(s->kernel)) {
+    s->cur = other;
+  } else {
+    void *t = s->bytes[0].ptr;
+    s->bytes[0].ptr = s->bytes[1].ptr;
+    s->bytes[1].ptr = t;
+  }
+  // new trajectory: clear the count history
+  CUDA_TRY(cudaMemsetAsync(s->counts.ptr, 0, s->counts.bytes, s->st));
+  s->steps_done = 0;
+  return BML_OK;
+}
+
+}  // namespace
+
+extern "C" int bml_read_lattice(bml_sim *s, uint8_t *out) {
+  if (!s || !out) return fail(BML_EINVAL, "NULL argument");
+  return read_impl(s, out, cudaMemcpyDeviceToHost);
+}
+
+extern "C" int bml_read_lattice_device(bml_sim *s, uint8_t *d_out) {
+  if (!s || !d_out) return fail(BML_EINVAL, "NULL argument");
+  return read_impl(s, d_out, cudaMemcpyDeviceToDevice);
+}
+
+extern "C" int bml_write_lattice(bml_sim *s, const uint8_t *in) {
+  if (!s || !in) return fail(BML_EINVAL, "NULL argument");
+  return write_impl(s, in, cudaMemcpyHostToDevice);
+}
+
+extern "C" int bml_write_lattice_device(bml_sim *s, const uint8_t *d_in) {
+  if (!s || !d_in) return fail(BML_EINVAL, "NULL argument");
+  return write_impl(s, d_in, cudaMemcpyDeviceToDevice);
+}

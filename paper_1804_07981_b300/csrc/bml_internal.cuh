@@ -1,0 +1,84 @@
+// Internal declarations shared by the CUDA translation units of libbml.
+//
+// Bit-packed layout: two bitplanes per lattice, L (LR occupancy) and T (TB
+// occupancy).  Row i is P 64-bit words; column j is bit (j % 64) of word
+// (j / 64) (LSB first).  W = ceil(N / 64) words carry cells; the last one
+// holds nb = N - 64 (W - 1) cells and its bits >= nb are always 0; words
+// W .. P-1 (P = W rounded up to even, for 16-byte vector access) are always
+// 0.  EMPTY is implicit: not L and not T.
+//
+// Byte layout (the plain form): one byte per cell, row pitch PB = N rounded
+// up to 16; padding bytes are always 0.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace bml {
+
+typedef unsigned long long u64;
+
+struct Geom {
+  int64_t M;   // rows
+  int64_t N;   // columns
+  int64_t W;   // words per row holding cells
+  int64_t P;   // plane pitch in words (even)
+  int64_t PB;  // byte-layout pitch in bytes (multiple of 16)
+  int32_t nb;  // cells in word W-1 (1..64)
+  u64 tail;    // mask of the valid bits of word W-1
+};
+
+Geom make_geom(int64_t M, int64_t N);
+
+// Seeded placement thresholds: floor(p * 2^64) clamped to 2^64 - 1.
+u64 placement_threshold(double p);
+
+// How the streaming kernel cuts a row into warp-wide column strips.  When the
+// row fits in one warp (W <= 32) the strip is the whole periodic row and
+// needs no halo; otherwise each strip carries `halo` redundant words on each
+// side (1, or 2 when the last word is too short to hold a k-step cone).
+struct StripPlan {
+  int32_t whole;
+  int32_t n_strips;
+  int32_t halo;
+  int32_t base;  // owned words per strip: base + (strip < rem)
+  int32_t rem;
+};
+
+StripPlan make_strip_plan(const Geom &g, int k);
+
+// ---- launchers (all asynchronous on `st`; return cudaGetLastError()) ----
+cudaError_t launch_init_planes(u64 *L, u64 *T, const Geom &g, u64 seed, u64 t_lr,
+                               u64 t_tb, cudaStream_t st);
+cudaError_t launch_init_bytes(uint8_t *c, const Geom &g, u64 seed, u64 t_lr, u64 t_tb,
+                              cudaStream_t st);
+// bytes (pitch PB) -> planes; sets *bad (device int) if a byte is not 0/1/2.
+cudaError_t launch_pack(const uint8_t *c, u64 *L, u64 *T, const Geom &g, int *bad,
+                        cudaStream_t st);
+// planes -> bytes (pitch PB).
+cudaError_t launch_unpack(const u64 *L, const u64 *T, uint8_t *c, const Geom &g,
+                          cudaStream_t st);
+// bytes (pitch PB) -> validity check only.
+cudaError_t launch_check_bytes(const uint8_t *c, const Geom &g, int *bad, cudaStream_t st);
+
+// Byte-per-cell phases: cur -> nxt, moved cars added to *moved.
+cudaError_t launch_byte_h(const uint8_t *cur, uint8_t *nxt, const Geom &g, u64 *moved,
+                          cudaStream_t st);
+cudaError_t launch_byte_v(const uint8_t *cur, uint8_t *nxt, const Geom &g, u64 *moved,
+                          cudaStream_t st);
+
+// Bitplane phases.  H: (L, T) -> Lh; V: (Lh, T) -> Tv.  Moved cars added to
+// *moved.
+cudaError_t launch_plane_h(const u64 *L, const u64 *T, u64 *Lh, const Geom &g, u64 *moved,
+                           cudaStream_t st);
+cudaError_t launch_plane_v(const u64 *Lh, const u64 *T, u64 *Tv, const Geom &g, u64 *moved,
+                           cudaStream_t st);
+
+// Streaming kernel: k full steps (k in 1, 2, 4, 8) from (Lin, Tin) to
+// (Lout, Tout); the counts of sub-step s are added to moved_lr[s],
+// moved_tb[s].  band_rows: rows per warp tile.
+cudaError_t launch_stream(const u64 *Lin, const u64 *Tin, u64 *Lout, u64 *Tout, const Geom &g,
+                          int k, int64_t band_rows, u64 *moved_lr, u64 *moved_tb,
+                          cudaStream_t st);
+
+}  // namespace bml

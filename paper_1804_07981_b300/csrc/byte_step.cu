@@ -1,0 +1,156 @@
+// Byte-per-cell step: the plain GPU form (Sec. 6 of the paper turns the
+// serial phase functions into kernels).  One horizontal and one vertical
+// launch per step, each reading and writing one byte per cell.
+//
+// A thread handles a 16-byte chunk (16 cells) with one 128-bit load and
+// computes the rules branch-free on byte lanes, the selection-and-masking
+// idea of Sec. 5 ("a = (C & x) | (~C & y)"): with per-byte bit masks of
+// LR, TB and EMPTY (1 in bit 0 of a byte), a moving LR car and the cell it
+// enters both flip bit 0, a moving TB car and its destination flip bit 1.
+//   horizontal: out = x ^ ((L & Er) | (Ll & E))          (Sec. 2 rule 1)
+//   vertical:   out = x ^ (((T & Eb) | (Tt & E)) << 1)   (Sec. 2 rule 2)
+// where Er / Ll are the right / left neighbours' masks (with wrap) and
+// Eb / Tt the lower / upper row's.
+#include "device_common.cuh"
+
+namespace bml {
+
+namespace {
+
+constexpr u64 kLsb = 0x0101010101010101ull;
+
+struct Chunk {
+  u64 lo, hi;
+};
+
+__device__ __forceinline__ Chunk load_chunk(const uint8_t *p) {
+  const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2 *>(p));
+  return Chunk{v.x, v.y};
+}
+__device__ __forceinline__ void store_chunk(uint8_t *p, Chunk c) {
+  ulonglong2 v;
+  v.x = c.lo;
+  v.y = c.hi;
+  __stcs(reinterpret_cast<ulonglong2 *>(p), v);
+}
+
+// per-byte masks (bit 0 of each byte) of the first n cells of a chunk
+__device__ __forceinline__ Chunk valid_bytes(int n) {
+  Chunk m;
+  m.lo = n >= 8 ? kLsb : (kLsb & ((1ull << (8 * n)) - 1ull));
+  m.hi = n >= 16 ? kLsb : (n <= 8 ? 0ull : (kLsb & ((1ull << (8 * (n - 8))) - 1ull)));
+  return m;
+}
+
+__device__ __forceinline__ Chunk lr_mask(Chunk x) { return Chunk{x.lo & kLsb, x.hi & kLsb}; }
+__device__ __forceinline__ Chunk tb_mask(Chunk x) {
+  return Chunk{(x.lo >> 1) & kLsb, (x.hi >> 1) & kLsb};
+}
+__device__ __forceinline__ Chunk empty_mask(Chunk x, Chunk valid) {
+  return Chunk{~(x.lo | (x.lo >> 1)) & valid.lo, ~(x.hi | (x.hi >> 1)) & valid.hi};
+}
+
+__device__ __forceinline__ uint32_t popc_chunk(Chunk c) {
+  return (uint32_t)(__popcll(c.lo) + __popcll(c.hi));
+}
+
+__global__ void byte_h_kernel(const uint8_t *__restrict__ cur, uint8_t *__restrict__ nxt, Geom g,
+                              u64 *moved) {
+  const int64_t nq = g.PB / 16, total = g.M * nq;
+  uint32_t cnt = 0;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx / nq, q = idx - i * nq;
+    const uint8_t *row = cur + i * g.PB;
+    const int64_t c0 = 16 * q;
+    const int nv = (int)(g.N - c0 < 16 ? g.N - c0 : 16);
+    const Chunk x = load_chunk(row + c0);
+    const Chunk L = lr_mask(x), E = empty_mask(x, valid_bytes(nv));
+    // neighbours across the chunk edge, with wrap (column N-1 <-> column 0)
+    const uint8_t right = row[c0 + nv < g.N ? c0 + nv : 0];
+    const uint8_t left = row[c0 > 0 ? c0 - 1 : g.N - 1];
+    const u64 rE = right == 0 ? 1ull : 0ull;
+    const u64 lL = left == 1 ? 1ull : 0ull;
+    Chunk Er, Ll;
+    Er.lo = (E.lo >> 8) | (E.hi << 56);
+    Er.hi = E.hi >> 8;
+    if (nv > 8)
+      Er.hi |= rE << (8 * (nv - 9));
+    else
+      Er.lo |= rE << (8 * (nv - 1));
+    Ll.lo = (L.lo << 8) | lL;
+    Ll.hi = (L.hi << 8) | (L.lo >> 56);
+    const Chunk mv{L.lo & Er.lo, L.hi & Er.hi};
+    Chunk out;
+    out.lo = x.lo ^ (mv.lo | (Ll.lo & E.lo));
+    out.hi = x.hi ^ (mv.hi | (Ll.hi & E.hi));
+    store_chunk(nxt + i * g.PB + c0, out);
+    cnt += popc_chunk(mv);
+  }
+  block_count_add(cnt, moved);
+}
+
+// One thread per (band of rows, chunk column); marches down the band keeping
+// the upper row's TB mask and the current row's EMPTY mask.
+__global__ void byte_v_kernel(const uint8_t *__restrict__ cur, uint8_t *__restrict__ nxt, Geom g,
+                              int64_t band, u64 *moved) {
+  const int64_t nq = g.PB / 16, nbands = (g.M + band - 1) / band, total = nbands * nq;
+  uint32_t cnt = 0;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = idx / nq, q = idx - b * nq;
+    const int64_t r0 = b * band, r1 = r0 + band < g.M ? r0 + band : g.M;
+    const int64_t c0 = 16 * q;
+    const int nv = (int)(g.N - c0 < 16 ? g.N - c0 : 16);
+    const Chunk valid = valid_bytes(nv);
+    const Chunk up = load_chunk(cur + (r0 > 0 ? r0 - 1 : g.M - 1) * g.PB + c0);
+    Chunk Tt = tb_mask(up);
+    Chunk x = load_chunk(cur + r0 * g.PB + c0);
+    Chunk E = empty_mask(x, valid);
+    for (int64_t i = r0; i < r1; ++i) {
+      const Chunk xn = load_chunk(cur + (i + 1 < g.M ? i + 1 : 0) * g.PB + c0);
+      const Chunk En = empty_mask(xn, valid);
+      const Chunk T = tb_mask(x);
+      const Chunk mv{T.lo & En.lo, T.hi & En.hi};
+      Chunk out;
+      out.lo = x.lo ^ ((mv.lo | (Tt.lo & E.lo)) << 1);
+      out.hi = x.hi ^ ((mv.hi | (Tt.hi & E.hi)) << 1);
+      store_chunk(nxt + i * g.PB + c0, out);
+      cnt += popc_chunk(mv);
+      Tt = T;
+      x = xn;
+      E = En;
+    }
+  }
+  block_count_add(cnt, moved);
+}
+
+int grid_cap(int64_t items, int threads) {
+  int64_t blocks = (items + threads - 1) / threads;
+  int dev = 0, sms = 148;
+  if (cudaGetDevice(&dev) == cudaSuccess)
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t cap = (int64_t)sms * 8;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  return (int)blocks;
+}
+
+}  // namespace
+
+cudaError_t launch_byte_h(const uint8_t *cur, uint8_t *nxt, const Geom &g, u64 *moved,
+                          cudaStream_t st) {
+  const int64_t items = g.M * (g.PB / 16);
+  byte_h_kernel<<<grid_cap(items, 256), 256, 0, st>>>(cur, nxt, g, moved);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_byte_v(const uint8_t *cur, uint8_t *nxt, const Geom &g, u64 *moved,
+                          cudaStream_t st) {
+  const int64_t band = 32;
+  const int64_t items = ((g.M + band - 1) / band) * (g.PB / 16);
+  byte_v_kernel<<<grid_cap(items, 256), 256, 0, st>>>(cur, nxt, g, band, moved);
+  return cudaGetLastError();
+}
+
+}  // namespace bml

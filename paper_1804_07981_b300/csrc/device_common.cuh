@@ -1,0 +1,66 @@
+// Device helpers shared by the kernels of libbml.
+#pragma once
+
+#include <stdint.h>
+
+#include "bml_internal.cuh"
+
+namespace bml {
+
+#define BML_FULL_MASK 0xffffffffu
+
+// Valid-cell mask of word w of a row: all ones for full words, the tail mask
+// for word W-1, zero for padding words.
+__device__ __forceinline__ u64 word_valid(int64_t w, const Geom &g) {
+  return w < g.W - 1 ? ~0ull : (w == g.W - 1 ? g.tail : 0ull);
+}
+
+// Bit position of the last cell of word w (the one whose right neighbour is
+// in the next word, or wraps to column 0).
+__device__ __forceinline__ int word_top(int64_t w, const Geom &g) {
+  return w == g.W - 1 ? g.nb - 1 : 63;
+}
+
+// 128-bit read-only load / streaming store of two consecutive words.
+__device__ __forceinline__ void ld2(const u64 *p, u64 &a, u64 &b) {
+  const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2 *>(p));
+  a = v.x;
+  b = v.y;
+}
+__device__ __forceinline__ void st2(u64 *p, u64 a, u64 b) {
+  ulonglong2 v;
+  v.x = a;
+  v.y = b;
+  __stcs(reinterpret_cast<ulonglong2 *>(p), v);
+}
+
+// Cross-word right shift by one cell: bit b of the result is bit b+1 of lo,
+// bit 63 is bit 0 of hi.  Written as two 32-bit funnel shifts.
+__device__ __forceinline__ u64 funnel_r1(u64 lo, u64 hi) {
+  const uint32_t l0 = (uint32_t)lo, l1 = (uint32_t)(lo >> 32), h0 = (uint32_t)hi;
+  const uint32_t r0 = __funnelshift_r(l0, l1, 1);
+  const uint32_t r1 = __funnelshift_r(l1, h0, 1);
+  return (u64)r0 | ((u64)r1 << 32);
+}
+// Cross-word left shift by one cell: bit 0 of the result is bit 63 of lo.
+__device__ __forceinline__ u64 funnel_l1(u64 lo, u64 hi) {
+  const uint32_t l1 = (uint32_t)(lo >> 32), h0 = (uint32_t)hi, h1 = (uint32_t)(hi >> 32);
+  const uint32_t r0 = __funnelshift_l(l1, h0, 1);
+  const uint32_t r1 = __funnelshift_l(h0, h1, 1);
+  return (u64)r0 | ((u64)r1 << 32);
+}
+
+// Add a per-thread count to a global 64-bit counter: warp reduction, then
+// one shared-memory add per warp, then one global atomic per block.  Every
+// thread of the block must call it (it contains __syncthreads).
+__device__ __forceinline__ void block_count_add(uint32_t v, u64 *dst) {
+  __shared__ unsigned long long s_sum;
+  if (threadIdx.x == 0) s_sum = 0;
+  __syncthreads();
+  const uint32_t w = __reduce_add_sync(BML_FULL_MASK, v);
+  if ((threadIdx.x & 31) == 0 && w) atomicAdd(&s_sum, (unsigned long long)w);
+  __syncthreads();
+  if (threadIdx.x == 0 && s_sum) atomicAdd(dst, s_sum);
+}
+
+}  // namespace bml

@@ -1,0 +1,199 @@
+"""GPU parity of every step kernel against the CPU oracle, through the C ABI.
+
+The automaton is integer: lattices and per-step moved counts must match the
+oracle bit for bit.  Shapes are chosen to cover one word and many words per
+row, whole-warp rows and multi-strip rows, every tail length class (N mod 64
+= 0, 1, 63, other), rows that need the two-word halo, several row bands with
+a ragged last band, and the degenerate 1-row / 1-column / 1-cell lattices.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1804_07981_b300.inputs import parse_golden, random_lattice
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+KERNEL_CASES = [
+    ("byte", 0), ("bitplane", 0), ("fused", 0),
+    ("tblock", 1), ("tblock", 2), ("tblock", 4), ("tblock", 8), ("auto", 0),
+]
+
+SHAPES = [
+    (1, 1), (1, 2), (2, 1), (1, 70), (70, 1), (3, 3), (5, 64), (7, 63), (9, 65),
+    (33, 127), (17, 129), (130, 200), (64, 2047), (40, 2048), (31, 2049),
+    (23, 2100), (29, 4097), (19, 4160), (300, 1000),
+]
+
+
+def make(lib, M, N, kernel, block_k, seed=1, p_lr=0.15, p_tb=0.15):
+    return lib.Lattice(M, N, seed=seed, p_lr=p_lr, p_tb=p_tb, kernel=kernel, block_k=block_k)
+
+
+def oracle_counts_equal(sim_counts, mlr, mtb):
+    tot, lr, tb = sim_counts
+    np.testing.assert_array_equal(lr, mlr)
+    np.testing.assert_array_equal(tb, mtb)
+    np.testing.assert_array_equal(tot, mlr + mtb)
+
+
+@pytest.mark.parametrize("kernel,block_k", [("byte", 0), ("fused", 0)])
+@pytest.mark.parametrize("M,N", [(256, 256), (37, 65), (5, 1), (1, 200), (100, 2047), (3, 4100)])
+def test_seeded_placement_matches_oracle(lib, kernel, block_k, M, N):
+    for seed, p_lr, p_tb in [(1, 0.15, 0.15), (7, 0.3, 0.1), (123456789, 0.5, 0.5), (2, 0.0, 1.0)]:
+        with make(lib, M, N, kernel, block_k, seed, p_lr, p_tb) as sim:
+            np.testing.assert_array_equal(sim.read(), oracle.init(M, N, seed, p_lr, p_tb))
+
+
+@pytest.mark.parametrize("kernel,block_k", KERNEL_CASES)
+@pytest.mark.parametrize("M,N", SHAPES)
+def test_random_lattices_match_oracle(lib, kernel, block_k, M, N):
+    K = 37  # not a multiple of any block depth: exercises the remainders
+    for seed, rho in [(M * 7919 + N, 0.3), (M + 3 * N, 0.6)]:
+        g0 = random_lattice(M, N, seed, rho / 2, rho / 2)
+        with make(lib, M, N, kernel, block_k) as sim:
+            sim.write(g0)
+            np.testing.assert_array_equal(sim.read(), g0)
+            sim.step(10)
+            sim.step(K - 10)
+            want, mlr, mtb = oracle.run(g0, K)
+            np.testing.assert_array_equal(sim.read(), want)
+            oracle_counts_equal(sim.moved_counts(), mlr, mtb)
+            assert sim.steps_done == K
+
+
+@pytest.mark.parametrize("kernel,block_k", KERNEL_CASES)
+def test_config_256_density_03_1024_steps(lib, kernel, block_k):
+    """256 x 256, each cell LR w.p. 0.15 and TB w.p. 0.15, seed 1, 1024 steps:
+    final lattice and every per-step count."""
+    M = N = 256
+    with make(lib, M, N, kernel, block_k, 1, 0.15, 0.15) as sim:
+        g0 = oracle.init(M, N, 1, 0.15, 0.15)
+        np.testing.assert_array_equal(sim.read(), g0)
+        sim.step(1024)
+        want, mlr, mtb = oracle.run(g0, 1024)
+        np.testing.assert_array_equal(sim.read(), want)
+        oracle_counts_equal(sim.moved_counts(), mlr, mtb)
+
+
+@pytest.mark.parametrize("kernel,block_k", KERNEL_CASES)
+@pytest.mark.parametrize("name", ["worked_4x4.txt", "worked_5x3.txt"])
+def test_worked_examples_on_gpu(lib, kernel, block_k, name):
+    shape, blocks = parse_golden(os.path.join(GOLDEN, name))
+    g0 = blocks[0][2]
+    states = [b[2] for b in blocks[2::2]]  # lattice after each full step
+    with make(lib, shape[0], shape[1], kernel, block_k) as sim:
+        sim.write(g0)
+        for t, want in enumerate(states):
+            sim.step(1)
+            np.testing.assert_array_equal(sim.read(), want)
+        tot, lr, tb = sim.moved_counts()
+        assert list(lr) == [b[1] for b in blocks[1::2]]
+        assert list(tb) == [b[1] for b in blocks[2::2]]
+
+
+@pytest.mark.parametrize("kernel,block_k", [("byte", 0), ("tblock", 8), ("auto", 0)])
+def test_checkpoint_resume(lib, kernel, block_k):
+    M, N, k = 90, 333, 25
+    with make(lib, M, N, kernel, block_k, 5, 0.18, 0.2) as a:
+        a.step(2 * k)
+        full = a.read()
+        _, lr_full, tb_full = a.moved_counts()
+    with make(lib, M, N, kernel, block_k, 5, 0.18, 0.2) as b:
+        b.step(k)
+        mid = b.read()
+    with make(lib, M, N, kernel, block_k, 99, 0.3, 0.3) as c:
+        c.write(mid)
+        assert c.steps_done == 0
+        c.step(k)
+        np.testing.assert_array_equal(c.read(), full)
+        _, lr2, tb2 = c.moved_counts()
+        np.testing.assert_array_equal(lr2, lr_full[k:])
+        np.testing.assert_array_equal(tb2, tb_full[k:])
+
+
+@pytest.mark.parametrize("kernel,block_k", [("byte", 0), ("fused", 0), ("tblock", 4)])
+def test_invalid_lattice_rejected_and_state_kept(lib, kernel, block_k):
+    M, N = 20, 70
+    with make(lib, M, N, kernel, block_k, 3, 0.2, 0.2) as sim:
+        sim.step(5)
+        before = sim.read()
+        bad = before.copy()
+        bad[7, 13] = 3
+        with pytest.raises(lib.BMLError) as e:
+            sim.write(bad)
+        assert e.value.code == lib.BML_EINVAL
+        np.testing.assert_array_equal(sim.read(), before)
+        assert sim.steps_done == 5
+
+
+def test_count_range_errors(lib):
+    with make(lib, 16, 16, "fused", 0) as sim:
+        sim.step(3)
+        with pytest.raises(lib.BMLError):
+            lib.bml_moved_counts(sim.handle, 2, 5)
+        with pytest.raises(lib.BMLError):
+            lib.bml_moved_counts(sim.handle, -1, 1)
+        tot, _, _ = lib.bml_moved_counts(sim.handle, 1, 2)
+        assert tot.shape == (2,)
+
+
+def test_count_history_grows(lib):
+    M, N = 24, 100
+    with lib.Lattice(M, N, seed=4, density=0.3, kernel="tblock", block_k=8,
+                     reserve_steps=16) as sim:
+        g0 = sim.read()
+        sim.step(5000)  # forces several reallocations of the history
+        want, mlr, mtb = oracle.run(g0, 5000)
+        np.testing.assert_array_equal(sim.read(), want)
+        oracle_counts_equal(sim.moved_counts(), mlr, mtb)
+
+
+def test_device_read_write_with_torch_memory(lib):
+    import torch
+    M, N = 123, 321
+    g0 = random_lattice(M, N, 77, 0.2, 0.2)
+    d_in = torch.from_numpy(g0).cuda()
+    d_out = torch.empty((M, N), dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    with make(lib, M, N, "tblock", 2) as sim:
+        lib.bml_write_lattice_device(sim.handle, d_in.data_ptr())
+        sim.step(11)
+        lib.bml_read_lattice_device(sim.handle, d_out.data_ptr())
+        sim.synchronize()
+        want, _, _ = oracle.run(g0, 11)
+        np.testing.assert_array_equal(d_out.cpu().numpy(), want)
+
+
+def test_torch_caching_allocator_owns_device_memory(lib):
+    import torch
+    lib.use_torch_allocator(True)
+    try:
+        before = torch.cuda.memory_allocated()
+        M, N = 512, 1000
+        with lib.Lattice(M, N, seed=9, density=0.35, kernel="tblock", block_k=4) as sim:
+            assert torch.cuda.memory_allocated() > before + M * N // 4
+            g0 = oracle.init(M, N, 9, 0.175, 0.175)
+            sim.step(40)
+            want, mlr, mtb = oracle.run(g0, 40)
+            np.testing.assert_array_equal(sim.read(), want)
+            oracle_counts_equal(sim.moved_counts(), mlr, mtb)
+        assert torch.cuda.memory_allocated() == before
+    finally:
+        lib.use_torch_allocator(False)
+
+
+def test_user_stream(lib):
+    import torch
+    s = torch.cuda.Stream()
+    M, N = 64, 640
+    with lib.Lattice(M, N, seed=2, density=0.3, kernel="fused", stream=s) as sim:
+        g0 = oracle.init(M, N, 2, 0.15, 0.15)
+        sim.step(9)
+        want, mlr, mtb = oracle.run(g0, 9)
+        np.testing.assert_array_equal(sim.read(), want)
+        oracle_counts_equal(sim.moved_counts(), mlr, mtb)
