@@ -135,6 +135,12 @@ int64_t bml_steps_done(const bml_sim *sim);
  * (rows per warp tile; 0 for kernels without bands). */
 int bml_get_config(const bml_sim *sim, int *kernel, int *block_k, int64_t *band_rows);
 
+/* Override the tiling of the streaming bitplane kernels (BML_KERNEL_AUTO,
+ * FUSED, TBLOCK): temporal depth block_k in {1, 2, 4, 8} (FUSED accepts only
+ * 1) and band height band_rows >= 1 (rows per warp tile).  BML_EINVAL for
+ * other kernels or values. */
+int bml_set_tiling(bml_sim *sim, int block_k, int64_t band_rows);
+
 /* Wait for all work enqueued by the object. */
 int bml_synchronize(bml_sim *sim);
 

@@ -73,6 +73,7 @@ _lib_read_dev = _sig("bml_read_lattice_device", [_vp, _vp])
 _lib_write_dev = _sig("bml_write_lattice_device", [_vp, _vp])
 _lib_steps_done = _sig("bml_steps_done", [_vp], _i64)
 _lib_get_config = _sig("bml_get_config", [_vp, ctypes.POINTER(_int), ctypes.POINTER(_int), _i64p])
+_lib_set_tiling = _sig("bml_set_tiling", [_vp, _int, _i64])
 _lib_sync = _sig("bml_synchronize", [_vp])
 _lib_destroy = _sig("bml_destroy", [_vp], None)
 _lib_last_error = _sig("bml_last_error", [], ctypes.c_char_p)
@@ -191,6 +192,10 @@ def bml_get_config(sim: int):
     return k.value, bk.value, br.value
 
 
+def bml_set_tiling(sim: int, block_k: int, band_rows: int) -> None:
+    _check(_lib_set_tiling(sim, block_k, band_rows))
+
+
 def bml_synchronize(sim: int) -> None:
     _check(_lib_sync(sim))
 
@@ -241,6 +246,9 @@ class Lattice:
     @property
     def config(self):
         return bml_get_config(self._h)
+
+    def set_tiling(self, block_k: int, band_rows: int) -> None:
+        bml_set_tiling(self._h, block_k, band_rows)
 
     def synchronize(self) -> None:
         bml_synchronize(self._h)

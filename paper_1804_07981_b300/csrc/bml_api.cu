@@ -405,6 +405,20 @@ extern "C" int bml_get_config(const bml_sim *s, int *kernel, int *block_k, int64
   return BML_OK;
 }
 
+extern "C" int bml_set_tiling(bml_sim *s, int block_k, int64_t band_rows) {
+  if (!s) return fail(BML_EINVAL, "sim is NULL");
+  if (!uses_planes(s->kernel) || s->kernel == BML_KERNEL_BITPLANE)
+    return fail(BML_EINVAL, "tiling applies to the streaming bitplane kernels only");
+  if (block_k != 1 && block_k != 2 && block_k != 4 && block_k != 8)
+    return fail(BML_EINVAL, "block_k must be 1, 2, 4 or 8 (got %d)", block_k);
+  if (s->kernel == BML_KERNEL_FUSED && block_k != 1)
+    return fail(BML_EINVAL, "the fused kernel runs one step per launch");
+  if (band_rows < 1 || band_rows > INT32_MAX) return fail(BML_EINVAL, "bad band_rows");
+  s->block_k = block_k;
+  s->band_rows = band_rows;
+  return BML_OK;
+}
+
 extern "C" int bml_synchronize(bml_sim *s) {
   if (!s) return fail(BML_EINVAL, "sim is NULL");
   CUDA_TRY(cudaStreamSynchronize(s->st));

@@ -17,8 +17,10 @@
 //
 // so each stage lags one row behind the previous one and keeps four words per
 // lane (T_{x-2}, T_{x-1}, Lh_{x-1}, E'_{x-1}).  The only horizontal
-// communication is one bit from each neighbouring lane per stage and row
-// (two warp shuffles).
+// communication is one 32-bit warp shuffle from each neighbouring lane per
+// stage and row: the right neighbour's low half of E (its bit 0 is the cell
+// right of this word) and the left neighbour's half holding its last cell,
+// pre-aligned to bit 31; the receiver funnel-shifts them in.
 //
 // Halos.  Each step widens the dependency cone by one row up and down and one
 // column left and right.  A band [r0, r1) therefore reads rows
@@ -29,9 +31,13 @@
 // the row).  Rows that fit in one warp (W <= 32) are whole periodic rings:
 // lane W-1's right neighbour is lane 0.
 //
+// The row loop runs in chunks of PF rows (the prefetch depth).  Chunks that
+// lie entirely in the steady part of the band (every stage counts its row and
+// the last stage stores) run without per-row predicates.
+//
 // Counts.  Sub-step s counts LR moves of its row x and TB moves of its
-// emitted row x-1, only for owned rows and words, in per-lane registers;
-// at the end they are reduced per warp, then per block in shared memory, and
+// emitted row x-1, only for owned rows and words, in per-lane registers; at
+// the end they are reduced per warp, then per block in shared memory, and
 // added with one 64-bit atomic per block and sub-step.
 #include "device_common.cuh"
 
@@ -40,123 +46,193 @@ namespace bml {
 namespace {
 
 constexpr int kWarpsPerBlock = 8;
-constexpr int kPrefetch = 4;
 
 template <int K>
+struct PF {
+  static constexpr int value = K >= 4 ? 2 : 4;
+};
+
+// Per-lane constants of the word a lane holds.
+struct LaneWord {
+  u64 valid;      // valid-cell mask (all ones for a full word, 0 if the lane is off)
+  uint32_t ins_lo, ins_hi;  // bit that receives the right neighbour's first cell
+  int top_hi;     // the word's last cell lies in the high half
+  int top_sh;     // left shift that moves the last cell to bit 31 of its half
+  int src_l, src_r;
+};
+
+template <int K>
+struct Pipe {
+  u64 prevT[K], curT[K], curLh[K], curE[K];
+};
+
+__device__ __forceinline__ uint32_t lo32(u64 x) { return (uint32_t)x; }
+__device__ __forceinline__ uint32_t hi32(u64 x) { return (uint32_t)(x >> 32); }
+__device__ __forceinline__ u64 mk64(uint32_t lo, uint32_t hi) { return (u64)lo | ((u64)hi << 32); }
+
+// One row through all K stages.  `cnt_lr_ok(s)` / `cnt_tb_ok(s)` say whether
+// stage s counts its horizontal / vertical moves for this row.
+template <int K, bool FULL, bool PRED>
+__device__ __forceinline__ void row_through(u64 &inL, u64 &inT, Pipe<K> &p, const LaneWord &lw,
+                                            int i, int B, uint32_t (&c_lr)[K],
+                                            uint32_t (&c_tb)[K]) {
+#pragma unroll
+  for (int s = 0; s < K; ++s) {
+    const u64 E = FULL ? ~(inL | inT) : (~(inL | inT) & lw.valid);
+    // right neighbour: bit 0 of its E; left neighbour: its last L cell at bit 31
+    const uint32_t send_l =
+        FULL ? hi32(inL) : ((lw.top_hi ? hi32(inL) : lo32(inL)) << lw.top_sh);
+    const uint32_t rr = __shfl_sync(BML_FULL_MASK, lo32(E), lw.src_r);
+    const uint32_t rl = __shfl_sync(BML_FULL_MASK, send_l, lw.src_l);
+    u64 Er;
+    if (FULL) {
+      Er = mk64(__funnelshift_r(lo32(E), hi32(E), 1), __funnelshift_r(hi32(E), rr, 1));
+    } else {
+      const uint32_t m = 0u - (rr & 1u);
+      Er = mk64(__funnelshift_r(lo32(E), hi32(E), 1) | (lw.ins_lo & m),
+                (hi32(E) >> 1) | (lw.ins_hi & m));
+    }
+    const u64 Ll = mk64(__funnelshift_l(rl, lo32(inL), 1), __funnelshift_l(lo32(inL), hi32(inL), 1));
+    const u64 mvH = inL & Er;
+    const u64 Lh = (inL & ~Er) | (Ll & E);
+    const u64 Ep = FULL ? ~(Lh | inT) : (~(Lh | inT) & lw.valid);
+    const u64 mvV = p.curT[s] & Ep;
+    const u64 oT = (p.curT[s] & ~Ep) | (p.prevT[s] & p.curE[s]);
+    const u64 oL = p.curLh[s];
+    // stage s works on band-relative row i - K - s (horizontal) and the row
+    // above it (vertical)
+    if (!PRED || (unsigned)(i - K - s) < (unsigned)B)
+      c_lr[s] += (uint32_t)(__popc(lo32(mvH)) + __popc(hi32(mvH)));
+    if (!PRED || (unsigned)(i - K - s - 1) < (unsigned)B)
+      c_tb[s] += (uint32_t)(__popc(lo32(mvV)) + __popc(hi32(mvV)));
+    p.prevT[s] = p.curT[s];
+    p.curT[s] = inT;
+    p.curLh[s] = Lh;
+    p.curE[s] = Ep;
+    inL = oL;
+    inT = oT;
+  }
+}
+
+template <int K, bool FULL>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     stream_kernel(const u64 *__restrict__ Lin, const u64 *__restrict__ Tin,
                   u64 *__restrict__ Lout, u64 *__restrict__ Tout, Geom g, StripPlan sp,
-                  int64_t band_rows, int64_t n_bands, u64 *__restrict__ moved_lr,
+                  int band_rows, int n_bands, u64 *__restrict__ moved_lr,
                   u64 *__restrict__ moved_tb) {
+  constexpr int P = PF<K>::value;
   __shared__ unsigned long long s_cnt[2 * K];
   for (int t = threadIdx.x; t < 2 * K; t += blockDim.x) s_cnt[t] = 0;
   __syncthreads();
 
   const int lane = threadIdx.x & 31;
-  const int64_t tile = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  const int tile = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   uint32_t c_lr[K], c_tb[K];
 #pragma unroll
   for (int s = 0; s < K; ++s) c_lr[s] = c_tb[s] = 0;
 
-  if (tile < (int64_t)sp.n_strips * n_bands) {  // warp-uniform
-    const int strip = (int)(tile % sp.n_strips);
-    const int64_t band = tile / sp.n_strips;
+  if (tile < sp.n_strips * n_bands) {  // warp-uniform
+    const int strip = tile % sp.n_strips;
+    const int band = tile / sp.n_strips;
 
     // ---- lane -> word of the periodic row ----
     bool on, own;
-    int64_t w;
-    int src_l, src_r;
+    int w;
+    LaneWord lw;
     if (sp.whole) {
-      on = lane < g.W;
+      const int W = (int)g.W;
+      on = lane < W;
       own = on;
       w = on ? lane : 0;
-      src_l = lane == 0 ? (int)g.W - 1 : lane - 1;
-      src_r = lane == (int)g.W - 1 ? 0 : lane + 1;
-      if (!on) src_l = src_r = lane;
+      lw.src_l = lane == 0 ? W - 1 : lane - 1;
+      lw.src_r = lane == W - 1 ? 0 : lane + 1;
+      if (!on) lw.src_l = lw.src_r = lane;
     } else {
       const int owned = sp.base + (strip < sp.rem ? 1 : 0);
-      const int64_t first = (int64_t)strip * sp.base + (strip < sp.rem ? strip : sp.rem);
+      const int first = strip * sp.base + (strip < sp.rem ? strip : sp.rem);
       const int span = owned + 2 * sp.halo;
       on = lane < span;
       own = on && lane >= sp.halo && lane < sp.halo + owned;
-      int64_t ww = first - sp.halo + lane;
-      ww %= g.W;
-      if (ww < 0) ww += g.W;
+      int ww = (first - sp.halo + lane) % (int)g.W;
+      if (ww < 0) ww += (int)g.W;
       w = on ? ww : 0;
-      src_l = lane > 0 ? lane - 1 : 0;
-      src_r = lane + 1 < span ? lane + 1 : lane;
-      if (!on) src_l = src_r = lane;
+      lw.src_l = lane > 0 ? lane - 1 : 0;
+      lw.src_r = lane + 1 < span ? lane + 1 : lane;
+      if (!on) lw.src_l = lw.src_r = lane;
     }
-    const u64 valid = on ? word_valid(w, g) : 0ull;
-    const int top = word_top(w, g);
+    const int top = w == g.W - 1 ? g.nb - 1 : 63;
+    lw.valid = on ? (w == g.W - 1 ? g.tail : ~0ull) : 0ull;
+    lw.ins_lo = top < 32 ? (1u << top) : 0u;
+    lw.ins_hi = top >= 32 ? (1u << (top - 32)) : 0u;
+    lw.top_hi = top >= 32;
+    lw.top_sh = 31 - (top & 31);
 
-    // ---- band rows ----
-    const int64_t r0 = band * band_rows;
-    const int64_t r1 = r0 + band_rows < g.M ? r0 + band_rows : g.M;
-    const int64_t xs = r0 - K, xe = r1 + K;  // unrolled input rows [xs, xe)
-    int64_t ld_row = xs % g.M;
-    if (ld_row < 0) ld_row += g.M;
+    // ---- band rows: unrolled input rows [r0 - K, r1 + K) ----
+    const int r0 = band * band_rows;
+    const int B = (r0 + band_rows < g.M ? band_rows : (int)g.M - r0);
+    const int n_in = B + 2 * K;
+    int ld_row = (r0 - K) % (int)g.M;
+    if (ld_row < 0) ld_row += (int)g.M;
+    const size_t pitch = (size_t)g.P;
+    const u64 *Lp = Lin + w + (size_t)ld_row * pitch;
+    const u64 *Tp = Tin + w + (size_t)ld_row * pitch;
+    const u64 *Lbase = Lin + w, *Tbase = Tin + w;
+    const int M = (int)g.M;
+    u64 *Lo = Lout + w + (size_t)r0 * pitch;
+    u64 *To = Tout + w + (size_t)r0 * pitch;
 
-    u64 prevT[K], curT[K], curLh[K], curE[K];
+    Pipe<K> p;
 #pragma unroll
-    for (int s = 0; s < K; ++s) prevT[s] = curT[s] = curLh[s] = curE[s] = 0;
+    for (int s = 0; s < K; ++s) p.prevT[s] = p.curT[s] = p.curLh[s] = p.curE[s] = 0;
 
-    const u64 *Lp = Lin + w, *Tp = Tin + w;
-    u64 bufL[kPrefetch], bufT[kPrefetch];
+    auto advance = [&]() {
+      if (++ld_row == M) {
+        ld_row = 0;
+        Lp = Lbase;
+        Tp = Tbase;
+      } else {
+        Lp += pitch;
+        Tp += pitch;
+      }
+    };
+
+    u64 bufL[P], bufT[P];
 #pragma unroll
-    for (int u = 0; u < kPrefetch; ++u) {
+    for (int u = 0; u < P; ++u) {
       bufL[u] = bufT[u] = 0;
-      if (xs + u < xe) {
+      if (u < n_in) {
         if (on) {
-          bufL[u] = __ldg(Lp + ld_row * g.P);
-          bufT[u] = __ldg(Tp + ld_row * g.P);
+          bufL[u] = __ldg(Lp);
+          bufT[u] = __ldg(Tp);
         }
-        if (++ld_row == g.M) ld_row = 0;
+        advance();
       }
     }
 
-    for (int64_t x0 = xs; x0 < xe; x0 += kPrefetch) {
+    for (int i0 = 0; i0 < n_in; i0 += P) {
+      // steady chunk: every row of it has all stages counting and a store
+      const bool steady = i0 >= 2 * K && i0 + P <= B + K;
 #pragma unroll
-      for (int u = 0; u < kPrefetch; ++u) {
-        const int64_t x = x0 + u;
-        if (x < xe) {  // warp-uniform
+      for (int u = 0; u < P; ++u) {
+        const int i = i0 + u;
+        if (steady || i < n_in) {  // warp-uniform
           u64 inL = bufL[u], inT = bufT[u];
-          if (x + kPrefetch < xe) {
+          if (i + P < n_in) {
             if (on) {
-              bufL[u] = __ldg(Lp + ld_row * g.P);
-              bufT[u] = __ldg(Tp + ld_row * g.P);
+              bufL[u] = __ldg(Lp);
+              bufT[u] = __ldg(Tp);
             }
-            if (++ld_row == g.M) ld_row = 0;
+            advance();
           }
-#pragma unroll
-          for (int s = 0; s < K; ++s) {
-            // horizontal phase of step s+1 on unrolled row x - s
-            const u64 E = ~(inL | inT) & valid;
-            const uint32_t rb = __shfl_sync(BML_FULL_MASK, (uint32_t)E & 1u, src_r);
-            const uint32_t lb = __shfl_sync(BML_FULL_MASK, (uint32_t)(inL >> top) & 1u, src_l);
-            const u64 Er = (E >> 1) | ((u64)rb << top);
-            const u64 Ll = (inL << 1) | (u64)lb;
-            const u64 mvH = inL & Er;
-            const u64 Lh = (inL & ~Er) | (Ll & E);
-            const u64 Ep = ~(Lh | inT) & valid;
-            // vertical phase of step s+1 on unrolled row x - s - 1
-            const u64 mvV = curT[s] & Ep;
-            const u64 oT = (curT[s] & ~Ep) | (prevT[s] & curE[s]);
-            const u64 oL = curLh[s];
-            const int64_t rh = x - s, rv = rh - 1;
-            if (rh >= r0 && rh < r1) c_lr[s] += (uint32_t)__popcll(mvH);
-            if (rv >= r0 && rv < r1) c_tb[s] += (uint32_t)__popcll(mvV);
-            prevT[s] = curT[s];
-            curT[s] = inT;
-            curLh[s] = Lh;
-            curE[s] = Ep;
-            inL = oL;
-            inT = oT;
-          }
-          const int64_t y = x - K;  // row of state K leaving the pipeline
-          if (y >= r0 && own) {
-            __stcs(Lout + y * g.P + w, inL);
-            __stcs(Tout + y * g.P + w, inT);
+          if (steady)
+            row_through<K, FULL, false>(inL, inT, p, lw, i, B, c_lr, c_tb);
+          else
+            row_through<K, FULL, true>(inL, inT, p, lw, i, B, c_lr, c_tb);
+          // row i - 2K of the band leaves the last stage
+          if ((steady || i >= 2 * K) && own) {
+            const size_t off = (size_t)(i - 2 * K) * pitch;
+            __stcs(Lo + off, inL);
+            __stcs(To + off, inT);
           }
         }
       }
@@ -192,9 +268,14 @@ cudaError_t launch_k(const u64 *Lin, const u64 *Tin, u64 *Lout, u64 *Tout, const
   const StripPlan sp = make_strip_plan(g, K);
   const int64_t n_bands = (g.M + band_rows - 1) / band_rows;
   const int64_t tiles = (int64_t)sp.n_strips * n_bands;
+  if (tiles > INT32_MAX - kWarpsPerBlock) return cudaErrorInvalidValue;
   const int64_t blocks = (tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
-  stream_kernel<K><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, st>>>(
-      Lin, Tin, Lout, Tout, g, sp, band_rows, n_bands, moved_lr, moved_tb);
+  if (g.nb == 64)
+    stream_kernel<K, true><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, st>>>(
+        Lin, Tin, Lout, Tout, g, sp, (int)band_rows, (int)n_bands, moved_lr, moved_tb);
+  else
+    stream_kernel<K, false><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, st>>>(
+        Lin, Tin, Lout, Tout, g, sp, (int)band_rows, (int)n_bands, moved_lr, moved_tb);
   return cudaGetLastError();
 }
 
@@ -224,7 +305,7 @@ StripPlan make_strip_plan(const Geom &g, int k) {
 cudaError_t launch_stream(const u64 *Lin, const u64 *Tin, u64 *Lout, u64 *Tout, const Geom &g,
                           int k, int64_t band_rows, u64 *moved_lr, u64 *moved_tb,
                           cudaStream_t st) {
-  if (band_rows < 1) return cudaErrorInvalidValue;
+  if (band_rows < 1 || band_rows > INT32_MAX) return cudaErrorInvalidValue;
   switch (k) {
     case 1: return launch_k<1>(Lin, Tin, Lout, Tout, g, band_rows, moved_lr, moved_tb, st);
     case 2: return launch_k<2>(Lin, Tin, Lout, Tout, g, band_rows, moved_lr, moved_tb, st);
