@@ -105,23 +105,23 @@ def _dist():
 
 def _cpu_sample(budget_s: float, threads: int):
     """Time the oracle, as it stands, on a band of rows of the workload
-    (periodic R x 32768 lattice, same density and placement rule).  Returns
-    (cell-updates/s, description)."""
+    (periodic R x 32768 lattice, same density and placement rule), repeating
+    8-step runs until about `budget_s` seconds of CPU work.  Returns
+    (cell-updates/s, description, seconds)."""
     import oracle
-    rows = 256
+    rows = 2048
     g = oracle.init(rows, N_COLS, 1, DENSITY / 2, DENSITY / 2)
+    done = 0
     t0 = time.perf_counter()
-    oracle.run(g, 1, threads=threads)
-    per = max(time.perf_counter() - t0, 1e-6)  # seconds per step for `rows` rows
-    rows = int(min(M_ROWS, max(64, rows * budget_s / (per * STEPS_PER_BENCH_STEP))))
-    g = oracle.init(rows, N_COLS, 1, DENSITY / 2, DENSITY / 2)
-    t0 = time.perf_counter()
-    oracle.run(g, STEPS_PER_BENCH_STEP, threads=threads)
-    dt = time.perf_counter() - t0
-    rate = rows * N_COLS * STEPS_PER_BENCH_STEP / dt
-    desc = ("oracle (C, OpenMP rows, %d threads) on a %d x %d periodic lattice at "
-            "density %.2f, %d steps, %.1f s" % (threads, rows, N_COLS, DENSITY,
-                                               STEPS_PER_BENCH_STEP, dt))
+    while True:
+        g, _, _ = oracle.run(g, STEPS_PER_BENCH_STEP, threads=threads)
+        done += STEPS_PER_BENCH_STEP
+        dt = time.perf_counter() - t0
+        if dt >= budget_s:
+            break
+    rate = rows * N_COLS * done / dt
+    desc = ("oracle (C, OpenMP rows, %d threads) on a %d x %d periodic band of the workload "
+            "(density %.2f), %d steps in %.1f s" % (threads, rows, N_COLS, DENSITY, done, dt))
     return rate, desc, dt
 
 

@@ -64,7 +64,7 @@ extern "C" {
 #define BML_KERNEL_BITPLANE 2 /* two uint64 bitplanes; one horizontal and one
                                  vertical launch per step                     */
 #define BML_KERNEL_FUSED 3    /* two bitplanes; one launch per step (both
-                                 phases in one streaming pass)                */
+                                 phases in one pass, no bands)                */
 #define BML_KERNEL_TBLOCK 4   /* two bitplanes; k full steps per launch       */
 
 typedef struct bml_sim bml_sim;
@@ -131,14 +131,16 @@ int bml_write_lattice_device(bml_sim *sim, const uint8_t *d_in);
 /* Number of steps taken since creation (or the last bml_write_lattice). */
 int64_t bml_steps_done(const bml_sim *sim);
 
-/* Kernel actually used (BML_KERNEL_*), its temporal depth and band height
- * (rows per warp tile; 0 for kernels without bands). */
+/* Kernel actually used (BML_KERNEL_*; AUTO reports the one it picked), its
+ * temporal depth and band height (rows per warp tile; 0 for kernels without
+ * bands: BYTE, BITPLANE and the one-pass FUSED kernel). */
 int bml_get_config(const bml_sim *sim, int *kernel, int *block_k, int64_t *band_rows);
 
-/* Override the tiling of the streaming bitplane kernels (BML_KERNEL_AUTO,
- * FUSED, TBLOCK): temporal depth block_k in {1, 2, 4, 8} (FUSED accepts only
- * 1) and band height band_rows >= 1 (rows per warp tile).  BML_EINVAL for
- * other kernels or values. */
+/* Override the tiling of the bitplane step of a BML_KERNEL_AUTO or TBLOCK
+ * object: temporal depth block_k in {1, 2, 4, 8} and band height band_rows
+ * >= 1 (rows per warp tile of the streaming kernel), or band_rows = 0 with
+ * block_k = 1 for the one-pass fused kernel.  BML_EINVAL for other kernels
+ * or values. */
 int bml_set_tiling(bml_sim *sim, int block_k, int64_t band_rows);
 
 /* Wait for all work enqueued by the object. */

@@ -30,6 +30,46 @@ int sm_count() {
   return sms;
 }
 
+// Horizontal phase on the word pair (a, a+1) of one row: returns the updated
+// L of both words, the pre-phase EMPTY masks and the number of LR cars that
+// moved out of the pair.
+struct HPair {
+  u64 La, Lb, Ea, Eb;
+  uint32_t moved;
+};
+
+__device__ __forceinline__ HPair h_pair(const u64 *__restrict__ Lr, const u64 *__restrict__ Tr,
+                                        int64_t a, const Geom &g, u64 La, u64 Lb, u64 Ta,
+                                        u64 Tb) {
+  const int64_t b = a + 1;
+  HPair r;
+  r.Ea = ~(La | Ta) & word_valid(a, g);
+  r.Eb = ~(Lb | Tb) & word_valid(b, g);
+  // left neighbour of column 64a: the last cell of word a-1 (or of word W-1)
+  const int64_t wl = a == 0 ? g.W - 1 : a - 1;
+  const u64 lbit = (__ldg(Lr + wl) >> word_top(wl, g)) & 1ull;
+  u64 Era, Erb, Llb;
+  if (b < g.W) {
+    // right neighbour of word b: bit 0 of word b+1, or of word 0 after N-1
+    const int64_t wr = b == g.W - 1 ? 0 : b + 1;
+    const u64 e0 = ~(__ldg(Lr + wr) | __ldg(Tr + wr)) & 1ull;
+    Era = funnel_r1(r.Ea, r.Eb);
+    Erb = (r.Eb >> 1) | (e0 << word_top(b, g));
+    Llb = funnel_l1(La, Lb);
+  } else {
+    // word a is the last word of the row; b is padding
+    const u64 e0 = ~(__ldg(Lr) | __ldg(Tr)) & 1ull;
+    Era = (r.Ea >> 1) | (e0 << word_top(a, g));
+    Erb = 0;
+    Llb = 0;
+  }
+  const u64 Lla = (La << 1) | lbit;
+  r.La = (La & ~Era) | (Lla & r.Ea);
+  r.Lb = (Lb & ~Erb) | (Llb & r.Eb);
+  r.moved = (uint32_t)(__popcll(La & Era) + __popcll(Lb & Erb));
+  return r;
+}
+
 // One thread per (row, pair of words): 128-bit loads of L and T.
 __global__ void __launch_bounds__(256) plane_h_kernel(const u64 *__restrict__ L,
                                                       const u64 *__restrict__ T,
@@ -39,37 +79,55 @@ __global__ void __launch_bounds__(256) plane_h_kernel(const u64 *__restrict__ L,
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = idx / np, p = idx - i * np;
-    const int64_t a = 2 * p, b = a + 1;
+    const int64_t a = 2 * p;
     const u64 *Lr = L + i * g.P, *Tr = T + i * g.P;
     u64 La, Lb, Ta, Tb;
     ld2(Lr + a, La, Lb);
     ld2(Tr + a, Ta, Tb);
-    const u64 Ea = ~(La | Ta) & word_valid(a, g);
-    const u64 Eb = ~(Lb | Tb) & word_valid(b, g);
-    // left neighbour of column 64a: the last cell of word a-1 (or of word W-1)
-    const int64_t wl = a == 0 ? g.W - 1 : a - 1;
-    const u64 lbit = (__ldg(Lr + wl) >> word_top(wl, g)) & 1ull;
-    u64 Era, Erb, Llb;
-    if (b < g.W) {
-      // right neighbour of word b: bit 0 of word b+1, or of word 0 after N-1
-      const int64_t wr = b == g.W - 1 ? 0 : b + 1;
-      const u64 e0 = ~(__ldg(Lr + wr) | __ldg(Tr + wr)) & 1ull;
-      Era = funnel_r1(Ea, Eb);
-      Erb = (Eb >> 1) | (e0 << word_top(b, g));
-      Llb = funnel_l1(La, Lb);
-    } else {
-      // word a is the last word of the row; b is padding
-      const u64 e0 = ~(__ldg(Lr) | __ldg(Tr)) & 1ull;
-      Era = (Ea >> 1) | (e0 << word_top(a, g));
-      Erb = 0;
-      Llb = 0;
-    }
-    const u64 Lla = (La << 1) | lbit;
-    const u64 mva = La & Era, mvb = Lb & Erb;
-    st2(Lh + i * g.P + a, (La & ~Era) | (Lla & Ea), (Lb & ~Erb) | (Llb & Eb));
-    cnt += (uint32_t)(__popcll(mva) + __popcll(mvb));
+    const HPair h = h_pair(Lr, Tr, a, g, La, Lb, Ta, Tb);
+    st2(Lh + i * g.P + a, h.La, h.Lb);
+    cnt += h.moved;
   }
   block_count_add(cnt, moved);
+}
+
+// Fused one-pass step without bands: one thread per (row i, pair of words)
+// computes both phases of row i.  It applies the horizontal rule to rows i
+// and i+1 (the vertical rule needs E' of row i+1) and reads T of row i-1;
+// neighbouring threads share those rows through L1/L2, so DRAM sees each
+// row about once while every thread is independent (no sequential march).
+__global__ void __launch_bounds__(256) fused_direct_kernel(const u64 *__restrict__ L,
+                                                           const u64 *__restrict__ T,
+                                                           u64 *__restrict__ Lo,
+                                                           u64 *__restrict__ To, Geom g,
+                                                           u64 *moved_lr, u64 *moved_tb) {
+  const int64_t np = g.P / 2, total = g.M * np;
+  uint32_t clr = 0, ctb = 0;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx / np, p = idx - i * np;
+    const int64_t a = 2 * p;
+    const int64_t up = i > 0 ? i - 1 : g.M - 1, dn = i + 1 < g.M ? i + 1 : 0;
+    const u64 *Lr = L + i * g.P, *Tr = T + i * g.P;
+    const u64 *Ln = L + dn * g.P, *Tn = T + dn * g.P;
+    u64 La, Lb, Ta, Tb, Lna, Lnb, Tna, Tnb, Tua, Tub;
+    ld2(Lr + a, La, Lb);
+    ld2(Tr + a, Ta, Tb);
+    ld2(Ln + a, Lna, Lnb);
+    ld2(Tn + a, Tna, Tnb);
+    ld2(T + up * g.P + a, Tua, Tub);
+    const HPair h = h_pair(Lr, Tr, a, g, La, Lb, Ta, Tb);
+    const HPair hn = h_pair(Ln, Tn, a, g, Lna, Lnb, Tna, Tnb);
+    const u64 va = word_valid(a, g), vb = word_valid(a + 1, g);
+    const u64 Epa = ~(h.La | Ta) & va, Epb = ~(h.Lb | Tb) & vb;
+    const u64 Ena = ~(hn.La | Tna) & va, Enb = ~(hn.Lb | Tnb) & vb;
+    st2(Lo + i * g.P + a, h.La, h.Lb);
+    st2(To + i * g.P + a, (Ta & ~Ena) | (Tua & Epa), (Tb & ~Enb) | (Tub & Epb));
+    clr += h.moved;
+    ctb += (uint32_t)(__popcll(Ta & Ena) + __popcll(Tb & Enb));
+  }
+  block_count_add(clr, moved_lr);
+  block_count_add(ctb, moved_tb);
 }
 
 // One thread per (band of rows, pair of words): marches down the band with
@@ -125,6 +183,14 @@ cudaError_t launch_plane_h(const u64 *L, const u64 *T, u64 *Lh, const Geom &g, u
                            cudaStream_t st) {
   const int64_t items = g.M * (g.P / 2);
   plane_h_kernel<<<grid_cap(items, 256, 8), 256, 0, st>>>(L, T, Lh, g, moved);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fused_direct(const u64 *L, const u64 *T, u64 *Lo, u64 *To, const Geom &g,
+                                u64 *moved_lr, u64 *moved_tb, cudaStream_t st) {
+  const int64_t items = g.M * (g.P / 2);
+  fused_direct_kernel<<<grid_cap(items, 256, 16), 256, 0, st>>>(L, T, Lo, To, g, moved_lr,
+                                                                 moved_tb);
   return cudaGetLastError();
 }
 

@@ -191,6 +191,16 @@ int enqueue_steps(bml_sim *s, int64_t k, u64 *lr, u64 *tb, bool commit) {
     }
     return BML_OK;
   }
+  // band_rows == 0: the direct one-pass fused kernel, one launch per step
+  if (s->band_rows == 0) {
+    for (int64_t t = 0; t < k; ++t) {
+      const int a = s->cur, b = 1 - s->cur;
+      CUDA_TRY(launch_fused_direct(plane_L(s, a), plane_T(s, a), plane_L(s, b), plane_T(s, b),
+                                   g, lr + t, tb + t, s->st));
+      if (commit) s->cur = b;
+    }
+    return BML_OK;
+  }
   // streaming kernels: depth block_k, remainder by powers of two
   int64_t done = 0;
   while (done < k) {
@@ -229,14 +239,31 @@ int autotune(bml_sim *s) {
       return BML_OK;
     }
   }
-  const int ks[] = {1, 2, 4, 8};
-  std::vector<int64_t> bands;
-  for (int64_t b : {16, 32, 64, 128, 256, 512, 1024}) {
-    if (b >= s->g.M) {
-      bands.push_back(s->g.M);
-      break;
+  // candidates: the direct fused kernel (depth 1, no bands), then the
+  // streaming kernel at each depth with fixed band heights and with band
+  // heights that make the tile count fill 1..4 whole waves of resident warps
+  int sms = 148;
+  CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  std::vector<std::pair<int, int64_t>> cands;
+  cands.push_back({1, 0});
+  for (int k : {1, 2, 4, 8}) {
+    std::vector<int64_t> bands;
+    for (int64_t b : {16, 32, 64, 128, 256, 512, 1024}) bands.push_back(b);
+    int wpb = 1;
+    const int per_sm = stream_occupancy(s->g, k, &wpb);
+    const int64_t resident = (int64_t)sms * per_sm * wpb;
+    const int64_t strips = make_strip_plan(s->g, k).n_strips;
+    for (int waves = 1; waves <= 4; ++waves) {
+      const int64_t nb = resident * waves / strips;
+      if (nb >= 1) bands.push_back((s->g.M + nb - 1) / nb);
     }
-    bands.push_back(b);
+    std::sort(bands.begin(), bands.end());
+    bands.erase(std::unique(bands.begin(), bands.end()), bands.end());
+    for (int64_t b : bands) {
+      if (b < 2 * k && b < s->g.M) continue;  // halo work would dominate
+      cands.push_back({k, b >= s->g.M ? s->g.M : b});
+      if (b >= s->g.M) break;
+    }
   }
   cudaEvent_t e0, e1;
   CUDA_TRY(cudaEventCreate(&e0));
@@ -245,12 +272,14 @@ int autotune(bml_sim *s) {
   const int64_t saved_b = s->band_rows;
   double best = 1e30;
   int best_k = 1;
-  int64_t best_b = bands[0];
+  int64_t best_b = 0;
   const double cells = (double)s->g.M * (double)s->g.N;
   const int reps = cells > 1e8 ? 3 : (cells > 1e6 ? 10 : 20);
   int rc = BML_OK;
-  for (int k : ks) {
-    for (int64_t b : bands) {
+  for (const auto &c : cands) {
+    {
+      const int k = c.first;
+      const int64_t b = c.second;
       s->block_k = k;
       s->band_rows = b;
       u64 *lr = (u64 *)s->scratch.ptr, *tb = lr + 8;
@@ -289,7 +318,7 @@ done:
   return BML_OK;
 }
 
-int64_t default_band(const Geom &g) { return g.M < 128 ? g.M : 128; }
+int64_t default_band(const Geom &g) { return g.M < 256 ? g.M : 256; }
 
 }  // namespace
 
@@ -317,7 +346,7 @@ extern "C" int bml_create_ex(int64_t M, int64_t N, uint64_t seed, double p_lr, d
   s->g = make_geom(M, N);
   s->kernel = kernel;
   s->block_k = kernel == BML_KERNEL_TBLOCK ? block_k : 1;
-  s->band_rows = default_band(s->g);
+  s->band_rows = kernel == BML_KERNEL_FUSED ? 0 : default_band(s->g);
   s->st = (cudaStream_t)stream;
   {
     std::lock_guard<std::mutex> lk(g_alloc_mu);
@@ -396,12 +425,13 @@ extern "C" int64_t bml_steps_done(const bml_sim *s) { return s ? s->steps_done :
 
 extern "C" int bml_get_config(const bml_sim *s, int *kernel, int *block_k, int64_t *band_rows) {
   if (!s) return fail(BML_EINVAL, "sim is NULL");
-  if (kernel) *kernel = s->kernel == BML_KERNEL_AUTO ? BML_KERNEL_TBLOCK : s->kernel;
+  if (kernel) {
+    *kernel = s->kernel;
+    if (s->kernel == BML_KERNEL_AUTO)
+      *kernel = s->band_rows == 0 ? BML_KERNEL_FUSED : BML_KERNEL_TBLOCK;
+  }
   if (block_k) *block_k = s->block_k;
-  if (band_rows)
-    *band_rows = (s->kernel == BML_KERNEL_BYTE || s->kernel == BML_KERNEL_BITPLANE)
-                     ? 0
-                     : s->band_rows;
+  if (band_rows) *band_rows = s->band_rows;
   return BML_OK;
 }
 
@@ -411,9 +441,10 @@ extern "C" int bml_set_tiling(bml_sim *s, int block_k, int64_t band_rows) {
     return fail(BML_EINVAL, "tiling applies to the streaming bitplane kernels only");
   if (block_k != 1 && block_k != 2 && block_k != 4 && block_k != 8)
     return fail(BML_EINVAL, "block_k must be 1, 2, 4 or 8 (got %d)", block_k);
-  if (s->kernel == BML_KERNEL_FUSED && block_k != 1)
-    return fail(BML_EINVAL, "the fused kernel runs one step per launch");
-  if (band_rows < 1 || band_rows > INT32_MAX) return fail(BML_EINVAL, "bad band_rows");
+  if (s->kernel == BML_KERNEL_FUSED && (block_k != 1 || band_rows != 0))
+    return fail(BML_EINVAL, "the fused kernel runs one step per launch without bands");
+  if (band_rows < 0 || band_rows > INT32_MAX || (band_rows == 0 && block_k != 1))
+    return fail(BML_EINVAL, "bad band_rows (0 selects the direct one-pass kernel, depth 1)");
   s->block_k = block_k;
   s->band_rows = band_rows;
   return BML_OK;

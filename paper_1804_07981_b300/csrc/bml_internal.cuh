@@ -74,6 +74,13 @@ cudaError_t launch_plane_h(const u64 *L, const u64 *T, u64 *Lh, const Geom &g, u
 cudaError_t launch_plane_v(const u64 *Lh, const u64 *T, u64 *Tv, const Geom &g, u64 *moved,
                            cudaStream_t st);
 
+// Fused one-pass step (both phases, one launch, no bands): (L, T) -> (Lo, To).
+cudaError_t launch_fused_direct(const u64 *L, const u64 *T, u64 *Lo, u64 *To, const Geom &g,
+                                u64 *moved_lr, u64 *moved_tb, cudaStream_t st);
+
+// Resident blocks per SM and warps per block of the streaming kernel at depth k.
+int stream_occupancy(const Geom &g, int k, int *warps_per_block);
+
 // Streaming kernel: k full steps (k in 1, 2, 4, 8) from (Lin, Tin) to
 // (Lout, Tout); the counts of sub-step s are added to moved_lr[s],
 // moved_tb[s].  band_rows: rows per warp tile.

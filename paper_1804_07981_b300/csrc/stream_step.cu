@@ -6,21 +6,24 @@
 // coalesced 256-byte access per plane.  The warp streams the rows of its band
 // from top to bottom through a pipeline of k stages held in registers; stage
 // s applies one full step (horizontal then vertical phase, Sec. 2) to the
-// rows that stage s-1 emits:
+// rows that stage s-1 emits.  With E = EMPTY before the horizontal phase:
 //
 //   receive row x (L_x, T_x) of state s:
-//     E_x   = ~(L_x | T_x)                       (masked to real cells)
-//     Lh_x  = (L_x & ~Er) | (Ll & E_x)           horizontal rule on row x
-//     E'_x  = ~(Lh_x | T_x)
-//     emit row x-1 of state s+1:
-//       L = Lh_{x-1},  T = (T_{x-1} & ~E'_x) | (T_{x-2} & E'_{x-1})
+//     mvH_x = L_x & Er_x            LR cars that leave (Er[j] = E[j+1])
+//     in_x  = mvH_x shifted one column right (the cells they enter)
+//     Lh_x  = L_x ^ mvH_x ^ in_x     horizontal rule on row x
+//     E'_x  = E_x ^ in_x ^ mvH_x     EMPTY after the horizontal phase
+//     mvV_{x-1} = T_{x-1} & E'_x     TB cars of row x-1 that move down
+//   emit row x-1 of state s+1:
+//     L = Lh_{x-1},  T = (T_{x-1} & ~E'_x) | mvV_{x-2}
 //
-// so each stage lags one row behind the previous one and keeps four words per
-// lane (T_{x-2}, T_{x-1}, Lh_{x-1}, E'_{x-1}).  The only horizontal
-// communication is one 32-bit warp shuffle from each neighbouring lane per
-// stage and row: the right neighbour's low half of E (its bit 0 is the cell
-// right of this word) and the left neighbour's half holding its last cell,
-// pre-aligned to bit 31; the receiver funnel-shifts them in.
+// since the cars entering row x-1 from above are exactly mvV_{x-2}, computed
+// one row earlier.  Each stage lags one row behind the previous one and keeps
+// three words per lane (T_{x-1}, Lh_{x-1}, mvV_{x-2}).  The only horizontal
+// communication per stage and row is two 32-bit warp shuffles: the right
+// neighbour's low half of E (its bit 0 is the cell right of this word) and
+// the left neighbour's half of mvH holding its last cell, pre-aligned to bit
+// 31; the receiver funnel-shifts them in.
 //
 // Halos.  Each step widens the dependency cone by one row up and down and one
 // column left and right.  A band [r0, r1) therefore reads rows
@@ -45,8 +48,9 @@ namespace bml {
 
 namespace {
 
-constexpr int kWarpsPerBlock = 8;
+constexpr int kWarpsPerBlock = 4;
 
+// rows prefetched per warp: deeper when a row costs little compute
 template <int K>
 struct PF {
   static constexpr int value = K >= 4 ? 2 : 4;
@@ -63,15 +67,16 @@ struct LaneWord {
 
 template <int K>
 struct Pipe {
-  u64 prevT[K], curT[K], curLh[K], curE[K];
+  u64 curT[K], curLh[K], prevMv[K];
 };
 
 __device__ __forceinline__ uint32_t lo32(u64 x) { return (uint32_t)x; }
 __device__ __forceinline__ uint32_t hi32(u64 x) { return (uint32_t)(x >> 32); }
 __device__ __forceinline__ u64 mk64(uint32_t lo, uint32_t hi) { return (u64)lo | ((u64)hi << 32); }
 
-// One row through all K stages.  `cnt_lr_ok(s)` / `cnt_tb_ok(s)` say whether
-// stage s counts its horizontal / vertical moves for this row.
+// One row through all K stages.  With PRED, stage s counts its moves only
+// for band rows (band-relative row i - K - s horizontally, the row above it
+// vertically).
 template <int K, bool FULL, bool PRED>
 __device__ __forceinline__ void row_through(u64 &inL, u64 &inT, Pipe<K> &p, const LaneWord &lw,
                                             int i, int B, uint32_t (&c_lr)[K],
@@ -79,11 +84,8 @@ __device__ __forceinline__ void row_through(u64 &inL, u64 &inT, Pipe<K> &p, cons
 #pragma unroll
   for (int s = 0; s < K; ++s) {
     const u64 E = FULL ? ~(inL | inT) : (~(inL | inT) & lw.valid);
-    // right neighbour: bit 0 of its E; left neighbour: its last L cell at bit 31
-    const uint32_t send_l =
-        FULL ? hi32(inL) : ((lw.top_hi ? hi32(inL) : lo32(inL)) << lw.top_sh);
+    // right neighbour: bit 0 of its E
     const uint32_t rr = __shfl_sync(BML_FULL_MASK, lo32(E), lw.src_r);
-    const uint32_t rl = __shfl_sync(BML_FULL_MASK, send_l, lw.src_l);
     u64 Er;
     if (FULL) {
       Er = mk64(__funnelshift_r(lo32(E), hi32(E), 1), __funnelshift_r(hi32(E), rr, 1));
@@ -92,30 +94,32 @@ __device__ __forceinline__ void row_through(u64 &inL, u64 &inT, Pipe<K> &p, cons
       Er = mk64(__funnelshift_r(lo32(E), hi32(E), 1) | (lw.ins_lo & m),
                 (hi32(E) >> 1) | (lw.ins_hi & m));
     }
-    const u64 Ll = mk64(__funnelshift_l(rl, lo32(inL), 1), __funnelshift_l(lo32(inL), hi32(inL), 1));
     const u64 mvH = inL & Er;
-    const u64 Lh = (inL & ~Er) | (Ll & E);
-    const u64 Ep = FULL ? ~(Lh | inT) : (~(Lh | inT) & lw.valid);
+    // left neighbour: its last cell of mvH, at bit 31
+    const uint32_t send_l =
+        FULL ? hi32(mvH) : ((lw.top_hi ? hi32(mvH) : lo32(mvH)) << lw.top_sh);
+    const uint32_t rl = __shfl_sync(BML_FULL_MASK, send_l, lw.src_l);
+    u64 in = mk64(__funnelshift_l(rl, lo32(mvH), 1), __funnelshift_l(lo32(mvH), hi32(mvH), 1));
+    if (!FULL) in &= lw.valid;
+    const u64 Lh = inL ^ mvH ^ in;
+    const u64 Ep = E ^ in ^ mvH;
     const u64 mvV = p.curT[s] & Ep;
-    const u64 oT = (p.curT[s] & ~Ep) | (p.prevT[s] & p.curE[s]);
+    const u64 oT = (p.curT[s] & ~Ep) | p.prevMv[s];
     const u64 oL = p.curLh[s];
-    // stage s works on band-relative row i - K - s (horizontal) and the row
-    // above it (vertical)
     if (!PRED || (unsigned)(i - K - s) < (unsigned)B)
       c_lr[s] += (uint32_t)(__popc(lo32(mvH)) + __popc(hi32(mvH)));
     if (!PRED || (unsigned)(i - K - s - 1) < (unsigned)B)
       c_tb[s] += (uint32_t)(__popc(lo32(mvV)) + __popc(hi32(mvV)));
-    p.prevT[s] = p.curT[s];
     p.curT[s] = inT;
     p.curLh[s] = Lh;
-    p.curE[s] = Ep;
+    p.prevMv[s] = mvV;
     inL = oL;
     inT = oT;
   }
 }
 
 template <int K, bool FULL>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 4)
     stream_kernel(const u64 *__restrict__ Lin, const u64 *__restrict__ Tin,
                   u64 *__restrict__ Lout, u64 *__restrict__ Tout, Geom g, StripPlan sp,
                   int band_rows, int n_bands, u64 *__restrict__ moved_lr,
@@ -183,7 +187,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 
     Pipe<K> p;
 #pragma unroll
-    for (int s = 0; s < K; ++s) p.prevT[s] = p.curT[s] = p.curLh[s] = p.curE[s] = 0;
+    for (int s = 0; s < K; ++s) p.curT[s] = p.curLh[s] = p.prevMv[s] = 0;
 
     auto advance = [&]() {
       if (++ld_row == M) {
@@ -279,7 +283,29 @@ cudaError_t launch_k(const u64 *Lin, const u64 *Tin, u64 *Lout, u64 *Tout, const
   return cudaGetLastError();
 }
 
+template <int K, bool FULL>
+int occupancy_of() {
+  int blocks = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, stream_kernel<K, FULL>,
+                                                    kWarpsPerBlock * 32, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return blocks > 0 ? blocks : 1;
+}
+
 }  // namespace
+
+int stream_occupancy(const Geom &g, int k, int *warps_per_block) {
+  if (warps_per_block) *warps_per_block = kWarpsPerBlock;
+  const bool full = g.nb == 64;
+  switch (k) {
+    case 1: return full ? occupancy_of<1, true>() : occupancy_of<1, false>();
+    case 2: return full ? occupancy_of<2, true>() : occupancy_of<2, false>();
+    case 4: return full ? occupancy_of<4, true>() : occupancy_of<4, false>();
+    default: return full ? occupancy_of<8, true>() : occupancy_of<8, false>();
+  }
+}
 
 StripPlan make_strip_plan(const Geom &g, int k) {
   StripPlan sp;

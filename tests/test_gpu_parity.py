@@ -197,3 +197,35 @@ def test_user_stream(lib):
         want, mlr, mtb = oracle.run(g0, 9)
         np.testing.assert_array_equal(sim.read(), want)
         oracle_counts_equal(sim.moved_counts(), mlr, mtb)
+
+
+@pytest.mark.parametrize("M,N", [(130, 200), (77, 4097), (300, 2100), (64, 64), (5, 129)])
+def test_explicit_tilings_match_oracle(lib, M, N):
+    """Every temporal depth with band heights that do not divide M, bands
+    shorter than the depth, one band, and the one-pass fused kernel."""
+    g0 = random_lattice(M, N, M + N, 0.17, 0.19)
+    K = 19
+    want, mlr, mtb = oracle.run(g0, K)
+    tilings = [(1, 0)] + [(k, b) for k in (1, 2, 4, 8) for b in (1, 3, 16, 37, M)]
+    for k, band in tilings:
+        with make(lib, M, N, "tblock", k) as sim:
+            sim.set_tiling(k, band)
+            sim.write(g0)
+            sim.step(K)
+            np.testing.assert_array_equal(sim.read(), want, err_msg=str((k, band)))
+            oracle_counts_equal(sim.moved_counts(), mlr, mtb)
+            assert sim.config[1:] == (k, band)
+
+
+def test_set_tiling_rejects_bad_values(lib):
+    with make(lib, 32, 64, "tblock", 2) as sim:
+        for k, band in [(3, 16), (2, 0), (1, -1), (16, 8)]:
+            with pytest.raises(lib.BMLError):
+                sim.set_tiling(k, band)
+    with make(lib, 32, 64, "byte", 0) as sim:
+        with pytest.raises(lib.BMLError):
+            sim.set_tiling(1, 16)
+    with make(lib, 32, 64, "fused", 0) as sim:
+        with pytest.raises(lib.BMLError):
+            sim.set_tiling(2, 16)
+        sim.set_tiling(1, 0)
