@@ -150,8 +150,83 @@ int bml_synchronize(bml_sim *sim);
  * allowed. */
 void bml_destroy(bml_sim *sim);
 
-/* Message describing the last failure on this thread ("" if none). */
+/* Message describing the last failure on this thread ("" if none); covers
+ * the single-lattice and the ensemble calls. */
 const char *bml_last_error(void);
+
+/* ------------------------------------------------------------------------
+ * Batched ensemble: `count` independent lattices of uneven shapes and
+ * densities advanced together.  Every lattice follows the model and the
+ * placement rule above (lattice l: M[l] x N[l], seed[l], p_lr[l], p_tb[l]).
+ * Each lattice row must fit one warp: 1 <= N[l] <= 2048; 1 <= M[l] <= 2^24;
+ * at most 2^36 cells in total.  One bml_ensemble_step call runs as one
+ * persistent cooperative launch per temporal depth used (replayed from a
+ * cached CUDA graph when the stream can be captured).  Lattices are numbered
+ * 0..count-1; "concatenated" byte buffers hold lattice 0's M*N bytes, then
+ * lattice 1's, and so on.  Steps of all lattices advance together.
+ * ------------------------------------------------------------------------ */
+typedef struct bml_ens bml_ens;
+
+/* Flags of bml_ensemble_create_ex. */
+#define BML_ENS_EARLY_EXIT 1u /* skip lattices that reached an absorbing fixed
+                                 point (a step with no move); their later
+                                 counts are 0 and their lattice stays as it is,
+                                 exactly as the automaton would evolve        */
+#define BML_ENS_NO_GRAPH 2u   /* launch directly instead of replaying graphs  */
+#define BML_ENS_TEST_STALL 4u /* test hook: the grid barrier waits for one
+                                 block more than exists and gives up after
+                                 20 ms; bml_ensemble_step returns
+                                 BML_ETIMEOUT and the ensemble becomes
+                                 unusable (BML_ESTATE afterwards)             */
+
+/* Create with autotuned tiling, no flags.  Arrays hold `count` entries and
+ * are read during the call only. */
+int bml_ensemble_create(int64_t count, const int64_t *M, const int64_t *N, const uint64_t *seed,
+                        const double *p_lr, const double *p_tb, void *stream, bml_ens **out);
+
+/* Full form: block_k in {1, 2, 4, 8} and band_rows >= 1 fix the temporal
+ * depth and the target band height; both 0 autotune them on this ensemble
+ * (the lattices are not advanced).  reserve_steps preallocates the traces
+ * (0 picks 1024; they grow on demand). */
+int bml_ensemble_create_ex(int64_t count, const int64_t *M, const int64_t *N,
+                           const uint64_t *seed, const double *p_lr, const double *p_tb,
+                           int block_k, int64_t band_rows, unsigned flags, void *stream,
+                           int64_t reserve_steps, bml_ens **out);
+
+/* Enqueue k >= 0 steps of every lattice; asynchronous. */
+int bml_ensemble_step(bml_ens *ens, int64_t k);
+
+/* Moved counts of one lattice for steps first+1 .. first+n (host arrays of n
+ * int64; any may be NULL).  Synchronises. */
+int bml_ensemble_moved_counts(bml_ens *ens, int64_t lattice, int64_t first, int64_t n,
+                              int64_t *out_total, int64_t *out_lr, int64_t *out_tb);
+
+/* Counts of all lattices for steps first+1 .. first+n: out_lr / out_tb are
+ * host arrays of count * n int64, lattice-major (either may be NULL). */
+int bml_ensemble_traces(bml_ens *ens, int64_t first, int64_t n, int64_t *out_lr,
+                        int64_t *out_tb);
+
+/* Per lattice, the 0-based index t of the first step t+1 in which no car
+ * moved (the lattice is at a fixed point from then on), or -1. */
+int bml_ensemble_jam_steps(bml_ens *ens, int64_t *out);
+
+/* Read one lattice (M[l]*N[l] bytes) or all lattices (concatenated). */
+int bml_ensemble_read_lattice(bml_ens *ens, int64_t lattice, uint8_t *out);
+int bml_ensemble_read_lattices(bml_ens *ens, uint8_t *out);
+
+/* Replace all lattices with concatenated bytes (values 0, 1, 2, else
+ * BML_EINVAL and no change); restarts every trajectory (steps_done = 0). */
+int bml_ensemble_write_lattices(bml_ens *ens, const uint8_t *in);
+
+int64_t bml_ensemble_steps_done(const bml_ens *ens);
+
+/* Temporal depth, band height and whether graph replay is in use. */
+int bml_ensemble_get_config(const bml_ens *ens, int *block_k, int64_t *band_rows, int *graphs);
+
+/* Wait for the ensemble's work; reports BML_ETIMEOUT if a barrier gave up. */
+int bml_ensemble_synchronize(bml_ens *ens);
+
+void bml_ensemble_destroy(bml_ens *ens);
 
 #ifdef __cplusplus
 }

@@ -269,3 +269,185 @@ class Lattice:
 
     def __exit__(self, *exc):
         self.close()
+
+
+# ----------------------------------------------------------------- ensemble --
+BML_ENS_EARLY_EXIT = 1
+BML_ENS_NO_GRAPH = 2
+BML_ENS_TEST_STALL = 4
+
+_lib_ens_create_ex = _sig("bml_ensemble_create_ex", [_i64, _vp, _vp, _vp, _vp, _vp, _int, _i64,
+                                                      ctypes.c_uint, _vp, _i64,
+                                                      ctypes.POINTER(_vp)])
+_lib_ens_create = _sig("bml_ensemble_create", [_i64, _vp, _vp, _vp, _vp, _vp, _vp,
+                                                ctypes.POINTER(_vp)])
+_lib_ens_step = _sig("bml_ensemble_step", [_vp, _i64])
+_lib_ens_counts = _sig("bml_ensemble_moved_counts", [_vp, _i64, _i64, _i64, _vp, _vp, _vp])
+_lib_ens_traces = _sig("bml_ensemble_traces", [_vp, _i64, _i64, _vp, _vp])
+_lib_ens_jam = _sig("bml_ensemble_jam_steps", [_vp, _vp])
+_lib_ens_read1 = _sig("bml_ensemble_read_lattice", [_vp, _i64, _vp])
+_lib_ens_read = _sig("bml_ensemble_read_lattices", [_vp, _vp])
+_lib_ens_write = _sig("bml_ensemble_write_lattices", [_vp, _vp])
+_lib_ens_steps = _sig("bml_ensemble_steps_done", [_vp], _i64)
+_lib_ens_cfg = _sig("bml_ensemble_get_config", [_vp, ctypes.POINTER(_int), _i64p,
+                                                 ctypes.POINTER(_int)])
+_lib_ens_sync = _sig("bml_ensemble_synchronize", [_vp])
+_lib_ens_destroy = _sig("bml_ensemble_destroy", [_vp], None)
+
+
+def _arr(a, dtype):
+    return np.ascontiguousarray(np.asarray(a, dtype=dtype))
+
+
+def bml_ensemble_create_ex(M, N, seed, p_lr, p_tb, block_k=0, band_rows=0, flags=0,
+                           stream=None, reserve_steps=0) -> int:
+    M, N = _arr(M, np.int64), _arr(N, np.int64)
+    seed, p_lr, p_tb = _arr(seed, np.uint64), _arr(p_lr, np.float64), _arr(p_tb, np.float64)
+    out = _vp()
+    _check(_lib_ens_create_ex(len(M), _host_ptr(M), _host_ptr(N), _host_ptr(seed),
+                              _host_ptr(p_lr), _host_ptr(p_tb), block_k, band_rows, flags,
+                              _stream_handle(stream), reserve_steps, ctypes.byref(out)))
+    return out.value
+
+
+def bml_ensemble_create(M, N, seed, p_lr, p_tb, stream=None) -> int:
+    M, N = _arr(M, np.int64), _arr(N, np.int64)
+    seed, p_lr, p_tb = _arr(seed, np.uint64), _arr(p_lr, np.float64), _arr(p_tb, np.float64)
+    out = _vp()
+    _check(_lib_ens_create(len(M), _host_ptr(M), _host_ptr(N), _host_ptr(seed), _host_ptr(p_lr),
+                           _host_ptr(p_tb), _stream_handle(stream), ctypes.byref(out)))
+    return out.value
+
+
+def bml_ensemble_step(ens: int, k: int) -> None:
+    _check(_lib_ens_step(ens, k))
+
+
+def bml_ensemble_moved_counts(ens: int, lattice: int, first: int, n: int):
+    tot, lr, tb = (np.zeros(n, dtype=np.int64) for _ in range(3))
+    _check(_lib_ens_counts(ens, lattice, first, n, _host_ptr(tot), _host_ptr(lr), _host_ptr(tb)))
+    return tot, lr, tb
+
+
+def bml_ensemble_traces(ens: int, count: int, first: int, n: int):
+    lr = np.zeros((count, n), dtype=np.int64)
+    tb = np.zeros((count, n), dtype=np.int64)
+    _check(_lib_ens_traces(ens, first, n, _host_ptr(lr), _host_ptr(tb)))
+    return lr, tb
+
+
+def bml_ensemble_jam_steps(ens: int, count: int) -> np.ndarray:
+    out = np.zeros(count, dtype=np.int64)
+    _check(_lib_ens_jam(ens, _host_ptr(out)))
+    return out
+
+
+def bml_ensemble_read_lattice(ens: int, lattice: int, M: int, N: int) -> np.ndarray:
+    out = np.empty((M, N), dtype=np.uint8)
+    _check(_lib_ens_read1(ens, lattice, _host_ptr(out)))
+    return out
+
+
+def bml_ensemble_read_lattices(ens: int, total_cells: int) -> np.ndarray:
+    out = np.empty(total_cells, dtype=np.uint8)
+    _check(_lib_ens_read(ens, _host_ptr(out)))
+    return out
+
+
+def bml_ensemble_write_lattices(ens: int, concatenated: np.ndarray) -> None:
+    a = np.ascontiguousarray(concatenated, dtype=np.uint8)
+    _check(_lib_ens_write(ens, _host_ptr(a)))
+
+
+def bml_ensemble_steps_done(ens: int) -> int:
+    return int(_lib_ens_steps(ens))
+
+
+def bml_ensemble_get_config(ens: int):
+    k, g = _int(), _int()
+    b = _i64()
+    _check(_lib_ens_cfg(ens, ctypes.byref(k), ctypes.byref(b), ctypes.byref(g)))
+    return k.value, b.value, bool(g.value)
+
+
+def bml_ensemble_synchronize(ens: int) -> None:
+    _check(_lib_ens_sync(ens))
+
+
+def bml_ensemble_destroy(ens: int) -> None:
+    _lib_ens_destroy(ens)
+
+
+class Ensemble:
+    """Owning wrapper of a bml_ens handle."""
+
+    def __init__(self, M, N, seed, p_lr, p_tb, block_k=0, band_rows=0, flags=0, stream=None,
+                 reserve_steps=0):
+        self.M = np.asarray(M, dtype=np.int64)
+        self.N = np.asarray(N, dtype=np.int64)
+        self.count = len(self.M)
+        self.cells = self.M * self.N
+        self.offsets = np.concatenate([[0], np.cumsum(self.cells)])
+        self._h = bml_ensemble_create_ex(self.M, self.N, seed, p_lr, p_tb, block_k, band_rows,
+                                         flags, stream, reserve_steps)
+
+    @property
+    def handle(self) -> int:
+        return self._h
+
+    def step(self, k: int) -> None:
+        bml_ensemble_step(self._h, k)
+
+    @property
+    def steps_done(self) -> int:
+        return bml_ensemble_steps_done(self._h)
+
+    def traces(self, first: int = 0, n: int | None = None):
+        if n is None:
+            n = self.steps_done - first
+        return bml_ensemble_traces(self._h, self.count, first, n)
+
+    def moved_counts(self, lattice: int, first: int = 0, n: int | None = None):
+        if n is None:
+            n = self.steps_done - first
+        return bml_ensemble_moved_counts(self._h, lattice, first, n)
+
+    def jam_steps(self) -> np.ndarray:
+        return bml_ensemble_jam_steps(self._h, self.count)
+
+    def read_all(self) -> list:
+        flat = bml_ensemble_read_lattices(self._h, int(self.offsets[-1]))
+        return [flat[self.offsets[l]:self.offsets[l + 1]].reshape(self.M[l], self.N[l])
+                for l in range(self.count)]
+
+    def read(self, lattice: int) -> np.ndarray:
+        return bml_ensemble_read_lattice(self._h, lattice, int(self.M[lattice]),
+                                         int(self.N[lattice]))
+
+    def write_all(self, lattices) -> None:
+        flat = np.concatenate([np.ascontiguousarray(g, dtype=np.uint8).ravel() for g in lattices])
+        bml_ensemble_write_lattices(self._h, flat)
+
+    @property
+    def config(self):
+        return bml_ensemble_get_config(self._h)
+
+    def synchronize(self) -> None:
+        bml_ensemble_synchronize(self._h)
+
+    def close(self) -> None:
+        if self._h:
+            bml_ensemble_destroy(self._h)
+            self._h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

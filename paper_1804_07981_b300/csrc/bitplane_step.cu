@@ -91,40 +91,60 @@ __global__ void __launch_bounds__(256) plane_h_kernel(const u64 *__restrict__ L,
   block_count_add(cnt, moved);
 }
 
-// Fused one-pass step without bands: one thread per (row i, pair of words)
-// computes both phases of row i.  It applies the horizontal rule to rows i
-// and i+1 (the vertical rule needs E' of row i+1) and reads T of row i-1;
-// neighbouring threads share those rows through L1/L2, so DRAM sees each
-// row about once while every thread is independent (no sequential march).
-__global__ void __launch_bounds__(256) fused_direct_kernel(const u64 *__restrict__ L,
-                                                           const u64 *__restrict__ T,
-                                                           u64 *__restrict__ Lo,
-                                                           u64 *__restrict__ To, Geom g,
-                                                           u64 *moved_lr, u64 *moved_tb) {
-  const int64_t np = g.P / 2, total = g.M * np;
+// Fused one-pass step without bands: one thread per (group of R rows, pair
+// of words).  It loads rows i0-1 .. i0+R of both planes at once (all loads
+// independent, so many bytes are in flight), applies the horizontal rule to
+// rows i0 .. i0+R (the vertical rule of row i0+R-1 needs E' of row i0+R) and
+// the vertical rule to rows i0 .. i0+R-1.  Neighbouring threads share rows
+// through L1/L2, so DRAM sees each row about once.
+template <int R>
+__global__ void __launch_bounds__(128) fused_rows_kernel(const u64 *__restrict__ L,
+                                                         const u64 *__restrict__ T,
+                                                         u64 *__restrict__ Lo,
+                                                         u64 *__restrict__ To, Geom g,
+                                                         u64 *moved_lr, u64 *moved_tb) {
+  const int np = (int)(g.P / 2);
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const int groups = (int)((g.M + R - 1) / R);
   uint32_t clr = 0, ctb = 0;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = idx / np, p = idx - i * np;
-    const int64_t a = 2 * p;
-    const int64_t up = i > 0 ? i - 1 : g.M - 1, dn = i + 1 < g.M ? i + 1 : 0;
-    const u64 *Lr = L + i * g.P, *Tr = T + i * g.P;
-    const u64 *Ln = L + dn * g.P, *Tn = T + dn * g.P;
-    u64 La, Lb, Ta, Tb, Lna, Lnb, Tna, Tnb, Tua, Tub;
-    ld2(Lr + a, La, Lb);
-    ld2(Tr + a, Ta, Tb);
-    ld2(Ln + a, Lna, Lnb);
-    ld2(Tn + a, Tna, Tnb);
-    ld2(T + up * g.P + a, Tua, Tub);
-    const HPair h = h_pair(Lr, Tr, a, g, La, Lb, Ta, Tb);
-    const HPair hn = h_pair(Ln, Tn, a, g, Lna, Lnb, Tna, Tnb);
+  if (p < np) {
+    const int64_t a = 2 * (int64_t)p;
     const u64 va = word_valid(a, g), vb = word_valid(a + 1, g);
-    const u64 Epa = ~(h.La | Ta) & va, Epb = ~(h.Lb | Tb) & vb;
-    const u64 Ena = ~(hn.La | Tna) & va, Enb = ~(hn.Lb | Tnb) & vb;
-    st2(Lo + i * g.P + a, h.La, h.Lb);
-    st2(To + i * g.P + a, (Ta & ~Ena) | (Tua & Epa), (Tb & ~Enb) | (Tub & Epb));
-    clr += h.moved;
-    ctb += (uint32_t)(__popcll(Ta & Ena) + __popcll(Tb & Enb));
+    for (int grp = blockIdx.y; grp < groups; grp += gridDim.y) {
+      const int64_t i0 = (int64_t)grp * R;
+      u64 La[R + 1], Lb[R + 1], Ta[R + 1], Tb[R + 1], Tua, Tub;
+      ld2(T + (i0 > 0 ? i0 - 1 : g.M - 1) * g.P + a, Tua, Tub);
+      int64_t rows[R + 1];
+#pragma unroll
+      for (int r = 0; r <= R; ++r) {
+        int64_t i = i0 + r;
+        while (i >= g.M) i -= g.M;
+        rows[r] = i;
+        ld2(L + i * g.P + a, La[r], Lb[r]);
+        ld2(T + i * g.P + a, Ta[r], Tb[r]);
+      }
+      u64 Ea[R + 1], Eb[R + 1], Ha[R + 1], Hb[R + 1];
+#pragma unroll
+      for (int r = 0; r <= R; ++r) {
+        const HPair h = h_pair(L + rows[r] * g.P, T + rows[r] * g.P, a, g, La[r], Lb[r], Ta[r],
+                               Tb[r]);
+        Ha[r] = h.La;
+        Hb[r] = h.Lb;
+        Ea[r] = ~(h.La | Ta[r]) & va;
+        Eb[r] = ~(h.Lb | Tb[r]) & vb;
+        if (r < R && i0 + r < g.M) clr += h.moved;
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        if (i0 + r < g.M) {
+          const u64 upa = r == 0 ? Tua : Ta[r - 1], upb = r == 0 ? Tub : Tb[r - 1];
+          st2(Lo + rows[r] * g.P + a, Ha[r], Hb[r]);
+          st2(To + rows[r] * g.P + a, (Ta[r] & ~Ea[r + 1]) | (upa & Ea[r]),
+              (Tb[r] & ~Eb[r + 1]) | (upb & Eb[r]));
+          ctb += (uint32_t)(__popcll(Ta[r] & Ea[r + 1]) + __popcll(Tb[r] & Eb[r + 1]));
+        }
+      }
+    }
   }
   block_count_add(clr, moved_lr);
   block_count_add(ctb, moved_tb);
@@ -188,9 +208,11 @@ cudaError_t launch_plane_h(const u64 *L, const u64 *T, u64 *Lh, const Geom &g, u
 
 cudaError_t launch_fused_direct(const u64 *L, const u64 *T, u64 *Lo, u64 *To, const Geom &g,
                                 u64 *moved_lr, u64 *moved_tb, cudaStream_t st) {
-  const int64_t items = g.M * (g.P / 2);
-  fused_direct_kernel<<<grid_cap(items, 256, 16), 256, 0, st>>>(L, T, Lo, To, g, moved_lr,
-                                                                 moved_tb);
+  constexpr int R = 4;
+  const int64_t np = g.P / 2;
+  const int64_t groups = (g.M + R - 1) / R;
+  dim3 grid((unsigned)((np + 127) / 128), (unsigned)(groups < 65535 ? groups : 65535));
+  fused_rows_kernel<R><<<grid, 128, 0, st>>>(L, T, Lo, To, g, moved_lr, moved_tb);
   return cudaGetLastError();
 }
 

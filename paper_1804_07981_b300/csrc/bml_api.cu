@@ -42,6 +42,8 @@ static int fail(int code, const char *fmt, ...) {
 
 extern "C" const char *bml_last_error(void) { return g_last_error.c_str(); }
 
+void bml::set_last_error(const char *msg) { g_last_error = msg; }
+
 // ------------------------------------------------------------- allocator --
 namespace {
 

@@ -30,6 +30,9 @@ struct Geom {
 
 Geom make_geom(int64_t M, int64_t N);
 
+// Record the message returned by bml_last_error() on this thread.
+void set_last_error(const char *msg);
+
 // Seeded placement thresholds: floor(p * 2^64) clamped to 2^64 - 1.
 u64 placement_threshold(double p);
 

@@ -1,0 +1,1057 @@
+// Batched ensemble: many independent lattices of uneven sizes and densities
+// advanced together by one persistent, cooperative launch per call (replayed
+// from a CUDA graph).
+//
+// Layout.  Every lattice has two bitplane buffers (ping-pong), each L then T,
+// M x P words (P = W rounded up to even), in one device pool.  Per-lattice
+// moved-count traces are [lattice][step] int64 arrays (LR and TB).
+//
+// Tiles.  Every lattice row fits one warp (N <= 2048, W <= 32 words).  A
+// lattice is cut into row bands; a warp tile packs G = 32 / W bands of
+// lattices with the same W side by side (lane group g = lanes
+// [gW, gW + W) is one whole periodic row of its band), so narrow lattices do
+// not leave lanes idle.  Each group streams its band through the same k-stage
+// register pipeline as the single-lattice streaming kernel (the stage math is
+// shared), with k-row halos read modulo M.
+//
+// Chunks.  One launch runs n chunks of k steps; between chunks every block
+// meets at a grid barrier whose waits are bounded by %globaltimer (on expiry
+// the kernel sets an error flag and returns; the host reports BML_ETIMEOUT).
+// The launch is cooperative, so all blocks are co-resident.  Data written in
+// one chunk is read by other blocks in the next, so the kernel loads and
+// stores lattice words through L2 (ld/st .cg), never through the
+// non-coherent read-only path.
+//
+// Jam early exit (optional).  A step in which no car moves leaves the lattice
+// unchanged, so every later step does too (an absorbing fixed point).  At the
+// start of each chunk a group checks the previous chunk's counts of its
+// lattice; after a zero-move step the lattice is frozen: its buffer index is
+// recorded and its tiles are skipped.  Later counts stay zero, which is what
+// the automaton would produce.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/bml.h"
+#include "bml_internal.cuh"
+#include "stage.cuh"
+
+namespace bml {
+
+struct EnsLattice {
+  int M, N, W, P;
+  int nb, pad;
+  u64 tail;
+  u64 off[2];  // word offset of buffer 0 / 1 (L plane; T plane at + M*P)
+};
+
+struct EnsGroup {
+  int lat, r0, len, pad;
+};
+
+struct EnsTile {
+  int W, G, first_group, max_len;
+  int min_len, pad0, pad1, pad2;
+};
+
+struct EnsCtrl {
+  long long steps;       // steps completed
+  long long last_depth;  // depth of the last chunk run (for jam checks)
+  int parity;            // buffer holding the state of lattices not frozen
+  int err;               // set by a barrier that timed out
+  unsigned bar_count;
+  unsigned bar_gen;
+};
+
+struct EnsParams {
+  const EnsLattice *lat;
+  const EnsTile *tiles;
+  const EnsGroup *groups;
+  int n_tiles;
+  int n_chunks;
+  u64 *pool;
+  u64 *tr_lr, *tr_tb;  // traces, [lattice][cap]
+  long long cap;
+  long long *frozen;   // first zero-move step of a frozen lattice, else -1
+  int *frozen_buf;     // buffer index holding a frozen lattice
+  EnsCtrl *ctrl;
+  int commit;          // 0: tuning launch, counts go to scratch, nothing frozen
+  int early_exit;
+  unsigned bar_target; // blocks expected at the barrier
+  long long timeout_ns;
+  u64 *scratch;        // tuning counts
+};
+
+namespace {
+
+constexpr int kEnsWarps = 4;
+
+__device__ __forceinline__ long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return (long long)t;
+}
+
+// Grid-wide barrier with a bounded wait.  Returns false if this or another
+// block gave up (the error flag is set).
+__device__ bool grid_barrier(EnsCtrl *ctrl, unsigned target, long long timeout_ns) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    volatile unsigned *gen = &ctrl->bar_gen;
+    volatile int *err = &ctrl->err;
+    const unsigned g0 = *gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&ctrl->bar_count, 1u) + 1u;
+    if (arrived == target) {
+      atomicExch(&ctrl->bar_count, 0u);
+      __threadfence();
+      atomicAdd(&ctrl->bar_gen, 1u);
+    } else {
+      const long long t0 = globaltimer_ns();
+      while (*gen == g0) {
+        if (*err) {
+          ok = 0;
+          break;
+        }
+        if (globaltimer_ns() - t0 > timeout_ns) {
+          atomicExch(&ctrl->err, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(200);
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+template <int K>
+struct PFE {
+  static constexpr int value = K >= 4 ? 2 : 4;
+};
+
+template <int K>
+__device__ void process_tile(const EnsParams &p, int t, long long step0, int par,
+                             long long prev_depth, int lane) {
+  constexpr int PF = PFE<K>::value;
+  const EnsTile tile = p.tiles[t];
+  const int W = tile.W;
+  const int grp = lane / W, wi = lane - grp * W;
+  bool on = grp < tile.G;
+  EnsGroup gr{0, 0, 0, 0};
+  EnsLattice L{};
+  if (on) {
+    gr = p.groups[tile.first_group + grp];
+    L = p.lat[gr.lat];
+  }
+  if (on && p.early_exit) {
+    long long fz = __ldcg(p.frozen + gr.lat);
+    if (fz < 0 && step0 > 0) {
+      const u64 *a = p.tr_lr + (long long)gr.lat * p.cap, *b = p.tr_tb + (long long)gr.lat * p.cap;
+      for (long long s = step0 - prev_depth; s < step0; ++s) {
+        if (s >= 0 && __ldcg(a + s) + __ldcg(b + s) == 0ull) {
+          fz = s;
+          break;
+        }
+      }
+      if (fz >= 0) {
+        p.frozen[gr.lat] = fz;  // every group of the lattice writes the same values
+        p.frozen_buf[gr.lat] = par;
+      }
+    }
+    if (fz >= 0) on = false;
+  }
+  if (!__any_sync(BML_FULL_MASK, on)) return;
+
+  LaneWord lw;
+  if (on) {
+    lw.src_l = grp * W + (wi == 0 ? W - 1 : wi - 1);
+    lw.src_r = grp * W + (wi == W - 1 ? 0 : wi + 1);
+  } else {
+    lw.src_l = lw.src_r = lane;
+  }
+  lane_word_bits(lw, on, on && wi == L.W - 1, on ? L.nb : 64, on ? L.tail : ~0ull);
+
+  const int M = on ? L.M : 1;
+  const size_t pitch = on ? (size_t)L.P : 0;
+  const size_t plane = (size_t)M * pitch;
+  const u64 *inbase = p.pool + (on ? L.off[par] : 0) + wi;
+  u64 *outbase = p.pool + (on ? L.off[par ^ 1] : 0) + wi;
+  const int len = gr.len, n_in = len + 2 * K;
+  int ld_row = on ? (gr.r0 - K) % M : 0;
+  if (ld_row < 0) ld_row += M;
+  const u64 *Lp = inbase + (size_t)ld_row * pitch;
+  u64 *Lo = outbase + (size_t)gr.r0 * pitch;
+
+  u64 curT[K], curLh[K], prevMv[K];
+  uint32_t c_lr[K], c_tb[K];
+#pragma unroll
+  for (int s = 0; s < K; ++s) curT[s] = curLh[s] = prevMv[s] = 0, c_lr[s] = c_tb[s] = 0;
+
+  u64 bufL[PF], bufT[PF];
+#pragma unroll
+  for (int u = 0; u < PF; ++u) {
+    bufL[u] = bufT[u] = 0;
+    if (on && u < n_in) {
+      bufL[u] = __ldcg(Lp);
+      bufT[u] = __ldcg(Lp + plane);
+      if (++ld_row == M) {
+        ld_row = 0;
+        Lp = inbase;
+      } else {
+        Lp += pitch;
+      }
+    }
+  }
+  const int n_max = tile.max_len + 2 * K;
+  for (int i0 = 0; i0 < n_max; i0 += PF) {
+    const bool steady = i0 >= 2 * K && i0 + PF <= tile.min_len + K;
+#pragma unroll
+    for (int u = 0; u < PF; ++u) {
+      const int i = i0 + u;
+      if (i < n_max) {  // warp-uniform
+        u64 inL = bufL[u], inT = bufT[u];
+        if (on && i + PF < n_in) {
+          bufL[u] = __ldcg(Lp);
+          bufT[u] = __ldcg(Lp + plane);
+          if (++ld_row == M) {
+            ld_row = 0;
+            Lp = inbase;
+          } else {
+            Lp += pitch;
+          }
+        }
+#pragma unroll
+        for (int s = 0; s < K; ++s) {
+          u64 mvH, mvV;
+          stage_step<false>(inL, inT, curT[s], curLh[s], prevMv[s], lw, mvH, mvV);
+          if (steady || (unsigned)(i - K - s) < (unsigned)len) c_lr[s] += popc64(mvH);
+          if (steady || (unsigned)(i - K - s - 1) < (unsigned)len) c_tb[s] += popc64(mvV);
+        }
+        if (on && i >= 2 * K && i - 2 * K < len) {
+          const size_t off = (size_t)(i - 2 * K) * pitch;
+          __stcg(Lo + off, inL);
+          __stcg(Lo + off + plane, inT);
+        }
+      }
+    }
+  }
+  // per-group reduction of the counts, then one atomic per group and step
+#pragma unroll
+  for (int s = 0; s < K; ++s) {
+    uint32_t a = on ? c_lr[s] : 0u, b = on ? c_tb[s] : 0u;
+    for (int off = 16; off > 0; off >>= 1) {
+      if (off < W) {
+        const uint32_t ua = __shfl_down_sync(BML_FULL_MASK, a, off);
+        const uint32_t ub = __shfl_down_sync(BML_FULL_MASK, b, off);
+        if (wi + off < W) {
+          a += ua;
+          b += ub;
+        }
+      }
+    }
+    if (on && wi == 0) {
+      if (p.commit) {
+        const long long slot = (long long)gr.lat * p.cap + step0 + s;
+        if (a) atomicAdd(p.tr_lr + slot, (unsigned long long)a);
+        if (b) atomicAdd(p.tr_tb + slot, (unsigned long long)b);
+      } else {
+        if (a) atomicAdd(p.scratch + s, (unsigned long long)a);
+        if (b) atomicAdd(p.scratch + K + s, (unsigned long long)b);
+      }
+    }
+  }
+}
+
+template <int K>
+__global__ void __launch_bounds__(kEnsWarps * 32, 4) ens_kernel(EnsParams p) {
+  const int lane = threadIdx.x & 31;
+  const int nwarps = gridDim.x * kEnsWarps;
+  const int wid = blockIdx.x * kEnsWarps + (threadIdx.x >> 5);
+  const long long base = __ldcg(&p.ctrl->steps);
+  const long long last_depth = __ldcg(&p.ctrl->last_depth);
+  const int par0 = *(volatile int *)&p.ctrl->parity;
+  for (int c = 0; c < p.n_chunks; ++c) {
+    const long long step0 = base + (long long)c * K;
+    const int par = (par0 + c) & 1;
+    const long long prev_depth = c == 0 ? last_depth : K;
+    for (int t = wid; t < p.n_tiles; t += nwarps) process_tile<K>(p, t, step0, par, prev_depth, lane);
+    if (c + 1 < p.n_chunks) {
+      if (!grid_barrier(p.ctrl, p.bar_target, p.timeout_ns)) return;
+    }
+  }
+}
+
+// Stream-ordered after ens_kernel: advance the step counter and parity.
+__global__ void ens_advance_kernel(EnsCtrl *ctrl, int n_chunks, int depth) {
+  if (threadIdx.x == 0 && blockIdx.x == 0 && ctrl->err == 0) {
+    ctrl->steps += (long long)n_chunks * depth;
+    ctrl->parity ^= (n_chunks & 1);
+    ctrl->last_depth = depth;
+  }
+}
+
+// ---- set-up kernels (not on the step path) ----
+__device__ __forceinline__ u64 sm64_at(u64 seed, u64 n) {
+  u64 z = seed + n * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// seeded placement of every lattice into buffer 0
+__global__ void ens_init_kernel(const EnsLattice *lat, int count, const u64 *seed,
+                                const u64 *t_lr, const u64 *t_tb, u64 *pool) {
+  for (int l = blockIdx.x; l < count; l += gridDim.x) {
+    const EnsLattice L = lat[l];
+    const long long words = (long long)L.M * L.P;
+    u64 *Lp = pool + L.off[0], *Tp = Lp + words;
+    for (long long idx = threadIdx.x; idx < words; idx += blockDim.x) {
+      const int i = (int)(idx / L.P), w = (int)(idx - (long long)i * L.P);
+      u64 lv = 0, tv = 0;
+      if (w < L.W) {
+        const int nbits = w == L.W - 1 ? L.nb : 64;
+        const u64 base = (u64)((long long)i * L.N + 64ll * w) + 1ull;
+        for (int b = 0; b < nbits; ++b) {
+          const u64 u = sm64_at(seed[l], base + (u64)b);
+          if (u < t_lr[l])
+            lv |= 1ull << b;
+          else if (u - t_lr[l] < t_tb[l])
+            tv |= 1ull << b;
+        }
+      }
+      Lp[idx] = lv;
+      Tp[idx] = tv;
+    }
+  }
+}
+
+// bytes (each lattice M*N, back to back at byte_off[l]) -> buffer `buf` of
+// every lattice; with pool == nullptr only the values are checked.
+__global__ void ens_pack_kernel(const EnsLattice *lat, int count, const long long *byte_off,
+                                const uint8_t *bytes, int buf, u64 *pool, int *bad) {
+  int badl = 0;
+  for (int l = blockIdx.x; l < count; l += gridDim.x) {
+    const EnsLattice L = lat[l];
+    const long long words = (long long)L.M * L.P;
+    const uint8_t *src = bytes + byte_off[l];
+    for (long long idx = threadIdx.x; idx < words; idx += blockDim.x) {
+      const int i = (int)(idx / L.P), w = (int)(idx - (long long)i * L.P);
+      u64 lv = 0, tv = 0;
+      if (w < L.W) {
+        const int nbits = w == L.W - 1 ? L.nb : 64;
+        const uint8_t *row = src + (long long)i * L.N + 64ll * w;
+        for (int b = 0; b < nbits; ++b) {
+          const uint32_t x = row[b];
+          badl |= x > 2u;
+          lv |= (u64)(x & 1u) << b;
+          tv |= (u64)((x >> 1) & 1u) << b;
+        }
+      }
+      if (pool) {
+        u64 *Lp = pool + L.off[buf];
+        Lp[idx] = lv;
+        Lp[words + idx] = tv;
+      }
+    }
+  }
+  if (badl) atomicOr(bad, 1);
+}
+
+// buffer of each lattice -> bytes, back to back
+__global__ void ens_unpack_kernel(const EnsLattice *lat, int count, const long long *byte_off,
+                                  const int *buf_of, const u64 *pool, uint8_t *bytes) {
+  for (int l = blockIdx.x; l < count; l += gridDim.x) {
+    const EnsLattice L = lat[l];
+    const long long words = (long long)L.M * L.P;
+    const u64 *Lp = pool + L.off[buf_of[l]], *Tp = Lp + words;
+    uint8_t *dst = bytes + byte_off[l];
+    const long long cells = (long long)L.M * L.N;
+    for (long long idx = threadIdx.x; idx < cells; idx += blockDim.x) {
+      const int i = (int)(idx / L.N), j = (int)(idx - (long long)i * L.N);
+      const long long wi = (long long)i * L.P + (j >> 6);
+      const int b = j & 63;
+      dst[idx] = (uint8_t)(((Lp[wi] >> b) & 1ull) | (((Tp[wi] >> b) & 1ull) << 1));
+    }
+  }
+}
+
+// first step (0-based entry) with no move, per lattice, over [0, steps)
+__global__ void ens_first_zero_kernel(const u64 *tr_lr, const u64 *tr_tb, long long cap,
+                                      int count, long long steps, long long *out) {
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < count; l += gridDim.x * blockDim.x) {
+    long long r = -1;
+    const u64 *a = tr_lr + (long long)l * cap, *b = tr_tb + (long long)l * cap;
+    for (long long s = 0; s < steps; ++s)
+      if (a[s] + b[s] == 0ull) {
+        r = s;
+        break;
+      }
+    out[l] = r;
+  }
+}
+
+// current buffer index of every lattice
+__global__ void ens_buf_of_kernel(const long long *frozen, const int *frozen_buf,
+                                  const EnsCtrl *ctrl, int count, int *buf_of) {
+  const int par = ctrl->parity;
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < count; l += gridDim.x * blockDim.x)
+    buf_of[l] = frozen[l] >= 0 ? frozen_buf[l] : par;
+}
+
+__global__ void ens_fill_kernel(long long *a, int count, long long v) {
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < count; l += gridDim.x * blockDim.x)
+    a[l] = v;
+}
+
+template <int K>
+int ens_occupancy() {
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ens_kernel<K>, kEnsWarps * 32, 0) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return b > 0 ? b : 1;
+}
+
+template <int K>
+cudaError_t launch_ens(const EnsParams &p, int grid, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kEnsWarps * 32);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, ens_kernel<K>, p);
+}
+
+}  // namespace
+}  // namespace bml
+
+// =================================================================== C ABI ==
+using namespace bml;
+
+namespace {
+
+int efail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  set_last_error(buf);
+  return code;
+}
+
+}  // namespace
+
+#define ECUDA(expr)                                                                       \
+  do {                                                                                    \
+    cudaError_t e_ = (expr);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return efail(BML_ECUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, \
+                   __LINE__);                                                             \
+  } while (0)
+
+struct bml_ens {
+  int count = 0;
+  std::vector<EnsLattice> lat;  // host copy
+  cudaStream_t st = nullptr;
+  int block_k = 0;
+  int64_t band_rows = 0;
+  unsigned flags = 0;
+  long long timeout_ns = 2000000000ll;
+  EnsLattice *d_lat = nullptr;
+  EnsTile *d_tiles = nullptr;
+  EnsGroup *d_groups = nullptr;
+  int n_tiles = 0;
+  u64 *pool = nullptr;
+  size_t pool_words = 0;
+  u64 *tr = nullptr;  // lr then tb, count * cap each
+  long long cap = 0;
+  long long *frozen = nullptr;
+  int *frozen_buf = nullptr;
+  int *buf_of = nullptr;
+  long long *byte_off_d = nullptr;
+  std::vector<long long> byte_off;
+  long long total_bytes = 0;
+  EnsCtrl *ctrl = nullptr;
+  u64 *scratch = nullptr;
+  int *flag = nullptr;
+  int grid[4] = {0, 0, 0, 0};  // persistent grid per depth index (k = 1, 2, 4, 8)
+  int64_t steps_done = 0;
+  bool failed = false;
+  std::map<int64_t, cudaGraphExec_t> graphs;
+  bool graphs_ok = true;
+};
+
+namespace {
+
+int kidx(int k) { return k == 1 ? 0 : k == 2 ? 1 : k == 4 ? 2 : 3; }
+
+void drop_graphs(bml_ens *e) {
+  for (auto &kv : e->graphs) cudaGraphExecDestroy(kv.second);
+  e->graphs.clear();
+}
+
+void ens_free(bml_ens *e) {
+  cudaStreamSynchronize(e->st);
+  drop_graphs(e);
+  cudaFree(e->d_lat);
+  cudaFree(e->d_tiles);
+  cudaFree(e->d_groups);
+  cudaFree(e->pool);
+  cudaFree(e->tr);
+  cudaFree(e->frozen);
+  cudaFree(e->frozen_buf);
+  cudaFree(e->buf_of);
+  cudaFree(e->byte_off_d);
+  cudaFree(e->ctrl);
+  cudaFree(e->scratch);
+  cudaFree(e->flag);
+}
+
+// Build tiles for target band height `band`: every lattice is cut into
+// round(M / band) bands (at least one) of near-equal length; groups of equal
+// word width are packed 32 / W to a warp tile, longest bands first, and the
+// tiles are ordered longest first for the round-robin assignment to warps.
+int build_tiles(bml_ens *e, int64_t band) {
+  std::vector<std::vector<EnsGroup>> byW(33);
+  for (int l = 0; l < e->count; ++l) {
+    const int M = e->lat[l].M;
+    int64_t nb = (int64_t)std::llround((double)M / (double)band);
+    if (nb < 1) nb = 1;
+    if (nb > M) nb = M;
+    // keep every band below 65536 rows (per-lane counters are 32-bit)
+    while ((M + nb - 1) / nb > 65535) ++nb;
+    const int base = (int)(M / nb), rem = (int)(M % nb);
+    int r0 = 0;
+    for (int64_t b = 0; b < nb; ++b) {
+      const int len = base + (b < rem ? 1 : 0);
+      byW[e->lat[l].W].push_back(EnsGroup{l, r0, len, 0});
+      r0 += len;
+    }
+  }
+  std::vector<EnsGroup> groups;
+  std::vector<EnsTile> tiles;
+  for (int W = 1; W <= 32; ++W) {
+    auto &v = byW[W];
+    std::sort(v.begin(), v.end(), [](const EnsGroup &a, const EnsGroup &b) {
+      return a.len != b.len ? a.len > b.len : a.lat < b.lat;
+    });
+    const int G = 32 / W;
+    for (size_t i = 0; i < v.size(); i += G) {
+      EnsTile t{};
+      t.W = W;
+      t.G = (int)std::min<size_t>(G, v.size() - i);
+      t.first_group = (int)groups.size();
+      t.max_len = v[i].len;
+      t.min_len = v[i + t.G - 1].len;
+      for (int g = 0; g < t.G; ++g) groups.push_back(v[i + g]);
+      tiles.push_back(t);
+    }
+  }
+  std::stable_sort(tiles.begin(), tiles.end(),
+                   [](const EnsTile &a, const EnsTile &b) { return a.max_len > b.max_len; });
+  cudaFree(e->d_tiles);
+  cudaFree(e->d_groups);
+  e->d_tiles = nullptr;
+  e->d_groups = nullptr;
+  ECUDA(cudaMalloc(&e->d_tiles, std::max<size_t>(1, tiles.size()) * sizeof(EnsTile)));
+  ECUDA(cudaMalloc(&e->d_groups, std::max<size_t>(1, groups.size()) * sizeof(EnsGroup)));
+  ECUDA(cudaMemcpyAsync(e->d_tiles, tiles.data(), tiles.size() * sizeof(EnsTile),
+                        cudaMemcpyHostToDevice, e->st));
+  ECUDA(cudaMemcpyAsync(e->d_groups, groups.data(), groups.size() * sizeof(EnsGroup),
+                        cudaMemcpyHostToDevice, e->st));
+  ECUDA(cudaStreamSynchronize(e->st));
+  e->n_tiles = (int)tiles.size();
+  e->band_rows = band;
+  drop_graphs(e);
+  return BML_OK;
+}
+
+EnsParams make_params(bml_ens *e, int n_chunks, int commit) {
+  EnsParams p{};
+  p.lat = e->d_lat;
+  p.tiles = e->d_tiles;
+  p.groups = e->d_groups;
+  p.n_tiles = e->n_tiles;
+  p.n_chunks = n_chunks;
+  p.pool = e->pool;
+  p.tr_lr = e->tr;
+  p.tr_tb = e->tr + (size_t)e->count * e->cap;
+  p.cap = e->cap;
+  p.frozen = e->frozen;
+  p.frozen_buf = e->frozen_buf;
+  p.ctrl = e->ctrl;
+  p.commit = commit;
+  p.early_exit = commit && (e->flags & BML_ENS_EARLY_EXIT) ? 1 : 0;
+  p.timeout_ns = e->timeout_ns;
+  p.scratch = e->scratch;
+  return p;
+}
+
+int grid_for(bml_ens *e, int k) {
+  int &g = e->grid[kidx(k)];
+  if (!g) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int occ = k == 1 ? ens_occupancy<1>() : k == 2 ? ens_occupancy<2>()
+                  : k == 4 ? ens_occupancy<4>() : ens_occupancy<8>();
+    g = sms * occ;
+  }
+  return g;
+}
+
+// Enqueue one persistent launch of n_chunks chunks of depth k.
+int enqueue_ens(bml_ens *e, int k, int n_chunks, int commit) {
+  if (n_chunks <= 0) return BML_OK;
+  EnsParams p = make_params(e, n_chunks, commit);
+  const int grid = grid_for(e, k);
+  p.bar_target = (unsigned)grid + ((e->flags & BML_ENS_TEST_STALL) ? 1u : 0u);
+  cudaError_t rc;
+  switch (k) {
+    case 1: rc = launch_ens<1>(p, grid, e->st); break;
+    case 2: rc = launch_ens<2>(p, grid, e->st); break;
+    case 4: rc = launch_ens<4>(p, grid, e->st); break;
+    default: rc = launch_ens<8>(p, grid, e->st); break;
+  }
+  if (rc != cudaSuccess) return efail(BML_ECUDA, "ensemble launch: %s", cudaGetErrorString(rc));
+  if (commit) {
+    ens_advance_kernel<<<1, 32, 0, e->st>>>(e->ctrl, n_chunks, k);
+    ECUDA(cudaGetLastError());
+  }
+  return BML_OK;
+}
+
+// k steps: full chunks at block_k, then the remainder by powers of two.
+int enqueue_steps_ens(bml_ens *e, int64_t k) {
+  const int64_t full = k / e->block_k;
+  int64_t left = k - full * e->block_k;
+  int64_t done = 0;
+  while (done < full) {
+    const int n = (int)std::min<int64_t>(full - done, 1 << 20);
+    int rc = enqueue_ens(e, e->block_k, n, 1);
+    if (rc) return rc;
+    done += n;
+  }
+  for (int d = 4; d >= 1; d >>= 1)
+    if (d < e->block_k && left >= d) {
+      int rc = enqueue_ens(e, d, 1, 1);
+      if (rc) return rc;
+      left -= d;
+    }
+  return BML_OK;
+}
+
+int grow_traces(bml_ens *e, long long need) {
+  if (need <= e->cap) return BML_OK;
+  long long ncap = e->cap > 0 ? e->cap : 1024;
+  while (ncap < need) ncap *= 2;
+  u64 *ntr = nullptr;
+  ECUDA(cudaMalloc(&ntr, (size_t)e->count * ncap * 2 * sizeof(u64)));
+  ECUDA(cudaMemsetAsync(ntr, 0, (size_t)e->count * ncap * 2 * sizeof(u64), e->st));
+  if (e->tr && e->steps_done > 0) {
+    for (int half = 0; half < 2; ++half)
+      ECUDA(cudaMemcpy2DAsync(ntr + (size_t)half * e->count * ncap, (size_t)ncap * 8,
+                              e->tr + (size_t)half * e->count * e->cap, (size_t)e->cap * 8,
+                              (size_t)e->steps_done * 8, (size_t)e->count,
+                              cudaMemcpyDeviceToDevice, e->st));
+  }
+  ECUDA(cudaStreamSynchronize(e->st));
+  cudaFree(e->tr);
+  e->tr = ntr;
+  e->cap = ncap;
+  drop_graphs(e);  // captured launches hold the old pointers
+  return BML_OK;
+}
+
+int check_err(bml_ens *e) {
+  EnsCtrl c;
+  ECUDA(cudaMemcpyAsync(&c, e->ctrl, sizeof c, cudaMemcpyDeviceToHost, e->st));
+  ECUDA(cudaStreamSynchronize(e->st));
+  if (c.err) {
+    e->failed = true;
+    return efail(BML_ETIMEOUT, "a grid barrier of the ensemble kernel timed out; the ensemble "
+                 "state is undefined");
+  }
+  return BML_OK;
+}
+
+int autotune_ens(bml_ens *e) {
+  cudaEvent_t a, b;
+  ECUDA(cudaEventCreate(&a));
+  ECUDA(cudaEventCreate(&b));
+  double best = 1e30;
+  int best_k = 4;
+  int64_t best_b = 128;
+  int rc = BML_OK;
+  for (int64_t band : {64, 128, 256, 512}) {
+    if ((rc = build_tiles(e, band))) break;
+    for (int k : {1, 2, 4, 8}) {
+      if ((rc = enqueue_ens(e, k, 1, 0))) break;  // warm-up, not committed
+      cudaEventRecord(a, e->st);
+      const int reps = 3;
+      for (int r = 0; r < reps && !rc; ++r) rc = enqueue_ens(e, k, 1, 0);
+      cudaEventRecord(b, e->st);
+      if (rc) break;
+      if (cudaEventSynchronize(b) != cudaSuccess) {
+        rc = efail(BML_ECUDA, "ensemble autotune: %s", cudaGetErrorString(cudaGetLastError()));
+        break;
+      }
+      float ms = 0;
+      cudaEventElapsedTime(&ms, a, b);
+      const double per = ms / (reps * k);
+      if (per < best) {
+        best = per;
+        best_k = k;
+        best_b = band;
+      }
+    }
+    if (rc) break;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (rc) return rc;
+  if ((rc = check_err(e))) return rc;
+  e->block_k = best_k;
+  return build_tiles(e, best_b);
+}
+
+}  // namespace
+
+extern "C" int bml_ensemble_create_ex(int64_t count, const int64_t *M, const int64_t *N,
+                                      const uint64_t *seed, const double *p_lr,
+                                      const double *p_tb, int block_k, int64_t band_rows,
+                                      unsigned flags, void *stream, int64_t reserve_steps,
+                                      bml_ens **out) {
+  if (!out || !M || !N || !seed || !p_lr || !p_tb) return efail(BML_EINVAL, "NULL argument");
+  if (count < 1 || count > (1 << 30)) return efail(BML_EINVAL, "count must be in [1, 2^30]");
+  if (block_k != 0 && block_k != 1 && block_k != 2 && block_k != 4 && block_k != 8)
+    return efail(BML_EINVAL, "block_k must be 0 (autotune), 1, 2, 4 or 8");
+  if (band_rows < 0) return efail(BML_EINVAL, "band_rows < 0");
+  if ((block_k == 0) != (band_rows == 0))
+    return efail(BML_EINVAL, "block_k and band_rows are both 0 (autotune) or both set");
+  if (reserve_steps < 0) return efail(BML_EINVAL, "reserve_steps < 0");
+  double total_cells = 0;
+  for (int64_t l = 0; l < count; ++l) {
+    if (M[l] < 1 || N[l] < 1 || N[l] > 2048 || M[l] > (1 << 24))
+      return efail(BML_EINVAL, "lattice %lld: need 1 <= N <= 2048 and 1 <= M <= 2^24",
+                   (long long)l);
+    if (!(p_lr[l] >= 0.0 && p_tb[l] >= 0.0 && p_lr[l] + p_tb[l] <= 1.0))
+      return efail(BML_EINVAL, "lattice %lld: bad p_lr/p_tb", (long long)l);
+    total_cells += (double)M[l] * (double)N[l];
+  }
+  if (total_cells > 68719476736.0) return efail(BML_EINVAL, "ensemble larger than 2^36 cells");
+
+  bml_ens *e = new (std::nothrow) bml_ens;
+  if (!e) return efail(BML_ENOMEM, "host allocation failed");
+  e->count = (int)count;
+  e->st = (cudaStream_t)stream;
+  e->flags = flags;
+  if (flags & BML_ENS_TEST_STALL) e->timeout_ns = 20000000ll;  // 20 ms
+  e->lat.resize(count);
+  e->byte_off.resize(count);
+  size_t words = 0;
+  long long bytes = 0;
+  for (int64_t l = 0; l < count; ++l) {
+    EnsLattice &L = e->lat[l];
+    L.M = (int)M[l];
+    L.N = (int)N[l];
+    L.W = (L.N + 63) / 64;
+    L.P = (L.W + 1) & ~1;
+    L.nb = L.N - 64 * (L.W - 1);
+    L.tail = L.nb == 64 ? ~0ull : ((1ull << L.nb) - 1ull);
+    L.pad = 0;
+    const size_t per = (size_t)2 * L.M * L.P;  // L and T
+    L.off[0] = words;
+    L.off[1] = words + per;
+    words += 2 * per;
+    e->byte_off[l] = bytes;
+    bytes += (long long)L.M * L.N;
+  }
+  e->pool_words = words;
+  e->total_bytes = bytes;
+  int rc = BML_OK;
+  std::vector<u64> tl(count), tt(count);
+  for (int64_t l = 0; l < count; ++l) {
+    tl[l] = placement_threshold(p_lr[l]);
+    tt[l] = placement_threshold(p_tb[l]);
+  }
+  u64 *d_seed = nullptr, *d_tl = nullptr, *d_tt = nullptr;
+#define ETRY(expr)                                                                          \
+  do {                                                                                      \
+    cudaError_t e_ = (expr);                                                                \
+    if (e_ != cudaSuccess) {                                                                \
+      rc = efail(e_ == cudaErrorMemoryAllocation ? BML_ENOMEM : BML_ECUDA, "%s: %s", #expr, \
+                 cudaGetErrorString(e_));                                                   \
+      goto fail_;                                                                           \
+    }                                                                                       \
+  } while (0)
+  ETRY(cudaMalloc(&e->d_lat, count * sizeof(EnsLattice)));
+  ETRY(cudaMalloc(&e->pool, words * sizeof(u64)));
+  ETRY(cudaMalloc(&e->frozen, count * sizeof(long long)));
+  ETRY(cudaMalloc(&e->frozen_buf, count * sizeof(int)));
+  ETRY(cudaMalloc(&e->buf_of, count * sizeof(int)));
+  ETRY(cudaMalloc(&e->byte_off_d, count * sizeof(long long)));
+  ETRY(cudaMalloc(&e->ctrl, sizeof(EnsCtrl)));
+  ETRY(cudaMalloc(&e->scratch, 16 * sizeof(u64)));
+  ETRY(cudaMalloc(&e->flag, 256));
+  ETRY(cudaMalloc(&d_seed, count * 8));
+  ETRY(cudaMalloc(&d_tl, count * 8));
+  ETRY(cudaMalloc(&d_tt, count * 8));
+  ETRY(cudaMemcpyAsync(e->d_lat, e->lat.data(), count * sizeof(EnsLattice),
+                       cudaMemcpyHostToDevice, e->st));
+  ETRY(cudaMemcpyAsync(e->byte_off_d, e->byte_off.data(), count * 8, cudaMemcpyHostToDevice,
+                       e->st));
+  ETRY(cudaMemcpyAsync(d_seed, seed, count * 8, cudaMemcpyHostToDevice, e->st));
+  ETRY(cudaMemcpyAsync(d_tl, tl.data(), count * 8, cudaMemcpyHostToDevice, e->st));
+  ETRY(cudaMemcpyAsync(d_tt, tt.data(), count * 8, cudaMemcpyHostToDevice, e->st));
+  ETRY(cudaMemsetAsync(e->pool, 0, words * sizeof(u64), e->st));
+  ETRY(cudaMemsetAsync(e->ctrl, 0, sizeof(EnsCtrl), e->st));
+  ETRY(cudaMemsetAsync(e->scratch, 0, 16 * sizeof(u64), e->st));
+  ETRY(cudaMemsetAsync(e->frozen_buf, 0, count * sizeof(int), e->st));
+  ens_fill_kernel<<<256, 256, 0, e->st>>>(e->frozen, (int)count, -1);
+  ETRY(cudaGetLastError());
+  ens_init_kernel<<<(unsigned)std::min<int64_t>(count, 148 * 16), 256, 0, e->st>>>(
+      e->d_lat, (int)count, d_seed, d_tl, d_tt, e->pool);
+  ETRY(cudaGetLastError());
+  ETRY(cudaStreamSynchronize(e->st));
+  cudaFree(d_seed);
+  cudaFree(d_tl);
+  cudaFree(d_tt);
+  d_seed = d_tl = d_tt = nullptr;
+  if ((rc = grow_traces(e, reserve_steps > 0 ? reserve_steps : 1024))) goto fail_;
+  if (block_k == 0) {
+    if ((rc = autotune_ens(e))) goto fail_;
+  } else {
+    e->block_k = block_k;
+    if ((rc = build_tiles(e, band_rows))) goto fail_;
+  }
+  *out = e;
+  return BML_OK;
+fail_:
+#undef ETRY
+  cudaFree(d_seed);
+  cudaFree(d_tl);
+  cudaFree(d_tt);
+  ens_free(e);
+  delete e;
+  return rc;
+}
+
+extern "C" int bml_ensemble_create(int64_t count, const int64_t *M, const int64_t *N,
+                                   const uint64_t *seed, const double *p_lr, const double *p_tb,
+                                   void *stream, bml_ens **out) {
+  return bml_ensemble_create_ex(count, M, N, seed, p_lr, p_tb, 0, 0, 0, stream, 0, out);
+}
+
+extern "C" void bml_ensemble_destroy(bml_ens *e) {
+  if (!e) return;
+  ens_free(e);
+  delete e;
+}
+
+extern "C" int bml_ensemble_step(bml_ens *e, int64_t k) {
+  if (!e) return efail(BML_EINVAL, "ensemble is NULL");
+  if (e->failed) return efail(BML_ESTATE, "ensemble failed earlier (barrier timeout)");
+  if (k < 0) return efail(BML_EINVAL, "k < 0");
+  if (k == 0) return BML_OK;
+  int rc = grow_traces(e, e->steps_done + k);
+  if (rc) return rc;
+  const bool use_graph = e->graphs_ok && !(e->flags & BML_ENS_NO_GRAPH);
+  if (use_graph) {
+    auto it = e->graphs.find(k);
+    if (it == e->graphs.end()) {
+      cudaGraph_t g = nullptr;
+      cudaGraphExec_t ge = nullptr;
+      bool ok = cudaStreamBeginCapture(e->st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      if (ok) {
+        const int erc = enqueue_steps_ens(e, k);
+        ok = cudaStreamEndCapture(e->st, &g) == cudaSuccess && erc == BML_OK;
+      }
+      if (ok) ok = cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
+      if (g) cudaGraphDestroy(g);
+      if (!ok) {
+        cudaGetLastError();
+        e->graphs_ok = false;  // fall back to direct launches from now on
+      } else {
+        it = e->graphs.emplace(k, ge).first;
+      }
+    }
+    if (e->graphs_ok) {
+      ECUDA(cudaGraphLaunch(it->second, e->st));
+      e->steps_done += k;
+      if (e->flags & BML_ENS_TEST_STALL) return check_err(e);
+      return BML_OK;
+    }
+  }
+  if ((rc = enqueue_steps_ens(e, k))) return rc;
+  e->steps_done += k;
+  if (e->flags & BML_ENS_TEST_STALL) return check_err(e);
+  return BML_OK;
+}
+
+extern "C" int bml_ensemble_synchronize(bml_ens *e) {
+  if (!e) return efail(BML_EINVAL, "ensemble is NULL");
+  ECUDA(cudaStreamSynchronize(e->st));
+  return check_err(e);
+}
+
+extern "C" int64_t bml_ensemble_steps_done(const bml_ens *e) { return e ? e->steps_done : -1; }
+
+extern "C" int bml_ensemble_get_config(const bml_ens *e, int *block_k, int64_t *band_rows,
+                                       int *graphs) {
+  if (!e) return efail(BML_EINVAL, "ensemble is NULL");
+  if (block_k) *block_k = e->block_k;
+  if (band_rows) *band_rows = e->band_rows;
+  if (graphs) *graphs = e->graphs_ok && !(e->flags & BML_ENS_NO_GRAPH) ? 1 : 0;
+  return BML_OK;
+}
+
+extern "C" int bml_ensemble_traces(bml_ens *e, int64_t first, int64_t n, int64_t *out_lr,
+                                   int64_t *out_tb) {
+  if (!e) return efail(BML_EINVAL, "ensemble is NULL");
+  if (first < 0 || n < 0 || first + n > e->steps_done)
+    return efail(BML_EINVAL, "step range outside [0, steps_done)");
+  if (n == 0) return BML_OK;
+  int rc = check_err(e);
+  if (rc) return rc;
+  for (int half = 0; half < 2; ++half) {
+    int64_t *dst = half ? out_tb : out_lr;
+    if (!dst) continue;
+    ECUDA(cudaMemcpy2DAsync(dst, (size_t)n * 8,
+                            e->tr + (size_t)half * e->count * e->cap + first, (size_t)e->cap * 8,
+                            (size_t)n * 8, (size_t)e->count, cudaMemcpyDeviceToHost, e->st));
+  }
+  ECUDA(cudaStreamSynchronize(e->st));
+  return BML_OK;
+}
+
+extern "C" int bml_ensemble_moved_counts(bml_ens *e, int64_t lattice, int64_t first, int64_t n,
+                                         int64_t *out_total, int64_t *out_lr, int64_t *out_tb) {
+  if (!e) return efail(BML_EINVAL, "ensemble is NULL");
+  if (lattice < 0 || lattice >= e->count) return efail(BML_EINVAL, "lattice out of range");
+  if (first < 0 || n < 0 || first + n > e->steps_done)
+    return efail(BML_EINVAL, "step range outside [0, steps_done)");
+  if (n == 0) return BML_OK;
+  int rc = check_err(e);
+  if (rc) return rc;
+  std::vector<int64_t> a((size_t)n), b((size_t)n);
+  ECUDA(cudaMemcpyAsync(a.data(), e->tr + (size_t)lattice * e->cap + first, (size_t)n * 8,
+                        cudaMemcpyDeviceToHost, e->st));
+  ECUDA(cudaMemcpyAsync(b.data(),
+                        e->tr + (size_t)e->count * e->cap + (size_t)lattice * e->cap + first,
+                        (size_t)n * 8, cudaMemcpyDeviceToHost, e->st));
+  ECUDA(cudaStreamSynchronize(e->st));
+  for (int64_t t = 0; t < n; ++t) {
+    if (out_lr) out_lr[t] = a[(size_t)t];
+    if (out_tb) out_tb[t] = b[(size_t)t];
+    if (out_total) out_total[t] = a[(size_t)t] + b[(size_t)t];
+  }
+  return BML_OK;
+}
+
+extern "C" int bml_ensemble_jam_steps(bml_ens *e, int64_t *out) {
+  if (!e || !out) return efail(BML_EINVAL, "NULL argument");
+  int rc = check_err(e);
+  if (rc) return rc;
+  long long *d = nullptr;
+  ECUDA(cudaMalloc(&d, (size_t)e->count * 8));
+  ens_first_zero_kernel<<<(e->count + 255) / 256, 256, 0, e->st>>>(
+      e->tr, e->tr + (size_t)e->count * e->cap, e->cap, e->count, e->steps_done, d);
+  cudaError_t r = cudaGetLastError();
+  if (r == cudaSuccess)
+    r = cudaMemcpyAsync(out, d, (size_t)e->count * 8, cudaMemcpyDeviceToHost, e->st);
+  if (r == cudaSuccess) r = cudaStreamSynchronize(e->st);
+  cudaFree(d);
+  if (r != cudaSuccess) return efail(BML_ECUDA, "jam steps: %s", cudaGetErrorString(r));
+  return BML_OK;
+}
+
+extern "C" int bml_ensemble_read_lattices(bml_ens *e, uint8_t *out) {
+  if (!e || !out) return efail(BML_EINVAL, "NULL argument");
+  int rc = check_err(e);
+  if (rc) return rc;
+  uint8_t *d = nullptr;
+  ECUDA(cudaMalloc(&d, (size_t)std::max<long long>(1, e->total_bytes)));
+  ens_buf_of_kernel<<<(e->count + 255) / 256, 256, 0, e->st>>>(e->frozen, e->frozen_buf, e->ctrl,
+                                                              e->count, e->buf_of);
+  ens_unpack_kernel<<<(unsigned)std::min(e->count, 148 * 16), 256, 0, e->st>>>(
+      e->d_lat, e->count, e->byte_off_d, e->buf_of, e->pool, d);
+  cudaError_t r = cudaGetLastError();
+  if (r == cudaSuccess)
+    r = cudaMemcpyAsync(out, d, (size_t)e->total_bytes, cudaMemcpyDeviceToHost, e->st);
+  if (r == cudaSuccess) r = cudaStreamSynchronize(e->st);
+  cudaFree(d);
+  if (r != cudaSuccess) return efail(BML_ECUDA, "read lattices: %s", cudaGetErrorString(r));
+  return BML_OK;
+}
+
+extern "C" int bml_ensemble_read_lattice(bml_ens *e, int64_t lattice, uint8_t *out) {
+  if (!e || !out) return efail(BML_EINVAL, "NULL argument");
+  if (lattice < 0 || lattice >= e->count) return efail(BML_EINVAL, "lattice out of range");
+  std::vector<uint8_t> all((size_t)e->total_bytes);
+  int rc = bml_ensemble_read_lattices(e, all.data());
+  if (rc) return rc;
+  const EnsLattice &L = e->lat[(size_t)lattice];
+  std::copy(all.begin() + e->byte_off[(size_t)lattice],
+            all.begin() + e->byte_off[(size_t)lattice] + (long long)L.M * L.N, out);
+  return BML_OK;
+}
+
+extern "C" int bml_ensemble_write_lattices(bml_ens *e, const uint8_t *in) {
+  if (!e || !in) return efail(BML_EINVAL, "NULL argument");
+  if (e->failed) return efail(BML_ESTATE, "ensemble failed earlier (barrier timeout)");
+  uint8_t *d = nullptr;
+  ECUDA(cudaMalloc(&d, (size_t)std::max<long long>(1, e->total_bytes)));
+  int hbad = 0;
+  EnsCtrl c0{};
+  const unsigned blocks = (unsigned)std::min(e->count, 148 * 16);
+  cudaError_t r = cudaMemcpyAsync(d, in, (size_t)e->total_bytes, cudaMemcpyHostToDevice, e->st);
+  if (r == cudaSuccess) r = cudaMemsetAsync(e->flag, 0, sizeof(int), e->st);
+  // check every value first, so that a rejected input leaves the state as it
+  // was; then pack into buffer 0 and restart all trajectories
+  if (r == cudaSuccess) {
+    ens_pack_kernel<<<blocks, 256, 0, e->st>>>(e->d_lat, e->count, e->byte_off_d, d, 0, nullptr,
+                                               e->flag);
+    r = cudaGetLastError();
+  }
+  if (r == cudaSuccess)
+    r = cudaMemcpyAsync(&hbad, e->flag, sizeof(int), cudaMemcpyDeviceToHost, e->st);
+  if (r == cudaSuccess) r = cudaStreamSynchronize(e->st);
+  if (r == cudaSuccess && !hbad) {
+    ens_pack_kernel<<<blocks, 256, 0, e->st>>>(e->d_lat, e->count, e->byte_off_d, d, 0, e->pool,
+                                               e->flag);
+    r = cudaGetLastError();
+    if (r == cudaSuccess)
+      r = cudaMemcpyAsync(e->ctrl, &c0, sizeof c0, cudaMemcpyHostToDevice, e->st);
+    if (r == cudaSuccess)
+      r = cudaMemsetAsync(e->tr, 0, (size_t)e->count * e->cap * 2 * sizeof(u64), e->st);
+    if (r == cudaSuccess) {
+      ens_fill_kernel<<<256, 256, 0, e->st>>>(e->frozen, e->count, -1);
+      r = cudaGetLastError();
+    }
+    if (r == cudaSuccess) r = cudaStreamSynchronize(e->st);
+    if (r == cudaSuccess) e->steps_done = 0;
+  }
+  cudaFree(d);
+  if (r != cudaSuccess) return efail(BML_ECUDA, "write lattices: %s", cudaGetErrorString(r));
+  if (hbad) return efail(BML_EINVAL, "a lattice holds a value other than 0, 1, 2");
+  return BML_OK;
+}

@@ -1,0 +1,85 @@
+// One pipeline stage of the streaming bitplane step, shared by the
+// single-lattice streaming kernel and the ensemble kernel.
+//
+// With E = EMPTY before the horizontal phase (Sec. 2 rules):
+//   mvH_x = L_x & Er_x            LR cars that leave (Er[j] = E[j+1])
+//   in_x  = mvH_x shifted one column right (the cells they enter)
+//   Lh_x  = L_x ^ mvH_x ^ in_x     horizontal rule on row x
+//   E'_x  = E_x ^ in_x ^ mvH_x     EMPTY after the horizontal phase
+//   mvV_{x-1} = T_{x-1} & E'_x     TB cars of row x-1 that move down
+//   emitted row x-1: L = Lh_{x-1}, T = (T_{x-1} & ~E'_x) | mvV_{x-2}
+// (the cars entering row x-1 from above are mvV_{x-2}, computed one row
+// earlier).  Horizontal neighbours come from two 32-bit warp shuffles: the
+// right neighbour's low half of E (bit 0 = the cell right of this word) and
+// the left neighbour's half of mvH holding its last cell, pre-aligned to bit
+// 31.
+#pragma once
+
+#include "device_common.cuh"
+
+namespace bml {
+
+// Per-lane constants of the word a lane holds.
+struct LaneWord {
+  u64 valid;                // valid-cell mask (all ones for a full word, 0 if the lane is off)
+  uint32_t ins_lo, ins_hi;  // bit that receives the right neighbour's first cell
+  int top_hi;               // the word's last cell lies in the high half
+  int top_sh;               // left shift that moves the last cell to bit 31 of its half
+  int src_l, src_r;         // lanes holding the left / right neighbour words
+};
+
+__device__ __forceinline__ void lane_word_bits(LaneWord &lw, bool on, bool last, int nb,
+                                               u64 tail) {
+  const int top = last ? nb - 1 : 63;
+  lw.valid = on ? (last ? tail : ~0ull) : 0ull;
+  lw.ins_lo = top < 32 ? (1u << top) : 0u;
+  lw.ins_hi = top >= 32 ? (1u << (top - 32)) : 0u;
+  lw.top_hi = top >= 32;
+  lw.top_sh = 31 - (top & 31);
+}
+
+__device__ __forceinline__ uint32_t lo32(u64 x) { return (uint32_t)x; }
+__device__ __forceinline__ uint32_t hi32(u64 x) { return (uint32_t)(x >> 32); }
+__device__ __forceinline__ u64 mk64(uint32_t lo, uint32_t hi) {
+  return (u64)lo | ((u64)hi << 32);
+}
+
+// Stage state: T_{x-1}, Lh_{x-1}, mvV_{x-2}.  Consumes row x (inL, inT) of
+// its input state, replaces them with row x-1 of the next state, and returns
+// the row's moved-car masks.  FULL: every word of the row holds 64 cells.
+template <bool FULL>
+__device__ __forceinline__ void stage_step(u64 &inL, u64 &inT, u64 &curT, u64 &curLh,
+                                           u64 &prevMv, const LaneWord &lw, u64 &mvH,
+                                           u64 &mvV) {
+  const u64 E = FULL ? ~(inL | inT) : (~(inL | inT) & lw.valid);
+  const uint32_t rr = __shfl_sync(BML_FULL_MASK, lo32(E), lw.src_r);
+  u64 Er;
+  if (FULL) {
+    Er = mk64(__funnelshift_r(lo32(E), hi32(E), 1), __funnelshift_r(hi32(E), rr, 1));
+  } else {
+    const uint32_t m = 0u - (rr & 1u);
+    Er = mk64(__funnelshift_r(lo32(E), hi32(E), 1) | (lw.ins_lo & m),
+              (hi32(E) >> 1) | (lw.ins_hi & m));
+  }
+  mvH = inL & Er;
+  const uint32_t send_l = FULL ? hi32(mvH) : ((lw.top_hi ? hi32(mvH) : lo32(mvH)) << lw.top_sh);
+  const uint32_t rl = __shfl_sync(BML_FULL_MASK, send_l, lw.src_l);
+  u64 in = mk64(__funnelshift_l(rl, lo32(mvH), 1), __funnelshift_l(lo32(mvH), hi32(mvH), 1));
+  if (!FULL) in &= lw.valid;
+  const u64 Lh = inL ^ mvH ^ in;
+  const u64 Ep = E ^ in ^ mvH;
+  mvV = curT & Ep;
+  const u64 oT = (curT & ~Ep) | prevMv;
+  const u64 oL = curLh;
+  curT = inT;
+  curLh = Lh;
+  prevMv = mvV;
+  inL = oL;
+  inT = oT;
+}
+
+__device__ __forceinline__ uint32_t popc64(u64 x) {
+  return (uint32_t)(__popc(lo32(x)) + __popc(hi32(x)));
+}
+
+}  // namespace bml

@@ -42,7 +42,7 @@
 // emitted row x-1, only for owned rows and words, in per-lane registers; at
 // the end they are reduced per warp, then per block in shared memory, and
 // added with one 64-bit atomic per block and sub-step.
-#include "device_common.cuh"
+#include "stage.cuh"
 
 namespace bml {
 
@@ -56,23 +56,10 @@ struct PF {
   static constexpr int value = K >= 4 ? 2 : 4;
 };
 
-// Per-lane constants of the word a lane holds.
-struct LaneWord {
-  u64 valid;      // valid-cell mask (all ones for a full word, 0 if the lane is off)
-  uint32_t ins_lo, ins_hi;  // bit that receives the right neighbour's first cell
-  int top_hi;     // the word's last cell lies in the high half
-  int top_sh;     // left shift that moves the last cell to bit 31 of its half
-  int src_l, src_r;
-};
-
 template <int K>
 struct Pipe {
   u64 curT[K], curLh[K], prevMv[K];
 };
-
-__device__ __forceinline__ uint32_t lo32(u64 x) { return (uint32_t)x; }
-__device__ __forceinline__ uint32_t hi32(u64 x) { return (uint32_t)(x >> 32); }
-__device__ __forceinline__ u64 mk64(uint32_t lo, uint32_t hi) { return (u64)lo | ((u64)hi << 32); }
 
 // One row through all K stages.  With PRED, stage s counts its moves only
 // for band rows (band-relative row i - K - s horizontally, the row above it
@@ -83,38 +70,10 @@ __device__ __forceinline__ void row_through(u64 &inL, u64 &inT, Pipe<K> &p, cons
                                             uint32_t (&c_tb)[K]) {
 #pragma unroll
   for (int s = 0; s < K; ++s) {
-    const u64 E = FULL ? ~(inL | inT) : (~(inL | inT) & lw.valid);
-    // right neighbour: bit 0 of its E
-    const uint32_t rr = __shfl_sync(BML_FULL_MASK, lo32(E), lw.src_r);
-    u64 Er;
-    if (FULL) {
-      Er = mk64(__funnelshift_r(lo32(E), hi32(E), 1), __funnelshift_r(hi32(E), rr, 1));
-    } else {
-      const uint32_t m = 0u - (rr & 1u);
-      Er = mk64(__funnelshift_r(lo32(E), hi32(E), 1) | (lw.ins_lo & m),
-                (hi32(E) >> 1) | (lw.ins_hi & m));
-    }
-    const u64 mvH = inL & Er;
-    // left neighbour: its last cell of mvH, at bit 31
-    const uint32_t send_l =
-        FULL ? hi32(mvH) : ((lw.top_hi ? hi32(mvH) : lo32(mvH)) << lw.top_sh);
-    const uint32_t rl = __shfl_sync(BML_FULL_MASK, send_l, lw.src_l);
-    u64 in = mk64(__funnelshift_l(rl, lo32(mvH), 1), __funnelshift_l(lo32(mvH), hi32(mvH), 1));
-    if (!FULL) in &= lw.valid;
-    const u64 Lh = inL ^ mvH ^ in;
-    const u64 Ep = E ^ in ^ mvH;
-    const u64 mvV = p.curT[s] & Ep;
-    const u64 oT = (p.curT[s] & ~Ep) | p.prevMv[s];
-    const u64 oL = p.curLh[s];
-    if (!PRED || (unsigned)(i - K - s) < (unsigned)B)
-      c_lr[s] += (uint32_t)(__popc(lo32(mvH)) + __popc(hi32(mvH)));
-    if (!PRED || (unsigned)(i - K - s - 1) < (unsigned)B)
-      c_tb[s] += (uint32_t)(__popc(lo32(mvV)) + __popc(hi32(mvV)));
-    p.curT[s] = inT;
-    p.curLh[s] = Lh;
-    p.prevMv[s] = mvV;
-    inL = oL;
-    inT = oT;
+    u64 mvH, mvV;
+    stage_step<FULL>(inL, inT, p.curT[s], p.curLh[s], p.prevMv[s], lw, mvH, mvV);
+    if (!PRED || (unsigned)(i - K - s) < (unsigned)B) c_lr[s] += popc64(mvH);
+    if (!PRED || (unsigned)(i - K - s - 1) < (unsigned)B) c_tb[s] += popc64(mvV);
   }
 }
 
@@ -164,12 +123,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 4)
       lw.src_r = lane + 1 < span ? lane + 1 : lane;
       if (!on) lw.src_l = lw.src_r = lane;
     }
-    const int top = w == g.W - 1 ? g.nb - 1 : 63;
-    lw.valid = on ? (w == g.W - 1 ? g.tail : ~0ull) : 0ull;
-    lw.ins_lo = top < 32 ? (1u << top) : 0u;
-    lw.ins_hi = top >= 32 ? (1u << (top - 32)) : 0u;
-    lw.top_hi = top >= 32;
-    lw.top_sh = 31 - (top & 31);
+    lane_word_bits(lw, on, w == g.W - 1, g.nb, g.tail);
 
     // ---- band rows: unrolled input rows [r0 - K, r1 + K) ----
     const int r0 = band * band_rows;

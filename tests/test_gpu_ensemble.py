@@ -1,0 +1,183 @@
+"""GPU parity of the batched ensemble against the CPU oracle (per lattice),
+through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1804_07981_b300.inputs import all_lattices, ensemble_params
+
+pytestmark = pytest.mark.gpu
+
+
+def oracle_ensemble(Ms, Ns, seeds, plr, ptb, K):
+    outs, lrs, tbs = [], [], []
+    for M, N, s, a, b in zip(Ms, Ns, seeds, plr, ptb):
+        g0 = oracle.init(int(M), int(N), int(s), float(a), float(b))
+        g, lr, tb = oracle.run(g0, K)
+        outs.append(g)
+        lrs.append(lr)
+        tbs.append(tb)
+    return outs, np.stack(lrs), np.stack(tbs)
+
+
+def mixed_shapes(count, seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    M = rng.integers(1, 140, size=count)
+    N = rng.integers(1, 2049, size=count)
+    n = min(count, 6)
+    N[:n] = [1, 63, 64, 65, 2047, 2048][:n]
+    M[:n] = [1, 2, 3, 17, 5, 1][:n]
+    rho = rng.uniform(0.1, 0.7, size=count)
+    f = rng.uniform(0.3, 0.7, size=count)
+    return M, N, np.arange(1, count + 1, dtype=np.uint64), rho * f, rho * (1 - f)
+
+
+@pytest.mark.parametrize("block_k,band", [(1, 16), (2, 37), (4, 64), (8, 128), (8, 9), (0, 0)])
+def test_ensemble_mixed_shapes_match_oracle(lib, block_k, band):
+    M, N, seeds, plr, ptb = mixed_shapes(48, 7)
+    K = 29
+    want, wlr, wtb = oracle_ensemble(M, N, seeds, plr, ptb, K)
+    with lib.Ensemble(M, N, seeds, plr, ptb, block_k=block_k, band_rows=band) as ens:
+        ens.step(10)
+        ens.step(K - 10)
+        got = ens.read_all()
+        lr, tb = ens.traces()
+        for l in range(len(M)):
+            np.testing.assert_array_equal(got[l], want[l], err_msg="lattice %d" % l)
+        np.testing.assert_array_equal(lr, wlr)
+        np.testing.assert_array_equal(tb, wtb)
+        tot, a, b = ens.moved_counts(5)
+        np.testing.assert_array_equal(tot, wlr[5] + wtb[5])
+        np.testing.assert_array_equal(ens.read(5), want[5])
+
+
+@pytest.mark.parametrize("M,N", [(1, 12), (2, 6), (3, 4), (4, 3), (6, 2), (12, 1), (1, 11),
+                                 (3, 3), (2, 5), (5, 2), (1, 1), (1, 2), (2, 1), (2, 2)])
+def test_ensemble_exhaustive_tiny_lattices(lib, M, N):
+    """Every configuration of an M x N lattice (M*N <= 12) as one ensemble
+    member each, 3 steps, against the oracle."""
+    gs = all_lattices(M, N)
+    count = gs.shape[0]
+    K = 3
+    og, olr, otb = oracle.run_batch(gs, K)
+    with lib.Ensemble(np.full(count, M), np.full(count, N), np.arange(count), np.zeros(count),
+                      np.zeros(count), block_k=2, band_rows=M, reserve_steps=8) as ens:
+        ens.write_all(gs)
+        ens.step(K)
+        got = np.stack(ens.read_all())
+        lr, tb = ens.traces()
+    np.testing.assert_array_equal(got, og)
+    np.testing.assert_array_equal(lr, olr)
+    np.testing.assert_array_equal(tb, otb)
+
+
+def test_ensemble_config4_style_subset(lib):
+    """A subset of the batched-ensemble workload (M, N uniform on
+    {64..2048}, density in [0.1, 0.6], LR fraction in [0.3, 0.7])."""
+    p = ensemble_params(4096, seed=1)
+    idx = np.arange(0, 4096, 256)  # 16 lattices
+    M, N = p["M"][idx], p["N"][idx]
+    K = 64
+    want, wlr, wtb = oracle_ensemble(M, N, p["seed"][idx], p["p_lr"][idx], p["p_tb"][idx], K)
+    with lib.Ensemble(M, N, p["seed"][idx], p["p_lr"][idx], p["p_tb"][idx]) as ens:
+        ens.step(K)
+        got = ens.read_all()
+        lr, tb = ens.traces()
+    for l in range(len(M)):
+        np.testing.assert_array_equal(got[l], want[l])
+    np.testing.assert_array_equal(lr, wlr)
+    np.testing.assert_array_equal(tb, wtb)
+
+
+@pytest.mark.parametrize("block_k", [2, 8])
+def test_ensemble_early_exit_exact(lib, block_k):
+    """High densities jam; skipping frozen lattices must not change anything."""
+    rng = np.random.Generator(np.random.PCG64(3))
+    count = 40
+    M = rng.integers(8, 60, size=count)
+    N = rng.integers(8, 200, size=count)
+    rho = rng.uniform(0.45, 0.9, size=count)
+    seeds = np.arange(100, 100 + count, dtype=np.uint64)
+    K = 300
+    want, wlr, wtb = oracle_ensemble(M, N, seeds, rho / 2, rho / 2, K)
+    jam_want = np.array([np.flatnonzero(a + b == 0)[0] if np.any(a + b == 0) else -1
+                         for a, b in zip(wlr, wtb)])
+    assert (jam_want >= 0).sum() > count // 2
+    with lib.Ensemble(M, N, seeds, rho / 2, rho / 2, block_k=block_k, band_rows=16,
+                      flags=lib.BML_ENS_EARLY_EXIT) as ens:
+        for _ in range(5):
+            ens.step(K // 5)
+        got = ens.read_all()
+        lr, tb = ens.traces()
+        jam = ens.jam_steps()
+    for l in range(count):
+        np.testing.assert_array_equal(got[l], want[l])
+    np.testing.assert_array_equal(lr, wlr)
+    np.testing.assert_array_equal(tb, wtb)
+    np.testing.assert_array_equal(jam, jam_want)
+
+
+def test_ensemble_graph_and_direct_launches_agree(lib):
+    import torch
+    M, N, seeds, plr, ptb = mixed_shapes(20, 11)
+    st = torch.cuda.Stream()
+    res = []
+    for flags in (0, lib.BML_ENS_NO_GRAPH):
+        with lib.Ensemble(M, N, seeds, plr, ptb, block_k=4, band_rows=32, flags=flags,
+                          stream=st) as ens:
+            for _ in range(4):
+                ens.step(12)
+            assert ens.config[2] == (flags == 0)
+            res.append((ens.read_all(), ens.traces()))
+    for a, b in zip(res[0][0], res[1][0]):
+        np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(res[0][1][0], res[1][1][0])
+    np.testing.assert_array_equal(res[0][1][1], res[1][1][1])
+
+
+def test_ensemble_write_rejects_bad_values(lib):
+    M, N, seeds, plr, ptb = mixed_shapes(5, 2)
+    with lib.Ensemble(M, N, seeds, plr, ptb, block_k=1, band_rows=8) as ens:
+        ens.step(3)
+        before = ens.read_all()
+        bad = [g.copy() for g in before]
+        bad[2].flat[0] = 7
+        with pytest.raises(lib.BMLError) as e:
+            ens.write_all(bad)
+        assert e.value.code == lib.BML_EINVAL
+        for a, b in zip(ens.read_all(), before):
+            np.testing.assert_array_equal(a, b)
+        assert ens.steps_done == 3
+
+
+def test_ensemble_barrier_timeout_is_reported(lib):
+    """A grid barrier that can never complete (test hook: it waits for one
+    block more than the grid has) gives up after its time limit; the call
+    reports BML_ETIMEOUT, the ensemble refuses further work, and the GPU
+    context stays usable."""
+    M, N, seeds, plr, ptb = mixed_shapes(8, 5)
+    with lib.Ensemble(M, N, seeds, plr, ptb, block_k=2, band_rows=16,
+                      flags=lib.BML_ENS_TEST_STALL | lib.BML_ENS_NO_GRAPH) as ens:
+        with pytest.raises(lib.BMLError) as e:
+            ens.step(8)  # four chunks: three barriers
+        assert e.value.code == lib.BML_ETIMEOUT
+        with pytest.raises(lib.BMLError) as e:
+            ens.step(2)
+        assert e.value.code == lib.BML_ESTATE
+    K = 9
+    want, wlr, wtb = oracle_ensemble(M, N, seeds, plr, ptb, K)
+    with lib.Ensemble(M, N, seeds, plr, ptb, block_k=2, band_rows=16) as ens:
+        ens.step(K)
+        lr, tb = ens.traces()
+    np.testing.assert_array_equal(lr, wlr)
+
+
+def test_ensemble_rejects_bad_arguments(lib):
+    with pytest.raises(lib.BMLError):
+        lib.bml_ensemble_create_ex([10], [4096], [1], [0.1], [0.1], 1, 16)
+    with pytest.raises(lib.BMLError):
+        lib.bml_ensemble_create_ex([10], [100], [1], [0.6], [0.6], 1, 16)
+    with pytest.raises(lib.BMLError):
+        lib.bml_ensemble_create_ex([10], [100], [1], [0.1], [0.1], 3, 16)
+    with pytest.raises(lib.BMLError):
+        lib.bml_ensemble_create_ex([10], [100], [1], [0.1], [0.1], 2, 0)
