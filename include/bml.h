@@ -155,6 +155,40 @@ void bml_destroy(bml_sim *sim);
 const char *bml_last_error(void);
 
 /* ------------------------------------------------------------------------
+ * Byte-per-cell step that allocates nothing (no counterpart in the paper).
+ *
+ * For callers that cannot allocate device memory when they step a lattice:
+ * code that runs inside a framework whose own pool owns every allocation,
+ * code being recorded into a pipeline in which an allocation would
+ * synchronise the device, or embedded users whose memory budget is fixed at
+ * start-up.  The caller owns the lattice and the count arrays; the one extra
+ * buffer the step needs (the lattice between its two phases) is a 16 MiB
+ * array compiled into the library, which every GPU that loads the library's
+ * device code holds until the process exits.
+ *
+ * d_cells: device pointer, 16-byte aligned, M rows of PB bytes each, PB = N
+ *   rounded up to a multiple of 16; cell (i, j) is byte i*PB + j (0/1/2);
+ *   bytes j >= N of a row are left untouched.  Stepped k times in place.
+ * d_moved_lr, d_moved_tb: device arrays of k int64; set to the counts of the
+ *   k steps (they are cleared first).
+ * stream: cudaStream_t (NULL = legacy default stream); the call only
+ *   enqueues work.
+ * Limits and errors: M * PB <= BML_NOALLOC_MAX_BYTES (else BML_EINVAL, use
+ *   bml_create_ex with BML_KERNEL_BYTE); NULL pointers, M < 1, N < 1, k < 0
+ *   or a misaligned d_cells give BML_EINVAL.  No cudaMalloc, cudaFree or any
+ *   other allocating routine is called.
+ * The first call on a device looks up the device address of the built-in
+ *   array (cudaGetSymbolAddress); make that first call before any stream
+ *   capture.  All calls share the one array: calls whose work overlaps on
+ *   the GPU (different streams, or other threads) race and corrupt each
+ *   other; order them on one stream.
+ * ------------------------------------------------------------------------ */
+#define BML_NOALLOC_MAX_BYTES (16u * 1024u * 1024u)
+
+int bml_step_bytes_noalloc(uint8_t *d_cells, int64_t M, int64_t N, int64_t k,
+                           int64_t *d_moved_lr, int64_t *d_moved_tb, void *stream);
+
+/* ------------------------------------------------------------------------
  * Batched ensemble: `count` independent lattices of uneven shapes and
  * densities advanced together.  Every lattice follows the model and the
  * placement rule above (lattice l: M[l] x N[l], seed[l], p_lr[l], p_tb[l]).

@@ -271,6 +271,19 @@ class Lattice:
         self.close()
 
 
+# --------------------------------------------------- allocation-free step --
+BML_NOALLOC_MAX_BYTES = 16 * 1024 * 1024
+
+_lib_noalloc = _sig("bml_step_bytes_noalloc", [_vp, _i64, _i64, _i64, _vp, _vp, _vp])
+
+
+def bml_step_bytes_noalloc(d_cells: int, M: int, N: int, k: int, d_moved_lr: int,
+                           d_moved_tb: int, stream=None) -> None:
+    """Step a caller-owned device lattice (M rows of N rounded up to 16
+    bytes) k times without any device allocation; see include/bml.h."""
+    _check(_lib_noalloc(d_cells, M, N, k, d_moved_lr, d_moved_tb, _stream_handle(stream)))
+
+
 # ----------------------------------------------------------------- ensemble --
 BML_ENS_EARLY_EXIT = 1
 BML_ENS_NO_GRAPH = 2
