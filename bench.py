@@ -29,6 +29,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -38,6 +40,17 @@ DENSITY = 0.38
 STEPS_PER_BENCH_STEP = 8
 BYTES_PER_CELL_STEP = 0.5  # 2 bits read + 2 bits written per cell per step
 WORKLOAD = "bml_32768x32768_rho0.38"
+# 32-bit integer ALU operations the bitplane step needs per 64-cell word:
+# E, Er, mvH, in, Lh, E', mvV, T' (two 32-bit operations each) and the two
+# count additions; popcounts run on another pipe and are not counted
+ALU_OPS_PER_CELL_STEP = 18.0 / 64.0
+SMS = 148
+ALU_LANES_PER_SM_CLK = 64  # integer ALU pipe: 2 warp instructions per clock per SM
+SM_MAX_MHZ = 2032.0
+# DRAM bytes (read + write, as counted by ncu for one launch) per cell, from
+# the captures summarised in profiles/ (16384 x 32768 cases); scaled by the
+# cell count of the run
+TRAFFIC_PER_CELL = {"stream_kernel<8>": 0.4252, "fused_rows_kernel": 0.4068}
 
 
 def _peaks():
@@ -125,6 +138,34 @@ def _cpu_sample(budget_s: float, threads: int):
     return rate, desc, dt
 
 
+def _ensemble_bench(bml, torch, stream, steps, seed_base=1):
+    """Batched ensemble of 4096 lattices (M, N uniform on {64..2048}, density
+    uniform on [0.1, 0.6], LR fraction uniform on [0.3, 0.7]), autotuned,
+    graph-replayed; `steps` steps timed with CUDA events after a warm-up."""
+    from paper_1804_07981_b300.inputs import ensemble_params
+    p = ensemble_params(4096, seed=1)
+    ens = bml.Ensemble(p["M"], p["N"], p["seed"] + np.uint64(seed_base - 1), p["p_lr"],
+                       p["p_tb"], stream=stream, reserve_steps=steps + 64)
+    ens.step(32)
+    ens.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ens.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    ens.synchronize()
+    ms = e0.elapsed_time(e1)
+    cells = int((p["M"] * p["N"]).sum())
+    k, band, graphs = ens.config
+    ens.close()
+    return {"metric": "ensemble lattice-steps/s", "lattices": 4096, "steps": steps,
+            "seconds": ms / 1e3, "unit": "lattice-steps/s",
+            "cell_updates_per_s": cells * steps / (ms / 1e3), "cells": cells,
+            "temporal_depth": k, "band_rows": band, "graph": graphs,
+            "workload": "4096 lattices, M,N ~ U{64..2048}, rho ~ U[0.1,0.6], "
+                        "LR fraction ~ U[0.3,0.7], seeds 1..4096"}
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -202,6 +243,8 @@ def run_ours(args):
     sim = bml.Lattice(M, N, seed=seed, p_lr=DENSITY / 2, p_tb=DENSITY / 2, kernel=args.kernel,
                       block_k=args.block_k, stream=stream,
                       reserve_steps=(K + W) * STEPS_PER_BENCH_STEP)
+    if args.band is not None:
+        sim.set_tiling(args.block_k or 1, args.band)
     kernel_id, block_k, band_rows = sim.config
     for _ in range(W):
         sim.step(STEPS_PER_BENCH_STEP)
@@ -227,33 +270,46 @@ def run_ours(args):
     assert (tot >= 0).all() and (tot <= cells).all()
 
     # dominant kernel: every launch in the timed region is the same kernel
-    if kernel_id in (bml.BML_KERNEL_TBLOCK, bml.BML_KERNEL_FUSED):
-        launches_per_step = STEPS_PER_BENCH_STEP // max(1, block_k)
-        kname = "stream_kernel<%d>" % max(1, block_k)
-        depth = max(1, block_k)
-        bytes_per_launch = BYTES_PER_CELL_STEP * cells  # one pass over both planes
-    elif kernel_id == bml.BML_KERNEL_BITPLANE:
-        launches_per_step = 2 * STEPS_PER_BENCH_STEP
-        kname, depth = "plane_h/plane_v", 1
-        bytes_per_launch = 0.4375 * cells
-    else:
-        launches_per_step = 2 * STEPS_PER_BENCH_STEP
-        kname, depth = "byte_h/byte_v", 1
-        bytes_per_launch = 2.0 * cells
-    launch_ms = ms / (K * launches_per_step)
     hbm_peak, peak_kind = _peaks()
-    achieved = bytes_per_launch / (launch_ms / 1e3) / 1e9
+    sm_mhz = (clk or {}).get("sm_mhz") or SM_MAX_MHZ
+    if kernel_id in (bml.BML_KERNEL_TBLOCK, bml.BML_KERNEL_FUSED):
+        depth = max(1, block_k)
+        launches_per_step = STEPS_PER_BENCH_STEP // depth
+        kname = "fused_rows_kernel" if band_rows == 0 else "stream_kernel<%d>" % depth
+    elif kernel_id == bml.BML_KERNEL_BITPLANE:
+        depth, launches_per_step, kname = 1, 2 * STEPS_PER_BENCH_STEP, "plane_h/plane_v"
+    else:
+        depth, launches_per_step, kname = 1, 2 * STEPS_PER_BENCH_STEP, "byte_h/byte_v"
+    launch_ms = ms / (K * launches_per_step)
+    cell_steps_per_launch = cells * depth
     effective = BYTES_PER_CELL_STEP * cells * lattice_steps / (ms / 1e3) / 1e9
-    roofline = {
-        "bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm_peak,
-        "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
-        "peak_kind": peak_kind, "launch_ms": launch_ms, "temporal_depth": depth,
-        "effective_GBps": effective, "effective_frac": effective / hbm_peak,
-    }
+    traffic = TRAFFIC_PER_CELL.get(kname)
+    if depth >= 2:
+        # bit logic with k steps per DRAM pass: bound by the integer ALU pipe
+        ops = ALU_OPS_PER_CELL_STEP * cell_steps_per_launch
+        achieved = ops / (launch_ms / 1e3) / 1e12
+        peak = SMS * ALU_LANES_PER_SM_CLK * sm_mhz * 1e6 / 1e12
+        roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
+                    "unit": "Tops/s", "frac": achieved / peak,
+                    "traffic": traffic * cells if traffic else None,
+                    "peak_kind": "derived: %d SMs x %d int32 lanes/clk x %.0f MHz sampled"
+                                 % (SMS, ALU_LANES_PER_SM_CLK, sm_mhz),
+                    "ops_per_cell_step": ALU_OPS_PER_CELL_STEP}
+    else:
+        bytes_per_launch = {"byte_h/byte_v": 2.0, "plane_h/plane_v": 0.375}.get(
+            kname, BYTES_PER_CELL_STEP) * cells
+        achieved = bytes_per_launch / (launch_ms / 1e3) / 1e9
+        roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm_peak,
+                    "unit": "GB/s", "frac": achieved / hbm_peak,
+                    "traffic": traffic * cells if traffic else None,
+                    "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"}
+    roofline.update({"launch_ms": launch_ms, "temporal_depth": depth,
+                     "hbm_effective_GBps": effective,
+                     "hbm_effective_frac": effective / hbm_peak,
+                     "hbm_peak_GBps": hbm_peak})
     gpu_launches = K * launches_per_step
 
     # ---------------- end to end through the C ABI with host buffers -------
-    import numpy as np
     e2e = None
     if not args.no_e2e:
         host_in = torch.empty((M, N), dtype=torch.uint8, pin_memory=True)
@@ -280,6 +336,12 @@ def run_ours(args):
                "seconds": dt}
     sim.close()
 
+    ens = None
+    if not args.no_ensemble:
+        ens = _ensemble_bench(bml, torch, stream, args.ensemble_steps, seed_base=1 + 4096 * rank)
+        ens_max = max_over_ranks(ens["seconds"])
+        ens["value"] = world * ens["lattices"] * ens["steps"] / ens_max
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         threads = os.cpu_count() or 1
@@ -301,7 +363,7 @@ def run_ours(args):
                        "temporal_depth": block_k, "band_rows": band_rows,
                        "l2": "inputs larger than L2 (2 x 256 MB bitplanes)",
                        "parallelism": "replicas x%d" % world},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "ensemble": ens,
             "gpu_launches": gpu_launches, "clocks": clk,
         }
         print(json.dumps(line))
@@ -319,6 +381,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--kernel", default="auto")
     ap.add_argument("--block-k", type=int, default=0)
+    ap.add_argument("--band", type=int, default=None, help="band rows (with --kernel tblock)")
+    ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--ensemble-steps", type=int, default=1024)
     ap.add_argument("--M", type=int, default=M_ROWS)
     ap.add_argument("--N", type=int, default=N_COLS)
     ap.add_argument("--no-e2e", action="store_true")
