@@ -76,3 +76,18 @@ def parse_golden(path: str):
             else:
                 cur[2].append([sym[ch] for ch in line])
     return shape, [(b[0], b[1], np.array(b[2], dtype=np.uint8)) for b in blocks]
+
+
+def mlp_init_params(in_dim: int, seed: int, hidden: int = 128, n_hidden: int = 3,
+                    n_out: int = 2) -> np.ndarray:
+    """Initial surrogate-network parameters, flat float64 in the order W1, b1,
+    W2, b2, ..., each W row-major [out][in]: He-uniform weights
+    (bound sqrt(6 / fan_in)), zero biases, from numpy PCG64(seed)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    dims = [in_dim] + [hidden] * n_hidden + [n_out]
+    parts = []
+    for l in range(len(dims) - 1):
+        bound = np.sqrt(6.0 / dims[l])
+        parts.append(rng.uniform(-bound, bound, size=(dims[l + 1], dims[l])).ravel())
+        parts.append(np.zeros(dims[l + 1]))
+    return np.concatenate(parts)
