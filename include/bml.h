@@ -155,6 +155,47 @@ void bml_destroy(bml_sim *sim);
 const char *bml_last_error(void);
 
 /* ------------------------------------------------------------------------
+ * Surrogate network (no counterpart in the paper; it serves the sweep budget
+ * allocator): x (67 features) -> [Linear 128, ReLU] x 3 -> Linear 2 ->
+ * (v_hat = predicted steady-state velocity, z = jam logit).  BF16 weights
+ * and activations on the tcgen05 tensor cores, FP32 accumulation, FP32
+ * master weights and AdamW (beta1 0.9, beta2 0.999, eps 1e-8, decoupled
+ * weight decay).  Loss per sample (v_hat - v)^2 + BCE-with-logits(z, jam),
+ * mean over the batch.  Parameters are a flat float array of
+ * bml_mlp_num_params() entries: W1 (128 x 67), b1 (128), W2 (128 x 128), b2,
+ * W3 (128 x 128), b3, W4 (2 x 128), b4 (2), each W row-major [out][in].
+ * d_* pointers are device memory; the calls synchronise the stream.
+ * ------------------------------------------------------------------------ */
+typedef struct bml_mlp bml_mlp;
+
+int bml_mlp_create(void *stream, bml_mlp **out);
+int64_t bml_mlp_num_params(const bml_mlp *mlp);
+/* Upload parameters (host float array) and reset the AdamW state. */
+int bml_mlp_set_params(bml_mlp *mlp, const float *host_params);
+int bml_mlp_get_params(bml_mlp *mlp, float *host_params);
+/* d_x: batch x 67 floats; d_out: batch x 2 floats (v_hat, z). */
+int bml_mlp_forward(bml_mlp *mlp, const float *d_x, int64_t batch, float *d_out);
+/* One AdamW step on the mean loss of the batch (d_v, d_jam: batch floats;
+ * jam is 0 or 1).  *h_loss (host, may be NULL) receives the loss before the
+ * update. */
+int bml_mlp_train_step(bml_mlp *mlp, const float *d_x, const float *d_v, const float *d_jam,
+                       int64_t batch, float lr, float weight_decay, float *h_loss);
+/* Gradients of the mean loss (host array in the parameter layout), no
+ * update. */
+int bml_mlp_grads(bml_mlp *mlp, const float *d_x, const float *d_v, const float *d_jam,
+                  int64_t batch, float *host_grads, float *h_loss);
+/* One AdamW step with caller-supplied gradients (host array). */
+int bml_mlp_apply_grads(bml_mlp *mlp, const float *host_grads, float lr, float weight_decay);
+void bml_mlp_destroy(bml_mlp *mlp);
+
+/* The tensor-core GEMM the network runs on: C (M x N, fp32, row-major, ldc)
+ * = A (M x K) * B (N x K)^T, A and B bf16 row-major with K contiguous (lda,
+ * ldb elements; multiples of 8, 16-byte aligned).  16 <= N <= 128,
+ * N % 16 == 0, K % 16 == 0.  Device pointers; synchronises the stream. */
+int bml_gemm_bf16(const void *A, int64_t lda, const void *B, int64_t ldb, float *C, int64_t ldc,
+                  int64_t M, int64_t N, int64_t K, void *stream);
+
+/* ------------------------------------------------------------------------
  * Byte-per-cell step that allocates nothing (no counterpart in the paper).
  *
  * For callers that cannot allocate device memory when they step a lattice:

@@ -271,6 +271,83 @@ class Lattice:
         self.close()
 
 
+# ------------------------------------------------------ surrogate network --
+_lib_mlp_create = _sig("bml_mlp_create", [_vp, ctypes.POINTER(_vp)])
+_lib_mlp_n = _sig("bml_mlp_num_params", [_vp], _i64)
+_lib_mlp_set = _sig("bml_mlp_set_params", [_vp, _vp])
+_lib_mlp_get = _sig("bml_mlp_get_params", [_vp, _vp])
+_lib_mlp_fwd = _sig("bml_mlp_forward", [_vp, _vp, _i64, _vp])
+_lib_mlp_train = _sig("bml_mlp_train_step", [_vp, _vp, _vp, _vp, _i64, ctypes.c_float,
+                                              ctypes.c_float, _vp])
+_lib_mlp_grads = _sig("bml_mlp_grads", [_vp, _vp, _vp, _vp, _i64, _vp, _vp])
+_lib_mlp_apply = _sig("bml_mlp_apply_grads", [_vp, _vp, ctypes.c_float, ctypes.c_float])
+_lib_mlp_destroy = _sig("bml_mlp_destroy", [_vp], None)
+_lib_gemm = _sig("bml_gemm_bf16", [_vp, _i64, _vp, _i64, _vp, _i64, _i64, _i64, _i64, _vp])
+
+
+def bml_gemm_bf16(A: int, lda: int, B: int, ldb: int, C: int, ldc: int, M: int, N: int, K: int,
+                  stream=None) -> None:
+    _check(_lib_gemm(A, lda, B, ldb, C, ldc, M, N, K, _stream_handle(stream)))
+
+
+class MLP:
+    """Owning wrapper of a bml_mlp handle.  Tensors passed to forward /
+    train_step are torch CUDA float32 tensors (device memory)."""
+
+    def __init__(self, stream=None):
+        out = _vp()
+        _check(_lib_mlp_create(_stream_handle(stream), ctypes.byref(out)))
+        self._h = out.value
+        self.n = int(_lib_mlp_n(self._h))
+
+    def set_params(self, flat: np.ndarray) -> None:
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        assert a.size == self.n
+        _check(_lib_mlp_set(self._h, _host_ptr(a)))
+
+    def get_params(self) -> np.ndarray:
+        a = np.empty(self.n, dtype=np.float32)
+        _check(_lib_mlp_get(self._h, _host_ptr(a)))
+        return a
+
+    def forward(self, x):
+        import torch
+        x = x.contiguous()
+        out = torch.empty((x.shape[0], 2), dtype=torch.float32, device=x.device)
+        _check(_lib_mlp_fwd(self._h, x.data_ptr(), x.shape[0], out.data_ptr()))
+        return out
+
+    def train_step(self, x, v, jam, lr: float, weight_decay: float = 0.0) -> float:
+        loss = ctypes.c_float()
+        _check(_lib_mlp_train(self._h, x.contiguous().data_ptr(), v.contiguous().data_ptr(),
+                              jam.contiguous().data_ptr(), x.shape[0], lr, weight_decay,
+                              ctypes.byref(loss)))
+        return loss.value
+
+    def grads(self, x, v, jam):
+        g = np.empty(self.n, dtype=np.float32)
+        loss = ctypes.c_float()
+        _check(_lib_mlp_grads(self._h, x.contiguous().data_ptr(), v.contiguous().data_ptr(),
+                              jam.contiguous().data_ptr(), x.shape[0], _host_ptr(g),
+                              ctypes.byref(loss)))
+        return g, loss.value
+
+    def apply_grads(self, grads: np.ndarray, lr: float, weight_decay: float = 0.0) -> None:
+        a = np.ascontiguousarray(grads, dtype=np.float32)
+        _check(_lib_mlp_apply(self._h, _host_ptr(a), lr, weight_decay))
+
+    def close(self) -> None:
+        if self._h:
+            _lib_mlp_destroy(self._h)
+            self._h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 # --------------------------------------------------- allocation-free step --
 BML_NOALLOC_MAX_BYTES = 16 * 1024 * 1024
 

@@ -1,0 +1,739 @@
+// Surrogate network on the 5th-generation tensor cores (tcgen05, sm_103a).
+//
+// Network: x (67) -> [Linear 128, ReLU] x 3 -> Linear 2 -> (v_hat, jam logit).
+// BF16 weights and activations, FP32 accumulation (in tensor memory), FP32
+// master weights and AdamW state.  The input dimension is padded to 80 and
+// the output to 16 columns so every GEMM has K % 16 == 0 and N % 16 == 0;
+// the batch is padded to a multiple of 128 (padding rows carry zero output
+// gradients, so they add nothing to any weight gradient).
+//
+// GEMM kernel.  C[M x N] = A[M x K] * B[N x K]^T with A, B BF16 and K
+// contiguous (K-major).  One CTA of 128 threads per 128-row tile of C and
+// all N <= 128 columns.  Per K chunk of 64 the threads copy A and B into
+// shared memory in the canonical no-swizzle K-major layout of tcgen05 (8-row
+// x 16-byte core matrices, stored contiguously: core (r/8, k/8) at
+// ((r/8) * 8 + k/8) * 128 bytes, so adjacent core matrices are 128 bytes
+// apart along K and 1024 bytes apart along M/N), make the writes visible to
+// the async proxy, and one thread issues 4 tcgen05.mma (M=128, N, K=16) into
+// the FP32 accumulator in tensor memory, then tcgen05.commit to an mbarrier
+// that all threads wait on (bounded by %globaltimer; on expiry an error flag
+// is set).  The epilogue reads the accumulator with tcgen05.ld (warp w owns
+// TMEM lanes 32w..32w+31 = rows) and applies bias / ReLU / conversion.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include <cuda_bf16.h>
+
+#include "../../include/bml.h"
+#include "bml_internal.cuh"
+
+namespace bml {
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int kIn = 67, kInPad = 80, kHid = 128, kOut = 2, kOutPad = 16;
+constexpr int kKC = 64;                       // K per shared-memory chunk
+constexpr int kSmemBytes = 72 * 1024;         // caps residency at 3 CTAs per SM (TMEM)
+constexpr long long kWaitNs = 1000000000ll;   // 1 s bound on any wait
+
+enum EpiMode { EPI_F32 = 0, EPI_RELU_BF16 = 1, EPI_F32_T = 2 };
+
+struct Epi {
+  int mode;
+  const float *bias;  // per column, or nullptr
+  float *out_f32;     // EPI_F32: [M][ldo]; EPI_F32_T: [N][ldo] (transposed)
+  bf16 *out_bf16;     // EPI_RELU_BF16: [M][ldo]
+  bf16 *out_bf16_t;   // EPI_RELU_BF16: optional [N][ldt] transposed copy
+  int ldo, ldt;
+  int *err;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return (long long)t;
+}
+
+// Shared-memory matrix descriptor: no swizzle, K-major, LBO = byte distance
+// of adjacent core matrices along K, SBO = along M/N; version field 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const long long t0 = gtimer();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (gtimer() - t0 > kWaitNs) return false;
+  }
+}
+
+__global__ void __launch_bounds__(128, 1)
+    umma_gemm_kernel(const bf16 *__restrict__ A, int lda, const bf16 *__restrict__ B, int ldb,
+                     int M, int N, int K, Epi epi) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t *sA = smem;                    // 128 rows x 64 bf16 = 16 KB
+  uint8_t *sB = smem + 16384;            // N rows x 64 bf16 <= 16 KB
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 32768);
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + 32768 + 16);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.x * 128;
+  const uint32_t ncols = N <= 32 ? 32u : (N <= 64 ? 64u : 128u);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(smem_u32(tmem_slot)), "r"(ncols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t taddr = *tmem_slot;
+  const uint32_t idesc = idesc_bf16(128, N);
+  uint32_t phase = 0;
+  bool ok = true;
+
+  for (int k0 = 0; k0 < K && ok; k0 += kKC) {
+    // stage A (128 x 64) and B (N x 64) chunks into the core-matrix layout
+    for (int c = tid; c < 128 * 8; c += 128) {
+      const int r = c >> 3, kc = c & 7, gk = k0 + kc * 8;
+      uint4 v = make_uint4(0, 0, 0, 0);
+      if (m0 + r < M && gk < K) v = *reinterpret_cast<const uint4 *>(A + (size_t)(m0 + r) * lda + gk);
+      *reinterpret_cast<uint4 *>(sA + ((r >> 3) * 8 + kc) * 128 + (r & 7) * 16) = v;
+    }
+    for (int c = tid; c < N * 8; c += 128) {
+      const int r = c >> 3, kc = c & 7, gk = k0 + kc * 8;
+      uint4 v = make_uint4(0, 0, 0, 0);
+      if (gk < K) v = *reinterpret_cast<const uint4 *>(B + (size_t)r * ldb + gk);
+      *reinterpret_cast<uint4 *>(sB + ((r >> 3) * 8 + kc) * 128 + (r & 7) * 16) = v;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int ksteps = (K - k0) >= kKC ? kKC / 16 : (K - k0 + 15) / 16;
+      for (int kk = 0; kk < ksteps; ++kk) {
+        const uint64_t ad = smem_desc(smem_u32(sA + kk * 256), 128, 1024);
+        const uint64_t bd = smem_desc(smem_u32(sB + kk * 256), 128, 1024);
+        const uint32_t acc = (k0 > 0 || kk > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+            :: "r"(taddr), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                   :: "r"(smem_u32(bar)) : "memory");
+    }
+    ok = mbar_wait(smem_u32(bar), phase);
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+  }
+  if (!ok) {
+    if (tid == 0) atomicExch(epi.err, 1);
+  } else {
+    // epilogue: thread (warp w, lane l) owns row m0 + 32w + l
+    const int row = m0 + warp * 32 + lane;
+    for (int c0 = 0; c0 < N; c0 += 16) {
+      uint32_t r[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+          "%11, %12, %13, %14, %15}, [%16];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+            "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+            "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (row < M) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int col = c0 + j;
+          float v = __uint_as_float(r[j]) + (epi.bias ? epi.bias[col] : 0.f);
+          if (epi.mode == EPI_F32) {
+            epi.out_f32[(size_t)row * epi.ldo + col] = v;
+          } else if (epi.mode == EPI_F32_T) {
+            epi.out_f32[(size_t)col * epi.ldo + row] = v;
+          } else {
+            const bf16 h = __float2bfloat16_rn(v > 0.f ? v : 0.f);
+            epi.out_bf16[(size_t)row * epi.ldo + col] = h;
+            if (epi.out_bf16_t) epi.out_bf16_t[(size_t)col * epi.ldt + row] = h;
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
+                 :: "r"(taddr), "r"(ncols) : "memory");
+}
+
+// ---- elementwise kernels ----
+
+// x fp32 [B][67] -> X bf16 [Bp][80] and XT [80][Bp]; padding is zero
+__global__ void prep_x_kernel(const float *__restrict__ x, int B, int Bp, bf16 *X, bf16 *XT) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Bp * kInPad;
+       i += gridDim.x * blockDim.x) {
+    const int b = i / kInPad, c = i - b * kInPad;
+    const float v = (b < B && c < kIn) ? x[(size_t)b * kIn + c] : 0.f;
+    const bf16 h = __float2bfloat16_rn(v);
+    X[i] = h;
+    if (XT) XT[(size_t)c * Bp + b] = h;
+  }
+}
+
+// outputs fp32 [Bp][16] -> loss (sum / B), dOut bf16 [Bp][16] and its
+// transpose [16][Bp], and the output-bias gradient (atomics on db4[0..1]).
+__global__ void loss_grad_kernel(const float *__restrict__ out, const float *__restrict__ v,
+                                 const float *__restrict__ jam, int B, int Bp, bf16 *G,
+                                 bf16 *GT, float *loss, float *db4) {
+  float l_sum = 0.f, g0 = 0.f, g1 = 0.f;
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < Bp; b += gridDim.x * blockDim.x) {
+    float d0 = 0.f, d1 = 0.f;
+    if (b < B) {
+      const float yv = out[(size_t)b * kOutPad + 0], z = out[(size_t)b * kOutPad + 1];
+      const float e = expf(-fabsf(z));
+      const float sig = z >= 0.f ? 1.f / (1.f + e) : e / (1.f + e);
+      const float dv = yv - v[b];
+      l_sum += dv * dv + fmaxf(z, 0.f) - z * jam[b] + log1pf(e);
+      d0 = 2.f * dv / (float)B;
+      d1 = (sig - jam[b]) / (float)B;
+      g0 += d0;
+      g1 += d1;
+    }
+    for (int c = 0; c < kOutPad; ++c) {
+      const bf16 h = __float2bfloat16_rn(c == 0 ? d0 : (c == 1 ? d1 : 0.f));
+      G[(size_t)b * kOutPad + c] = h;
+      GT[(size_t)c * Bp + b] = h;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    l_sum += __shfl_down_sync(0xffffffffu, l_sum, o);
+    g0 += __shfl_down_sync(0xffffffffu, g0, o);
+    g1 += __shfl_down_sync(0xffffffffu, g1, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(loss, l_sum / (float)B);
+    atomicAdd(db4 + 0, g0);
+    atomicAdd(db4 + 1, g1);
+  }
+}
+
+// dZ = dH * (H > 0): bf16 [Bp][128] and transpose [128][Bp]; bias gradient
+// = column sums (atomics), over the first B rows.
+__global__ void relu_bwd_kernel(const float *__restrict__ dH, const bf16 *__restrict__ H, int B,
+                                int Bp, bf16 *dZ, bf16 *dZT, float *db) {
+  const int col = threadIdx.x;  // 128 threads = 128 columns
+  float s = 0.f;
+  for (int b = blockIdx.x; b < Bp; b += gridDim.x) {
+    const size_t i = (size_t)b * kHid + col;
+    const float g = (b < B && __bfloat162float(H[i]) > 0.f) ? dH[i] : 0.f;
+    s += g;
+    const bf16 h = __float2bfloat16_rn(g);
+    dZ[i] = h;
+    dZT[(size_t)col * Bp + b] = h;
+  }
+  atomicAdd(db + col, s);
+}
+
+// column sums of a bf16-free fp32 gradient are not needed for layer 4 (done
+// in loss_grad_kernel).
+
+// AdamW over the flat master parameters (oracle layout).  The gradient of
+// entry i is read from the layer's padded gradient buffer; the updated
+// weight is also written as BF16 into the padded forward copy and the
+// transposed backward copy.
+struct Layer {
+  int out, in;        // true sizes
+  int in_pad;         // padded row length of the forward copy
+  int out_pad;        // padded rows of the forward copy
+  long long w_off, b_off;   // offsets of W and b in the flat vector
+  const float *gW;    // gradient [out_pad][in_pad]
+  const float *gb;    // gradient [out]
+  bf16 *W, *WT;       // [out_pad][in_pad], [in_pad][out_pad] (WT may be null)
+};
+
+struct Layers {
+  Layer l[4];
+};
+
+__global__ void adamw_kernel(float *w, float *m, float *v, Layers Ls, long long n, float lr,
+                             float wd, float b1, float b2, float eps, float c1, float c2,
+                             const float *ext_grad) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    // locate the layer and whether i is a weight or a bias
+    int L = 3;
+    while (L > 0 && i < Ls.l[L].w_off) --L;
+    const Layer &ly = Ls.l[L];
+    float g;
+    int r = -1, c = -1;
+    if (i < ly.b_off) {
+      const long long j = i - ly.w_off;
+      r = (int)(j / ly.in);
+      c = (int)(j - (long long)r * ly.in);
+      g = ext_grad ? ext_grad[i] : ly.gW[(size_t)r * ly.in_pad + c];
+    } else {
+      g = ext_grad ? ext_grad[i] : ly.gb[i - ly.b_off];
+    }
+    const float mi = b1 * m[i] + (1.f - b1) * g;
+    const float vi = b2 * v[i] + (1.f - b2) * g * g;
+    m[i] = mi;
+    v[i] = vi;
+    const float mh = mi / c1, vh = vi / c2;
+    const float wi = w[i] - lr * (mh / (sqrtf(vh) + eps) + wd * w[i]);
+    w[i] = wi;
+    if (r >= 0) {
+      const bf16 h = __float2bfloat16_rn(wi);
+      ly.W[(size_t)r * ly.in_pad + c] = h;
+      if (ly.WT) ly.WT[(size_t)c * ly.out_pad + r] = h;
+    }
+  }
+}
+
+// master fp32 -> bf16 forward / transposed copies (after set_params)
+__global__ void cast_params_kernel(const float *w, Layers Ls) {
+  for (int L = 0; L < 4; ++L) {
+    const Layer &ly = Ls.l[L];
+    const int n = ly.out * ly.in;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+      const int r = j / ly.in, c = j - r * ly.in;
+      const bf16 h = __float2bfloat16_rn(w[ly.w_off + j]);
+      ly.W[(size_t)r * ly.in_pad + c] = h;
+      if (ly.WT) ly.WT[(size_t)c * ly.out_pad + r] = h;
+    }
+  }
+}
+
+}  // namespace
+}  // namespace bml
+
+// =================================================================== C ABI ==
+using namespace bml;
+
+namespace {
+
+int mfail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  set_last_error(buf);
+  return code;
+}
+
+#define MCUDA(expr)                                                                         \
+  do {                                                                                      \
+    cudaError_t e_ = (expr);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      return mfail(BML_ECUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__,   \
+                   __LINE__);                                                               \
+  } while (0)
+
+bool g_attr_done = false;
+
+cudaError_t launch_gemm(const bf16 *A, int lda, const bf16 *B, int ldb, int M, int N, int K,
+                        const Epi &epi, cudaStream_t st) {
+  if (!g_attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(umma_gemm_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    if (e != cudaSuccess) return e;
+    g_attr_done = true;
+  }
+  if (N < 16 || N > 128 || N % 16 || K % 16 || lda % 8 || ldb % 8) return cudaErrorInvalidValue;
+  umma_gemm_kernel<<<(M + 127) / 128, 128, kSmemBytes, st>>>(A, lda, B, ldb, M, N, K, epi);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+struct bml_mlp {
+  cudaStream_t st = nullptr;
+  long long n = 0;  // parameters
+  float *w = nullptr, *m = nullptr, *v = nullptr;  // master, AdamW moments
+  long long t = 0;
+  // bf16 weights: forward [out_pad][in_pad], transposed [in_pad][out_pad]
+  bf16 *W[4] = {}, *WT[4] = {};
+  float *gW[4] = {}, *gb[4] = {};
+  float *b[4] = {};  // views into w (biases)
+  Layers layers;
+  // activation buffers for a padded batch of up to cap rows
+  int cap = 0;
+  bf16 *X = nullptr, *XT = nullptr, *H[3] = {}, *HT[3] = {}, *G = nullptr, *GT = nullptr;
+  bf16 *dZ = nullptr, *dZT = nullptr;
+  float *out = nullptr, *dH = nullptr, *loss = nullptr;
+  float *bias4 = nullptr;  // padded output bias [16]
+  int *err = nullptr;
+};
+
+namespace {
+
+const int kOutDims[4] = {kHid, kHid, kHid, kOut};
+const int kInDims[4] = {kIn, kHid, kHid, kHid};
+const int kInPads[4] = {kInPad, kHid, kHid, kHid};
+const int kOutPads[4] = {kHid, kHid, kHid, kOutPad};
+
+void mlp_free_batch(bml_mlp *p) {
+  cudaFree(p->X);
+  cudaFree(p->XT);
+  for (int i = 0; i < 3; ++i) {
+    cudaFree(p->H[i]);
+    cudaFree(p->HT[i]);
+    p->H[i] = p->HT[i] = nullptr;
+  }
+  cudaFree(p->G);
+  cudaFree(p->GT);
+  cudaFree(p->dZ);
+  cudaFree(p->dZT);
+  cudaFree(p->out);
+  cudaFree(p->dH);
+  p->X = p->XT = p->G = p->GT = p->dZ = p->dZT = nullptr;
+  p->out = p->dH = nullptr;
+  p->cap = 0;
+}
+
+int ensure_batch(bml_mlp *p, int Bp) {
+  if (Bp <= p->cap) return BML_OK;
+  mlp_free_batch(p);
+  MCUDA(cudaMalloc(&p->X, (size_t)Bp * kInPad * 2));
+  MCUDA(cudaMalloc(&p->XT, (size_t)Bp * kInPad * 2));
+  for (int i = 0; i < 3; ++i) {
+    MCUDA(cudaMalloc(&p->H[i], (size_t)Bp * kHid * 2));
+    MCUDA(cudaMalloc(&p->HT[i], (size_t)Bp * kHid * 2));
+  }
+  MCUDA(cudaMalloc(&p->G, (size_t)Bp * kOutPad * 2));
+  MCUDA(cudaMalloc(&p->GT, (size_t)Bp * kOutPad * 2));
+  MCUDA(cudaMalloc(&p->dZ, (size_t)Bp * kHid * 2));
+  MCUDA(cudaMalloc(&p->dZT, (size_t)Bp * kHid * 2));
+  MCUDA(cudaMalloc(&p->out, (size_t)Bp * kOutPad * 4));
+  MCUDA(cudaMalloc(&p->dH, (size_t)Bp * kHid * 4));
+  p->cap = Bp;
+  return BML_OK;
+}
+
+int check_mlp_err(bml_mlp *p) {
+  int h = 0;
+  MCUDA(cudaMemcpyAsync(&h, p->err, sizeof h, cudaMemcpyDeviceToHost, p->st));
+  MCUDA(cudaStreamSynchronize(p->st));
+  if (h) return mfail(BML_ETIMEOUT, "a tensor-core completion wait timed out");
+  return BML_OK;
+}
+
+// Forward pass of a padded batch Bp (X already staged).  keep_t: also write
+// the transposed activations needed by the backward pass.
+int forward_staged(bml_mlp *p, int Bp, bool keep_t) {
+  const bf16 *in = p->X;
+  int in_ld = kInPad;
+  for (int l = 0; l < 3; ++l) {
+    Epi e{};
+    e.mode = EPI_RELU_BF16;
+    e.bias = p->b[l];
+    e.out_bf16 = p->H[l];
+    e.out_bf16_t = keep_t ? p->HT[l] : nullptr;
+    e.ldo = kHid;
+    e.ldt = Bp;
+    e.err = p->err;
+    MCUDA(launch_gemm(in, in_ld, p->W[l], kInPads[l], Bp, kHid, in_ld, e, p->st));
+    in = p->H[l];
+    in_ld = kHid;
+  }
+  Epi e{};
+  e.mode = EPI_F32;
+  e.bias = p->bias4;
+  e.out_f32 = p->out;
+  e.ldo = kOutPad;
+  e.err = p->err;
+  MCUDA(launch_gemm(p->H[2], kHid, p->W[3], kHid, Bp, kOutPad, kHid, e, p->st));
+  return BML_OK;
+}
+
+}  // namespace
+
+extern "C" int bml_mlp_create(void *stream, bml_mlp **out) {
+  if (!out) return mfail(BML_EINVAL, "out is NULL");
+  bml_mlp *p = new (std::nothrow) bml_mlp;
+  if (!p) return mfail(BML_ENOMEM, "host allocation failed");
+  p->st = (cudaStream_t)stream;
+  long long off = 0;
+  for (int l = 0; l < 4; ++l) {
+    Layer &ly = p->layers.l[l];
+    ly.out = kOutDims[l];
+    ly.in = kInDims[l];
+    ly.in_pad = kInPads[l];
+    ly.out_pad = kOutPads[l];
+    ly.w_off = off;
+    off += (long long)ly.out * ly.in;
+    ly.b_off = off;
+    off += ly.out;
+  }
+  p->n = off;
+  int rc = BML_OK;
+  cudaError_t e = cudaSuccess;
+#define MTRY(expr)      \
+  if (e == cudaSuccess) e = (expr)
+  MTRY(cudaMalloc(&p->w, p->n * 4));
+  MTRY(cudaMalloc(&p->m, p->n * 4));
+  MTRY(cudaMalloc(&p->v, p->n * 4));
+  MTRY(cudaMalloc(&p->err, 256));
+  MTRY(cudaMalloc(&p->loss, 256));
+  MTRY(cudaMalloc(&p->bias4, kOutPad * 4));
+  for (int l = 0; l < 4; ++l) {
+    Layer &ly = p->layers.l[l];
+    MTRY(cudaMalloc(&p->W[l], (size_t)ly.out_pad * ly.in_pad * 2));
+    MTRY(cudaMalloc(&p->WT[l], (size_t)ly.out_pad * ly.in_pad * 2));
+    MTRY(cudaMalloc(&p->gW[l], (size_t)ly.out_pad * ly.in_pad * 4));
+    MTRY(cudaMalloc(&p->gb[l], (size_t)kOutPad * 8 * 4 + ly.out * 4));
+    if (e == cudaSuccess) {
+      e = cudaMemsetAsync(p->W[l], 0, (size_t)ly.out_pad * ly.in_pad * 2, p->st);
+      MTRY(cudaMemsetAsync(p->WT[l], 0, (size_t)ly.out_pad * ly.in_pad * 2, p->st));
+    }
+    ly.gW = p->gW[l];
+    ly.gb = p->gb[l];
+    ly.W = p->W[l];
+    ly.WT = p->WT[l];
+  }
+  MTRY(cudaMemsetAsync(p->w, 0, p->n * 4, p->st));
+  MTRY(cudaMemsetAsync(p->m, 0, p->n * 4, p->st));
+  MTRY(cudaMemsetAsync(p->v, 0, p->n * 4, p->st));
+  MTRY(cudaMemsetAsync(p->err, 0, 256, p->st));
+  MTRY(cudaMemsetAsync(p->bias4, 0, kOutPad * 4, p->st));
+  MTRY(cudaStreamSynchronize(p->st));
+#undef MTRY
+  if (e != cudaSuccess) {
+    rc = mfail(e == cudaErrorMemoryAllocation ? BML_ENOMEM : BML_ECUDA, "mlp create: %s",
+               cudaGetErrorString(e));
+    bml_mlp_destroy(p);
+    return rc;
+  }
+  for (int l = 0; l < 3; ++l) p->b[l] = p->w + p->layers.l[l].b_off;
+  *out = p;
+  return BML_OK;
+}
+
+extern "C" void bml_mlp_destroy(bml_mlp *p) {
+  if (!p) return;
+  cudaStreamSynchronize(p->st);
+  mlp_free_batch(p);
+  cudaFree(p->w);
+  cudaFree(p->m);
+  cudaFree(p->v);
+  cudaFree(p->err);
+  cudaFree(p->loss);
+  cudaFree(p->bias4);
+  for (int l = 0; l < 4; ++l) {
+    cudaFree(p->W[l]);
+    cudaFree(p->WT[l]);
+    cudaFree(p->gW[l]);
+    cudaFree(p->gb[l]);
+  }
+  delete p;
+}
+
+extern "C" int64_t bml_mlp_num_params(const bml_mlp *p) { return p ? p->n : -1; }
+
+extern "C" int bml_mlp_set_params(bml_mlp *p, const float *host) {
+  if (!p || !host) return mfail(BML_EINVAL, "NULL argument");
+  MCUDA(cudaMemcpyAsync(p->w, host, p->n * 4, cudaMemcpyHostToDevice, p->st));
+  MCUDA(cudaMemsetAsync(p->m, 0, p->n * 4, p->st));
+  MCUDA(cudaMemsetAsync(p->v, 0, p->n * 4, p->st));
+  MCUDA(cudaMemcpyAsync(p->bias4, p->w + p->layers.l[3].b_off, kOut * 4,
+                        cudaMemcpyDeviceToDevice, p->st));
+  p->t = 0;
+  cast_params_kernel<<<64, 256, 0, p->st>>>(p->w, p->layers);
+  MCUDA(cudaGetLastError());
+  MCUDA(cudaStreamSynchronize(p->st));
+  return BML_OK;
+}
+
+extern "C" int bml_mlp_get_params(bml_mlp *p, float *host) {
+  if (!p || !host) return mfail(BML_EINVAL, "NULL argument");
+  MCUDA(cudaMemcpyAsync(host, p->w, p->n * 4, cudaMemcpyDeviceToHost, p->st));
+  MCUDA(cudaStreamSynchronize(p->st));
+  return BML_OK;
+}
+
+extern "C" int bml_mlp_forward(bml_mlp *p, const float *d_x, int64_t batch, float *d_out) {
+  if (!p || !d_x || !d_out) return mfail(BML_EINVAL, "NULL argument");
+  if (batch < 1 || batch > (1 << 24)) return mfail(BML_EINVAL, "batch must be in [1, 2^24]");
+  const int B = (int)batch, Bp = (B + 127) / 128 * 128;
+  int rc = ensure_batch(p, Bp);
+  if (rc) return rc;
+  prep_x_kernel<<<256, 256, 0, p->st>>>(d_x, B, Bp, p->X, nullptr);
+  MCUDA(cudaGetLastError());
+  if ((rc = forward_staged(p, Bp, false))) return rc;
+  MCUDA(cudaMemcpy2DAsync(d_out, kOut * 4, p->out, kOutPad * 4, kOut * 4, B,
+                          cudaMemcpyDeviceToDevice, p->st));
+  return check_mlp_err(p);
+}
+
+// Gradients of the mean loss on a batch into gW / gb (no update).
+static int compute_grads(bml_mlp *p, const float *d_x, const float *d_v, const float *d_jam,
+                         int B, float *h_loss) {
+  const int Bp = (B + 127) / 128 * 128;
+  int rc = ensure_batch(p, Bp);
+  if (rc) return rc;
+  MCUDA(cudaMemsetAsync(p->loss, 0, 4, p->st));
+  for (int l = 0; l < 4; ++l)
+    MCUDA(cudaMemsetAsync(p->gb[l], 0, p->layers.l[l].out * 4, p->st));
+  prep_x_kernel<<<256, 256, 0, p->st>>>(d_x, B, Bp, p->X, p->XT);
+  MCUDA(cudaGetLastError());
+  if ((rc = forward_staged(p, Bp, true))) return rc;
+  loss_grad_kernel<<<(Bp + 255) / 256, 256, 0, p->st>>>(p->out, d_v, d_jam, B, Bp, p->G, p->GT,
+                                                        p->loss, p->gb[3]);
+  MCUDA(cudaGetLastError());
+  // layer 4: dW4^T [128][16] = H3^T (128 x Bp) . G^T (16 x Bp)^T, stored transposed
+  {
+    Epi e{};
+    e.mode = EPI_F32_T;
+    e.out_f32 = p->gW[3];
+    e.ldo = kHid;
+    e.err = p->err;
+    MCUDA(launch_gemm(p->HT[2], Bp, p->GT, Bp, kHid, kOutPad, Bp, e, p->st));
+    Epi d{};
+    d.mode = EPI_F32;
+    d.out_f32 = p->dH;
+    d.ldo = kHid;
+    d.err = p->err;
+    MCUDA(launch_gemm(p->G, kOutPad, p->WT[3], kOutPad, Bp, kHid, kOutPad, d, p->st));
+  }
+  for (int l = 2; l >= 0; --l) {
+    relu_bwd_kernel<<<256, kHid, 0, p->st>>>(p->dH, p->H[l], B, Bp, p->dZ, p->dZT, p->gb[l]);
+    MCUDA(cudaGetLastError());
+    const bf16 *prevT = l > 0 ? p->HT[l - 1] : p->XT;
+    const int in_pad = kInPads[l];
+    Epi e{};
+    e.mode = EPI_F32;
+    e.out_f32 = p->gW[l];
+    e.ldo = in_pad;
+    e.err = p->err;
+    MCUDA(launch_gemm(p->dZT, Bp, prevT, Bp, kHid, in_pad, Bp, e, p->st));
+    if (l > 0) {
+      Epi d{};
+      d.mode = EPI_F32;
+      d.out_f32 = p->dH;
+      d.ldo = kHid;
+      d.err = p->err;
+      MCUDA(launch_gemm(p->dZ, kHid, p->WT[l], kHid, Bp, kHid, kHid, d, p->st));
+    }
+  }
+  if (h_loss) {
+    MCUDA(cudaMemcpyAsync(h_loss, p->loss, 4, cudaMemcpyDeviceToHost, p->st));
+  }
+  return check_mlp_err(p);
+}
+
+static int adamw(bml_mlp *p, float lr, float wd, const float *d_ext) {
+  p->t += 1;
+  const double b1 = 0.9, b2 = 0.999;
+  const float c1 = (float)(1.0 - std::pow(b1, (double)p->t));
+  const float c2 = (float)(1.0 - std::pow(b2, (double)p->t));
+  adamw_kernel<<<128, 256, 0, p->st>>>(p->w, p->m, p->v, p->layers, p->n, lr, wd, (float)b1,
+                                       (float)b2, 1e-8f, c1, c2, d_ext);
+  MCUDA(cudaGetLastError());
+  MCUDA(cudaMemcpyAsync(p->bias4, p->w + p->layers.l[3].b_off, kOut * 4,
+                        cudaMemcpyDeviceToDevice, p->st));
+  return BML_OK;
+}
+
+extern "C" int bml_mlp_train_step(bml_mlp *p, const float *d_x, const float *d_v,
+                                  const float *d_jam, int64_t batch, float lr,
+                                  float weight_decay, float *h_loss) {
+  if (!p || !d_x || !d_v || !d_jam) return mfail(BML_EINVAL, "NULL argument");
+  if (batch < 1 || batch > (1 << 24)) return mfail(BML_EINVAL, "batch must be in [1, 2^24]");
+  if (!(lr >= 0.f) || !(weight_decay >= 0.f)) return mfail(BML_EINVAL, "bad lr / weight_decay");
+  int rc = compute_grads(p, d_x, d_v, d_jam, (int)batch, h_loss);
+  if (rc) return rc;
+  if ((rc = adamw(p, lr, weight_decay, nullptr))) return rc;
+  MCUDA(cudaStreamSynchronize(p->st));
+  return BML_OK;
+}
+
+extern "C" int bml_mlp_grads(bml_mlp *p, const float *d_x, const float *d_v, const float *d_jam,
+                             int64_t batch, float *host_grads, float *h_loss) {
+  if (!p || !d_x || !d_v || !d_jam || !host_grads) return mfail(BML_EINVAL, "NULL argument");
+  if (batch < 1 || batch > (1 << 24)) return mfail(BML_EINVAL, "batch must be in [1, 2^24]");
+  int rc = compute_grads(p, d_x, d_v, d_jam, (int)batch, h_loss);
+  if (rc) return rc;
+  // gather the padded gradient buffers into the flat parameter layout
+  for (int l = 0; l < 4; ++l) {
+    const Layer &ly = p->layers.l[l];
+    MCUDA(cudaMemcpy2DAsync(host_grads + ly.w_off, (size_t)ly.in * 4, p->gW[l],
+                            (size_t)ly.in_pad * 4, (size_t)ly.in * 4, ly.out,
+                            cudaMemcpyDeviceToHost, p->st));
+    MCUDA(cudaMemcpyAsync(host_grads + ly.b_off, p->gb[l], (size_t)ly.out * 4,
+                          cudaMemcpyDeviceToHost, p->st));
+  }
+  MCUDA(cudaStreamSynchronize(p->st));
+  return BML_OK;
+}
+
+extern "C" int bml_mlp_apply_grads(bml_mlp *p, const float *host_grads, float lr,
+                                   float weight_decay) {
+  if (!p || !host_grads) return mfail(BML_EINVAL, "NULL argument");
+  float *d = nullptr;
+  MCUDA(cudaMalloc(&d, p->n * 4));
+  cudaError_t e = cudaMemcpyAsync(d, host_grads, p->n * 4, cudaMemcpyHostToDevice, p->st);
+  int rc = BML_OK;
+  if (e == cudaSuccess) rc = adamw(p, lr, weight_decay, d);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->st);
+  cudaFree(d);
+  if (e != cudaSuccess) return mfail(BML_ECUDA, "apply grads: %s", cudaGetErrorString(e));
+  return rc;
+}
+
+extern "C" int bml_gemm_bf16(const void *A, int64_t lda, const void *B, int64_t ldb, float *C,
+                             int64_t ldc, int64_t M, int64_t N, int64_t K, void *stream) {
+  if (!A || !B || !C) return mfail(BML_EINVAL, "NULL argument");
+  if (M < 1 || M > (1 << 24) || N < 16 || N > 128 || N % 16 || K < 16 || K % 16 ||
+      K > (1 << 24) || lda < K || ldb < K || ldc < N || lda % 8 || ldb % 8)
+    return mfail(BML_EINVAL, "bml_gemm_bf16: need 16 <= N <= 128, N % 16 == 0, K % 16 == 0, "
+                 "lda, ldb >= K and multiples of 8, ldc >= N");
+  if ((uintptr_t)A % 16 || (uintptr_t)B % 16) return mfail(BML_EINVAL, "A, B not 16-byte aligned");
+  int *err = nullptr;
+  MCUDA(cudaMalloc(&err, 4));
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemsetAsync(err, 0, 4, st);
+  Epi ep{};
+  ep.mode = EPI_F32;
+  ep.out_f32 = C;
+  ep.ldo = (int)ldc;
+  ep.err = err;
+  if (e == cudaSuccess)
+    e = launch_gemm((const bf16 *)A, (int)lda, (const bf16 *)B, (int)ldb, (int)M, (int)N, (int)K,
+                    ep, st);
+  int h = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, err, 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(err);
+  if (e != cudaSuccess) return mfail(BML_ECUDA, "gemm: %s", cudaGetErrorString(e));
+  if (h) return mfail(BML_ETIMEOUT, "a tensor-core completion wait timed out");
+  return BML_OK;
+}

@@ -1,0 +1,116 @@
+"""GPU parity of the surrogate network (tcgen05 tensor-core GEMMs, BF16
+operands, FP32 accumulation) against the fp64 oracle on the same
+BF16-rounded weights and inputs."""
+import numpy as np
+import pytest
+
+from oracle import mlp as ref
+from paper_1804_07981_b300.inputs import mlp_init_params
+
+pytestmark = pytest.mark.gpu
+
+IN = 67
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 128, 128), (1, 16, 16), (200, 48, 80), (384, 128, 640),
+                                   (77, 16, 1024), (128, 80, 256)])
+def test_gemm_matches_matmul(lib, M, N, K):
+    import torch
+    g = torch.Generator().manual_seed(M * 1000 + N + K)
+    A = torch.randn(M, K, generator=g).to(torch.bfloat16).cuda()
+    B = torch.randn(N, K, generator=g).to(torch.bfloat16).cuda()
+    C = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
+    lib.bml_gemm_bf16(A.data_ptr(), K, B.data_ptr(), K, C.data_ptr(), N, M, N, K)
+    want = A.double().cpu() @ B.double().cpu().T
+    # fp32 accumulation of exact bf16 products
+    assert torch.allclose(C.double().cpu(), want, rtol=1e-4, atol=1e-3 * np.sqrt(K))
+
+
+def _batch(B, seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    x = rng.uniform(0, 1, size=(B, IN))
+    v = rng.uniform(0, 1, size=B)
+    jam = (rng.uniform(size=B) < 0.4).astype(np.float64)
+    return x, v, jam
+
+
+def _rounded_params(seed):
+    flat = mlp_init_params(IN, seed)
+    rng = np.random.Generator(np.random.PCG64(seed + 1))
+    ps = ref.unflatten(flat, IN)
+    for p in ps[1::2]:
+        p += rng.normal(0, 0.05, size=p.shape)
+    return ref.bf16_round(ref.flatten(ps))
+
+
+@pytest.mark.parametrize("B", [1, 100, 128, 300])
+def test_forward_matches_oracle(lib, B):
+    import torch
+    flat = _rounded_params(11)
+    x, v, jam = _batch(B, 12)
+    xr = ref.bf16_round(x)
+    net = lib.MLP()
+    net.set_params(flat.astype(np.float32))
+    out = net.forward(torch.tensor(xr, dtype=torch.float32, device="cuda")).cpu().numpy()
+    want, _ = ref.forward(ref.unflatten(flat, IN), xr)
+    err = np.abs(out - want).max() / np.abs(want).max()
+    assert err <= 1e-2, err
+    net.close()
+
+
+@pytest.mark.parametrize("B", [64, 256, 1000])
+def test_gradients_match_oracle(lib, B):
+    import torch
+    flat = _rounded_params(21)
+    x, v, jam = _batch(B, 22)
+    xr = ref.bf16_round(x)
+    net = lib.MLP()
+    net.set_params(flat.astype(np.float32))
+    t = lambda a: torch.tensor(a, dtype=torch.float32, device="cuda")
+    g, loss = net.grads(t(xr), t(v), t(jam))
+    ps = ref.unflatten(flat, IN)
+    want, want_loss = ref.backward(ps, xr, v, jam)
+    assert abs(loss - want_loss) <= 1e-2 * abs(want_loss)
+    gs = ref.unflatten(g.astype(np.float64), IN)
+    for i, (a, w) in enumerate(zip(gs, want)):
+        a, w = a.ravel(), w.ravel()
+        cos = a @ w / (np.linalg.norm(a) * np.linalg.norm(w) + 1e-30)
+        rel = np.linalg.norm(a - w) / (np.linalg.norm(w) + 1e-30)
+        assert cos >= 0.999 and rel <= 2e-2, (i, cos, rel)
+    net.close()
+
+
+def test_adamw_matches_oracle(lib):
+    flat = _rounded_params(31)
+    rng = np.random.Generator(np.random.PCG64(32))
+    net = lib.MLP()
+    net.set_params(flat.astype(np.float32))
+    opt = ref.AdamW(flat.size)
+    w = flat.astype(np.float32).astype(np.float64)
+    for step in range(3):
+        g = rng.normal(0, 1e-2, size=flat.size).astype(np.float32)
+        net.apply_grads(g, lr=1e-3, weight_decay=0.01)
+        w = opt.step(w, g.astype(np.float64), lr=1e-3, wd=0.01)
+    got = net.get_params().astype(np.float64)
+    assert np.max(np.abs(got - w)) <= 1e-6
+    net.close()
+
+
+def test_training_reduces_loss(lib):
+    """A few hundred AdamW steps on a smooth synthetic target drive the loss
+    well below its starting value (the update path works end to end)."""
+    import torch
+    rng = np.random.Generator(np.random.PCG64(41))
+    B = 512
+    x = rng.uniform(0, 1, size=(B, IN))
+    v = 0.5 * x[:, 0] + 0.3 * x[:, 5] ** 2
+    jam = (x[:, 1] + x[:, 2] > 1.0).astype(np.float64)
+    t = lambda a: torch.tensor(a, dtype=torch.float32, device="cuda")
+    net = lib.MLP()
+    net.set_params(mlp_init_params(IN, 42).astype(np.float32))
+    X, V, J = t(x), t(v), t(jam)
+    first = net.train_step(X, V, J, lr=1e-3)
+    for _ in range(300):
+        last = net.train_step(X, V, J, lr=1e-3)
+    assert last < 0.25 * first, (first, last)
+    net.close()
