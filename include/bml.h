@@ -295,6 +295,22 @@ int bml_ensemble_write_lattices(bml_ens *ens, const uint8_t *in);
 
 int64_t bml_ensemble_steps_done(const bml_ens *ens);
 
+/* Number of cars of every lattice (host array of count int64; conserved by
+ * the dynamics, recounted by bml_ensemble_write_lattices). */
+int bml_ensemble_car_counts(bml_ens *ens, int64_t *out);
+
+/* Surrogate inputs from the traces: d_out (device, count x (3 + points)
+ * floats, lattice-major) = [cars / (M N), M / 2048, N / 2048, mean velocity
+ * of each of `points` equal windows of steps first+1 .. first+n], velocity =
+ * moved cars / cars (0 without cars).  n must be a multiple of points and the
+ * steps already taken.  Synchronises. */
+int bml_ensemble_features(bml_ens *ens, int64_t first, int64_t n, int points, float *d_out);
+
+/* Labels over the steps taken so far: d_v[l] = mean velocity over the last
+ * `window` steps, d_jam[l] = 1 if some step moved no car (the lattice is at
+ * a fixed point), else 0 (device arrays of count floats).  Synchronises. */
+int bml_ensemble_labels(bml_ens *ens, int64_t window, float *d_v, float *d_jam);
+
 /* Temporal depth, band height and whether graph replay is in use. */
 int bml_ensemble_get_config(const bml_ens *ens, int *block_k, int64_t *band_rows, int *graphs);
 

@@ -382,6 +382,9 @@ _lib_ens_steps = _sig("bml_ensemble_steps_done", [_vp], _i64)
 _lib_ens_cfg = _sig("bml_ensemble_get_config", [_vp, ctypes.POINTER(_int), _i64p,
                                                  ctypes.POINTER(_int)])
 _lib_ens_sync = _sig("bml_ensemble_synchronize", [_vp])
+_lib_ens_cars = _sig("bml_ensemble_car_counts", [_vp, _vp])
+_lib_ens_feat = _sig("bml_ensemble_features", [_vp, _i64, _i64, _int, _vp])
+_lib_ens_lab = _sig("bml_ensemble_labels", [_vp, _i64, _vp, _vp])
 _lib_ens_destroy = _sig("bml_ensemble_destroy", [_vp], None)
 
 
@@ -521,6 +524,26 @@ class Ensemble:
     @property
     def config(self):
         return bml_ensemble_get_config(self._h)
+
+    def car_counts(self) -> np.ndarray:
+        out = np.zeros(self.count, dtype=np.int64)
+        _check(_lib_ens_cars(self._h, _host_ptr(out)))
+        return out
+
+    def features(self, first: int, n: int, points: int):
+        """Device tensor (count, 3 + points) float32 of surrogate inputs."""
+        import torch
+        out = torch.empty((self.count, 3 + points), dtype=torch.float32, device="cuda")
+        _check(_lib_ens_feat(self._h, first, n, points, out.data_ptr()))
+        return out
+
+    def labels(self, window: int):
+        """Device tensors (v, jam), each (count,) float32."""
+        import torch
+        v = torch.empty(self.count, dtype=torch.float32, device="cuda")
+        jam = torch.empty(self.count, dtype=torch.float32, device="cuda")
+        _check(_lib_ens_lab(self._h, window, v.data_ptr(), jam.data_ptr()))
+        return v, jam
 
     def synchronize(self) -> None:
         bml_ensemble_synchronize(self._h)

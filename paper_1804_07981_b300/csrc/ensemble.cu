@@ -408,6 +408,71 @@ __global__ void ens_buf_of_kernel(const long long *frozen, const int *frozen_buf
     buf_of[l] = frozen[l] >= 0 ? frozen_buf[l] : par;
 }
 
+// number of cars of every lattice in buffer `buf` (conserved by the dynamics)
+__global__ void ens_cars_kernel(const EnsLattice *lat, int count, const u64 *pool, int buf,
+                                long long *cars) {
+  __shared__ unsigned long long s;
+  for (int l = blockIdx.x; l < count; l += gridDim.x) {
+    if (threadIdx.x == 0) s = 0;
+    __syncthreads();
+    const EnsLattice L = lat[l];
+    const long long words = 2ll * L.M * L.P;  // both planes
+    const u64 *p = pool + L.off[buf];
+    unsigned long long c = 0;
+    for (long long i = threadIdx.x; i < words; i += blockDim.x) c += __popcll(p[i]);
+    atomicAdd(&s, c);
+    __syncthreads();
+    if (threadIdx.x == 0) cars[l] = (long long)s;
+    __syncthreads();
+  }
+}
+
+// Surrogate inputs: [cars/(M N), M/2048, N/2048, mean velocity of each of
+// `points` windows of steps first .. first+n-1]; velocity = moved / cars.
+__global__ void ens_features_kernel(const EnsLattice *lat, const long long *cars,
+                                    const u64 *tr_lr, const u64 *tr_tb, long long cap,
+                                    int count, long long first, long long n, int points,
+                                    float *out) {
+  const int stride = 3 + points;
+  const long long per = n / points;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+       idx < (long long)count * points; idx += (long long)gridDim.x * blockDim.x) {
+    const int l = (int)(idx / points), p = (int)(idx - (long long)l * points);
+    const EnsLattice L = lat[l];
+    const double c = (double)cars[l];
+    const u64 *a = tr_lr + (long long)l * cap + first + p * per;
+    const u64 *b = tr_tb + (long long)l * cap + first + p * per;
+    double sum = 0.0;
+    for (long long t = 0; t < per; ++t) sum += (double)(a[t] + b[t]);
+    out[(long long)l * stride + 3 + p] = c > 0 ? (float)(sum / (c * (double)per)) : 0.f;
+    if (p == 0) {
+      out[(long long)l * stride + 0] = (float)(c / ((double)L.M * (double)L.N));
+      out[(long long)l * stride + 1] = (float)L.M / 2048.f;
+      out[(long long)l * stride + 2] = (float)L.N / 2048.f;
+    }
+  }
+}
+
+// Labels: mean velocity over steps steps-window .. steps-1, and jam = some
+// step in 0 .. steps-1 moved no car.
+__global__ void ens_labels_kernel(const long long *cars, const u64 *tr_lr, const u64 *tr_tb,
+                                  long long cap, int count, long long steps, long long window,
+                                  float *v, float *jam) {
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < count; l += gridDim.x * blockDim.x) {
+    const u64 *a = tr_lr + (long long)l * cap, *b = tr_tb + (long long)l * cap;
+    double sum = 0.0;
+    int j = 0;
+    for (long long t = 0; t < steps; ++t) {
+      const u64 m = a[t] + b[t];
+      if (m == 0) j = 1;
+      if (t >= steps - window) sum += (double)m;
+    }
+    const double c = (double)cars[l];
+    v[l] = c > 0 ? (float)(sum / (c * (double)window)) : 0.f;
+    jam[l] = (float)j;
+  }
+}
+
 __global__ void ens_fill_kernel(long long *a, int count, long long v) {
   for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < count; l += gridDim.x * blockDim.x)
     a[l] = v;
@@ -484,6 +549,7 @@ struct bml_ens {
   u64 *tr = nullptr;  // lr then tb, count * cap each
   long long cap = 0;
   long long *frozen = nullptr;
+  long long *cars = nullptr;
   int *frozen_buf = nullptr;
   int *buf_of = nullptr;
   long long *byte_off_d = nullptr;
@@ -517,6 +583,7 @@ void ens_free(bml_ens *e) {
   cudaFree(e->pool);
   cudaFree(e->tr);
   cudaFree(e->frozen);
+  cudaFree(e->cars);
   cudaFree(e->frozen_buf);
   cudaFree(e->buf_of);
   cudaFree(e->byte_off_d);
@@ -806,6 +873,7 @@ extern "C" int bml_ensemble_create_ex(int64_t count, const int64_t *M, const int
   ETRY(cudaMalloc(&e->d_lat, count * sizeof(EnsLattice)));
   ETRY(cudaMalloc(&e->pool, words * sizeof(u64)));
   ETRY(cudaMalloc(&e->frozen, count * sizeof(long long)));
+  ETRY(cudaMalloc(&e->cars, count * sizeof(long long)));
   ETRY(cudaMalloc(&e->frozen_buf, count * sizeof(int)));
   ETRY(cudaMalloc(&e->buf_of, count * sizeof(int)));
   ETRY(cudaMalloc(&e->byte_off_d, count * sizeof(long long)));
@@ -830,6 +898,9 @@ extern "C" int bml_ensemble_create_ex(int64_t count, const int64_t *M, const int
   ETRY(cudaGetLastError());
   ens_init_kernel<<<(unsigned)std::min<int64_t>(count, 148 * 16), 256, 0, e->st>>>(
       e->d_lat, (int)count, d_seed, d_tl, d_tt, e->pool);
+  ETRY(cudaGetLastError());
+  ens_cars_kernel<<<(unsigned)std::min<int64_t>(count, 148 * 16), 256, 0, e->st>>>(
+      e->d_lat, (int)count, e->pool, 0, e->cars);
   ETRY(cudaGetLastError());
   ETRY(cudaStreamSynchronize(e->st));
   cudaFree(d_seed);
@@ -1047,11 +1118,53 @@ extern "C" int bml_ensemble_write_lattices(bml_ens *e, const uint8_t *in) {
       ens_fill_kernel<<<256, 256, 0, e->st>>>(e->frozen, e->count, -1);
       r = cudaGetLastError();
     }
+    if (r == cudaSuccess) {
+      ens_cars_kernel<<<blocks, 256, 0, e->st>>>(e->d_lat, e->count, e->pool, 0, e->cars);
+      r = cudaGetLastError();
+    }
     if (r == cudaSuccess) r = cudaStreamSynchronize(e->st);
     if (r == cudaSuccess) e->steps_done = 0;
   }
   cudaFree(d);
   if (r != cudaSuccess) return efail(BML_ECUDA, "write lattices: %s", cudaGetErrorString(r));
   if (hbad) return efail(BML_EINVAL, "a lattice holds a value other than 0, 1, 2");
+  return BML_OK;
+}
+
+extern "C" int bml_ensemble_car_counts(bml_ens *e, int64_t *out) {
+  if (!e || !out) return efail(BML_EINVAL, "NULL argument");
+  ECUDA(cudaMemcpyAsync(out, e->cars, (size_t)e->count * 8, cudaMemcpyDeviceToHost, e->st));
+  ECUDA(cudaStreamSynchronize(e->st));
+  return BML_OK;
+}
+
+extern "C" int bml_ensemble_features(bml_ens *e, int64_t first, int64_t n, int points,
+                                     float *d_out) {
+  if (!e || !d_out) return efail(BML_EINVAL, "NULL argument");
+  if (points < 1 || n < points || n % points || first < 0 || first + n > e->steps_done)
+    return efail(BML_EINVAL, "need points >= 1, n a multiple of points, and steps "
+                 "[first, first+n) already taken");
+  int rc = check_err(e);
+  if (rc) return rc;
+  const long long items = (long long)e->count * points;
+  ens_features_kernel<<<(unsigned)std::min<long long>((items + 255) / 256, 4096), 256, 0, e->st>>>(
+      e->d_lat, e->cars, e->tr, e->tr + (size_t)e->count * e->cap, e->cap, e->count, first, n,
+      points, d_out);
+  ECUDA(cudaGetLastError());
+  ECUDA(cudaStreamSynchronize(e->st));
+  return BML_OK;
+}
+
+extern "C" int bml_ensemble_labels(bml_ens *e, int64_t window, float *d_v, float *d_jam) {
+  if (!e || !d_v || !d_jam) return efail(BML_EINVAL, "NULL argument");
+  if (window < 1 || window > e->steps_done)
+    return efail(BML_EINVAL, "need 1 <= window <= steps_done");
+  int rc = check_err(e);
+  if (rc) return rc;
+  ens_labels_kernel<<<(e->count + 255) / 256, 256, 0, e->st>>>(
+      e->cars, e->tr, e->tr + (size_t)e->count * e->cap, e->cap, e->count, e->steps_done, window,
+      d_v, d_jam);
+  ECUDA(cudaGetLastError());
+  ECUDA(cudaStreamSynchronize(e->st));
   return BML_OK;
 }

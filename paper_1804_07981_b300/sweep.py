@@ -1,0 +1,248 @@
+"""Surrogate-guided density sweep: allocating long-run step budgets.
+
+A density sweep asks, for every (density, seed) run of an L x L lattice, for
+the steady-state velocity and whether the run jams within T_long steps (the
+phase behaviour of Sec. 2 of the paper: free-flowing below the transition,
+globally jammed above it, coexistence near it).  Running every run to T_long
+is the exact answer; most runs are settled long before.
+
+Every step of the automaton, the features, the labels and the network run in
+the CUDA library; this module only orders the calls.
+
+Arms:
+
+- exact: all runs to T_long in one ensemble with jam early exit (a run that
+  jammed costs nothing afterwards, and its answer is exact).
+- surrogate: all runs to B0 (jam early exit).  At step `probe` the network
+  reads the features (density, size, `points` window means of the moved
+  fraction over the first `probe` steps) and predicts the jam probability.
+  A run jammed by B0 is answered exactly (jam, velocity 0).  A run that is
+  flowing freely at B0 (velocity over the last `window` steps >= v_free)
+  and that the network is confident will not jam (p < tau) stops at B0 and
+  is answered by that velocity.  Every other run continues exactly to
+  T_long in a second ensemble.
+- no surrogate (what the method gives without the network): the same B0
+  stage, then every run not jammed by B0 must continue to T_long, since
+  nothing tells which of them will still jam.
+
+The exact arm judges the others: per-density mean velocity and jam fraction.
+"""
+from __future__ import annotations
+
+import json
+import time
+
+import numpy as np
+
+from . import bml
+from .inputs import ensemble_params
+
+POINTS = 64
+PROBE = 512
+
+
+def _sync(torch):
+    torch.cuda.synchronize()
+
+
+def training_set(count, T, window, seed, lo=64, hi=2048, stream=None):
+    """Batched-ensemble runs with M, N uniform on {lo..hi}, density uniform on
+    [0.1, 0.6], LR fraction uniform on [0.3, 0.7]; returns device tensors
+    (features at PROBE steps, velocity label, jam label) and the seconds."""
+    import torch
+    p = ensemble_params(count, seed=seed, lo=lo, hi=hi)
+    t0 = time.perf_counter()
+    ens = bml.Ensemble(p["M"], p["N"], p["seed"] + np.uint64(seed * 100003), p["p_lr"],
+                       p["p_tb"], flags=bml.BML_ENS_EARLY_EXIT, stream=stream,
+                       reserve_steps=T)
+    ens.step(PROBE)
+    X = ens.features(0, PROBE, POINTS)
+    ens.step(T - PROBE)
+    v, jam = ens.labels(window)
+    _sync(torch)
+    secs = time.perf_counter() - t0
+    ens.close()
+    return X, v, jam, secs
+
+
+def train(X, v, jam, steps=2000, batch=1024, lr=1e-3, wd=1e-4, seed=0, stream=None):
+    """AdamW on random mini-batches; returns the network and the loss curve."""
+    import torch
+    from .inputs import mlp_init_params
+    net = bml.MLP(stream=stream)
+    net.set_params(mlp_init_params(X.shape[1], seed).astype(np.float32))
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    n = X.shape[0]
+    losses = []
+    for s in range(steps):
+        idx = torch.randint(0, n, (min(batch, n),), device="cuda", generator=g)
+        losses.append(net.train_step(X[idx], v[idx], jam[idx], lr=lr, weight_decay=wd))
+    return net, losses
+
+
+def sweep_runs(densities, n_seeds, L):
+    rho = np.repeat(np.asarray(densities, dtype=np.float64), n_seeds)
+    seeds = np.tile(np.arange(1, n_seeds + 1, dtype=np.uint64), len(densities))
+    M = np.full(rho.size, L, dtype=np.int64)
+    return M, M.copy(), seeds, rho / 2, rho / 2, rho
+
+
+def exact_arm(runs, T_long, window, stream=None):
+    import torch
+    M, N, seeds, plr, ptb, _ = runs
+    t0 = time.perf_counter()
+    ens = bml.Ensemble(M, N, seeds, plr, ptb, flags=bml.BML_ENS_EARLY_EXIT, stream=stream,
+                       reserve_steps=T_long)
+    ens.step(T_long)
+    v, jam = ens.labels(window)
+    _sync(torch)
+    secs = time.perf_counter() - t0
+    out = (v.cpu().numpy().astype(np.float64), jam.cpu().numpy().astype(np.float64))
+    ens.close()
+    return out, secs
+
+
+def surrogate_arm(runs, net, T_long, B0, window, tau, v_free=0.99, stream=None, use_net=True):
+    """Returns ((v, jam) answers, seconds, number of runs extended to T_long)."""
+    import torch
+    M, N, seeds, plr, ptb, _ = runs
+    t0 = time.perf_counter()
+    ens = bml.Ensemble(M, N, seeds, plr, ptb, flags=bml.BML_ENS_EARLY_EXIT, stream=stream,
+                       reserve_steps=T_long)
+    ens.step(PROBE)
+    if use_net:
+        X = ens.features(0, PROBE, POINTS)
+        z = net.forward(X)[:, 1]
+        p_jam = torch.sigmoid(z).cpu().numpy()
+    ens.step(B0 - PROBE)
+    v0, jam0 = (t.cpu().numpy().astype(np.float64) for t in ens.labels(window))
+    jammed = jam0 > 0
+    if use_net:
+        extend = ~jammed & ((p_jam >= tau) | (v0 < v_free))
+    else:
+        extend = ~jammed
+    v, jam = np.where(jammed, 0.0, v0), jam0.copy()
+    idx = np.flatnonzero(extend)
+    if idx.size:
+        states = ens.read_all()
+        ext = bml.Ensemble(M[idx], N[idx], seeds[idx], plr[idx], ptb[idx],
+                           flags=bml.BML_ENS_EARLY_EXIT, stream=stream,
+                           block_k=ens.config[0], band_rows=ens.config[1],
+                           reserve_steps=T_long - B0)
+        ext.write_all([states[i] for i in idx])
+        ext.step(T_long - B0)
+        ve, je = (t.cpu().numpy().astype(np.float64) for t in ext.labels(window))
+        v[idx], jam[idx] = ve, je
+        ext.close()
+    _sync(torch)
+    secs = time.perf_counter() - t0
+    ens.close()
+    return (v, jam), secs, int(idx.size)
+
+
+def plain_byte_estimate(runs, T_long, every, sample_stride, chunk=1024, stream=None):
+    """The plain per-lattice GPU form on the same sweep: one lattice at a time
+    with the byte-per-cell kernel, stepping in chunks of `chunk` and stopping
+    a run once a step moved no car (the same early exit as the other arms).
+    Times every `sample_stride`-th density with one seed and extrapolates
+    each sampled time to that density's runs and to the densities skipped
+    between samples."""
+    import torch
+    M, N, seeds, plr, ptb, rho = runs
+    keys = np.unique(rho)
+    per_key = {}
+    sampled = keys[::sample_stride]
+    for k in sampled:
+        i = int(np.flatnonzero(rho == k)[0])
+        _sync(torch)
+        t0 = time.perf_counter()
+        sim = bml.Lattice(int(M[i]), int(N[i]), seed=int(seeds[i]), p_lr=float(plr[i]),
+                          p_tb=float(ptb[i]), kernel="byte", stream=stream,
+                          reserve_steps=T_long)
+        done = 0
+        while done < T_long:
+            n = min(chunk, T_long - done)
+            sim.step(n)
+            tot, _, _ = sim.moved_counts(done, n)
+            done += n
+            if np.any(tot == 0):
+                break
+        sim.close()
+        per_key[float(k)] = time.perf_counter() - t0
+    sk = np.array(sorted(per_key))
+    est = 0.0
+    for k in keys:
+        nearest = sk[np.argmin(np.abs(sk - k))]
+        est += per_key[float(nearest)] * np.sum(rho == k)
+    return est, {"sampled_densities": len(sk), "seconds_sampled": float(sum(per_key.values()))}
+
+
+def per_density(rho, v, jam):
+    keys = np.unique(rho)
+    return (keys, np.array([v[rho == k].mean() for k in keys]),
+            np.array([jam[rho == k].mean() for k in keys]))
+
+
+def compare(runs, answer, exact):
+    rho = runs[5]
+    _, ve, je = per_density(rho, *exact)
+    _, va, ja = per_density(rho, *answer)
+    return {"max_abs_dv": float(np.max(np.abs(va - ve))),
+            "max_abs_djam_fraction": float(np.max(np.abs(ja - je))),
+            "run_velocity_mae": float(np.mean(np.abs(answer[0] - exact[0]))),
+            "run_jam_misclassified": float(np.mean(answer[1] != exact[1]))}
+
+
+def run(cfg: dict, stream=None) -> dict:
+    """Train the surrogate, then run the three arms on one sweep; returns a
+    summary dict (times in seconds)."""
+    import torch
+    X, v, jam, t_data = training_set(cfg["train_count"], cfg["train_T"], cfg["window"],
+                                     seed=cfg.get("train_seed", 7), lo=cfg["train_lo"],
+                                     hi=cfg["train_hi"], stream=stream)
+    t0 = time.perf_counter()
+    net, losses = train(X, v, jam, steps=cfg["train_steps"], stream=stream)
+    _sync(torch)
+    t_train = time.perf_counter() - t0
+    runs = sweep_runs(cfg["densities"], cfg["seeds"], cfg["L"])
+    exact, t_exact = exact_arm(runs, cfg["T_long"], cfg["window"], stream)
+    sur, t_sur, n_ext = surrogate_arm(runs, net, cfg["T_long"], cfg["B0"], cfg["window"],
+                                      cfg["tau"], cfg["v_free"], stream)
+    base, t_base, n_base = surrogate_arm(runs, None, cfg["T_long"], cfg["B0"], cfg["window"],
+                                         cfg["tau"], cfg["v_free"], stream, use_net=False)
+    plain = None
+    if cfg.get("plain_sample_stride"):
+        est, info = plain_byte_estimate(runs, cfg["T_long"], every=1,
+                                        sample_stride=cfg["plain_sample_stride"], stream=stream)
+        plain = {"seconds_estimated": est, **info}
+    return {
+        "plain_byte_per_lattice": plain,
+        "config": cfg, "runs": int(runs[0].size),
+        "training": {"seconds_data": t_data, "seconds_train": t_train,
+                     "loss_first": losses[0], "loss_last": float(np.mean(losses[-50:]))},
+        "exact": {"seconds": t_exact},
+        "surrogate": {"seconds": t_sur, "extended_runs": n_ext, **compare(runs, sur, exact)},
+        "no_surrogate": {"seconds": t_base, "extended_runs": n_base,
+                         **compare(runs, base, exact)},
+    }
+
+
+FULL = {
+    "densities": [round(0.25 + 0.005 * i, 3) for i in range(41)], "seeds": 64, "L": 1024,
+    "T_long": 100000, "B0": 10000, "window": 1024, "tau": 0.01, "v_free": 0.99,
+    "train_count": 4096, "train_T": 100000, "train_lo": 64, "train_hi": 2048,
+    "train_steps": 4000, "plain_sample_stride": 4,
+}
+
+SMALL = {
+    "densities": [round(0.25 + 0.02 * i, 3) for i in range(11)], "seeds": 16, "L": 128,
+    "T_long": 8192, "B0": 2048, "window": 256, "tau": 0.01, "v_free": 0.99,
+    "train_count": 4096, "train_T": 8192, "train_lo": 64, "train_hi": 256,
+    "train_steps": 3000,
+}
+
+
+if __name__ == "__main__":
+    import sys
+    cfg = FULL if "--full" in sys.argv else SMALL
+    print(json.dumps(run(cfg)))

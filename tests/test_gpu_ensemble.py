@@ -181,3 +181,24 @@ def test_ensemble_rejects_bad_arguments(lib):
         lib.bml_ensemble_create_ex([10], [100], [1], [0.1], [0.1], 3, 16)
     with pytest.raises(lib.BMLError):
         lib.bml_ensemble_create_ex([10], [100], [1], [0.1], [0.1], 2, 0)
+
+
+def test_features_and_labels_match_oracle(lib):
+    """Surrogate inputs and labels computed on the device from the ensemble's
+    traces equal the oracle's, computed from the oracle's own runs."""
+    from oracle import features as F
+    M, N, seeds, plr, ptb = mixed_shapes(30, 13)
+    K, points, window = 128, 16, 32
+    want, wlr, wtb = oracle_ensemble(M, N, seeds, plr, ptb, K)
+    cars = np.array([int(((oracle.init(int(m), int(n), int(s), float(a), float(b))) != 0).sum())
+                     for m, n, s, a, b in zip(M, N, seeds, plr, ptb)])
+    with lib.Ensemble(M, N, seeds, plr, ptb, block_k=4, band_rows=32) as ens:
+        ens.step(K)
+        np.testing.assert_array_equal(ens.car_counts(), cars)
+        f = ens.features(0, K, points).cpu().numpy()
+        v, jam = (t.cpu().numpy() for t in ens.labels(window))
+    wf = F.features(wlr + wtb, cars, M, N, 0, K, points)
+    wv, wj = F.labels(wlr + wtb, cars, window)
+    np.testing.assert_allclose(f, wf, rtol=1e-6, atol=1e-7)
+    np.testing.assert_allclose(v, wv, rtol=1e-6, atol=1e-7)
+    np.testing.assert_array_equal(jam, wj)
