@@ -109,6 +109,29 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+def dist_max(x: float, world: int, device: str = "cuda") -> float:
+    """Maximum of x over all ranks (x itself when world == 1)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def dist_barrier(world: int) -> None:
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def job_rate(world: int, units_per_rank: float, seconds: float) -> float:
+    """Whole-job throughput of `world` replicas that each processed
+    units_per_rank units, timed by the slowest rank (weak scaling)."""
+    return world * units_per_rank / seconds
+
+
 def _dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -226,18 +249,11 @@ def run_ours(args):
     K, W = args.steps, args.warmup
 
     def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
+        dist_barrier(world)
         torch.cuda.synchronize()
 
     def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return dist_max(x, world)
 
     # ---------------- device-resident run (value, roofline) ----------------
     sim = bml.Lattice(M, N, seed=seed, p_lr=DENSITY / 2, p_tb=DENSITY / 2, kernel=args.kernel,
@@ -264,7 +280,7 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
     ms_max = max_over_ranks(ms)
     lattice_steps = K * STEPS_PER_BENCH_STEP
-    value = world * cells * lattice_steps / (ms_max / 1e3)
+    value = job_rate(world, cells * lattice_steps, ms_max / 1e3)
     # counts of the timed steps must be complete and plausible
     tot, _, _ = sim.moved_counts(W * STEPS_PER_BENCH_STEP, lattice_steps)
     assert (tot >= 0).all() and (tot <= cells).all()
@@ -330,7 +346,7 @@ def run_ours(args):
         bml.bml_read_lattice(sim.handle, M, N, out=hout)
         dt = time.perf_counter() - t0
         dt = max_over_ranks(dt)
-        e2e = {"value": world * cells * lattice_steps / dt, "unit": "cell-updates/s",
+        e2e = {"value": job_rate(world, cells * lattice_steps, dt), "unit": "cell-updates/s",
                "h2d_bytes_per_step": cells / K,
                "d2h_bytes_per_step": cells / K + STEPS_PER_BENCH_STEP * 3 * 8,
                "seconds": dt}
@@ -340,7 +356,7 @@ def run_ours(args):
     if not args.no_ensemble:
         ens = _ensemble_bench(bml, torch, stream, args.ensemble_steps, seed_base=1 + 4096 * rank)
         ens_max = max_over_ranks(ens["seconds"])
-        ens["value"] = world * ens["lattices"] * ens["steps"] / ens_max
+        ens["value"] = job_rate(world, ens["lattices"] * ens["steps"], ens_max)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

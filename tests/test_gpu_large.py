@@ -1,0 +1,113 @@
+"""Parity at the workloads' full sizes, where the oracle cannot run the whole
+job: exact cross-checks between independent GPU paths, oracle runs on
+sampled windows whose dependency cone fits inside them, and properties that
+hold at any size."""
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+EMPTY, LR, TB = 0, 1, 2
+
+
+@pytest.mark.parametrize("rho", [0.20, 0.35, 0.50])
+def test_4096_byte_and_bitplane_agree_for_4096_steps(lib, rho):
+    """Single lattice 4096 x 4096, densities {0.20, 0.35, 0.50} split evenly,
+    seeds 1-3, 4096 steps: the byte-per-cell kernel and the bit-packed
+    autotuned kernel give the same lattice and per-step counts."""
+    M = N = 4096
+    for seed in (1, 2, 3):
+        out = []
+        for kernel in ("byte", "auto"):
+            with lib.Lattice(M, N, seed=seed, density=rho, kernel=kernel,
+                             reserve_steps=4096) as sim:
+                sim.step(4096)
+                out.append((sim.read(), sim.moved_counts()))
+        np.testing.assert_array_equal(out[0][0], out[1][0])
+        for a, b in zip(out[0][1], out[1][1]):
+            np.testing.assert_array_equal(a, b)
+
+
+def test_4096_against_threaded_oracle(lib):
+    """One 4096^2 run against the oracle itself (threaded, identical results
+    for any thread count) for 512 steps: lattice and every count."""
+    import os
+    bml = lib
+    M = N = 4096
+    g0 = oracle.init(M, N, 1, 0.175, 0.175)
+    want, mlr, mtb = oracle.run(g0, 512, threads=os.cpu_count() or 1)
+    with bml.Lattice(M, N, seed=1, density=0.35) as sim:
+        np.testing.assert_array_equal(sim.read(), g0)
+        sim.step(512)
+        np.testing.assert_array_equal(sim.read(), want)
+        _, lr, tb = sim.moved_counts()
+    np.testing.assert_array_equal(lr, mlr)
+    np.testing.assert_array_equal(tb, mtb)
+
+
+def _window_init(i0, j0, S, M, N, seed, p):
+    """Cells of rows i0..i0+S-1, columns j0..j0+S-1 (mod M, N) of the seeded
+    placement, computed one by one with the oracle's generator."""
+    t = oracle.threshold(p)
+    w = np.zeros((S, S), dtype=np.uint8)
+    for a in range(S):
+        i = (i0 + a) % M
+        for b in range(S):
+            j = (j0 + b) % N
+            u = oracle.splitmix64(seed, i * N + j + 1)
+            w[a, b] = LR if u < t else (TB if u - t < t else EMPTY)
+    return w
+
+
+def test_32768_sampled_windows_in_bench_configuration(lib):
+    """32768 x 32768, density 0.38, seed 1, in the launch configuration the
+    benchmark times (autotuned depth and band): after 8 steps every cell's
+    state depends only on the 17 x 17 cells around it, so the oracle run on
+    a 33 x 33 window (wrapped as its own small torus) gives the exact state
+    of the 17 x 17 centre of the window."""
+    M = N = 32768
+    t, S = 8, 33
+    with lib.Lattice(M, N, seed=1, density=0.38) as sim:
+        sim.step(t)
+        got = sim.read()
+    rng = np.random.Generator(np.random.PCG64(5))
+    corners = rng.integers(0, M, size=(32, 2))
+    corners[0] = [M - 16, N - 16]  # a window across both wrap seams
+    for i0, j0 in corners:
+        w = _window_init(int(i0), int(j0), S, M, N, 1, 0.19)
+        w_t, _, _ = oracle.run(w, t)
+        rows = (np.arange(t, S - t) + i0) % M
+        cols = (np.arange(t, S - t) + j0) % N
+        np.testing.assert_array_equal(got[np.ix_(rows, cols)], w_t[t:S - t, t:S - t])
+
+
+def test_32768_full_run_properties(lib):
+    """The benchmark's full job (10^4 steps at 32768^2): LR cars per row and
+    TB cars per column are conserved; every LR move adds 1 to the column
+    index of one car (mod N) and every TB move adds 1 to a row index
+    (mod M), so the summed counts equal the change of those index sums
+    modulo N and M; no step moves more cars than exist."""
+    M = N = 32768
+    with lib.Lattice(M, N, seed=1, density=0.38, reserve_steps=10000) as sim:
+        g0 = sim.read()
+        sim.step(10000)
+        g1 = sim.read()
+        _, lr, tb = sim.moved_counts()
+    cols = np.arange(N, dtype=np.int64)
+    rows = np.arange(M, dtype=np.int64)
+    per = {}
+    for name, g in (("0", g0), ("1", g1)):
+        is_lr, is_tb = g == LR, g == TB
+        per[name] = (is_lr.sum(axis=1), is_tb.sum(axis=0),   # LR per row, TB per column
+                     is_lr.sum(axis=0), is_tb.sum(axis=1))   # LR per column, TB per row
+        del is_lr, is_tb
+    np.testing.assert_array_equal(per["0"][0], per["1"][0])
+    np.testing.assert_array_equal(per["0"][1], per["1"][1])
+    s_lr0, s_lr1 = int(per["0"][2] @ cols), int(per["1"][2] @ cols)
+    s_tb0, s_tb1 = int(per["0"][3] @ rows), int(per["1"][3] @ rows)
+    assert (int(lr.sum()) - (s_lr1 - s_lr0)) % N == 0
+    assert (int(tb.sum()) - (s_tb1 - s_tb0)) % M == 0
+    n_lr, n_tb = int(per["0"][0].sum()), int(per["0"][1].sum())
+    assert lr.min() >= 0 and lr.max() <= n_lr and tb.min() >= 0 and tb.max() <= n_tb
