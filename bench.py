@@ -260,8 +260,9 @@ def run_ours(args):
                       block_k=args.block_k, stream=stream,
                       reserve_steps=(K + W) * STEPS_PER_BENCH_STEP)
     if args.band is not None:
-        sim.set_tiling(args.block_k or 1, args.band)
+        sim.set_tiling(args.block_k or 1, args.band, args.lane_words)
     kernel_id, block_k, band_rows = sim.config
+    lane_words = sim.tiling[2] if kernel_id in (bml.BML_KERNEL_TBLOCK, bml.BML_KERNEL_FUSED) else 1
     for _ in range(W):
         sim.step(STEPS_PER_BENCH_STEP)
     sim.synchronize()
@@ -291,7 +292,8 @@ def run_ours(args):
     if kernel_id in (bml.BML_KERNEL_TBLOCK, bml.BML_KERNEL_FUSED):
         depth = max(1, block_k)
         launches_per_step = STEPS_PER_BENCH_STEP // depth
-        kname = "fused_rows_kernel" if band_rows == 0 else "stream_kernel<%d>" % depth
+        kname = ("fused_rows_kernel" if band_rows == 0 else
+                 ("stream2_kernel<%d>" if lane_words == 2 else "stream_kernel<%d>") % depth)
     elif kernel_id == bml.BML_KERNEL_BITPLANE:
         depth, launches_per_step, kname = 1, 2 * STEPS_PER_BENCH_STEP, "plane_h/plane_v"
     else:
@@ -377,6 +379,7 @@ def run_ours(args):
                        "kernel": {0: "auto", 1: "byte", 2: "bitplane", 3: "fused",
                                   4: "tblock"}[kernel_id],
                        "temporal_depth": block_k, "band_rows": band_rows,
+                       "lane_words": lane_words,
                        "l2": "inputs larger than L2 (2 x 256 MB bitplanes)",
                        "parallelism": "replicas x%d" % world},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "ensemble": ens,
@@ -398,6 +401,7 @@ def main():
     ap.add_argument("--kernel", default="auto")
     ap.add_argument("--block-k", type=int, default=0)
     ap.add_argument("--band", type=int, default=None, help="band rows (with --kernel tblock)")
+    ap.add_argument("--lane-words", type=int, default=1, help="1 or 2 (with --band)")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--ensemble-steps", type=int, default=1024)
     ap.add_argument("--M", type=int, default=M_ROWS)

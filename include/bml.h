@@ -143,6 +143,15 @@ int bml_get_config(const bml_sim *sim, int *kernel, int *block_k, int64_t *band_
  * or values. */
 int bml_set_tiling(bml_sim *sim, int block_k, int64_t band_rows);
 
+/* As bml_set_tiling, choosing also the 64-cell words each lane of the
+ * streaming kernel holds: 1, or 2 (rows of full words only: N % 64 == 0, an
+ * even number > 32 of words per row; band_rows >= 1).  bml_set_tiling
+ * selects 1. */
+int bml_set_tiling_ex(bml_sim *sim, int block_k, int64_t band_rows, int lane_words);
+
+/* Current tiling of the bitplane kernels (band_rows 0: one-pass kernel). */
+int bml_get_tiling(const bml_sim *sim, int *block_k, int64_t *band_rows, int *lane_words);
+
 /* Wait for all work enqueued by the object. */
 int bml_synchronize(bml_sim *sim);
 

@@ -74,6 +74,8 @@ _lib_write_dev = _sig("bml_write_lattice_device", [_vp, _vp])
 _lib_steps_done = _sig("bml_steps_done", [_vp], _i64)
 _lib_get_config = _sig("bml_get_config", [_vp, ctypes.POINTER(_int), ctypes.POINTER(_int), _i64p])
 _lib_set_tiling = _sig("bml_set_tiling", [_vp, _int, _i64])
+_lib_set_tiling_ex = _sig("bml_set_tiling_ex", [_vp, _int, _i64, _int])
+_lib_get_tiling = _sig("bml_get_tiling", [_vp, ctypes.POINTER(_int), _i64p, ctypes.POINTER(_int)])
 _lib_sync = _sig("bml_synchronize", [_vp])
 _lib_destroy = _sig("bml_destroy", [_vp], None)
 _lib_last_error = _sig("bml_last_error", [], ctypes.c_char_p)
@@ -196,6 +198,17 @@ def bml_set_tiling(sim: int, block_k: int, band_rows: int) -> None:
     _check(_lib_set_tiling(sim, block_k, band_rows))
 
 
+def bml_set_tiling_ex(sim: int, block_k: int, band_rows: int, lane_words: int) -> None:
+    _check(_lib_set_tiling_ex(sim, block_k, band_rows, lane_words))
+
+
+def bml_get_tiling(sim: int):
+    k, lw = _int(), _int()
+    b = _i64()
+    _check(_lib_get_tiling(sim, ctypes.byref(k), ctypes.byref(b), ctypes.byref(lw)))
+    return k.value, b.value, lw.value
+
+
 def bml_synchronize(sim: int) -> None:
     _check(_lib_sync(sim))
 
@@ -247,8 +260,15 @@ class Lattice:
     def config(self):
         return bml_get_config(self._h)
 
-    def set_tiling(self, block_k: int, band_rows: int) -> None:
-        bml_set_tiling(self._h, block_k, band_rows)
+    def set_tiling(self, block_k: int, band_rows: int, lane_words: int = 1) -> None:
+        if lane_words == 1:
+            bml_set_tiling(self._h, block_k, band_rows)
+        else:
+            bml_set_tiling_ex(self._h, block_k, band_rows, lane_words)
+
+    @property
+    def tiling(self):
+        return bml_get_tiling(self._h)
 
     def synchronize(self) -> None:
         bml_synchronize(self._h)

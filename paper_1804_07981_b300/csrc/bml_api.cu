@@ -79,6 +79,7 @@ struct bml_sim {
   int kernel = BML_KERNEL_AUTO;
   int block_k = 1;
   int64_t band_rows = 0;
+  int lane_words = 1;  // streaming kernel: 64-cell words per lane (1 or 2)
   cudaStream_t st = nullptr;
   Allocator alloc;
   // state: bitplane kernels use L[cur], T[cur]; the byte kernel uses c[0]
@@ -209,8 +210,12 @@ int enqueue_steps(bml_sim *s, int64_t k, u64 *lr, u64 *tb, bool commit) {
     int d = s->block_k;
     while (d > k - done) d >>= 1;
     const int a = s->cur, b = 1 - s->cur;
-    CUDA_TRY(launch_stream(plane_L(s, a), plane_T(s, a), plane_L(s, b), plane_T(s, b), g, d,
-                           s->band_rows, lr + done, tb + done, s->st));
+    if (s->lane_words == 2)
+      CUDA_TRY(launch_stream2(plane_L(s, a), plane_T(s, a), plane_L(s, b), plane_T(s, b), g, d,
+                              s->band_rows, lr + done, tb + done, s->st));
+    else
+      CUDA_TRY(launch_stream(plane_L(s, a), plane_T(s, a), plane_L(s, b), plane_T(s, b), g, d,
+                             s->band_rows, lr + done, tb + done, s->st));
     if (commit) s->cur = b;
     done += d;
   }
@@ -226,7 +231,12 @@ struct TuneKey {
   }
 };
 std::mutex g_tune_mu;
-std::map<TuneKey, std::pair<int, int64_t>> g_tune_cache;
+struct Tiling {
+  int k;
+  int64_t band;
+  int lane_words;
+};
+std::map<TuneKey, Tiling> g_tune_cache;
 
 int autotune(bml_sim *s) {
   int dev = 0;
@@ -236,8 +246,9 @@ int autotune(bml_sim *s) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) {
-      s->block_k = it->second.first;
-      s->band_rows = it->second.second;
+      s->block_k = it->second.k;
+      s->band_rows = it->second.band;
+      s->lane_words = it->second.lane_words;
       return BML_OK;
     }
   }
@@ -246,25 +257,28 @@ int autotune(bml_sim *s) {
   // heights that make the tile count fill 1..4 whole waves of resident warps
   int sms = 148;
   CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  std::vector<std::pair<int, int64_t>> cands;
-  cands.push_back({1, 0});
-  for (int k : {1, 2, 4, 8}) {
-    std::vector<int64_t> bands;
-    for (int64_t b : {16, 32, 64, 128, 256, 512, 1024}) bands.push_back(b);
-    int wpb = 1;
-    const int per_sm = stream_occupancy(s->g, k, &wpb);
-    const int64_t resident = (int64_t)sms * per_sm * wpb;
-    const int64_t strips = make_strip_plan(s->g, k).n_strips;
-    for (int waves = 1; waves <= 4; ++waves) {
-      const int64_t nb = resident * waves / strips;
-      if (nb >= 1) bands.push_back((s->g.M + nb - 1) / nb);
-    }
-    std::sort(bands.begin(), bands.end());
-    bands.erase(std::unique(bands.begin(), bands.end()), bands.end());
-    for (int64_t b : bands) {
-      if (b < 2 * k && b < s->g.M) continue;  // halo work would dominate
-      cands.push_back({k, b >= s->g.M ? s->g.M : b});
-      if (b >= s->g.M) break;
+  std::vector<Tiling> cands;
+  cands.push_back({1, 0, 1});
+  for (int lw : {1, 2}) {
+    if (lw == 2 && !stream2_applies(s->g)) continue;
+    for (int k : {1, 2, 4, 8}) {
+      std::vector<int64_t> bands;
+      for (int64_t b : {16, 32, 64, 128, 256, 512, 1024}) bands.push_back(b);
+      int wpb = 4;
+      const int per_sm = lw == 2 ? stream2_occupancy(k) : stream_occupancy(s->g, k, &wpb);
+      const int64_t resident = (int64_t)sms * per_sm * wpb;
+      const int64_t strips = lw == 2 ? stream2_strips(s->g) : make_strip_plan(s->g, k).n_strips;
+      for (int waves = 1; waves <= 4; ++waves) {
+        const int64_t nb = resident * waves / strips;
+        if (nb >= 1) bands.push_back((s->g.M + nb - 1) / nb);
+      }
+      std::sort(bands.begin(), bands.end());
+      bands.erase(std::unique(bands.begin(), bands.end()), bands.end());
+      for (int64_t b : bands) {
+        if (b < 2 * k && b < s->g.M) continue;  // halo work would dominate
+        cands.push_back({k, b >= s->g.M ? s->g.M : b, lw});
+        if (b >= s->g.M) break;
+      }
     }
   }
   cudaEvent_t e0, e1;
@@ -272,18 +286,20 @@ int autotune(bml_sim *s) {
   CUDA_TRY(cudaEventCreate(&e1));
   const int saved_k = s->block_k;
   const int64_t saved_b = s->band_rows;
+  const int saved_lw = s->lane_words;
   double best = 1e30;
-  int best_k = 1;
+  int best_k = 1, best_lw = 1;
   int64_t best_b = 0;
   const double cells = (double)s->g.M * (double)s->g.N;
   const int reps = cells > 1e8 ? 3 : (cells > 1e6 ? 10 : 20);
   int rc = BML_OK;
   for (const auto &c : cands) {
     {
-      const int k = c.first;
-      const int64_t b = c.second;
+      const int k = c.k;
+      const int64_t b = c.band;
       s->block_k = k;
       s->band_rows = b;
+      s->lane_words = c.lane_words;
       u64 *lr = (u64 *)s->scratch.ptr, *tb = lr + 8;
       // warm-up (non-committing: reads cur, writes the other buffer)
       if ((rc = enqueue_steps(s, k, lr, tb, false))) goto done;
@@ -302,6 +318,7 @@ int autotune(bml_sim *s) {
         best = per_step;
         best_k = k;
         best_b = b;
+        best_lw = c.lane_words;
       }
     }
   }
@@ -311,12 +328,14 @@ done:
   if (rc) {
     s->block_k = saved_k;
     s->band_rows = saved_b;
+    s->lane_words = saved_lw;
     return rc;
   }
   s->block_k = best_k;
   s->band_rows = best_b;
+  s->lane_words = best_lw;
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_tune_cache[key] = {best_k, best_b};
+  g_tune_cache[key] = {best_k, best_b, best_lw};
   return BML_OK;
 }
 
@@ -437,6 +456,27 @@ extern "C" int bml_get_config(const bml_sim *s, int *kernel, int *block_k, int64
   return BML_OK;
 }
 
+extern "C" int bml_set_tiling_ex(bml_sim *s, int block_k, int64_t band_rows, int lane_words) {
+  if (!s) return fail(BML_EINVAL, "sim is NULL");
+  if (lane_words != 1 && lane_words != 2) return fail(BML_EINVAL, "lane_words must be 1 or 2");
+  if (lane_words == 2 && (!stream2_applies(s->g) || band_rows == 0))
+    return fail(BML_EINVAL, "two words per lane need N %% 64 == 0, an even number of words "
+                "per row, more than 32 of them, and band_rows >= 1");
+  int rc = bml_set_tiling(s, block_k, band_rows);
+  if (rc) return rc;
+  s->lane_words = lane_words;
+  return BML_OK;
+}
+
+extern "C" int bml_get_tiling(const bml_sim *s, int *block_k, int64_t *band_rows,
+                              int *lane_words) {
+  if (!s) return fail(BML_EINVAL, "sim is NULL");
+  if (block_k) *block_k = s->block_k;
+  if (band_rows) *band_rows = s->band_rows;
+  if (lane_words) *lane_words = s->lane_words;
+  return BML_OK;
+}
+
 extern "C" int bml_set_tiling(bml_sim *s, int block_k, int64_t band_rows) {
   if (!s) return fail(BML_EINVAL, "sim is NULL");
   if (!uses_planes(s->kernel) || s->kernel == BML_KERNEL_BITPLANE)
@@ -449,6 +489,7 @@ extern "C" int bml_set_tiling(bml_sim *s, int block_k, int64_t band_rows) {
     return fail(BML_EINVAL, "bad band_rows (0 selects the direct one-pass kernel, depth 1)");
   s->block_k = block_k;
   s->band_rows = band_rows;
+  s->lane_words = 1;
   return BML_OK;
 }
 

@@ -91,4 +91,12 @@ cudaError_t launch_stream(const u64 *Lin, const u64 *Tin, u64 *Lout, u64 *Tout, 
                           int k, int64_t band_rows, u64 *moved_lr, u64 *moved_tb,
                           cudaStream_t st);
 
+// Two-words-per-lane streaming kernel (rows of full words, W even, W > 32).
+bool stream2_applies(const Geom &g);
+int64_t stream2_strips(const Geom &g);
+int stream2_occupancy(int k);
+cudaError_t launch_stream2(const u64 *Lin, const u64 *Tin, u64 *Lout, u64 *Tout, const Geom &g,
+                           int k, int64_t band_rows, u64 *moved_lr, u64 *moved_tb,
+                           cudaStream_t st);
+
 }  // namespace bml

@@ -1,0 +1,228 @@
+// Streaming bitplane step with two words per lane (rows whose every word holds
+// 64 cells, N % 64 == 0, and wider than one warp strip).
+//
+// Same pipeline as stream_step.cu (k stages in registers, the Sec. 2 rules
+// per stage, the TB cars entering a row being the previous row's TB move
+// mask), but lane l of a warp holds one aligned pair of ring words: pair
+// first-1+l of the W/2 pairs of the row (W even), read and written with
+// 128-bit accesses.  The shift between the two words of a lane is an
+// in-register funnel shift; lanes 0 and owned+1 hold halo pairs (a 128-column
+// cone), lanes 1..owned are stored and counted (up to 30 pairs per warp).
+// Per stage and row a lane makes two 32-bit shuffles for two words: the right
+// lane's low half of E and the left lane's high half of the LR move mask.
+#include "stage.cuh"
+
+namespace bml {
+
+namespace {
+
+constexpr int kWarps2 = 4;
+
+template <int K>
+struct PF2 {
+  static constexpr int value = K >= 4 ? 2 : 4;
+};
+
+struct PairState {
+  u64 Ta, Tb, La, Lb, Ma, Mb;  // T_{x-1}, Lh_{x-1}, mvV_{x-2} of both words
+};
+
+__device__ __forceinline__ uint32_t fsr(uint32_t lo, uint32_t hi) { return __funnelshift_r(lo, hi, 1); }
+__device__ __forceinline__ uint32_t fsl(uint32_t lo, uint32_t hi) { return __funnelshift_l(lo, hi, 1); }
+
+// One stage on the word pair (a, b) of this lane; see stage.cuh for the rule.
+__device__ __forceinline__ void stage_pair(u64 &La, u64 &Lb, u64 &Ta, u64 &Tb, PairState &st,
+                                           int src_l, int src_r, uint32_t &c_lr,
+                                           uint32_t &c_tb, bool cnt_h, bool cnt_v) {
+  const u64 Ea = ~(La | Ta), Eb = ~(Lb | Tb);
+  const uint32_t rr = __shfl_sync(BML_FULL_MASK, lo32(Ea), src_r);
+  const u64 Era = mk64(fsr(lo32(Ea), hi32(Ea)), fsr(hi32(Ea), lo32(Eb)));
+  const u64 Erb = mk64(fsr(lo32(Eb), hi32(Eb)), fsr(hi32(Eb), rr));
+  const u64 mHa = La & Era, mHb = Lb & Erb;
+  const uint32_t rl = __shfl_sync(BML_FULL_MASK, hi32(mHb), src_l);
+  const u64 ina = mk64(fsl(rl, lo32(mHa)), fsl(lo32(mHa), hi32(mHa)));
+  const u64 inb = mk64(fsl(hi32(mHa), lo32(mHb)), fsl(lo32(mHb), hi32(mHb)));
+  const u64 Lha = La ^ mHa ^ ina, Lhb = Lb ^ mHb ^ inb;
+  const u64 Epa = Ea ^ ina ^ mHa, Epb = Eb ^ inb ^ mHb;
+  const u64 mVa = st.Ta & Epa, mVb = st.Tb & Epb;
+  const u64 oTa = (st.Ta & ~Epa) | st.Ma, oTb = (st.Tb & ~Epb) | st.Mb;
+  if (cnt_h) c_lr += popc64(mHa) + popc64(mHb);
+  if (cnt_v) c_tb += popc64(mVa) + popc64(mVb);
+  La = st.La;
+  Lb = st.Lb;
+  st.Ta = Ta;
+  st.Tb = Tb;
+  st.La = Lha;
+  st.Lb = Lhb;
+  st.Ma = mVa;
+  st.Mb = mVb;
+  Ta = oTa;
+  Tb = oTb;
+}
+
+template <int K>
+__global__ void __launch_bounds__(kWarps2 * 32, K >= 8 ? 2 : 3)
+    stream2_kernel(const u64 *__restrict__ Lin, const u64 *__restrict__ Tin,
+                   u64 *__restrict__ Lout, u64 *__restrict__ Tout, Geom g, int n_strips,
+                   int base, int rem, int band_rows, int n_bands, u64 *__restrict__ moved_lr,
+                   u64 *__restrict__ moved_tb) {
+  constexpr int P = PF2<K>::value;
+  __shared__ unsigned long long s_cnt[2 * K];
+  for (int t = threadIdx.x; t < 2 * K; t += blockDim.x) s_cnt[t] = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int tile = blockIdx.x * kWarps2 + (threadIdx.x >> 5);
+  uint32_t c_lr[K], c_tb[K];
+#pragma unroll
+  for (int s = 0; s < K; ++s) c_lr[s] = c_tb[s] = 0;
+
+  if (tile < n_strips * n_bands) {
+    const int strip = tile % n_strips, band = tile / n_strips;
+    const int owned = base + (strip < rem ? 1 : 0);  // pairs
+    const int first = strip * base + (strip < rem ? strip : rem);
+    const int WP = (int)(g.W / 2);
+    int pw = (first - 1 + lane) % WP;
+    if (pw < 0) pw += WP;
+    const int wa = 2 * pw;
+    const bool own = lane >= 1 && lane <= owned;
+    const int src_l = lane > 0 ? lane - 1 : 0, src_r = lane < 31 ? lane + 1 : 31;
+
+    const int r0 = band * band_rows;
+    const int B = r0 + band_rows < g.M ? band_rows : (int)g.M - r0;
+    const int n_in = B + 2 * K;
+    const int M = (int)g.M;
+    int ld_row = (r0 - K) % M;
+    if (ld_row < 0) ld_row += M;
+    const size_t pitch = (size_t)g.P;
+    size_t roff = (size_t)ld_row * pitch;
+
+    PairState st[K];
+#pragma unroll
+    for (int s = 0; s < K; ++s) st[s] = PairState{0, 0, 0, 0, 0, 0};
+
+    u64 bLa[P], bLb[P], bTa[P], bTb[P];
+#pragma unroll
+    for (int u = 0; u < P; ++u) {
+      bLa[u] = bLb[u] = bTa[u] = bTb[u] = 0;
+      if (u < n_in) {
+        ld2(Lin + roff + wa, bLa[u], bLb[u]);
+        ld2(Tin + roff + wa, bTa[u], bTb[u]);
+        if (++ld_row == M) {
+          ld_row = 0;
+          roff = 0;
+        } else {
+          roff += pitch;
+        }
+      }
+    }
+    for (int i0 = 0; i0 < n_in; i0 += P) {
+      const bool steady = i0 >= 2 * K && i0 + P <= B + K;
+#pragma unroll
+      for (int u = 0; u < P; ++u) {
+        const int i = i0 + u;
+        if (steady || i < n_in) {
+          u64 La = bLa[u], Lb = bLb[u], Ta = bTa[u], Tb = bTb[u];
+          if (i + P < n_in) {
+            ld2(Lin + roff + wa, bLa[u], bLb[u]);
+            ld2(Tin + roff + wa, bTa[u], bTb[u]);
+            if (++ld_row == M) {
+              ld_row = 0;
+              roff = 0;
+            } else {
+              roff += pitch;
+            }
+          }
+#pragma unroll
+          for (int s = 0; s < K; ++s)
+            stage_pair(La, Lb, Ta, Tb, st[s], src_l, src_r, c_lr[s], c_tb[s],
+                       steady || (unsigned)(i - K - s) < (unsigned)B,
+                       steady || (unsigned)(i - K - s - 1) < (unsigned)B);
+          if (steady || i >= 2 * K) {
+            const size_t off = (size_t)(r0 + i - 2 * K) * pitch;
+            if (own) {
+              st2(Lout + off + wa, La, Lb);
+              st2(Tout + off + wa, Ta, Tb);
+            }
+          }
+        }
+      }
+    }
+    if (!own) {
+#pragma unroll
+      for (int s = 0; s < K; ++s) c_lr[s] = c_tb[s] = 0;
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < K; ++s) {
+    const uint32_t a = __reduce_add_sync(BML_FULL_MASK, c_lr[s]);
+    const uint32_t b = __reduce_add_sync(BML_FULL_MASK, c_tb[s]);
+    if (lane == 0) {
+      if (a) atomicAdd(&s_cnt[s], (unsigned long long)a);
+      if (b) atomicAdd(&s_cnt[K + s], (unsigned long long)b);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < K) {
+    if (s_cnt[threadIdx.x]) atomicAdd(moved_lr + threadIdx.x, s_cnt[threadIdx.x]);
+  } else if (threadIdx.x < 2 * K) {
+    const int s = threadIdx.x - K;
+    if (s_cnt[K + s]) atomicAdd(moved_tb + s, s_cnt[K + s]);
+  }
+}
+
+template <int K>
+cudaError_t launch2_k(const u64 *Lin, const u64 *Tin, u64 *Lout, u64 *Tout, const Geom &g,
+                      int64_t band_rows, u64 *moved_lr, u64 *moved_tb, cudaStream_t st) {
+  const int64_t WP = g.W / 2;
+  const int64_t n_strips = (WP + 29) / 30;
+  const int base = (int)(WP / n_strips), rem = (int)(WP % n_strips);
+  const int64_t n_bands = (g.M + band_rows - 1) / band_rows;
+  const int64_t tiles = n_strips * n_bands;
+  if (tiles > INT32_MAX - kWarps2) return cudaErrorInvalidValue;
+  const int64_t blocks = (tiles + kWarps2 - 1) / kWarps2;
+  stream2_kernel<K><<<(unsigned)blocks, kWarps2 * 32, 0, st>>>(
+      Lin, Tin, Lout, Tout, g, (int)n_strips, base, rem, (int)band_rows, (int)n_bands,
+      moved_lr, moved_tb);
+  return cudaGetLastError();
+}
+
+template <int K>
+int occupancy2() {
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, stream2_kernel<K>, kWarps2 * 32, 0) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return b > 0 ? b : 1;
+}
+
+}  // namespace
+
+bool stream2_applies(const Geom &g) { return g.nb == 64 && g.W % 2 == 0 && g.W > 32; }
+
+int64_t stream2_strips(const Geom &g) { return (g.W / 2 + 29) / 30; }
+
+int stream2_occupancy(int k) {
+  switch (k) {
+    case 1: return occupancy2<1>();
+    case 2: return occupancy2<2>();
+    case 4: return occupancy2<4>();
+    default: return occupancy2<8>();
+  }
+}
+
+cudaError_t launch_stream2(const u64 *Lin, const u64 *Tin, u64 *Lout, u64 *Tout, const Geom &g,
+                           int k, int64_t band_rows, u64 *moved_lr, u64 *moved_tb,
+                           cudaStream_t st) {
+  if (!stream2_applies(g) || band_rows < 1 || band_rows > INT32_MAX) return cudaErrorInvalidValue;
+  switch (k) {
+    case 1: return launch2_k<1>(Lin, Tin, Lout, Tout, g, band_rows, moved_lr, moved_tb, st);
+    case 2: return launch2_k<2>(Lin, Tin, Lout, Tout, g, band_rows, moved_lr, moved_tb, st);
+    case 4: return launch2_k<4>(Lin, Tin, Lout, Tout, g, band_rows, moved_lr, moved_tb, st);
+    case 8: return launch2_k<8>(Lin, Tin, Lout, Tout, g, band_rows, moved_lr, moved_tb, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace bml

@@ -229,3 +229,29 @@ def test_set_tiling_rejects_bad_values(lib):
         with pytest.raises(lib.BMLError):
             sim.set_tiling(2, 16)
         sim.set_tiling(1, 0)
+
+
+@pytest.mark.parametrize("M,N", [(100, 4096), (77, 6144), (40, 32768), (5, 2112 * 2)])
+def test_two_words_per_lane_tilings_match_oracle(lib, M, N):
+    """The streaming kernel with two 64-cell words per lane (rows of full
+    words, an even number of them) at every depth and ragged bands."""
+    g0 = random_lattice(M, N, M * 3 + N, 0.18, 0.2)
+    K = 21
+    want, mlr, mtb = oracle.run(g0, K)
+    for k, band in [(1, 7), (2, 16), (4, 33), (8, 19), (8, M)]:
+        with make(lib, M, N, "tblock", k) as sim:
+            sim.set_tiling(k, band, lane_words=2)
+            assert sim.tiling == (k, band, 2)
+            sim.write(g0)
+            sim.step(K)
+            np.testing.assert_array_equal(sim.read(), want, err_msg=str((k, band)))
+            oracle_counts_equal(sim.moved_counts(), mlr, mtb)
+
+
+def test_two_words_per_lane_rejected_where_it_does_not_apply(lib):
+    with make(lib, 16, 100, "tblock", 2) as sim:       # N % 64 != 0
+        with pytest.raises(lib.BMLError):
+            sim.set_tiling(2, 8, lane_words=2)
+    with make(lib, 16, 64 * 33, "tblock", 2) as sim:   # odd number of words
+        with pytest.raises(lib.BMLError):
+            sim.set_tiling(2, 8, lane_words=2)
