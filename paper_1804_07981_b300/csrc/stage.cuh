@@ -78,6 +78,36 @@ __device__ __forceinline__ void stage_step(u64 &inL, u64 &inT, u64 &curT, u64 &c
   inT = oT;
 }
 
+// The same stage with the state read from one set and written to another
+// (callers alternate two sets from row to row, so no value is copied).
+template <bool FULL>
+__device__ __forceinline__ void stage_step_pp(u64 &inL, u64 &inT, const u64 curT, const u64 curLh,
+                                              const u64 prevMv, u64 &nT, u64 &nLh, u64 &nMv,
+                                              const LaneWord &lw, u64 &mvH, u64 &mvV) {
+  const u64 E = FULL ? ~(inL | inT) : (~(inL | inT) & lw.valid);
+  const uint32_t rr = __shfl_sync(BML_FULL_MASK, lo32(E), lw.src_r);
+  u64 Er;
+  if (FULL) {
+    Er = mk64(__funnelshift_r(lo32(E), hi32(E), 1), __funnelshift_r(hi32(E), rr, 1));
+  } else {
+    const uint32_t m = 0u - (rr & 1u);
+    Er = mk64(__funnelshift_r(lo32(E), hi32(E), 1) | (lw.ins_lo & m),
+              (hi32(E) >> 1) | (lw.ins_hi & m));
+  }
+  mvH = inL & Er;
+  const uint32_t send_l = FULL ? hi32(mvH) : ((lw.top_hi ? hi32(mvH) : lo32(mvH)) << lw.top_sh);
+  const uint32_t rl = __shfl_sync(BML_FULL_MASK, send_l, lw.src_l);
+  u64 in = mk64(__funnelshift_l(rl, lo32(mvH), 1), __funnelshift_l(lo32(mvH), hi32(mvH), 1));
+  if (!FULL) in &= lw.valid;
+  const u64 Ep = E ^ in ^ mvH;
+  mvV = curT & Ep;
+  nT = inT;
+  nLh = inL ^ mvH ^ in;
+  nMv = mvV;
+  inT = (curT & ~Ep) | prevMv;
+  inL = curLh;
+}
+
 __device__ __forceinline__ uint32_t popc64(u64 x) {
   return (uint32_t)(__popc(lo32(x)) + __popc(hi32(x)));
 }

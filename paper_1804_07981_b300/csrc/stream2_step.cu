@@ -31,9 +31,10 @@ __device__ __forceinline__ uint32_t fsr(uint32_t lo, uint32_t hi) { return __fun
 __device__ __forceinline__ uint32_t fsl(uint32_t lo, uint32_t hi) { return __funnelshift_l(lo, hi, 1); }
 
 // One stage on the word pair (a, b) of this lane; see stage.cuh for the rule.
-__device__ __forceinline__ void stage_pair(u64 &La, u64 &Lb, u64 &Ta, u64 &Tb, PairState &st,
-                                           int src_l, int src_r, uint32_t &c_lr,
-                                           uint32_t &c_tb, bool cnt_h, bool cnt_v) {
+__device__ __forceinline__ void stage_pair(u64 &La, u64 &Lb, u64 &Ta, u64 &Tb,
+                                           const PairState &st, PairState &nx, int src_l,
+                                           int src_r, uint32_t &c_lr, uint32_t &c_tb,
+                                           bool cnt_h, bool cnt_v) {
   const u64 Ea = ~(La | Ta), Eb = ~(Lb | Tb);
   const uint32_t rr = __shfl_sync(BML_FULL_MASK, lo32(Ea), src_r);
   const u64 Era = mk64(fsr(lo32(Ea), hi32(Ea)), fsr(hi32(Ea), lo32(Eb)));
@@ -48,14 +49,14 @@ __device__ __forceinline__ void stage_pair(u64 &La, u64 &Lb, u64 &Ta, u64 &Tb, P
   const u64 oTa = (st.Ta & ~Epa) | st.Ma, oTb = (st.Tb & ~Epb) | st.Mb;
   if (cnt_h) c_lr += popc64(mHa) + popc64(mHb);
   if (cnt_v) c_tb += popc64(mVa) + popc64(mVb);
+  nx.Ta = Ta;
+  nx.Tb = Tb;
+  nx.La = Lha;
+  nx.Lb = Lhb;
+  nx.Ma = mVa;
+  nx.Mb = mVb;
   La = st.La;
   Lb = st.Lb;
-  st.Ta = Ta;
-  st.Tb = Tb;
-  st.La = Lha;
-  st.Lb = Lhb;
-  st.Ma = mVa;
-  st.Mb = mVb;
   Ta = oTa;
   Tb = oTb;
 }
@@ -96,9 +97,9 @@ __global__ void __launch_bounds__(kWarps2 * 32, K >= 8 ? 2 : 3)
     const size_t pitch = (size_t)g.P;
     size_t roff = (size_t)ld_row * pitch;
 
-    PairState st[K];
+    PairState st[2][K];  // state sets, alternated row by row (P is even)
 #pragma unroll
-    for (int s = 0; s < K; ++s) st[s] = PairState{0, 0, 0, 0, 0, 0};
+    for (int s = 0; s < K; ++s) st[0][s] = st[1][s] = PairState{0, 0, 0, 0, 0, 0};
 
     u64 bLa[P], bLb[P], bTa[P], bTb[P];
 #pragma unroll
@@ -134,7 +135,8 @@ __global__ void __launch_bounds__(kWarps2 * 32, K >= 8 ? 2 : 3)
           }
 #pragma unroll
           for (int s = 0; s < K; ++s)
-            stage_pair(La, Lb, Ta, Tb, st[s], src_l, src_r, c_lr[s], c_tb[s],
+            stage_pair(La, Lb, Ta, Tb, st[u & 1][s], st[(u & 1) ^ 1][s], src_l, src_r, c_lr[s],
+                       c_tb[s],
                        steady || (unsigned)(i - K - s) < (unsigned)B,
                        steady || (unsigned)(i - K - s - 1) < (unsigned)B);
           if (steady || i >= 2 * K) {

@@ -65,20 +65,21 @@ struct Pipe {
 // for band rows (band-relative row i - K - s horizontally, the row above it
 // vertically).
 template <int K, bool FULL, bool PRED>
-__device__ __forceinline__ void row_through(u64 &inL, u64 &inT, Pipe<K> &p, const LaneWord &lw,
-                                            int i, int B, uint32_t (&c_lr)[K],
-                                            uint32_t (&c_tb)[K]) {
+__device__ __forceinline__ void row_through(u64 &inL, u64 &inT, const Pipe<K> &src, Pipe<K> &dst,
+                                            const LaneWord &lw, int i, int B,
+                                            uint32_t (&c_lr)[K], uint32_t (&c_tb)[K]) {
 #pragma unroll
   for (int s = 0; s < K; ++s) {
     u64 mvH, mvV;
-    stage_step<FULL>(inL, inT, p.curT[s], p.curLh[s], p.prevMv[s], lw, mvH, mvV);
+    stage_step_pp<FULL>(inL, inT, src.curT[s], src.curLh[s], src.prevMv[s], dst.curT[s],
+                        dst.curLh[s], dst.prevMv[s], lw, mvH, mvV);
     if (!PRED || (unsigned)(i - K - s) < (unsigned)B) c_lr[s] += popc64(mvH);
     if (!PRED || (unsigned)(i - K - s - 1) < (unsigned)B) c_tb[s] += popc64(mvV);
   }
 }
 
 template <int K, bool FULL>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, 4)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, K >= 8 ? 3 : 4)
     stream_kernel(const u64 *__restrict__ Lin, const u64 *__restrict__ Tin,
                   u64 *__restrict__ Lout, u64 *__restrict__ Tout, Geom g, StripPlan sp,
                   int band_rows, int n_bands, u64 *__restrict__ moved_lr,
@@ -139,9 +140,12 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 4)
     u64 *Lo = Lout + w + (size_t)r0 * pitch;
     u64 *To = Tout + w + (size_t)r0 * pitch;
 
-    Pipe<K> p;
+    Pipe<K> pp[2];  // state sets, alternated row by row (P is even)
 #pragma unroll
-    for (int s = 0; s < K; ++s) p.curT[s] = p.curLh[s] = p.prevMv[s] = 0;
+    for (int s = 0; s < K; ++s) {
+      pp[0].curT[s] = pp[0].curLh[s] = pp[0].prevMv[s] = 0;
+      pp[1].curT[s] = pp[1].curLh[s] = pp[1].prevMv[s] = 0;
+    }
 
     auto advance = [&]() {
       if (++ld_row == M) {
@@ -183,9 +187,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 4)
             advance();
           }
           if (steady)
-            row_through<K, FULL, false>(inL, inT, p, lw, i, B, c_lr, c_tb);
+            row_through<K, FULL, false>(inL, inT, pp[u & 1], pp[(u & 1) ^ 1], lw, i, B, c_lr,
+                                        c_tb);
           else
-            row_through<K, FULL, true>(inL, inT, p, lw, i, B, c_lr, c_tb);
+            row_through<K, FULL, true>(inL, inT, pp[u & 1], pp[(u & 1) ^ 1], lw, i, B, c_lr,
+                                       c_tb);
           // row i - 2K of the band leaves the last stage
           if ((steady || i >= 2 * K) && own) {
             const size_t off = (size_t)(i - 2 * K) * pitch;
