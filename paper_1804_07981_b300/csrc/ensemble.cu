@@ -192,10 +192,15 @@ __device__ void process_tile(const EnsParams &p, int t, long long step0, int par
   const u64 *Lp = inbase + (size_t)ld_row * pitch;
   u64 *Lo = outbase + (size_t)gr.r0 * pitch;
 
-  u64 curT[K], curLh[K], prevMv[K];
+  // two state sets, alternated row by row (PF is even), so no value is copied
+  u64 curT[2][K], curLh[2][K], prevMv[2][K];
   uint32_t c_lr[K], c_tb[K];
 #pragma unroll
-  for (int s = 0; s < K; ++s) curT[s] = curLh[s] = prevMv[s] = 0, c_lr[s] = c_tb[s] = 0;
+  for (int s = 0; s < K; ++s) {
+    curT[0][s] = curLh[0][s] = prevMv[0][s] = 0;
+    curT[1][s] = curLh[1][s] = prevMv[1][s] = 0;
+    c_lr[s] = c_tb[s] = 0;
+  }
 
   u64 bufL[PF], bufT[PF];
 #pragma unroll
@@ -230,10 +235,12 @@ __device__ void process_tile(const EnsParams &p, int t, long long step0, int par
             Lp += pitch;
           }
         }
+        const int a = u & 1, b = a ^ 1;
 #pragma unroll
         for (int s = 0; s < K; ++s) {
           u64 mvH, mvV;
-          stage_step<false>(inL, inT, curT[s], curLh[s], prevMv[s], lw, mvH, mvV);
+          stage_step_pp<false>(inL, inT, curT[a][s], curLh[a][s], prevMv[a][s], curT[b][s],
+                               curLh[b][s], prevMv[b][s], lw, mvH, mvV);
           if (steady || (unsigned)(i - K - s) < (unsigned)len) c_lr[s] += popc64(mvH);
           if (steady || (unsigned)(i - K - s - 1) < (unsigned)len) c_tb[s] += popc64(mvV);
         }
@@ -273,7 +280,7 @@ __device__ void process_tile(const EnsParams &p, int t, long long step0, int par
 }
 
 template <int K>
-__global__ void __launch_bounds__(kEnsWarps * 32, 4) ens_kernel(EnsParams p) {
+__global__ void __launch_bounds__(kEnsWarps * 32, K >= 8 ? 3 : 4) ens_kernel(EnsParams p) {
   const int lane = threadIdx.x & 31;
   const int nwarps = gridDim.x * kEnsWarps;
   const int wid = blockIdx.x * kEnsWarps + (threadIdx.x >> 5);
