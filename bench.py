@@ -50,7 +50,7 @@ SM_MAX_MHZ = 2032.0
 # DRAM bytes (read + write, as counted by ncu for one launch) per cell, from
 # the captures summarised in profiles/ (16384 x 32768 cases); scaled by the
 # cell count of the run
-TRAFFIC_PER_CELL = {"stream_kernel<8>": 0.4252, "fused_rows_kernel": 0.4068}
+TRAFFIC_PER_CELL = {"stream2_kernel<8>": 0.4299, "fused_rows_kernel": 0.4068}
 
 
 def _peaks():

@@ -293,19 +293,30 @@ int autotune(bml_sim *s) {
   const double cells = (double)s->g.M * (double)s->g.N;
   const int reps = cells > 1e8 ? 3 : (cells > 1e6 ? 10 : 20);
   int rc = BML_OK;
-  for (const auto &c : cands) {
-    {
-      const int k = c.k;
-      const int64_t b = c.band;
-      s->block_k = k;
-      s->band_rows = b;
+  // pass 1: every candidate, few repetitions; pass 2: the best four again
+  // with more repetitions, so that near-ties are decided by a steadier time
+  std::vector<std::pair<double, size_t>> scored;
+  for (int pass = 0; pass < 2; ++pass) {
+    std::vector<size_t> which;
+    if (pass == 0) {
+      for (size_t i = 0; i < cands.size(); ++i) which.push_back(i);
+    } else {
+      std::sort(scored.begin(), scored.end());
+      for (size_t i = 0; i < scored.size() && i < 4; ++i) which.push_back(scored[i].second);
+      scored.clear();
+    }
+    const int r = pass == 0 ? reps : 3 * reps;
+    for (size_t ci : which) {
+      const Tiling &c = cands[ci];
+      s->block_k = c.k;
+      s->band_rows = c.band;
       s->lane_words = c.lane_words;
       u64 *lr = (u64 *)s->scratch.ptr, *tb = lr + 8;
       // warm-up (non-committing: reads cur, writes the other buffer)
-      if ((rc = enqueue_steps(s, k, lr, tb, false))) goto done;
+      if ((rc = enqueue_steps(s, c.k, lr, tb, false))) goto done;
       cudaEventRecord(e0, s->st);
-      for (int r = 0; r < reps; ++r)
-        if ((rc = enqueue_steps(s, k, lr, tb, false))) goto done;
+      for (int q = 0; q < r; ++q)
+        if ((rc = enqueue_steps(s, c.k, lr, tb, false))) goto done;
       cudaEventRecord(e1, s->st);
       if (cudaEventSynchronize(e1) != cudaSuccess) {
         rc = fail(BML_ECUDA, "autotune: %s", cudaGetErrorString(cudaGetLastError()));
@@ -313,11 +324,12 @@ int autotune(bml_sim *s) {
       }
       float ms = 0;
       cudaEventElapsedTime(&ms, e0, e1);
-      const double per_step = (double)ms / (reps * k);
-      if (per_step < best) {
+      const double per_step = (double)ms / (r * c.k);
+      scored.push_back({per_step, ci});
+      if (pass == 1 && per_step < best) {
         best = per_step;
-        best_k = k;
-        best_b = b;
+        best_k = c.k;
+        best_b = c.band;
         best_lw = c.lane_words;
       }
     }
