@@ -71,3 +71,35 @@ def test_null_handles_are_rejected(lib):
         lib.bml_moved_counts(None, 0, 1)
     assert lib.bml_steps_done(None) == -1
     lib.bml_destroy(None)
+
+
+def test_allocation_failure_reports_enomem(lib):
+    """An allocator that refuses memory makes creation fail with BML_ENOMEM
+    (no CUDA call precedes the first allocation, so this runs on CPU)."""
+    calls = []
+
+    @lib.ALLOC_FN
+    def refuse(nbytes, stream, ctx):
+        calls.append(nbytes)
+        return None
+
+    @lib.FREE_FN
+    def never(ptr, nbytes, stream, ctx):
+        raise AssertionError("nothing was allocated")
+
+    lib._check(lib._lib_set_allocator(refuse, never, None))
+    try:
+        with pytest.raises(lib.BMLError) as e:
+            lib.bml_create_ex(64, 64, 1, 0.1, 0.1, kernel=lib.BML_KERNEL_FUSED)
+        assert e.value.code == lib.BML_ENOMEM
+        assert len(calls) == 1
+    finally:
+        lib.use_torch_allocator(False)
+
+
+def test_set_allocator_needs_both_functions(lib):
+    @lib.ALLOC_FN
+    def a(nbytes, stream, ctx):
+        return None
+    with pytest.raises(lib.BMLError):
+        lib._check(lib._lib_set_allocator(a, lib.FREE_FN(), None))

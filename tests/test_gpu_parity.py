@@ -255,3 +255,40 @@ def test_two_words_per_lane_rejected_where_it_does_not_apply(lib):
     with make(lib, 16, 64 * 33, "tblock", 2) as sim:   # odd number of words
         with pytest.raises(lib.BMLError):
             sim.set_tiling(2, 8, lane_words=2)
+
+
+@pytest.mark.parametrize("fail_at", [1, 2, 3, 5])
+def test_allocation_failure_mid_creation_frees_everything(lib, fail_at):
+    """The n-th device allocation fails: creation returns BML_ENOMEM and every
+    allocation made before it is released (no leak); the next creation with
+    a working allocator succeeds."""
+    import torch
+    live = {}
+    count = [0]
+
+    @lib.ALLOC_FN
+    def alloc(nbytes, stream, ctx):
+        count[0] += 1
+        if count[0] == fail_at:
+            return None
+        p = torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(),
+                                               stream or 0)
+        live[p] = nbytes
+        return p
+
+    @lib.FREE_FN
+    def free(ptr, nbytes, stream, ctx):
+        assert ptr in live
+        del live[ptr]
+        torch.cuda.caching_allocator_delete(ptr)
+
+    lib._check(lib._lib_set_allocator(alloc, free, None))
+    try:
+        with pytest.raises(lib.BMLError) as e:
+            lib.bml_create_ex(64, 300, 1, 0.1, 0.1, kernel=lib.BML_KERNEL_TBLOCK, block_k=2)
+        assert e.value.code == lib.BML_ENOMEM
+        assert not live, "allocations leaked"
+    finally:
+        lib.use_torch_allocator(False)
+    with make(lib, 64, 300, "tblock", 2) as sim:
+        sim.step(3)
