@@ -41,16 +41,17 @@ STEPS_PER_BENCH_STEP = 8
 BYTES_PER_CELL_STEP = 0.5  # 2 bits read + 2 bits written per cell per step
 WORKLOAD = "bml_32768x32768_rho0.38"
 # 32-bit integer ALU operations the bitplane step needs per 64-cell word:
-# E, Er, mvH, in, Lh, E', mvV, T' (two 32-bit operations each) and the two
-# count additions; popcounts run on another pipe and are not counted
-ALU_OPS_PER_CELL_STEP = 18.0 / 64.0
+# E, Er, mvH, in, Lh, mvV, T' (two 32-bit operations each; mvV = T_{x-1} &
+# ~(Lh_x | T_x) is one three-input operation) and the two count additions;
+# popcounts run on another pipe and are not counted
+ALU_OPS_PER_CELL_STEP = 16.0 / 64.0
 SMS = 148
 ALU_LANES_PER_SM_CLK = 64  # integer ALU pipe: 2 warp instructions per clock per SM
 SM_MAX_MHZ = 2032.0
 # DRAM bytes (read + write, as counted by ncu for one launch) per cell, from
 # the captures summarised in profiles/ (16384 x 32768 cases); scaled by the
 # cell count of the run
-TRAFFIC_PER_CELL = {"stream2_kernel<8>": 0.4299, "fused_rows_kernel": 0.4068}
+TRAFFIC_PER_CELL = {"fused_rows_kernel": 0.4068}
 
 
 def _peaks():

@@ -5,11 +5,13 @@
 //   mvH_x = L_x & Er_x            LR cars that leave (Er[j] = E[j+1])
 //   in_x  = mvH_x shifted one column right (the cells they enter)
 //   Lh_x  = L_x ^ mvH_x ^ in_x     horizontal rule on row x
-//   E'_x  = E_x ^ in_x ^ mvH_x     EMPTY after the horizontal phase
+//   E'_x  = ~(Lh_x | T_x)          EMPTY after the horizontal phase (TB cars
+//                                  do not move in it)
 //   mvV_{x-1} = T_{x-1} & E'_x     TB cars of row x-1 that move down
-//   emitted row x-1: L = Lh_{x-1}, T = (T_{x-1} & ~E'_x) | mvV_{x-2}
+//   emitted row x-1: L = Lh_{x-1}, T = (T_{x-1} & ~mvV_{x-1}) | mvV_{x-2}
 // (the cars entering row x-1 from above are mvV_{x-2}, computed one row
-// earlier).  Horizontal neighbours come from two 32-bit warp shuffles: the
+// earlier).  Written this way E' is never formed: mvV and the emitted T are
+// one three-input logic operation each.  Horizontal neighbours come from two 32-bit warp shuffles: the
 // right neighbour's low half of E (bit 0 = the cell right of this word) and
 // the left neighbour's half of mvH holding its last cell, pre-aligned to bit
 // 31.
@@ -67,9 +69,8 @@ __device__ __forceinline__ void stage_step(u64 &inL, u64 &inT, u64 &curT, u64 &c
   u64 in = mk64(__funnelshift_l(rl, lo32(mvH), 1), __funnelshift_l(lo32(mvH), hi32(mvH), 1));
   if (!FULL) in &= lw.valid;
   const u64 Lh = inL ^ mvH ^ in;
-  const u64 Ep = E ^ in ^ mvH;
-  mvV = curT & Ep;
-  const u64 oT = (curT & ~Ep) | prevMv;
+  mvV = curT & ~(Lh | inT);
+  const u64 oT = (curT & ~mvV) | prevMv;
   const u64 oL = curLh;
   curT = inT;
   curLh = Lh;
@@ -99,12 +100,11 @@ __device__ __forceinline__ void stage_step_pp(u64 &inL, u64 &inT, const u64 curT
   const uint32_t rl = __shfl_sync(BML_FULL_MASK, send_l, lw.src_l);
   u64 in = mk64(__funnelshift_l(rl, lo32(mvH), 1), __funnelshift_l(lo32(mvH), hi32(mvH), 1));
   if (!FULL) in &= lw.valid;
-  const u64 Ep = E ^ in ^ mvH;
-  mvV = curT & Ep;
-  nT = inT;
   nLh = inL ^ mvH ^ in;
+  mvV = curT & ~(nLh | inT);
+  nT = inT;
   nMv = mvV;
-  inT = (curT & ~Ep) | prevMv;
+  inT = (curT & ~mvV) | prevMv;
   inL = curLh;
 }
 

@@ -10,6 +10,12 @@
 // cone), lanes 1..owned are stored and counted (up to 30 pairs per warp).
 // Per stage and row a lane makes two 32-bit shuffles for two words: the right
 // lane's low half of E and the left lane's high half of the LR move mask.
+//
+// Moved-car counts: one 32-bit register per stage and lane holds the LR moves
+// in its low 16 bits and the TB moves in its high 16 bits (a lane moves at
+// most 128 cars of each kind per row, so a field cannot overflow within 511
+// rows); the kernel flushes both fields to the block's counters every 256
+// rows.  This keeps the depth-8 kernel within 255 registers without spills.
 #include "stage.cuh"
 
 namespace bml {
@@ -33,8 +39,8 @@ __device__ __forceinline__ uint32_t fsl(uint32_t lo, uint32_t hi) { return __fun
 // One stage on the word pair (a, b) of this lane; see stage.cuh for the rule.
 __device__ __forceinline__ void stage_pair(u64 &La, u64 &Lb, u64 &Ta, u64 &Tb,
                                            const PairState &st, PairState &nx, int src_l,
-                                           int src_r, uint32_t &c_lr, uint32_t &c_tb,
-                                           bool cnt_h, bool cnt_v) {
+                                           int src_r, uint32_t &cnt, bool cnt_h,
+                                           bool cnt_v) {
   const u64 Ea = ~(La | Ta), Eb = ~(Lb | Tb);
   const uint32_t rr = __shfl_sync(BML_FULL_MASK, lo32(Ea), src_r);
   const u64 Era = mk64(fsr(lo32(Ea), hi32(Ea)), fsr(hi32(Ea), lo32(Eb)));
@@ -44,11 +50,10 @@ __device__ __forceinline__ void stage_pair(u64 &La, u64 &Lb, u64 &Ta, u64 &Tb,
   const u64 ina = mk64(fsl(rl, lo32(mHa)), fsl(lo32(mHa), hi32(mHa)));
   const u64 inb = mk64(fsl(hi32(mHa), lo32(mHb)), fsl(lo32(mHb), hi32(mHb)));
   const u64 Lha = La ^ mHa ^ ina, Lhb = Lb ^ mHb ^ inb;
-  const u64 Epa = Ea ^ ina ^ mHa, Epb = Eb ^ inb ^ mHb;
-  const u64 mVa = st.Ta & Epa, mVb = st.Tb & Epb;
-  const u64 oTa = (st.Ta & ~Epa) | st.Ma, oTb = (st.Tb & ~Epb) | st.Mb;
-  if (cnt_h) c_lr += popc64(mHa) + popc64(mHb);
-  if (cnt_v) c_tb += popc64(mVa) + popc64(mVb);
+  const u64 mVa = st.Ta & ~(Lha | Ta), mVb = st.Tb & ~(Lhb | Tb);
+  const u64 oTa = (st.Ta & ~mVa) | st.Ma, oTb = (st.Tb & ~mVb) | st.Mb;
+  if (cnt_h) cnt += popc64(mHa) + popc64(mHb);
+  if (cnt_v) cnt += (popc64(mVa) + popc64(mVb)) << 16;
   nx.Ta = Ta;
   nx.Tb = Tb;
   nx.La = Lha;
@@ -59,6 +64,24 @@ __device__ __forceinline__ void stage_pair(u64 &La, u64 &Lb, u64 &Ta, u64 &Tb,
   Lb = st.Lb;
   Ta = oTa;
   Tb = oTb;
+}
+
+// Adds the packed per-lane counts of every stage (lanes that own no pair
+// contribute nothing) to the block's counters and clears them.
+template <int K>
+__device__ __forceinline__ void flush_counts(uint32_t (&cnt)[K], bool own, int lane,
+                                             unsigned long long *s_cnt) {
+#pragma unroll
+  for (int s = 0; s < K; ++s) {
+    const uint32_t c = own ? cnt[s] : 0u;
+    const uint32_t a = __reduce_add_sync(BML_FULL_MASK, c & 0xffffu);
+    const uint32_t b = __reduce_add_sync(BML_FULL_MASK, c >> 16);
+    if (lane == 0) {
+      if (a) atomicAdd(&s_cnt[s], (unsigned long long)a);
+      if (b) atomicAdd(&s_cnt[K + s], (unsigned long long)b);
+    }
+    cnt[s] = 0;
+  }
 }
 
 template <int K>
@@ -73,9 +96,10 @@ __global__ void __launch_bounds__(kWarps2 * 32, K >= 8 ? 2 : 3)
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int tile = blockIdx.x * kWarps2 + (threadIdx.x >> 5);
-  uint32_t c_lr[K], c_tb[K];
+  uint32_t cnt[K];  // per stage: LR moves (bits 0-15), TB moves (bits 16-31)
 #pragma unroll
-  for (int s = 0; s < K; ++s) c_lr[s] = c_tb[s] = 0;
+  for (int s = 0; s < K; ++s) cnt[s] = 0;
+  bool own = false;
 
   if (tile < n_strips * n_bands) {
     const int strip = tile % n_strips, band = tile / n_strips;
@@ -85,7 +109,7 @@ __global__ void __launch_bounds__(kWarps2 * 32, K >= 8 ? 2 : 3)
     int pw = (first - 1 + lane) % WP;
     if (pw < 0) pw += WP;
     const int wa = 2 * pw;
-    const bool own = lane >= 1 && lane <= owned;
+    own = lane >= 1 && lane <= owned;
     const int src_l = lane > 0 ? lane - 1 : 0, src_r = lane < 31 ? lane + 1 : 31;
 
     const int r0 = band * band_rows;
@@ -117,6 +141,7 @@ __global__ void __launch_bounds__(kWarps2 * 32, K >= 8 ? 2 : 3)
       }
     }
     for (int i0 = 0; i0 < n_in; i0 += P) {
+      if ((i0 & 255) == 0 && i0 > 0) flush_counts<K>(cnt, own, lane, s_cnt);
       const bool steady = i0 >= 2 * K && i0 + P <= B + K;
 #pragma unroll
       for (int u = 0; u < P; ++u) {
@@ -135,8 +160,7 @@ __global__ void __launch_bounds__(kWarps2 * 32, K >= 8 ? 2 : 3)
           }
 #pragma unroll
           for (int s = 0; s < K; ++s)
-            stage_pair(La, Lb, Ta, Tb, st[u & 1][s], st[(u & 1) ^ 1][s], src_l, src_r, c_lr[s],
-                       c_tb[s],
+            stage_pair(La, Lb, Ta, Tb, st[u & 1][s], st[(u & 1) ^ 1][s], src_l, src_r, cnt[s],
                        steady || (unsigned)(i - K - s) < (unsigned)B,
                        steady || (unsigned)(i - K - s - 1) < (unsigned)B);
           if (steady || i >= 2 * K) {
@@ -149,20 +173,8 @@ __global__ void __launch_bounds__(kWarps2 * 32, K >= 8 ? 2 : 3)
         }
       }
     }
-    if (!own) {
-#pragma unroll
-      for (int s = 0; s < K; ++s) c_lr[s] = c_tb[s] = 0;
-    }
   }
-#pragma unroll
-  for (int s = 0; s < K; ++s) {
-    const uint32_t a = __reduce_add_sync(BML_FULL_MASK, c_lr[s]);
-    const uint32_t b = __reduce_add_sync(BML_FULL_MASK, c_tb[s]);
-    if (lane == 0) {
-      if (a) atomicAdd(&s_cnt[s], (unsigned long long)a);
-      if (b) atomicAdd(&s_cnt[K + s], (unsigned long long)b);
-    }
-  }
+  flush_counts<K>(cnt, own, lane, s_cnt);
   __syncthreads();
   if (threadIdx.x < K) {
     if (s_cnt[threadIdx.x]) atomicAdd(moved_lr + threadIdx.x, s_cnt[threadIdx.x]);

@@ -12,10 +12,10 @@
 //     mvH_x = L_x & Er_x            LR cars that leave (Er[j] = E[j+1])
 //     in_x  = mvH_x shifted one column right (the cells they enter)
 //     Lh_x  = L_x ^ mvH_x ^ in_x     horizontal rule on row x
-//     E'_x  = E_x ^ in_x ^ mvH_x     EMPTY after the horizontal phase
+//     E'_x  = ~(Lh_x | T_x)          EMPTY after the horizontal phase
 //     mvV_{x-1} = T_{x-1} & E'_x     TB cars of row x-1 that move down
 //   emit row x-1 of state s+1:
-//     L = Lh_{x-1},  T = (T_{x-1} & ~E'_x) | mvV_{x-2}
+//     L = Lh_{x-1},  T = (T_{x-1} & ~mvV_{x-1}) | mvV_{x-2}
 //
 // since the cars entering row x-1 from above are exactly mvV_{x-2}, computed
 // one row earlier.  Each stage lags one row behind the previous one and keeps

@@ -248,6 +248,26 @@ def test_two_words_per_lane_tilings_match_oracle(lib, M, N):
             oracle_counts_equal(sim.moved_counts(), mlr, mtb)
 
 
+@pytest.mark.parametrize("band", [300, 700, 12000])
+def test_two_words_per_lane_tall_bands_count_exactly(lib, band):
+    """Bands taller than the 16-bit per-lane count fields can hold without a
+    flush: free flow at density 0.2 moves about 13 LR and 13 TB cars per lane
+    (128 cells) and row, so one 12000-row band puts about 150000 moves of
+    each kind on every lane and stage.  Lattice and every count against the
+    oracle."""
+    import os
+    M, N, K = 12000, 4096, 16
+    g0 = random_lattice(M, N, 4242, 0.1, 0.1)
+    want, mlr, mtb = oracle.run(g0, K, threads=os.cpu_count() or 1)
+    assert mlr.min() // (N // 128) > 65535    # per lane of a one-band tile, every step
+    with make(lib, M, N, "tblock", 8) as sim:
+        sim.set_tiling(8, band, lane_words=2)
+        sim.write(g0)
+        sim.step(K)
+        np.testing.assert_array_equal(sim.read(), want)
+        oracle_counts_equal(sim.moved_counts(), mlr, mtb)
+
+
 def test_two_words_per_lane_rejected_where_it_does_not_apply(lib):
     with make(lib, 16, 100, "tblock", 2) as sim:       # N % 64 != 0
         with pytest.raises(lib.BMLError):
