@@ -40,6 +40,10 @@ DENSITY = 0.38
 STEPS_PER_BENCH_STEP = 8
 BYTES_PER_CELL_STEP = 0.5  # 2 bits read + 2 bits written per cell per step
 WORKLOAD = "bml_32768x32768_rho0.38"
+
+
+def workload_name(M, N):
+    return "bml_%dx%d_rho%.2f" % (M, N, DENSITY)
 # 32-bit integer ALU operations the bitplane step needs per 64-cell word:
 # E, Er, mvH, in, Lh, mvV, T' (two 32-bit operations each; mvV = T_{x-1} &
 # ~(Lh_x | T_x) is one three-input operation) and the two count additions;
@@ -375,7 +379,7 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u64 bitplanes" if kernel_id != bml.BML_KERNEL_BYTE else "u8",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "M": M, "N": N, "density": DENSITY,
+            "config": {"workload": workload_name(M, N), "M": M, "N": N, "density": DENSITY,
                        "seed": 1, "lattice_steps_per_step": STEPS_PER_BENCH_STEP,
                        "kernel": {0: "auto", 1: "byte", 2: "bitplane", 3: "fused",
                                   4: "tblock"}[kernel_id],

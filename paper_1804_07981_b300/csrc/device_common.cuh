@@ -21,6 +21,21 @@ __device__ __forceinline__ int word_top(int64_t w, const Geom &g) {
   return w == g.W - 1 ? g.nb - 1 : 63;
 }
 
+// Asynchronous 16-byte copy global -> shared (bypassing L1), its commit and
+// its wait (all but the N most recent committed groups complete; the copied
+// bytes are then visible to the issuing thread).
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // 128-bit read-only load / streaming store of two consecutive words.
 __device__ __forceinline__ void ld2(const u64 *p, u64 &a, u64 &b) {
   const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2 *>(p));

@@ -16,6 +16,11 @@
 // most 128 cars of each kind per row, so a field cannot overflow within 511
 // rows); the kernel flushes both fields to the block's counters every 256
 // rows.  This keeps the depth-8 kernel within 255 registers without spills.
+//
+// Input rows reach the warp through a ring of kRing row slots in shared
+// memory, filled kAhead rows ahead with cp.async (16 bytes per lane and
+// plane); a slot is refilled two rows after it was last read.  The prefetch
+// holds no registers and its wait is explicit.
 #include "stage.cuh"
 
 namespace bml {
@@ -23,11 +28,12 @@ namespace bml {
 namespace {
 
 constexpr int kWarps2 = 4;
+constexpr int kRing = 8;   // row slots per warp
+constexpr int kAhead = 6;  // rows in flight ahead of the row being consumed
+static_assert(kAhead <= kRing - 2 && (kRing & (kRing - 1)) == 0, "ring layout");
 
-template <int K>
-struct PF2 {
-  static constexpr int value = K >= 4 ? 2 : 4;
-};
+// Rows per unrolled chunk: even, since the stage state sets alternate by row.
+constexpr int kChunk = 2;
 
 struct PairState {
   u64 Ta, Tb, La, Lb, Ma, Mb;  // T_{x-1}, Lh_{x-1}, mvV_{x-2} of both words
@@ -90,8 +96,9 @@ __global__ void __launch_bounds__(kWarps2 * 32, K >= 8 ? 2 : 3)
                    u64 *__restrict__ Lout, u64 *__restrict__ Tout, Geom g, int n_strips,
                    int base, int rem, int band_rows, int n_bands, u64 *__restrict__ moved_lr,
                    u64 *__restrict__ moved_tb) {
-  constexpr int P = PF2<K>::value;
+  constexpr int P = kChunk;
   __shared__ unsigned long long s_cnt[2 * K];
+  __shared__ __align__(16) ulonglong2 s_ring[kWarps2][kRing][2][32];  // [warp][slot][plane][lane]
   for (int t = threadIdx.x; t < 2 * K; t += blockDim.x) s_cnt[t] = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31;
@@ -125,13 +132,13 @@ __global__ void __launch_bounds__(kWarps2 * 32, K >= 8 ? 2 : 3)
 #pragma unroll
     for (int s = 0; s < K; ++s) st[0][s] = st[1][s] = PairState{0, 0, 0, 0, 0, 0};
 
-    u64 bLa[P], bLb[P], bTa[P], bTb[P];
+    ulonglong2 (*ring)[2][32] = s_ring[threadIdx.x >> 5];
+    // rows 0 .. kAhead-1 in flight, one commit group per row (empty past n_in)
 #pragma unroll
-    for (int u = 0; u < P; ++u) {
-      bLa[u] = bLb[u] = bTa[u] = bTb[u] = 0;
+    for (int u = 0; u < kAhead; ++u) {
       if (u < n_in) {
-        ld2(Lin + roff + wa, bLa[u], bLb[u]);
-        ld2(Tin + roff + wa, bTa[u], bTb[u]);
+        cp_async16(&ring[u][0][lane], Lin + roff + wa);
+        cp_async16(&ring[u][1][lane], Tin + roff + wa);
         if (++ld_row == M) {
           ld_row = 0;
           roff = 0;
@@ -139,6 +146,7 @@ __global__ void __launch_bounds__(kWarps2 * 32, K >= 8 ? 2 : 3)
           roff += pitch;
         }
       }
+      cp_async_commit();
     }
     for (int i0 = 0; i0 < n_in; i0 += P) {
       if ((i0 & 255) == 0 && i0 > 0) flush_counts<K>(cnt, own, lane, s_cnt);
@@ -147,10 +155,10 @@ __global__ void __launch_bounds__(kWarps2 * 32, K >= 8 ? 2 : 3)
       for (int u = 0; u < P; ++u) {
         const int i = i0 + u;
         if (steady || i < n_in) {
-          u64 La = bLa[u], Lb = bLb[u], Ta = bTa[u], Tb = bTb[u];
-          if (i + P < n_in) {
-            ld2(Lin + roff + wa, bLa[u], bLb[u]);
-            ld2(Tin + roff + wa, bTa[u], bTb[u]);
+          if (i + kAhead < n_in) {
+            const int sl = (i + kAhead) & (kRing - 1);
+            cp_async16(&ring[sl][0][lane], Lin + roff + wa);
+            cp_async16(&ring[sl][1][lane], Tin + roff + wa);
             if (++ld_row == M) {
               ld_row = 0;
               roff = 0;
@@ -158,6 +166,11 @@ __global__ void __launch_bounds__(kWarps2 * 32, K >= 8 ? 2 : 3)
               roff += pitch;
             }
           }
+          cp_async_commit();
+          cp_async_wait<kAhead>();  // row i has landed
+          const ulonglong2 vL = ring[i & (kRing - 1)][0][lane];
+          const ulonglong2 vT = ring[i & (kRing - 1)][1][lane];
+          u64 La = vL.x, Lb = vL.y, Ta = vT.x, Tb = vT.y;
 #pragma unroll
           for (int s = 0; s < K; ++s)
             stage_pair(La, Lb, Ta, Tb, st[u & 1][s], st[(u & 1) ^ 1][s], src_l, src_r, cnt[s],
