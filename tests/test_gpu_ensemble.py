@@ -51,6 +51,28 @@ def test_ensemble_mixed_shapes_match_oracle(lib, block_k, band):
         np.testing.assert_array_equal(ens.read(5), want[5])
 
 
+def test_ensemble_tall_bands_count_exactly(lib):
+    """One band of 16000 rows per lattice group: at density 0.24 about 6 LR
+    and 6 TB cars move per lane (64 cells) and row, over 90000 per lane and
+    stage over the band, more than one 16-bit count field holds between
+    flushes.  Lattices and traces against the oracle."""
+    M = np.array([16000, 16000, 15999, 16000])
+    N = np.array([64, 128, 100, 2048])
+    seeds = np.arange(11, 15, dtype=np.uint64)
+    plr, ptb = np.full(4, 0.12), np.full(4, 0.12)
+    K = 16
+    want, wlr, wtb = oracle_ensemble(M, N, seeds, plr, ptb, K)
+    assert wlr[0].min() > 65535        # lattice 0: one lane per row
+    with lib.Ensemble(M, N, seeds, plr, ptb, block_k=8, band_rows=16000) as ens:
+        ens.step(K)
+        got = ens.read_all()
+        lr, tb = ens.traces()
+    for l in range(len(M)):
+        np.testing.assert_array_equal(got[l], want[l], err_msg="lattice %d" % l)
+    np.testing.assert_array_equal(lr, wlr)
+    np.testing.assert_array_equal(tb, wtb)
+
+
 @pytest.mark.parametrize("M,N", [(1, 12), (2, 6), (3, 4), (4, 3), (6, 2), (12, 1), (1, 11),
                                  (3, 3), (2, 5), (5, 2), (1, 1), (1, 2), (2, 1), (2, 2)])
 def test_ensemble_exhaustive_tiny_lattices(lib, M, N):
