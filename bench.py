@@ -53,9 +53,9 @@ SMS = 148
 ALU_LANES_PER_SM_CLK = 64  # integer ALU pipe: 2 warp instructions per clock per SM
 SM_MAX_MHZ = 2032.0
 # DRAM bytes (read + write, as counted by ncu for one launch) per cell, from
-# the captures summarised in profiles/ (16384 x 32768 cases); scaled by the
-# cell count of the run
-TRAFFIC_PER_CELL = {"fused_rows_kernel": 0.4068}
+# the captures summarised in profiles/ (stream2_kernel<8>: 32768 x 32768;
+# fused_rows_kernel: 16384 x 32768); scaled by the cell count of the run
+TRAFFIC_PER_CELL = {"stream2_kernel<8>": 0.4700, "fused_rows_kernel": 0.4068}
 
 
 def _peaks():
