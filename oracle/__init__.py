@@ -7,7 +7,7 @@ this package imports nothing from the product.
 
 `bml_oracle.c` is the plain serial byte-per-cell simulator (Marzolla 2018,
 Sec. 2 rules, Sec. 3 layout and double buffer, Sec. 4 row-parallel loop for
-the threaded mode).  `mlp.py` is the fp64 reference for the surrogate
+the threaded mode), with Model II (Sec. 2) in `run_model`.  `mlp.py` is the fp64 reference for the surrogate
 network.  `features.py` holds the trace features and labels the surrogate
 is trained on.
 """
@@ -61,6 +61,9 @@ def _load():
             lib.oracle_phase.restype = i64
             lib.oracle_run_batch.argtypes = [vp, i64, i64, i64, i64, vp, vp]
             lib.oracle_run_batch.restype = ctypes.c_int
+            lib.oracle_run_model.argtypes = [vp, i64, i64, i64, ctypes.c_int, u64, i64,
+                                             vp, vp, ctypes.c_int]
+            lib.oracle_run_model.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -99,6 +102,23 @@ def run(g: np.ndarray, K: int, threads: int = 1):
     rc = _load().oracle_run(_ptr(g), M, N, K, _ptr(mlr), _ptr(mtb), threads)
     if rc != 0:
         raise RuntimeError("oracle_run failed (%d)" % rc)
+    return g, mlr, mtb
+
+
+def run_model(g: np.ndarray, K: int, model: int, tie_seed: int = 0, t0: int = 0,
+              threads: int = 1):
+    """Advance a copy of g by K steps of Model II (model=2, the only one
+    accepted); the first step has index t0 (it selects the tie-break bits).
+
+    Returns (lattice after K steps, moved_lr[K], moved_tb[K]) as int64."""
+    g = np.ascontiguousarray(g, dtype=np.uint8).copy()
+    M, N = g.shape
+    mlr = np.zeros(K, dtype=np.int64)
+    mtb = np.zeros(K, dtype=np.int64)
+    rc = _load().oracle_run_model(_ptr(g), M, N, K, model, tie_seed, t0, _ptr(mlr),
+                                  _ptr(mtb), threads)
+    if rc != 0:
+        raise RuntimeError("oracle_run_model failed (%d)" % rc)
     return g, mlr, mtb
 
 

@@ -36,6 +36,8 @@
  *   cell = LR if u < t_lr, else TB if u - t_lr < t_tb, else EMPTY,
  *   t_x = floor(p_x * 2^64) clamped to 2^64 - 1.
  *
+ * Model II: oracle_run_model below (reading stated there).
+ *
  * Threaded mode: the row loop of each phase may be split across OpenMP
  * threads exactly as Sec. 4 describes ("parallel for" over rows).  Every
  * cell is computed by the same expression from the same inputs, so the
@@ -177,6 +179,103 @@ int64_t oracle_phase(const uint8_t *cur, uint8_t *next, int64_t M, int64_t N,
 {
     if (phase == 0) return horizontal_phase(cur, next, M, N, 1);
     return vertical_phase(cur, next, M, N, 1);
+}
+
+/*
+ * Model II (Sec. 2: a variation of the original BML paper).  Every vehicle
+ * moves in one synchronous phase per step, from the state at the start of
+ * the step; a vehicle's target cell (right for LR, below for TB, with
+ * wrap-around) must be EMPTY at that time.  If an LR vehicle (from the left)
+ * and a TB vehicle (from above) both target the same empty cell, one of
+ * them, chosen at random, moves and the other stands still.  The paper does
+ * not fix the random choice; here the LR vehicle wins the cell (i,j) at step
+ * t iff bit (j mod 64) of SplitMix64 output n = t*M*W + i*W + floor(j/64) + 1
+ * from state tie_seed is 1 (W = ceil(N/64)); t counts steps from 0.
+ */
+static int lr_wins(uint64_t tie_seed, int64_t t, int64_t M, int64_t N,
+                   int64_t i, int64_t j)
+{
+    const uint64_t W = (uint64_t)((N + 63) / 64);
+    const uint64_t n = (uint64_t)t * (uint64_t)M * W + (uint64_t)i * W +
+                       (uint64_t)(j / 64) + 1;
+    return (int)((oracle_splitmix64(tie_seed, n) >> (j % 64)) & 1u);
+}
+
+/* Whether an LR vehicle from the left may enter cell (i,j) of cur, and
+ * whether a TB vehicle from above may (both need the cell empty). */
+static void entries(const uint8_t *cur, int64_t M, int64_t N, int model,
+                    uint64_t tie_seed, int64_t t, int64_t i, int64_t j,
+                    int *lr_in, int *tb_in)
+{
+    *lr_in = *tb_in = 0;
+    if (cur[i * N + j] != EMPTY) return;
+    const int from_left = cur[i * N + (j - 1 + N) % N] == LR;
+    const int from_top = cur[((i - 1 + M) % M) * N + j] == TB;
+    if (model == 2 && from_left && from_top) {
+        const int lr = lr_wins(tie_seed, t, M, N, i, j);
+        *lr_in = lr;
+        *tb_in = !lr;
+    } else {
+        *lr_in = from_left;
+        *tb_in = from_top;
+    }
+}
+
+static void model_step(const uint8_t *cur, uint8_t *next, int64_t M, int64_t N,
+                       int model, uint64_t tie_seed, int64_t t, int threads,
+                       int64_t *mlr, int64_t *mtb)
+{
+    int64_t a = 0, b = 0;
+#pragma omp parallel for reduction(+ : a, b) num_threads(threads) schedule(static)
+    for (int64_t i = 0; i < M; i++) {
+        for (int64_t j = 0; j < N; j++) {
+            const uint8_t c = cur[i * N + j];
+            uint8_t out = EMPTY;
+            int lr_in, tb_in;
+            if (c == LR) {
+                /* the right neighbour accepts this LR vehicle? */
+                entries(cur, M, N, model, tie_seed, t, i, (j + 1) % N, &lr_in, &tb_in);
+                if (lr_in) a++;
+                else out = LR;
+            }
+            if (c == TB) {
+                entries(cur, M, N, model, tie_seed, t, (i + 1) % M, j, &lr_in, &tb_in);
+                if (tb_in) b++;
+                else out = TB;
+            }
+            entries(cur, M, N, model, tie_seed, t, i, j, &lr_in, &tb_in);
+            if (lr_in) out = LR;
+            if (tb_in) out = TB;
+            next[i * N + j] = out;
+        }
+    }
+    *mlr = a;
+    *mtb = b;
+}
+
+/*
+ * Advance g by K steps of Model II (model = 2; no other model is accepted);
+ * the first step has index t0 (it selects the tie-break bits).
+ * Counts as in oracle_run.  Returns 0, -1 on bad arguments, -2 on no memory.
+ */
+int oracle_run_model(uint8_t *g, int64_t M, int64_t N, int64_t K, int model,
+                     uint64_t tie_seed, int64_t t0, int64_t *moved_lr,
+                     int64_t *moved_tb, int threads)
+{
+    if (!g || M <= 0 || N <= 0 || K < 0 || t0 < 0 || model != 2)
+        return -1;
+    if (threads < 1) threads = 1;
+    uint8_t *tmp = (uint8_t *)malloc((size_t)(M * N));
+    if (!tmp) return -2;
+    for (int64_t t = 0; t < K; t++) {
+        int64_t a, b;
+        model_step(g, tmp, M, N, model, tie_seed, t0 + t, threads, &a, &b);
+        memcpy(g, tmp, (size_t)(M * N));
+        if (moved_lr) moved_lr[t] = a;
+        if (moved_tb) moved_tb[t] = b;
+    }
+    free(tmp);
+    return 0;
 }
 
 /*
