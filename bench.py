@@ -13,6 +13,10 @@ no flush is needed between timed steps.  With --gpus N > 1 (torchrun) each
 rank runs an independent replica (weak scaling); there is no data-path
 collective.
 
+Sub-measurements on the same JSON line: "ensemble" (4096 lattices, the
+batched API), "model2" (the Sec. 2 Model II variant on the bench lattice,
+tie-break seed = placement seed, 1024 steps; --no-model2 skips it).
+
 --impl reference times the CPU oracle (test infrastructure) on the host
 cores on a bounded sample of the same workload.
 """
@@ -49,6 +53,12 @@ def workload_name(M, N):
 # ~(Lh_x | T_x) is one three-input operation) and the two count additions;
 # popcounts run on another pipe and are not counted
 ALU_OPS_PER_CELL_STEP = 16.0 / 64.0
+# Model II (one synchronous phase, random tie-break), per 64-cell word and
+# step: E, fromL (funnel), inLR (2: E & fromL & (~T_{x-1} | coin)), inTB (2),
+# mvH (funnel), L', T' = 9 operations per 32-bit half = 18; the tie-break
+# word (SplitMix64: three xor-shifts of 64 bits = 12, a 64-bit add = 2; its
+# multiplies run on the FMA pipe); 2 count additions: 34 per 64 cell-steps
+MODEL2_ALU_OPS_PER_CELL_STEP = 34.0 / 64.0
 SMS = 148
 ALU_LANES_PER_SM_CLK = 64  # integer ALU pipe: 2 warp instructions per clock per SM
 SM_MAX_MHZ = 2032.0
@@ -192,6 +202,39 @@ def _ensemble_bench(bml, torch, stream, steps, seed_base=1):
             "temporal_depth": k, "band_rows": band, "graph": graphs,
             "workload": "4096 lattices, M,N ~ U{64..2048}, rho ~ U[0.1,0.6], "
                         "LR fraction ~ U[0.3,0.7], seeds 1..4096"}
+
+
+def _model2_bench(bml, torch, stream, M, N, steps, sm_mhz, seed=1):
+    """Model II on the bench lattice (same placement), autotuned, `steps`
+    steps timed with CUDA events after a warm-up; the counts of the timed
+    steps are checked for plausibility."""
+    with bml.Lattice(M, N, seed=seed, density=DENSITY, stream=stream,
+                     reserve_steps=steps + 64) as sim:
+        sim.set_model(bml.BML_MODEL_II, seed)
+        k, band, lw = sim.tiling
+        sim.step(3 * k)
+        sim.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(steps)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        tot, _, _ = sim.moved_counts(3 * k, steps)
+        cells = M * N
+        assert (tot >= 0).all() and (tot <= cells).all()
+    launches = (steps + k - 1) // k
+    ops = MODEL2_ALU_OPS_PER_CELL_STEP * cells * steps
+    achieved = ops / (ms / 1e3) / 1e12
+    peak = SMS * ALU_LANES_PER_SM_CLK * sm_mhz * 1e6 / 1e12
+    return {"metric": "cell-updates/s", "value": cells * steps / (ms / 1e3),
+            "unit": "cell-updates/s", "steps": steps, "seconds": ms / 1e3,
+            "workload": workload_name(M, N) + "_model2_tie1",
+            "kernel": "model2_kernel<%d>" % k, "temporal_depth": k, "band_rows": band,
+            "gpu_launches": launches,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "ops_per_cell_step": MODEL2_ALU_OPS_PER_CELL_STEP}}
 
 
 def run_reference(args):
@@ -365,6 +408,13 @@ def run_ours(args):
         ens_max = max_over_ranks(ens["seconds"])
         ens["value"] = job_rate(world, ens["lattices"] * ens["steps"], ens_max)
 
+    m2 = None
+    if not args.no_model2:
+        m2 = _model2_bench(bml, torch, stream, M, N, args.model2_steps,
+                           (clk or {}).get("sm_mhz") or SM_MAX_MHZ, seed=1 + rank)
+        m2_max = max_over_ranks(m2["seconds"])
+        m2["value"] = job_rate(world, M * N * m2["steps"], m2_max)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         threads = os.cpu_count() or 1
@@ -388,6 +438,7 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (2 x 256 MB bitplanes)",
                        "parallelism": "replicas x%d" % world},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "ensemble": ens,
+            "model2": m2,
             "gpu_launches": gpu_launches, "clocks": clk,
         }
         print(json.dumps(line))
@@ -409,6 +460,8 @@ def main():
     ap.add_argument("--lane-words", type=int, default=1, help="1 or 2 (with --band)")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--ensemble-steps", type=int, default=1024)
+    ap.add_argument("--no-model2", action="store_true")
+    ap.add_argument("--model2-steps", type=int, default=1024)
     ap.add_argument("--M", type=int, default=M_ROWS)
     ap.add_argument("--N", type=int, default=N_COLS)
     ap.add_argument("--no-e2e", action="store_true")

@@ -152,6 +152,35 @@ int bml_set_tiling_ex(bml_sim *sim, int block_k, int64_t band_rows, int lane_wor
 /* Current tiling of the bitplane kernels (band_rows 0: one-pass kernel). */
 int bml_get_tiling(const bml_sim *sim, int *block_k, int64_t *band_rows, int *lane_words);
 
+/* ------------------------------------------------------------------------
+ * Model II (Sec. 2: a variation of the original model).  Every vehicle
+ * moves in one synchronous phase per step, from the state at the start of
+ * the step, into its target cell (right for LR, below for TB, wrap-around)
+ * if that cell is EMPTY; an EMPTY cell wanted by both an LR vehicle (from
+ * its left) and a TB vehicle (from above) goes to one of them at random.
+ * The paper does not fix the random choice: the LR vehicle wins cell (i,j)
+ * at step t (t = 0 for the first step after bml_create_ex or
+ * bml_write_lattice, i.e. t = bml_steps_done() before the step) iff bit
+ * (j mod 64) of the SplitMix64 output n = t*M*W + i*W + floor(j/64) + 1
+ * from state tie_seed is 1 (W = ceil(N/64)).  Moved counts: LR and TB
+ * vehicles that changed cell in the step.
+ * ---------------------------------------------------------------------- */
+#define BML_MODEL_I 1  /* the paper's model: H phase then V phase (default) */
+#define BML_MODEL_II 2 /* one synchronous phase, random tie-break */
+
+/* Select the update rule for the following steps (the lattice and the
+ * count history are kept).  Model II runs on the streaming bitplane kernel
+ * (k steps per launch, one 64-cell word per lane, any N): the object must
+ * have been created with BML_KERNEL_TBLOCK or BML_KERNEL_AUTO, otherwise
+ * BML_EINVAL.  Selecting a model autotunes its tiling (cached per shape,
+ * model and device; bml_set_tiling_ex may override it, lane_words 1 only
+ * for Model II).  Synchronises the object's stream.  BML_EINVAL for an
+ * unknown model; the object is unchanged on failure. */
+int bml_set_model(bml_sim *sim, int model, uint64_t tie_seed);
+
+/* Current model and tie-break seed. */
+int bml_get_model(const bml_sim *sim, int *model, uint64_t *tie_seed);
+
 /* Wait for all work enqueued by the object. */
 int bml_synchronize(bml_sim *sim);
 

@@ -36,6 +36,9 @@ BML_KERNEL_BITPLANE = 2
 BML_KERNEL_FUSED = 3
 BML_KERNEL_TBLOCK = 4
 
+BML_MODEL_I = 1
+BML_MODEL_II = 2
+
 KERNELS = {"auto": BML_KERNEL_AUTO, "byte": BML_KERNEL_BYTE, "bitplane": BML_KERNEL_BITPLANE,
            "fused": BML_KERNEL_FUSED, "tblock": BML_KERNEL_TBLOCK}
 
@@ -76,6 +79,8 @@ _lib_get_config = _sig("bml_get_config", [_vp, ctypes.POINTER(_int), ctypes.POIN
 _lib_set_tiling = _sig("bml_set_tiling", [_vp, _int, _i64])
 _lib_set_tiling_ex = _sig("bml_set_tiling_ex", [_vp, _int, _i64, _int])
 _lib_get_tiling = _sig("bml_get_tiling", [_vp, ctypes.POINTER(_int), _i64p, ctypes.POINTER(_int)])
+_lib_set_model = _sig("bml_set_model", [_vp, _int, _u64])
+_lib_get_model = _sig("bml_get_model", [_vp, ctypes.POINTER(_int), ctypes.POINTER(_u64)])
 _lib_sync = _sig("bml_synchronize", [_vp])
 _lib_destroy = _sig("bml_destroy", [_vp], None)
 _lib_last_error = _sig("bml_last_error", [], ctypes.c_char_p)
@@ -209,6 +214,16 @@ def bml_get_tiling(sim: int):
     return k.value, b.value, lw.value
 
 
+def bml_set_model(sim: int, model: int, tie_seed: int = 0) -> None:
+    _check(_lib_set_model(sim, model, tie_seed))
+
+
+def bml_get_model(sim: int):
+    m, seed = _int(), _u64()
+    _check(_lib_get_model(sim, ctypes.byref(m), ctypes.byref(seed)))
+    return m.value, seed.value
+
+
 def bml_synchronize(sim: int) -> None:
     _check(_lib_sync(sim))
 
@@ -269,6 +284,15 @@ class Lattice:
     @property
     def tiling(self):
         return bml_get_tiling(self._h)
+
+    def set_model(self, model: int, tie_seed: int = 0) -> None:
+        """BML_MODEL_I (default) or BML_MODEL_II (one synchronous phase,
+        random tie-break seeded by tie_seed)."""
+        bml_set_model(self._h, model, tie_seed)
+
+    @property
+    def model(self):
+        return bml_get_model(self._h)
 
     def synchronize(self) -> None:
         bml_synchronize(self._h)

@@ -80,6 +80,8 @@ struct bml_sim {
   int block_k = 1;
   int64_t band_rows = 0;
   int lane_words = 1;  // streaming kernel: 64-cell words per lane (1 or 2)
+  int model = BML_MODEL_I;
+  u64 tie_seed = 0;  // Model II tie-break generator state
   cudaStream_t st = nullptr;
   Allocator alloc;
   // state: bitplane kernels use L[cur], T[cur]; the byte kernel uses c[0]
@@ -173,10 +175,24 @@ int grow_counts(bml_sim *s, int64_t need) {
   return BML_OK;
 }
 
-// Enqueue `k` steps with the configured kernel.  lr/tb point at the count
-// slots of the first step.
-int enqueue_steps(bml_sim *s, int64_t k, u64 *lr, u64 *tb, bool commit) {
+// Enqueue `k` steps with the configured model and kernel.  lr/tb point at
+// the count slots of the first step, whose index is t0 (Model II tie-breaks).
+int enqueue_steps(bml_sim *s, int64_t k, u64 *lr, u64 *tb, bool commit, int64_t t0 = 0) {
   const Geom &g = s->g;
+  if (s->model == BML_MODEL_II) {
+    int64_t done = 0;
+    while (done < k) {
+      int d = s->block_k;
+      while (d > k - done) d >>= 1;
+      const int a = s->cur, b = 1 - s->cur;
+      CUDA_TRY(launch_model2(plane_L(s, a), plane_T(s, a), plane_L(s, b), plane_T(s, b), g, d,
+                             s->band_rows, s->tie_seed, (u64)(t0 + done), lr + done, tb + done,
+                             s->st));
+      if (commit) s->cur = b;
+      done += d;
+    }
+    return BML_OK;
+  }
   if (s->kernel == BML_KERNEL_BYTE) {
     uint8_t *c0 = (uint8_t *)s->bytes[0].ptr, *c1 = (uint8_t *)s->bytes[1].ptr;
     for (int64_t t = 0; t < k; ++t) {
@@ -222,12 +238,15 @@ int enqueue_steps(bml_sim *s, int64_t k, u64 *lr, u64 *tb, bool commit) {
   return BML_OK;
 }
 
+int64_t default_band(const Geom &g) { return g.M < 256 ? g.M : 256; }
+
 // ------------------------------------------------------------ autotuner --
 struct TuneKey {
   int64_t M, N;
   int dev;
+  int model;
   bool operator<(const TuneKey &o) const {
-    return std::tie(M, N, dev) < std::tie(o.M, o.N, o.dev);
+    return std::tie(M, N, dev, model) < std::tie(o.M, o.N, o.dev, o.model);
   }
 };
 std::mutex g_tune_mu;
@@ -241,7 +260,7 @@ std::map<TuneKey, Tiling> g_tune_cache;
 int autotune(bml_sim *s) {
   int dev = 0;
   CUDA_TRY(cudaGetDevice(&dev));
-  const TuneKey key{s->g.M, s->g.N, dev};
+  const TuneKey key{s->g.M, s->g.N, dev, s->model};
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
@@ -257,15 +276,17 @@ int autotune(bml_sim *s) {
   // heights that make the tile count fill 1..4 whole waves of resident warps
   int sms = 148;
   CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const bool m2 = s->model == BML_MODEL_II;
   std::vector<Tiling> cands;
-  cands.push_back({1, 0, 1});
+  if (!m2) cands.push_back({1, 0, 1});  // Model II has no one-pass kernel
   for (int lw : {1, 2}) {
-    if (lw == 2 && !stream2_applies(s->g)) continue;
+    if (lw == 2 && (m2 || !stream2_applies(s->g))) continue;
     for (int k : {1, 2, 4, 8}) {
       std::vector<int64_t> bands;
       for (int64_t b : {16, 32, 64, 128, 256, 512, 1024}) bands.push_back(b);
       int wpb = 4;
-      const int per_sm = lw == 2 ? stream2_occupancy(k) : stream_occupancy(s->g, k, &wpb);
+      const int per_sm = m2 ? model2_occupancy(s->g, k)
+                            : (lw == 2 ? stream2_occupancy(k) : stream_occupancy(s->g, k, &wpb));
       const int64_t resident = (int64_t)sms * per_sm * wpb;
       const int64_t strips = lw == 2 ? stream2_strips(s->g) : make_strip_plan(s->g, k).n_strips;
       for (int waves = 1; waves <= 4; ++waves) {
@@ -289,7 +310,7 @@ int autotune(bml_sim *s) {
   const int saved_lw = s->lane_words;
   double best = 1e30;
   int best_k = 1, best_lw = 1;
-  int64_t best_b = 0;
+  int64_t best_b = m2 ? default_band(s->g) : 0;
   const double cells = (double)s->g.M * (double)s->g.N;
   const int reps = cells > 1e8 ? 3 : (cells > 1e6 ? 10 : 20);
   int rc = BML_OK;
@@ -350,8 +371,6 @@ done:
   g_tune_cache[key] = {best_k, best_b, best_lw};
   return BML_OK;
 }
-
-int64_t default_band(const Geom &g) { return g.M < 256 ? g.M : 256; }
 
 }  // namespace
 
@@ -448,7 +467,8 @@ extern "C" int bml_step(bml_sim *s, int64_t k) {
   if (k == 0) return BML_OK;
   int rc = grow_counts(s, s->steps_done + k);
   if (rc) return rc;
-  rc = enqueue_steps(s, k, cnt_lr(s) + s->steps_done, cnt_tb(s) + s->steps_done, true);
+  rc = enqueue_steps(s, k, cnt_lr(s) + s->steps_done, cnt_tb(s) + s->steps_done, true,
+                     s->steps_done);
   if (rc) return rc;
   s->steps_done += k;
   return BML_OK;
@@ -474,6 +494,8 @@ extern "C" int bml_set_tiling_ex(bml_sim *s, int block_k, int64_t band_rows, int
   if (lane_words == 2 && (!stream2_applies(s->g) || band_rows == 0))
     return fail(BML_EINVAL, "two words per lane need N %% 64 == 0, an even number of words "
                 "per row, more than 32 of them, and band_rows >= 1");
+  if (lane_words == 2 && s->model == BML_MODEL_II)
+    return fail(BML_EINVAL, "Model II runs one word per lane");
   int rc = bml_set_tiling(s, block_k, band_rows);
   if (rc) return rc;
   s->lane_words = lane_words;
@@ -499,9 +521,43 @@ extern "C" int bml_set_tiling(bml_sim *s, int block_k, int64_t band_rows) {
     return fail(BML_EINVAL, "the fused kernel runs one step per launch without bands");
   if (band_rows < 0 || band_rows > INT32_MAX || (band_rows == 0 && block_k != 1))
     return fail(BML_EINVAL, "bad band_rows (0 selects the direct one-pass kernel, depth 1)");
+  if (band_rows == 0 && s->model == BML_MODEL_II)
+    return fail(BML_EINVAL, "Model II has no one-pass kernel (band_rows >= 1)");
   s->block_k = block_k;
   s->band_rows = band_rows;
   s->lane_words = 1;
+  return BML_OK;
+}
+
+extern "C" int bml_set_model(bml_sim *s, int model, uint64_t tie_seed) {
+  if (!s) return fail(BML_EINVAL, "sim is NULL");
+  if (model != BML_MODEL_I && model != BML_MODEL_II)
+    return fail(BML_EINVAL, "unknown model %d", model);
+  if (model == BML_MODEL_II && s->kernel != BML_KERNEL_TBLOCK && s->kernel != BML_KERNEL_AUTO)
+    return fail(BML_EINVAL, "Model II needs an object created with BML_KERNEL_TBLOCK or AUTO");
+  const int old_model = s->model, old_k = s->block_k, old_lw = s->lane_words;
+  const int64_t old_b = s->band_rows;
+  const u64 old_seed = s->tie_seed;
+  s->model = model;
+  s->tie_seed = tie_seed;
+  int rc = BML_OK;
+  if (s->kernel == BML_KERNEL_AUTO || model == BML_MODEL_II) rc = autotune(s);
+  if (!rc && cudaStreamSynchronize(s->st) != cudaSuccess)
+    rc = fail(BML_ECUDA, "set_model: %s", cudaGetErrorString(cudaGetLastError()));
+  if (rc) {
+    s->model = old_model;
+    s->tie_seed = old_seed;
+    s->block_k = old_k;
+    s->band_rows = old_b;
+    s->lane_words = old_lw;
+  }
+  return rc;
+}
+
+extern "C" int bml_get_model(const bml_sim *s, int *model, uint64_t *tie_seed) {
+  if (!s) return fail(BML_EINVAL, "sim is NULL");
+  if (model) *model = s->model;
+  if (tie_seed) *tie_seed = s->tie_seed;
   return BML_OK;
 }
 

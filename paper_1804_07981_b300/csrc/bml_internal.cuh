@@ -91,6 +91,13 @@ cudaError_t launch_stream(const u64 *Lin, const u64 *Tin, u64 *Lout, u64 *Tout, 
                           int k, int64_t band_rows, u64 *moved_lr, u64 *moved_tb,
                           cudaStream_t st);
 
+// Model II streaming kernel (one synchronous phase, random tie-break of
+// contested cells; k in 1, 2, 4, 8): t0 = index of the launch's first step.
+int model2_occupancy(const Geom &g, int k);
+cudaError_t launch_model2(const u64 *Lin, const u64 *Tin, u64 *Lout, u64 *Tout, const Geom &g,
+                          int k, int64_t band_rows, u64 tie_seed, u64 t0, u64 *moved_lr,
+                          u64 *moved_tb, cudaStream_t st);
+
 // Two-words-per-lane streaming kernel (rows of full words, W even, W > 32).
 bool stream2_applies(const Geom &g);
 int64_t stream2_strips(const Geom &g);

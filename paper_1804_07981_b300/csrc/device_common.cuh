@@ -21,6 +21,15 @@ __device__ __forceinline__ int word_top(int64_t w, const Geom &g) {
   return w == g.W - 1 ? g.nb - 1 : 63;
 }
 
+// n-th output (n >= 1) of SplitMix64 (Steele, Lea, Flood 2014) started from
+// state `seed`: the placement's and the Model II tie-break's generator.
+__device__ __forceinline__ u64 splitmix64_at(u64 seed, u64 n) {
+  u64 z = seed + n * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
 // Asynchronous 16-byte copy global -> shared (bypassing L1), its commit and
 // its wait (all but the N most recent committed groups complete; the copied
 // bytes are then visible to the issuing thread).

@@ -30,13 +30,6 @@ u64 placement_threshold(double p) {
   return (u64)x;
 }
 
-__device__ __forceinline__ u64 splitmix64_at(u64 seed, u64 n) {
-  u64 z = seed + n * 0x9E3779B97F4A7C15ull;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
-
 // 0 EMPTY, 1 LR, 2 TB
 __device__ __forceinline__ uint32_t place(u64 seed, u64 n, u64 t_lr, u64 t_tb) {
   const u64 u = splitmix64_at(seed, n);

@@ -70,6 +70,11 @@ def test_null_handles_are_rejected(lib):
     with pytest.raises(lib.BMLError):
         lib.bml_moved_counts(None, 0, 1)
     assert lib.bml_steps_done(None) == -1
+    with pytest.raises(lib.BMLError) as e:
+        lib.bml_set_model(None, lib.BML_MODEL_II, 1)
+    assert e.value.code == lib.BML_EINVAL
+    with pytest.raises(lib.BMLError):
+        lib.bml_get_model(None)
     lib.bml_destroy(None)
 
 
