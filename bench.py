@@ -15,7 +15,10 @@ collective.
 
 Sub-measurements on the same JSON line: "ensemble" (4096 lattices, the
 batched API), "model2" (the Sec. 2 Model II variant on the bench lattice,
-tie-break seed = placement seed, 1024 steps; --no-model2 skips it).
+tie-break seed = placement seed, 1024 steps; --no-model2 skips it),
+"byte_kernel" (the plain byte-per-cell form on the bench lattice, 16 steps,
+against the HBM peak), "configs" (256^2 for 1024 steps; 4096^2 byte vs
+bit-packed over 3 densities x 3 seeds x 4096 steps; rank 0 of a 1-GPU run).
 
 --impl reference times the CPU oracle (test infrastructure) on the host
 cores on a bounded sample of the same workload.
@@ -237,6 +240,64 @@ def _model2_bench(bml, torch, stream, M, N, steps, sm_mhz, seed=1):
                          "ops_per_cell_step": MODEL2_ALU_OPS_PER_CELL_STEP}}
 
 
+def _timed_steps(torch, stream, sim, steps):
+    """Milliseconds of `steps` steps on the object's stream (CUDA events)."""
+    sim.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def _byte_bench(bml, torch, stream, M, N, steps, hbm_peak, seed=1):
+    """The plain byte-per-cell form (one byte per cell, a horizontal and a
+    vertical kernel per step: 4 B of DRAM traffic per cell-step) on the bench
+    lattice."""
+    with bml.Lattice(M, N, seed=seed, density=DENSITY, kernel="byte", stream=stream,
+                     reserve_steps=steps + 8) as sim:
+        sim.step(2)
+        ms = _timed_steps(torch, stream, sim, steps)
+    cells = M * N
+    gbs = 4.0 * cells * steps / (ms / 1e3) / 1e9
+    return {"metric": "cell-updates/s", "value": cells * steps / (ms / 1e3),
+            "unit": "cell-updates/s", "steps": steps, "seconds": ms / 1e3,
+            "kernel": "byte_h + byte_v", "gpu_launches": 2 * steps,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": gbs / hbm_peak, "bytes_per_cell_step": 4.0}}
+
+
+def _config_benches(bml, torch, stream):
+    """The two smaller workloads: 256 x 256 at density 0.3 (seed 1, 1024
+    steps; latency-bound) and 4096 x 4096 at densities 0.20/0.35/0.50,
+    seeds 1-3, 4096 steps, byte-per-cell kernel against the autotuned
+    bit-packed kernel (lattice creation and autotuning outside the timed
+    steps)."""
+    out = {}
+    with bml.Lattice(256, 256, seed=1, p_lr=0.15, p_tb=0.15, stream=stream,
+                     reserve_steps=1024 + 64) as sim:
+        ms = _timed_steps(torch, stream, sim, 1024)
+        k, band, lw = sim.tiling
+    out["256x256_rho0.30_1024steps"] = {"seconds": ms / 1e3,
+                                        "cell_updates_per_s": 65536 * 1024 / (ms / 1e3),
+                                        "tiling": [k, band, lw]}
+    tot = {"byte": 0.0, "auto": 0.0}
+    for rho in (0.20, 0.35, 0.50):
+        for seed in (1, 2, 3):
+            for kernel in ("byte", "auto"):
+                with bml.Lattice(4096, 4096, seed=seed, density=rho, kernel=kernel,
+                                 stream=stream, reserve_steps=4096 + 64) as sim:
+                    tot[kernel] += _timed_steps(torch, stream, sim, 4096) / 1e3
+    cs = 9 * 4096 * 4096 * 4096
+    out["4096x4096_rho0.20-0.50_seeds1-3_4096steps"] = {
+        "byte_seconds": tot["byte"], "bitplane_seconds": tot["auto"],
+        "byte_cell_updates_per_s": cs / tot["byte"],
+        "bitplane_cell_updates_per_s": cs / tot["auto"],
+        "bitplane_over_byte": tot["byte"] / tot["auto"]}
+    return out
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -408,6 +469,15 @@ def run_ours(args):
         ens_max = max_over_ranks(ens["seconds"])
         ens["value"] = job_rate(world, ens["lattices"] * ens["steps"], ens_max)
 
+    byte = None
+    if not args.no_byte:
+        byte = _byte_bench(bml, torch, stream, M, N, args.byte_steps, hbm_peak, seed=1 + rank)
+        byte["value"] = job_rate(world, M * N * byte["steps"], max_over_ranks(byte["seconds"]))
+
+    small = None
+    if not args.no_configs and world == 1:
+        small = _config_benches(bml, torch, stream)
+
     m2 = None
     if not args.no_model2:
         m2 = _model2_bench(bml, torch, stream, M, N, args.model2_steps,
@@ -438,7 +508,7 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (2 x 256 MB bitplanes)",
                        "parallelism": "replicas x%d" % world},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "ensemble": ens,
-            "model2": m2,
+            "model2": m2, "byte_kernel": byte, "configs": small,
             "gpu_launches": gpu_launches, "clocks": clk,
         }
         print(json.dumps(line))
@@ -461,6 +531,9 @@ def main():
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--ensemble-steps", type=int, default=1024)
     ap.add_argument("--no-model2", action="store_true")
+    ap.add_argument("--no-byte", action="store_true")
+    ap.add_argument("--byte-steps", type=int, default=16)
+    ap.add_argument("--no-configs", action="store_true")
     ap.add_argument("--model2-steps", type=int, default=1024)
     ap.add_argument("--M", type=int, default=M_ROWS)
     ap.add_argument("--N", type=int, default=N_COLS)
