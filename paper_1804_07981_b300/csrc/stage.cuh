@@ -25,6 +25,7 @@ namespace bml {
 struct LaneWord {
   u64 valid;                // valid-cell mask (all ones for a full word, 0 if the lane is off)
   uint32_t ins_lo, ins_hi;  // bit that receives the right neighbour's first cell
+  uint32_t mul_lo, mul_hi;  // lo * mul_lo + hi * mul_hi has the word's last cell at bit 31
   int top_hi;               // the word's last cell lies in the high half
   int top_sh;               // left shift that moves the last cell to bit 31 of its half
   int src_l, src_r;         // lanes holding the left / right neighbour words
@@ -36,6 +37,8 @@ __device__ __forceinline__ void lane_word_bits(LaneWord &lw, bool on, bool last,
   lw.valid = on ? (last ? tail : ~0ull) : 0ull;
   lw.ins_lo = top < 32 ? (1u << top) : 0u;
   lw.ins_hi = top >= 32 ? (1u << (top - 32)) : 0u;
+  lw.mul_lo = top < 32 ? (1u << (31 - top)) : 0u;
+  lw.mul_hi = top >= 32 ? (1u << (63 - top)) : 0u;
   lw.top_hi = top >= 32;
   lw.top_sh = 31 - (top & 31);
 }
@@ -48,39 +51,15 @@ __device__ __forceinline__ u64 mk64(uint32_t lo, uint32_t hi) {
 
 // Stage state: T_{x-1}, Lh_{x-1}, mvV_{x-2}.  Consumes row x (inL, inT) of
 // its input state, replaces them with row x-1 of the next state, and returns
-// the row's moved-car masks.  FULL: every word of the row holds 64 cells.
-template <bool FULL>
-__device__ __forceinline__ void stage_step(u64 &inL, u64 &inT, u64 &curT, u64 &curLh,
-                                           u64 &prevMv, const LaneWord &lw, u64 &mvH,
-                                           u64 &mvV) {
-  const u64 E = FULL ? ~(inL | inT) : (~(inL | inT) & lw.valid);
-  const uint32_t rr = __shfl_sync(BML_FULL_MASK, lo32(E), lw.src_r);
-  u64 Er;
-  if (FULL) {
-    Er = mk64(__funnelshift_r(lo32(E), hi32(E), 1), __funnelshift_r(hi32(E), rr, 1));
-  } else {
-    const uint32_t m = 0u - (rr & 1u);
-    Er = mk64(__funnelshift_r(lo32(E), hi32(E), 1) | (lw.ins_lo & m),
-              (hi32(E) >> 1) | (lw.ins_hi & m));
-  }
-  mvH = inL & Er;
-  const uint32_t send_l = FULL ? hi32(mvH) : ((lw.top_hi ? hi32(mvH) : lo32(mvH)) << lw.top_sh);
-  const uint32_t rl = __shfl_sync(BML_FULL_MASK, send_l, lw.src_l);
-  u64 in = mk64(__funnelshift_l(rl, lo32(mvH), 1), __funnelshift_l(lo32(mvH), hi32(mvH), 1));
-  if (!FULL) in &= lw.valid;
-  const u64 Lh = inL ^ mvH ^ in;
-  mvV = curT & ~(Lh | inT);
-  const u64 oT = (curT & ~mvV) | prevMv;
-  const u64 oL = curLh;
-  curT = inT;
-  curLh = Lh;
-  prevMv = mvV;
-  inL = oL;
-  inT = oT;
-}
-
-// The same stage with the state read from one set and written to another
-// (callers alternate two sets from row to row, so no value is copied).
+// the row's moved-car masks.  The state is read from one set and written to
+// another (callers alternate two sets from row to row, so no value is
+// copied).  FULL: every word of the row holds 64 cells.
+//
+// Words with fewer cells (the last word of a row whose N is not a multiple of
+// 64): the right neighbour's first cell enters at this word's last cell as
+// rr * ins (a product on the FMA pipe); the higher bits of that product fall
+// outside the row and stay out of mvH because L is zero there.  The last
+// cell sent to the left neighbour is placed at bit 31 by two multiply-adds.
 template <bool FULL>
 __device__ __forceinline__ void stage_step_pp(u64 &inL, u64 &inT, const u64 curT, const u64 curLh,
                                               const u64 prevMv, u64 &nT, u64 &nLh, u64 &nMv,
@@ -91,12 +70,11 @@ __device__ __forceinline__ void stage_step_pp(u64 &inL, u64 &inT, const u64 curT
   if (FULL) {
     Er = mk64(__funnelshift_r(lo32(E), hi32(E), 1), __funnelshift_r(hi32(E), rr, 1));
   } else {
-    const uint32_t m = 0u - (rr & 1u);
-    Er = mk64(__funnelshift_r(lo32(E), hi32(E), 1) | (lw.ins_lo & m),
-              (hi32(E) >> 1) | (lw.ins_hi & m));
+    Er = mk64(__funnelshift_r(lo32(E), hi32(E), 1) | (rr * lw.ins_lo),
+              (hi32(E) >> 1) | (rr * lw.ins_hi));
   }
   mvH = inL & Er;
-  const uint32_t send_l = FULL ? hi32(mvH) : ((lw.top_hi ? hi32(mvH) : lo32(mvH)) << lw.top_sh);
+  const uint32_t send_l = FULL ? hi32(mvH) : hi32(mvH) * lw.mul_hi + lo32(mvH) * lw.mul_lo;
   const uint32_t rl = __shfl_sync(BML_FULL_MASK, send_l, lw.src_l);
   u64 in = mk64(__funnelshift_l(rl, lo32(mvH), 1), __funnelshift_l(lo32(mvH), hi32(mvH), 1));
   if (!FULL) in &= lw.valid;
