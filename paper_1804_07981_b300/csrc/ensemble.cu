@@ -50,12 +50,15 @@ struct EnsLattice {
 };
 
 struct EnsGroup {
-  int lat, r0, len, pad;
+  int lat, r0, len, lane0;  // lattice, band rows [r0, r0+len), first lane in its tile
 };
 
+// A warp's work: up to 32 lanes holding the rows of one or more bands (groups)
+// of possibly different word widths; lane_grp[l] = group slot of lane l
+// (0xff: idle lane).
 struct EnsTile {
-  int W, G, first_group, max_len;
-  int min_len, pad0, pad1, pad2;
+  int G, first_group, max_len, min_len;
+  unsigned char lane_grp[32];
 };
 
 struct EnsCtrl {
@@ -143,16 +146,17 @@ template <int K>
 __device__ void process_tile(const EnsParams &p, int t, long long step0, int par,
                              long long prev_depth, int lane) {
   constexpr int PF = PFE<K>::value;
-  const EnsTile tile = p.tiles[t];
-  const int W = tile.W;
-  const int grp = lane / W, wi = lane - grp * W;
-  bool on = grp < tile.G;
+  const EnsTile &tile = p.tiles[t];
+  const int grp = tile.lane_grp[lane];
+  bool on = grp != 0xff;
   EnsGroup gr{0, 0, 0, 0};
   EnsLattice L{};
   if (on) {
     gr = p.groups[tile.first_group + grp];
     L = p.lat[gr.lat];
   }
+  const int W = on ? L.W : 1;           // words per row of this lane's lattice
+  const int wi = on ? lane - gr.lane0 : 0;  // this lane's word of the row
   if (on && p.early_exit) {
     long long fz = __ldcg(p.frozen + gr.lat);
     if (fz < 0 && step0 > 0) {
@@ -174,8 +178,8 @@ __device__ void process_tile(const EnsParams &p, int t, long long step0, int par
 
   LaneWord lw;
   if (on) {
-    lw.src_l = grp * W + (wi == 0 ? W - 1 : wi - 1);
-    lw.src_r = grp * W + (wi == W - 1 ? 0 : wi + 1);
+    lw.src_l = gr.lane0 + (wi == 0 ? W - 1 : wi - 1);
+    lw.src_r = gr.lane0 + (wi == W - 1 ? 0 : wi + 1);
   } else {
     lw.src_l = lw.src_r = lane;
   }
@@ -256,14 +260,14 @@ __device__ void process_tile(const EnsParams &p, int t, long long step0, int par
 #pragma unroll
   for (int s = 0; s < K; ++s) {
     uint32_t a = on ? c_lr[s] : 0u, b = on ? c_tb[s] : 0u;
+    // segmented sum over each group's lanes [lane0, lane0 + W): every lane
+    // shuffles, a lane adds only a partner of its own group
     for (int off = 16; off > 0; off >>= 1) {
-      if (off < W) {
-        const uint32_t ua = __shfl_down_sync(BML_FULL_MASK, a, off);
-        const uint32_t ub = __shfl_down_sync(BML_FULL_MASK, b, off);
-        if (wi + off < W) {
-          a += ua;
-          b += ub;
-        }
+      const uint32_t ua = __shfl_down_sync(BML_FULL_MASK, a, off);
+      const uint32_t ub = __shfl_down_sync(BML_FULL_MASK, b, off);
+      if (wi + off < W) {
+        a += ua;
+        b += ub;
       }
     }
     if (on && wi == 0) {
@@ -604,7 +608,12 @@ void ens_free(bml_ens *e) {
 // word width are packed 32 / W to a warp tile, longest bands first, and the
 // tiles are ordered longest first for the round-robin assignment to warps.
 int build_tiles(bml_ens *e, int64_t band) {
-  std::vector<std::vector<EnsGroup>> byW(33);
+  // bands of every lattice, longest first
+  struct Band {
+    EnsGroup g;
+    int W;
+  };
+  std::vector<Band> all;
   for (int l = 0; l < e->count; ++l) {
     const int M = e->lat[l].M;
     int64_t nb = (int64_t)std::llround((double)M / (double)band);
@@ -616,28 +625,66 @@ int build_tiles(bml_ens *e, int64_t band) {
     int r0 = 0;
     for (int64_t b = 0; b < nb; ++b) {
       const int len = base + (b < rem ? 1 : 0);
-      byW[e->lat[l].W].push_back(EnsGroup{l, r0, len, 0});
+      all.push_back(Band{EnsGroup{l, r0, len, 0}, e->lat[l].W});
       r0 += len;
     }
   }
+  std::sort(all.begin(), all.end(), [](const Band &a, const Band &b) {
+    if (a.g.len != b.g.len) return a.g.len > b.g.len;
+    if (a.W != b.W) return a.W > b.W;
+    return a.g.lat != b.g.lat ? a.g.lat < b.g.lat : a.g.r0 < b.g.r0;
+  });
+  // first fit into warps of 32 lanes: a band joins the first open warp with
+  // room for its W lanes; a warp closes once the bands reaching it are more
+  // than 1/8 shorter than its longest (every band runs the warp's longest
+  // band's rows), or when it is full
+  std::vector<std::vector<EnsGroup>> tg;
+  std::vector<int> used, maxlen, minlen;
+  std::vector<size_t> open;
+  for (const Band &x : all) {
+    size_t chosen = SIZE_MAX;
+    for (size_t k = 0; k < open.size();) {
+      const size_t ti = open[k];
+      if ((int64_t)maxlen[ti] * 7 > (int64_t)x.g.len * 8) {
+        open.erase(open.begin() + (std::ptrdiff_t)k);
+        continue;
+      }
+      if (32 - used[ti] >= x.W) {
+        chosen = ti;
+        break;
+      }
+      ++k;
+    }
+    if (chosen == SIZE_MAX) {
+      chosen = tg.size();
+      tg.emplace_back();
+      used.push_back(0);
+      maxlen.push_back(x.g.len);
+      minlen.push_back(x.g.len);
+      open.push_back(chosen);
+    }
+    EnsGroup g = x.g;
+    g.lane0 = used[chosen];
+    tg[chosen].push_back(g);
+    used[chosen] += x.W;
+    minlen[chosen] = std::min(minlen[chosen], x.g.len);
+    if (used[chosen] == 32) open.erase(std::find(open.begin(), open.end(), chosen));
+  }
   std::vector<EnsGroup> groups;
   std::vector<EnsTile> tiles;
-  for (int W = 1; W <= 32; ++W) {
-    auto &v = byW[W];
-    std::sort(v.begin(), v.end(), [](const EnsGroup &a, const EnsGroup &b) {
-      return a.len != b.len ? a.len > b.len : a.lat < b.lat;
-    });
-    const int G = 32 / W;
-    for (size_t i = 0; i < v.size(); i += G) {
-      EnsTile t{};
-      t.W = W;
-      t.G = (int)std::min<size_t>(G, v.size() - i);
-      t.first_group = (int)groups.size();
-      t.max_len = v[i].len;
-      t.min_len = v[i + t.G - 1].len;
-      for (int g = 0; g < t.G; ++g) groups.push_back(v[i + g]);
-      tiles.push_back(t);
+  for (size_t ti = 0; ti < tg.size(); ++ti) {
+    EnsTile t{};
+    t.G = (int)tg[ti].size();
+    t.first_group = (int)groups.size();
+    t.max_len = maxlen[ti];
+    t.min_len = minlen[ti];
+    for (int l = 0; l < 32; ++l) t.lane_grp[l] = 0xff;
+    for (int j = 0; j < t.G; ++j) {
+      const EnsGroup &g = tg[ti][j];
+      for (int l = g.lane0; l < g.lane0 + e->lat[g.lat].W; ++l) t.lane_grp[l] = (unsigned char)j;
+      groups.push_back(g);
     }
+    tiles.push_back(t);
   }
   std::stable_sort(tiles.begin(), tiles.end(),
                    [](const EnsTile &a, const EnsTile &b) { return a.max_len > b.max_len; });
