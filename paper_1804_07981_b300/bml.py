@@ -361,12 +361,15 @@ class MLP:
         _check(_lib_mlp_fwd(self._h, x.data_ptr(), x.shape[0], out.data_ptr()))
         return out
 
-    def train_step(self, x, v, jam, lr: float, weight_decay: float = 0.0) -> float:
+    def train_step(self, x, v, jam, lr: float, weight_decay: float = 0.0,
+                   want_loss: bool = True):
+        """One AdamW step; returns the batch loss before the update, or None
+        when want_loss is False (then nothing waits for the device)."""
         loss = ctypes.c_float()
         _check(_lib_mlp_train(self._h, x.contiguous().data_ptr(), v.contiguous().data_ptr(),
                               jam.contiguous().data_ptr(), x.shape[0], lr, weight_decay,
-                              ctypes.byref(loss)))
-        return loss.value
+                              ctypes.byref(loss) if want_loss else None))
+        return loss.value if want_loss else None
 
     def grads(self, x, v, jam):
         g = np.empty(self.n, dtype=np.float32)

@@ -65,8 +65,11 @@ def training_set(count, T, window, seed, lo=64, hi=2048, stream=None):
     return X, v, jam, secs
 
 
-def train(X, v, jam, steps=2000, batch=1024, lr=1e-3, wd=1e-4, seed=0, stream=None):
-    """AdamW on random mini-batches; returns the network and the loss curve."""
+def train(X, v, jam, steps=2000, batch=1024, lr=1e-3, wd=1e-4, seed=0, stream=None,
+          loss_tail=50):
+    """AdamW on random mini-batches; returns the network and the losses of
+    the first step and of the last `loss_tail` steps (only those steps wait
+    for the device to report their loss)."""
     import torch
     from .inputs import mlp_init_params
     net = bml.MLP(stream=stream)
@@ -76,7 +79,10 @@ def train(X, v, jam, steps=2000, batch=1024, lr=1e-3, wd=1e-4, seed=0, stream=No
     losses = []
     for s in range(steps):
         idx = torch.randint(0, n, (min(batch, n),), device="cuda", generator=g)
-        losses.append(net.train_step(X[idx], v[idx], jam[idx], lr=lr, weight_decay=wd))
+        want = s == 0 or s >= steps - loss_tail
+        loss = net.train_step(X[idx], v[idx], jam[idx], lr=lr, weight_decay=wd, want_loss=want)
+        if want:
+            losses.append(loss)
     return net, losses
 
 

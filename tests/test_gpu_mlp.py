@@ -114,3 +114,27 @@ def test_training_reduces_loss(lib):
         last = net.train_step(X, V, J, lr=1e-3)
     assert last < 0.25 * first, (first, last)
     net.close()
+
+
+def test_training_without_loss_readback_updates_identically(lib):
+    """Steps that do not report their loss (nothing waits for the device)
+    apply the same updates as steps that do (up to the rounding order of
+    the bias-gradient sums, which blocks add with float atomics)."""
+    import torch
+    rng = np.random.Generator(np.random.PCG64(43))
+    B = 256
+    x = rng.uniform(0, 1, size=(B, IN))
+    v = 0.4 * x[:, 3]
+    jam = (x[:, 4] > 0.5).astype(np.float64)
+    t = lambda a: torch.tensor(a, dtype=torch.float32, device="cuda")
+    X, V, J = t(x), t(v), t(jam)
+    params = []
+    for want in (True, False):
+        net = lib.MLP()
+        net.set_params(mlp_init_params(IN, 44).astype(np.float32))
+        for _ in range(20):
+            out = net.train_step(X, V, J, lr=1e-3, weight_decay=1e-4, want_loss=want)
+            assert (out is None) == (not want)
+        params.append(net.get_params())
+        net.close()
+    np.testing.assert_allclose(params[0], params[1], rtol=1e-5, atol=1e-8)
