@@ -233,7 +233,8 @@ def _model2_bench(bml, torch, stream, M, N, steps, sm_mhz, seed=1):
     return {"metric": "cell-updates/s", "value": cells * steps / (ms / 1e3),
             "unit": "cell-updates/s", "steps": steps, "seconds": ms / 1e3,
             "workload": workload_name(M, N) + "_model2_tie1",
-            "kernel": "model2_kernel<%d>" % k, "temporal_depth": k, "band_rows": band,
+            "kernel": ("stream2_kernel<%d, Model II>" if lw == 2 else "model2_kernel<%d>") % k,
+            "temporal_depth": k, "band_rows": band, "lane_words": lw,
             "gpu_launches": launches,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                          "frac": achieved / peak, "traffic": None,

@@ -185,9 +185,14 @@ int enqueue_steps(bml_sim *s, int64_t k, u64 *lr, u64 *tb, bool commit, int64_t 
       int d = s->block_k;
       while (d > k - done) d >>= 1;
       const int a = s->cur, b = 1 - s->cur;
-      CUDA_TRY(launch_model2(plane_L(s, a), plane_T(s, a), plane_L(s, b), plane_T(s, b), g, d,
-                             s->band_rows, s->tie_seed, (u64)(t0 + done), lr + done, tb + done,
-                             s->st));
+      if (s->lane_words == 2)
+        CUDA_TRY(launch_stream2(plane_L(s, a), plane_T(s, a), plane_L(s, b), plane_T(s, b), g, d,
+                                s->band_rows, lr + done, tb + done, s->st, 2, s->tie_seed,
+                                (u64)(t0 + done)));
+      else
+        CUDA_TRY(launch_model2(plane_L(s, a), plane_T(s, a), plane_L(s, b), plane_T(s, b), g, d,
+                               s->band_rows, s->tie_seed, (u64)(t0 + done), lr + done,
+                               tb + done, s->st));
       if (commit) s->cur = b;
       done += d;
     }
@@ -280,13 +285,14 @@ int autotune(bml_sim *s) {
   std::vector<Tiling> cands;
   if (!m2) cands.push_back({1, 0, 1});  // Model II has no one-pass kernel
   for (int lw : {1, 2}) {
-    if (lw == 2 && (m2 || !stream2_applies(s->g))) continue;
+    if (lw == 2 && !stream2_applies(s->g)) continue;
     for (int k : {1, 2, 4, 8}) {
       std::vector<int64_t> bands;
       for (int64_t b : {16, 32, 64, 128, 256, 512, 1024}) bands.push_back(b);
       int wpb = 4;
-      const int per_sm = m2 ? model2_occupancy(s->g, k)
-                            : (lw == 2 ? stream2_occupancy(k) : stream_occupancy(s->g, k, &wpb));
+      const int per_sm = lw == 2 ? stream2_occupancy(k, m2 ? 2 : 1)
+                                 : (m2 ? model2_occupancy(s->g, k)
+                                       : stream_occupancy(s->g, k, &wpb));
       const int64_t resident = (int64_t)sms * per_sm * wpb;
       const int64_t strips = lw == 2 ? stream2_strips(s->g) : make_strip_plan(s->g, k).n_strips;
       for (int waves = 1; waves <= 4; ++waves) {
@@ -494,8 +500,6 @@ extern "C" int bml_set_tiling_ex(bml_sim *s, int block_k, int64_t band_rows, int
   if (lane_words == 2 && (!stream2_applies(s->g) || band_rows == 0))
     return fail(BML_EINVAL, "two words per lane need N %% 64 == 0, an even number of words "
                 "per row, more than 32 of them, and band_rows >= 1");
-  if (lane_words == 2 && s->model == BML_MODEL_II)
-    return fail(BML_EINVAL, "Model II runs one word per lane");
   int rc = bml_set_tiling(s, block_k, band_rows);
   if (rc) return rc;
   s->lane_words = lane_words;

@@ -98,12 +98,14 @@ cudaError_t launch_model2(const u64 *Lin, const u64 *Tin, u64 *Lout, u64 *Tout, 
                           int k, int64_t band_rows, u64 tie_seed, u64 t0, u64 *moved_lr,
                           u64 *moved_tb, cudaStream_t st);
 
-// Two-words-per-lane streaming kernel (rows of full words, W even, W > 32).
+// Two-words-per-lane streaming kernel (rows of full words, W even, W > 32);
+// model 1 (the paper's model) or 2 (Model II, with tie_seed and the index
+// t0 of the launch's first step).
 bool stream2_applies(const Geom &g);
 int64_t stream2_strips(const Geom &g);
-int stream2_occupancy(int k);
+int stream2_occupancy(int k, int model = 1);
 cudaError_t launch_stream2(const u64 *Lin, const u64 *Tin, u64 *Lout, u64 *Tout, const Geom &g,
                            int k, int64_t band_rows, u64 *moved_lr, u64 *moved_tb,
-                           cudaStream_t st);
+                           cudaStream_t st, int model = 1, u64 tie_seed = 0, u64 t0 = 0);
 
 }  // namespace bml

@@ -21,6 +21,12 @@
 // memory, filled kAhead rows ahead with cp.async (16 bytes per lane and
 // plane); a slot is refilled two rows after it was last read.  The prefetch
 // holds no registers and its wait is explicit.
+//
+// MODEL = 2 runs the Model II rule of model2_step.cu (one synchronous phase,
+// tie-break words from the step, row and word indices) on the same
+// structure: per stage and row a lane draws the two tie-break words of its
+// pair, shuffles the left lane's last L cell and bit 0 of the right lane's
+// inLR, and the state word handed on is inTB instead of mvV.
 #include "stage.cuh"
 
 namespace bml {
@@ -72,6 +78,35 @@ __device__ __forceinline__ void stage_pair(u64 &La, u64 &Lb, u64 &Ta, u64 &Tb,
   Tb = oTb;
 }
 
+// One Model II stage on the word pair (a, b); st.M is inTB of the row above.
+__device__ __forceinline__ void stage_pair_m2(u64 &La, u64 &Lb, u64 &Ta, u64 &Tb,
+                                              const PairState &st, PairState &nx, int src_l,
+                                              int src_r, uint32_t &cnt, bool cnt_h, bool cnt_v,
+                                              u64 coinA, u64 coinB) {
+  const u64 Ea = ~(La | Ta), Eb = ~(Lb | Tb);
+  const uint32_t rl = __shfl_sync(BML_FULL_MASK, hi32(Lb), src_l);
+  const u64 fLa = mk64(fsl(rl, lo32(La)), fsl(lo32(La), hi32(La)));
+  const u64 fLb = mk64(fsl(hi32(La), lo32(Lb)), fsl(lo32(Lb), hi32(Lb)));
+  const u64 iLa = Ea & fLa & (~st.Ta | coinA), iLb = Eb & fLb & (~st.Tb | coinB);
+  const u64 iTa = Ea & st.Ta & ~(fLa & coinA), iTb = Eb & st.Tb & ~(fLb & coinB);
+  const uint32_t rr = __shfl_sync(BML_FULL_MASK, lo32(iLa), src_r);
+  const u64 mHa = mk64(fsr(lo32(iLa), hi32(iLa)), fsr(hi32(iLa), lo32(iLb)));
+  const u64 mHb = mk64(fsr(lo32(iLb), hi32(iLb)), fsr(hi32(iLb), rr));
+  const u64 oTa = (st.Ta & ~iTa) | st.Ma, oTb = (st.Tb & ~iTb) | st.Mb;
+  if (cnt_h) cnt += popc64(mHa) + popc64(mHb);
+  if (cnt_v) cnt += (popc64(iTa) + popc64(iTb)) << 16;
+  nx.Ta = Ta;
+  nx.Tb = Tb;
+  nx.La = (La & ~mHa) | iLa;
+  nx.Lb = (Lb & ~mHb) | iLb;
+  nx.Ma = iTa;
+  nx.Mb = iTb;
+  La = st.La;
+  Lb = st.Lb;
+  Ta = oTa;
+  Tb = oTb;
+}
+
 // Adds the packed per-lane counts of every stage (lanes that own no pair
 // contribute nothing) to the block's counters and clears them.
 template <int K>
@@ -90,12 +125,12 @@ __device__ __forceinline__ void flush_counts(uint32_t (&cnt)[K], bool own, int l
   }
 }
 
-template <int K>
+template <int K, int MODEL>
 __global__ void __launch_bounds__(kWarps2 * 32, K >= 8 ? 2 : 3)
     stream2_kernel(const u64 *__restrict__ Lin, const u64 *__restrict__ Tin,
                    u64 *__restrict__ Lout, u64 *__restrict__ Tout, Geom g, int n_strips,
                    int base, int rem, int band_rows, int n_bands, u64 *__restrict__ moved_lr,
-                   u64 *__restrict__ moved_tb) {
+                   u64 *__restrict__ moved_tb, u64 tie_seed, u64 t0) {
   constexpr int P = kChunk;
   __shared__ unsigned long long s_cnt[2 * K];
   __shared__ __align__(16) ulonglong2 s_ring[kWarps2][kRing][2][32];  // [warp][slot][plane][lane]
@@ -127,6 +162,10 @@ __global__ void __launch_bounds__(kWarps2 * 32, K >= 8 ? 2 : 3)
     if (ld_row < 0) ld_row += M;
     const size_t pitch = (size_t)g.P;
     size_t roff = (size_t)ld_row * pitch;
+    // Model II tie-break counters: n = t*M*W + x*W + w + 1 for word w of row x
+    const u64 W64 = (u64)g.W, MW = (u64)g.M * W64;
+    const u64 nbase = t0 * MW + (u64)wa + 1;
+    int x0 = ld_row;  // lattice row of input row i (stage 0)
 
     PairState st[2][K];  // state sets, alternated row by row (P is even)
 #pragma unroll
@@ -172,10 +211,24 @@ __global__ void __launch_bounds__(kWarps2 * 32, K >= 8 ? 2 : 3)
           const ulonglong2 vT = ring[i & (kRing - 1)][1][lane];
           u64 La = vL.x, Lb = vL.y, Ta = vT.x, Tb = vT.y;
 #pragma unroll
-          for (int s = 0; s < K; ++s)
-            stage_pair(La, Lb, Ta, Tb, st[u & 1][s], st[(u & 1) ^ 1][s], src_l, src_r, cnt[s],
-                       steady || (unsigned)(i - K - s) < (unsigned)B,
-                       steady || (unsigned)(i - K - s - 1) < (unsigned)B);
+          for (int s = 0; s < K; ++s) {
+            if constexpr (MODEL == 2) {
+              int x = x0 - s;  // lattice row of this stage's row
+              while (x < 0) x += M;
+              const u64 n = nbase + (u64)s * MW + (u64)x * W64;
+              stage_pair_m2(La, Lb, Ta, Tb, st[u & 1][s], st[(u & 1) ^ 1][s], src_l, src_r,
+                            cnt[s], steady || (unsigned)(i - K - s) < (unsigned)B,
+                            steady || (unsigned)(i - K - s - 1) < (unsigned)B,
+                            splitmix64_at(tie_seed, n), splitmix64_at(tie_seed, n + 1));
+            } else {
+              stage_pair(La, Lb, Ta, Tb, st[u & 1][s], st[(u & 1) ^ 1][s], src_l, src_r, cnt[s],
+                         steady || (unsigned)(i - K - s) < (unsigned)B,
+                         steady || (unsigned)(i - K - s - 1) < (unsigned)B);
+            }
+          }
+          if constexpr (MODEL == 2) {
+            if (++x0 == M) x0 = 0;
+          }
           if (steady || i >= 2 * K) {
             const size_t off = (size_t)(r0 + i - 2 * K) * pitch;
             if (own) {
@@ -197,9 +250,10 @@ __global__ void __launch_bounds__(kWarps2 * 32, K >= 8 ? 2 : 3)
   }
 }
 
-template <int K>
+template <int K, int MODEL>
 cudaError_t launch2_k(const u64 *Lin, const u64 *Tin, u64 *Lout, u64 *Tout, const Geom &g,
-                      int64_t band_rows, u64 *moved_lr, u64 *moved_tb, cudaStream_t st) {
+                      int64_t band_rows, u64 *moved_lr, u64 *moved_tb, u64 tie_seed, u64 t0,
+                      cudaStream_t st) {
   const int64_t WP = g.W / 2;
   const int64_t n_strips = (WP + 29) / 30;
   const int base = (int)(WP / n_strips), rem = (int)(WP % n_strips);
@@ -207,17 +261,17 @@ cudaError_t launch2_k(const u64 *Lin, const u64 *Tin, u64 *Lout, u64 *Tout, cons
   const int64_t tiles = n_strips * n_bands;
   if (tiles > INT32_MAX - kWarps2) return cudaErrorInvalidValue;
   const int64_t blocks = (tiles + kWarps2 - 1) / kWarps2;
-  stream2_kernel<K><<<(unsigned)blocks, kWarps2 * 32, 0, st>>>(
+  stream2_kernel<K, MODEL><<<(unsigned)blocks, kWarps2 * 32, 0, st>>>(
       Lin, Tin, Lout, Tout, g, (int)n_strips, base, rem, (int)band_rows, (int)n_bands,
-      moved_lr, moved_tb);
+      moved_lr, moved_tb, tie_seed, t0);
   return cudaGetLastError();
 }
 
-template <int K>
+template <int K, int MODEL>
 int occupancy2() {
   int b = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, stream2_kernel<K>, kWarps2 * 32, 0) !=
-      cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, stream2_kernel<K, MODEL>, kWarps2 * 32,
+                                                    0) != cudaSuccess) {
     cudaGetLastError();
     return 1;
   }
@@ -230,24 +284,41 @@ bool stream2_applies(const Geom &g) { return g.nb == 64 && g.W % 2 == 0 && g.W >
 
 int64_t stream2_strips(const Geom &g) { return (g.W / 2 + 29) / 30; }
 
-int stream2_occupancy(int k) {
+int stream2_occupancy(int k, int model) {
+  if (model == 2) {
+    switch (k) {
+      case 1: return occupancy2<1, 2>();
+      case 2: return occupancy2<2, 2>();
+      case 4: return occupancy2<4, 2>();
+      default: return occupancy2<8, 2>();
+    }
+  }
   switch (k) {
-    case 1: return occupancy2<1>();
-    case 2: return occupancy2<2>();
-    case 4: return occupancy2<4>();
-    default: return occupancy2<8>();
+    case 1: return occupancy2<1, 1>();
+    case 2: return occupancy2<2, 1>();
+    case 4: return occupancy2<4, 1>();
+    default: return occupancy2<8, 1>();
   }
 }
 
 cudaError_t launch_stream2(const u64 *Lin, const u64 *Tin, u64 *Lout, u64 *Tout, const Geom &g,
                            int k, int64_t band_rows, u64 *moved_lr, u64 *moved_tb,
-                           cudaStream_t st) {
+                           cudaStream_t st, int model, u64 tie_seed, u64 t0) {
   if (!stream2_applies(g) || band_rows < 1 || band_rows > INT32_MAX) return cudaErrorInvalidValue;
+  if (model == 2) {
+    switch (k) {
+      case 1: return launch2_k<1, 2>(Lin, Tin, Lout, Tout, g, band_rows, moved_lr, moved_tb, tie_seed, t0, st);
+      case 2: return launch2_k<2, 2>(Lin, Tin, Lout, Tout, g, band_rows, moved_lr, moved_tb, tie_seed, t0, st);
+      case 4: return launch2_k<4, 2>(Lin, Tin, Lout, Tout, g, band_rows, moved_lr, moved_tb, tie_seed, t0, st);
+      case 8: return launch2_k<8, 2>(Lin, Tin, Lout, Tout, g, band_rows, moved_lr, moved_tb, tie_seed, t0, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (k) {
-    case 1: return launch2_k<1>(Lin, Tin, Lout, Tout, g, band_rows, moved_lr, moved_tb, st);
-    case 2: return launch2_k<2>(Lin, Tin, Lout, Tout, g, band_rows, moved_lr, moved_tb, st);
-    case 4: return launch2_k<4>(Lin, Tin, Lout, Tout, g, band_rows, moved_lr, moved_tb, st);
-    case 8: return launch2_k<8>(Lin, Tin, Lout, Tout, g, band_rows, moved_lr, moved_tb, st);
+    case 1: return launch2_k<1, 1>(Lin, Tin, Lout, Tout, g, band_rows, moved_lr, moved_tb, 0, 0, st);
+    case 2: return launch2_k<2, 1>(Lin, Tin, Lout, Tout, g, band_rows, moved_lr, moved_tb, 0, 0, st);
+    case 4: return launch2_k<4, 1>(Lin, Tin, Lout, Tout, g, band_rows, moved_lr, moved_tb, 0, 0, st);
+    case 8: return launch2_k<8, 1>(Lin, Tin, Lout, Tout, g, band_rows, moved_lr, moved_tb, 0, 0, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -45,6 +45,24 @@ def test_model2_every_depth_matches_oracle(lib, M, N):
             assert sim.model == (lib.BML_MODEL_II, 77)
 
 
+@pytest.mark.parametrize("M,N", [(100, 4096), (77, 6144), (40, 32768), (5, 4224)])
+def test_model2_two_words_per_lane_matches_oracle(lib, M, N):
+    """The two-words-per-lane kernel (rows of full words, an even number of
+    them, more than 32) at every depth and ragged bands."""
+    g0 = random_lattice(M, N, 5 * M + N, 0.1, 0.1)
+    K = 21
+    want, mlr, mtb = oracle.run_model(g0, K, 2, tie_seed=13)
+    for k, band in [(1, 7), (2, 16), (4, 33), (8, 19), (8, M)]:
+        with lib.Lattice(M, N, seed=1, density=0.2, kernel="tblock", block_k=k) as sim:
+            sim.set_model(lib.BML_MODEL_II, 13)
+            sim.set_tiling(k, band, lane_words=2)
+            assert sim.tiling == (k, band, 2)
+            sim.write(g0)
+            sim.step(K)
+            np.testing.assert_array_equal(sim.read(), want, err_msg=str((k, band)))
+            counts_equal(sim.moved_counts(), mlr, mtb)
+
+
 def test_model2_autotuned_256_density_03_1024_steps(lib):
     M = N = 256
     with lib.Lattice(M, N, seed=1, p_lr=0.15, p_tb=0.15, reserve_steps=1024) as sim:
@@ -132,8 +150,12 @@ def test_model2_rejections(lib):
             sim.set_model(7, 1)
         sim.set_model(lib.BML_MODEL_II, 1)
         with pytest.raises(lib.BMLError):
-            sim.set_tiling(2, 8, lane_words=2)
-        with pytest.raises(lib.BMLError):
             sim.set_tiling(1, 0)
         sim.set_tiling(2, 8)
         assert sim.tiling == (2, 8, 1)
+        sim.set_tiling(2, 8, lane_words=2)
+        assert sim.tiling == (2, 8, 2)
+    with lib.Lattice(16, 100, seed=1, density=0.2, kernel="tblock", block_k=2) as sim:
+        sim.set_model(lib.BML_MODEL_II, 1)
+        with pytest.raises(lib.BMLError):       # N % 64 != 0: one word per lane only
+            sim.set_tiling(2, 8, lane_words=2)
