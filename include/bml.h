@@ -66,6 +66,13 @@ extern "C" {
 #define BML_KERNEL_FUSED 3    /* two bitplanes; one launch per step (both
                                  phases in one pass, no bands)                */
 #define BML_KERNEL_TBLOCK 4   /* two bitplanes; k full steps per launch       */
+#define BML_KERNEL_RESIDENT 5 /* two bitplanes kept in one thread block's
+                                 shared memory; every step of a bml_step
+                                 call (up to 4096 per launch) in one launch.
+                                 Small lattices only: 4*M*P*8 bytes plus
+                                 32 KiB must fit the block's shared memory
+                                 (P = ceil(N/64) rounded up to even; about
+                                 M*P <= 5000 words on B300), else BML_EINVAL */
 
 typedef struct bml_sim bml_sim;
 
@@ -149,7 +156,8 @@ int bml_set_tiling(bml_sim *sim, int block_k, int64_t band_rows);
  * selects 1. */
 int bml_set_tiling_ex(bml_sim *sim, int block_k, int64_t band_rows, int lane_words);
 
-/* Current tiling of the bitplane kernels (band_rows 0: one-pass kernel). */
+/* Current tiling of the bitplane kernels (band_rows 0: one-pass kernel;
+ * lane_words 0 with block_k 0: the resident kernel). */
 int bml_get_tiling(const bml_sim *sim, int *block_k, int64_t *band_rows, int *lane_words);
 
 /* ------------------------------------------------------------------------
@@ -173,8 +181,8 @@ int bml_get_tiling(const bml_sim *sim, int *block_k, int64_t *band_rows, int *la
  * (k steps per launch, one 64-cell word per lane, any N): the object must
  * have been created with BML_KERNEL_TBLOCK or BML_KERNEL_AUTO, otherwise
  * BML_EINVAL.  Selecting a model autotunes its tiling (cached per shape,
- * model and device; bml_set_tiling_ex may override it, lane_words 1 only
- * for Model II).  Synchronises the object's stream.  BML_EINVAL for an
+ * model and device; bml_set_tiling_ex may override it).  Synchronises the
+ * object's stream.  BML_EINVAL for an
  * unknown model; the object is unchanged on failure. */
 int bml_set_model(bml_sim *sim, int model, uint64_t tie_seed);
 

@@ -35,12 +35,14 @@ BML_KERNEL_BYTE = 1
 BML_KERNEL_BITPLANE = 2
 BML_KERNEL_FUSED = 3
 BML_KERNEL_TBLOCK = 4
+BML_KERNEL_RESIDENT = 5
 
 BML_MODEL_I = 1
 BML_MODEL_II = 2
 
 KERNELS = {"auto": BML_KERNEL_AUTO, "byte": BML_KERNEL_BYTE, "bitplane": BML_KERNEL_BITPLANE,
-           "fused": BML_KERNEL_FUSED, "tblock": BML_KERNEL_TBLOCK}
+           "fused": BML_KERNEL_FUSED, "tblock": BML_KERNEL_TBLOCK,
+           "resident": BML_KERNEL_RESIDENT}
 
 _i64, _u64, _dbl, _int, _vp = (ctypes.c_int64, ctypes.c_uint64, ctypes.c_double,
                                ctypes.c_int, ctypes.c_void_p)

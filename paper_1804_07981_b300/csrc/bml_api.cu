@@ -74,12 +74,16 @@ extern "C" int bml_set_allocator(bml_alloc_fn alloc, bml_free_fn free_fn, void *
 }
 
 // ------------------------------------------------------------------ sim --
+// Longest launch (in steps) the autotuner times; its count scratch holds
+// this many LR and TB counts.
+constexpr int kTuneSteps = 64;
+
 struct bml_sim {
   Geom g;
   int kernel = BML_KERNEL_AUTO;
   int block_k = 1;
   int64_t band_rows = 0;
-  int lane_words = 1;  // streaming kernel: 64-cell words per lane (1 or 2)
+  int lane_words = 1;  // streaming kernel: 64-cell words per lane (1 or 2); 0: resident kernel
   int model = BML_MODEL_I;
   u64 tie_seed = 0;  // Model II tie-break generator state
   cudaStream_t st = nullptr;
@@ -93,7 +97,7 @@ struct bml_sim {
   int64_t cap = 0;
   int64_t steps_done = 0;
   DevBuf flag;     // one int for value checks
-  DevBuf scratch;  // 16 u64 of counts for autotuning launches
+  DevBuf scratch;  // kTuneSteps LR then kTuneSteps TB counts for autotuning launches
 };
 
 namespace {
@@ -215,6 +219,19 @@ int enqueue_steps(bml_sim *s, int64_t k, u64 *lr, u64 *tb, bool commit, int64_t 
     }
     return BML_OK;
   }
+  // lane_words == 0: the resident kernel, up to resident_max_steps() per launch
+  if (s->lane_words == 0) {
+    int64_t done = 0;
+    while (done < k) {
+      const int d = (int)std::min<int64_t>(k - done, resident_max_steps());
+      const int a = s->cur, b = 1 - s->cur;
+      CUDA_TRY(launch_resident(plane_L(s, a), plane_T(s, a), plane_L(s, b), plane_T(s, b), g, d,
+                               lr + done, tb + done, s->st));
+      if (commit) s->cur = b;
+      done += d;
+    }
+    return BML_OK;
+  }
   // band_rows == 0: the direct one-pass fused kernel, one launch per step
   if (s->band_rows == 0) {
     for (int64_t t = 0; t < k; ++t) {
@@ -284,6 +301,8 @@ int autotune(bml_sim *s) {
   const bool m2 = s->model == BML_MODEL_II;
   std::vector<Tiling> cands;
   if (!m2) cands.push_back({1, 0, 1});  // Model II has no one-pass kernel
+  // the resident kernel, timed on 64-step launches (a call runs all its steps in one)
+  if (!m2 && resident_applies(s->g)) cands.push_back({kTuneSteps, s->g.M, 0});
   for (int lw : {1, 2}) {
     if (lw == 2 && !stream2_applies(s->g)) continue;
     for (int k : {1, 2, 4, 8}) {
@@ -338,7 +357,11 @@ int autotune(bml_sim *s) {
       s->block_k = c.k;
       s->band_rows = c.band;
       s->lane_words = c.lane_words;
-      u64 *lr = (u64 *)s->scratch.ptr, *tb = lr + 8;
+      if (c.k > kTuneSteps) {
+        rc = fail(BML_EINVAL, "autotune: candidate depth %d exceeds the count scratch", c.k);
+        goto done;
+      }
+      u64 *lr = (u64 *)s->scratch.ptr, *tb = lr + kTuneSteps;
       // warm-up (non-committing: reads cur, writes the other buffer)
       if ((rc = enqueue_steps(s, c.k, lr, tb, false))) goto done;
       cudaEventRecord(e0, s->st);
@@ -370,6 +393,7 @@ done:
     s->lane_words = saved_lw;
     return rc;
   }
+  if (best_lw == 0) best_k = 0;  // resident: every step of a call in one launch
   s->block_k = best_k;
   s->band_rows = best_b;
   s->lane_words = best_lw;
@@ -390,8 +414,11 @@ extern "C" int bml_create_ex(int64_t M, int64_t N, uint64_t seed, double p_lr, d
   if (!(p_lr >= 0.0 && p_tb >= 0.0 && p_lr + p_tb <= 1.0))
     return fail(BML_EINVAL, "need p_lr >= 0, p_tb >= 0, p_lr + p_tb <= 1 (got %g, %g)", p_lr,
                 p_tb);
-  if (kernel < BML_KERNEL_AUTO || kernel > BML_KERNEL_TBLOCK)
+  if (kernel < BML_KERNEL_AUTO || kernel > BML_KERNEL_RESIDENT)
     return fail(BML_EINVAL, "unknown kernel %d", kernel);
+  if (kernel == BML_KERNEL_RESIDENT && !resident_applies(make_geom(M, N)))
+    return fail(BML_EINVAL, "lattice %lld x %lld does not fit one block's shared memory",
+                (long long)M, (long long)N);
   if (kernel == BML_KERNEL_TBLOCK) {
     if (block_k == 0) block_k = 4;
     if (block_k != 1 && block_k != 2 && block_k != 4 && block_k != 8)
@@ -403,8 +430,12 @@ extern "C" int bml_create_ex(int64_t M, int64_t N, uint64_t seed, double p_lr, d
   if (!s) return fail(BML_ENOMEM, "host allocation failed");
   s->g = make_geom(M, N);
   s->kernel = kernel;
-  s->block_k = kernel == BML_KERNEL_TBLOCK ? block_k : 1;
+  s->block_k = kernel == BML_KERNEL_TBLOCK ? block_k : (kernel == BML_KERNEL_RESIDENT ? 0 : 1);
   s->band_rows = kernel == BML_KERNEL_FUSED ? 0 : default_band(s->g);
+  if (kernel == BML_KERNEL_RESIDENT) {
+    s->band_rows = s->g.M;
+    s->lane_words = 0;
+  }
   s->st = (cudaStream_t)stream;
   {
     std::lock_guard<std::mutex> lk(g_alloc_mu);
@@ -430,7 +461,7 @@ extern "C" int bml_create_ex(int64_t M, int64_t N, uint64_t seed, double p_lr, d
     }
   }
   if ((rc = dev_alloc(s, s->flag, 256))) goto fail_;
-  if ((rc = dev_alloc(s, s->scratch, 16 * sizeof(u64)))) goto fail_;
+  if ((rc = dev_alloc(s, s->scratch, 2 * kTuneSteps * sizeof(u64)))) goto fail_;
   if ((rc = grow_counts(s, reserve_steps > 0 ? reserve_steps : 4096))) goto fail_;
   if (kernel == BML_KERNEL_AUTO) {
     if ((rc = autotune(s))) goto fail_;
@@ -487,7 +518,8 @@ extern "C" int bml_get_config(const bml_sim *s, int *kernel, int *block_k, int64
   if (kernel) {
     *kernel = s->kernel;
     if (s->kernel == BML_KERNEL_AUTO)
-      *kernel = s->band_rows == 0 ? BML_KERNEL_FUSED : BML_KERNEL_TBLOCK;
+      *kernel = s->lane_words == 0 ? BML_KERNEL_RESIDENT
+                                   : (s->band_rows == 0 ? BML_KERNEL_FUSED : BML_KERNEL_TBLOCK);
   }
   if (block_k) *block_k = s->block_k;
   if (band_rows) *band_rows = s->band_rows;
@@ -517,7 +549,8 @@ extern "C" int bml_get_tiling(const bml_sim *s, int *block_k, int64_t *band_rows
 
 extern "C" int bml_set_tiling(bml_sim *s, int block_k, int64_t band_rows) {
   if (!s) return fail(BML_EINVAL, "sim is NULL");
-  if (!uses_planes(s->kernel) || s->kernel == BML_KERNEL_BITPLANE)
+  if (!uses_planes(s->kernel) || s->kernel == BML_KERNEL_BITPLANE ||
+      s->kernel == BML_KERNEL_RESIDENT)
     return fail(BML_EINVAL, "tiling applies to the streaming bitplane kernels only");
   if (block_k != 1 && block_k != 2 && block_k != 4 && block_k != 8)
     return fail(BML_EINVAL, "block_k must be 1, 2, 4 or 8 (got %d)", block_k);

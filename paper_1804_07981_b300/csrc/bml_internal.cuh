@@ -98,6 +98,13 @@ cudaError_t launch_model2(const u64 *Lin, const u64 *Tin, u64 *Lout, u64 *Tout, 
                           int k, int64_t band_rows, u64 tie_seed, u64 t0, u64 *moved_lr,
                           u64 *moved_tb, cudaStream_t st);
 
+// Resident kernel: the whole lattice in one block's shared memory, k <=
+// resident_max_steps() steps per launch.
+bool resident_applies(const Geom &g);
+int resident_max_steps();
+cudaError_t launch_resident(const u64 *Lin, const u64 *Tin, u64 *Lout, u64 *Tout, const Geom &g,
+                            int k, u64 *moved_lr, u64 *moved_tb, cudaStream_t st);
+
 // Two-words-per-lane streaming kernel (rows of full words, W even, W > 32);
 // model 1 (the paper's model) or 2 (Model II, with tie_seed and the index
 // t0 of the launch's first step).

@@ -57,6 +57,9 @@ def test_create_rejects_bad_kernel_and_depth(lib):
     with pytest.raises(lib.BMLError) as e:
         lib.bml_create_ex(8, 8, 1, 0.1, 0.1, kernel=9)
     assert e.value.code == lib.BML_EINVAL
+    with pytest.raises(lib.BMLError) as e:            # far too large for one block
+        lib.bml_create_ex(4096, 4096, 1, 0.1, 0.1, kernel=lib.BML_KERNEL_RESIDENT, block_k=0)
+    assert e.value.code == lib.BML_EINVAL
     with pytest.raises(lib.BMLError) as e:
         lib.bml_create_ex(8, 8, 1, 0.1, 0.1, kernel=lib.BML_KERNEL_TBLOCK, block_k=3)
     assert e.value.code == lib.BML_EINVAL

@@ -20,7 +20,7 @@ GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 KERNEL_CASES = [
     ("byte", 0), ("bitplane", 0), ("fused", 0),
-    ("tblock", 1), ("tblock", 2), ("tblock", 4), ("tblock", 8), ("auto", 0),
+    ("tblock", 1), ("tblock", 2), ("tblock", 4), ("tblock", 8), ("auto", 0), ("resident", 0),
 ]
 
 SHAPES = [
@@ -215,6 +215,24 @@ def test_explicit_tilings_match_oracle(lib, M, N):
             np.testing.assert_array_equal(sim.read(), want, err_msg=str((k, band)))
             oracle_counts_equal(sim.moved_counts(), mlr, mtb)
             assert sim.config[1:] == (k, band)
+
+
+def test_resident_kernel_long_calls(lib):
+    """The resident kernel runs a call's steps in launches of up to 4096:
+    5000 steps in one call, then 3 more; lattice and every count."""
+    M, N = 48, 200
+    g0 = random_lattice(M, N, 5, 0.15, 0.15)
+    want, mlr, mtb = oracle.run(g0, 5003)
+    with make(lib, M, N, "resident", 0) as sim:
+        assert sim.config[0] == lib.BML_KERNEL_RESIDENT
+        assert sim.tiling == (0, M, 0)
+        sim.write(g0)
+        sim.step(5000)
+        sim.step(3)
+        np.testing.assert_array_equal(sim.read(), want)
+        oracle_counts_equal(sim.moved_counts(), mlr, mtb)
+        with pytest.raises(lib.BMLError):
+            sim.set_tiling(1, 16)
 
 
 def test_set_tiling_rejects_bad_values(lib):
