@@ -118,6 +118,16 @@ int bml_step(bml_sim *sim, int64_t k);
 int bml_moved_counts(bml_sim *sim, int64_t first, int64_t n, int64_t *out_total,
                      int64_t *out_lr, int64_t *out_tb);
 
+/* Enqueue copies of the LR and TB moved counts of steps first+1 ..
+ * first+n into host arrays of n int64 each (either may be NULL; the total
+ * is their sum) on the object's stream and return without waiting: a
+ * caller can read every step's result while the steps run.  The values are
+ * valid once the stream has been synchronised (bml_synchronize, or any call
+ * documented to synchronise).  The host arrays should be page-locked, or the
+ * copy waits for the stream.  Same range rule as bml_moved_counts. */
+int bml_moved_counts_async(bml_sim *sim, int64_t first, int64_t n, int64_t *out_lr,
+                           int64_t *out_tb);
+
 /* Copy the current lattice (M*N bytes, format above) to host memory `out`.
  * Synchronises the stream. */
 int bml_read_lattice(bml_sim *sim, uint8_t *out);

@@ -72,6 +72,7 @@ _lib_create_ex = _sig("bml_create_ex", [_i64, _i64, _u64, _dbl, _dbl, _int, _int
 _lib_reserve = _sig("bml_reserve_steps", [_vp, _i64])
 _lib_step = _sig("bml_step", [_vp, _i64])
 _lib_counts = _sig("bml_moved_counts", [_vp, _i64, _i64, _vp, _vp, _vp])
+_lib_counts_async = _sig("bml_moved_counts_async", [_vp, _i64, _i64, _vp, _vp])
 _lib_read = _sig("bml_read_lattice", [_vp, _vp])
 _lib_write = _sig("bml_write_lattice", [_vp, _vp])
 _lib_read_dev = _sig("bml_read_lattice_device", [_vp, _vp])
@@ -168,6 +169,18 @@ def bml_moved_counts(sim: int, first: int, n: int):
     tb = np.zeros(n, dtype=np.int64)
     _check(_lib_counts(sim, first, n, _host_ptr(tot), _host_ptr(lr), _host_ptr(tb)))
     return tot, lr, tb
+
+
+def bml_moved_counts_async(sim: int, first: int, n: int, out_lr: np.ndarray,
+                           out_tb: np.ndarray) -> None:
+    """Enqueue the LR / TB count copies of steps first+1..first+n into the
+    given int64 host arrays (page-locked, e.g. from a pinned torch tensor);
+    valid after the stream is synchronised."""
+    for a in (out_lr, out_tb):
+        if a is not None and (a.dtype != np.int64 or a.size < n or not a.flags.c_contiguous):
+            raise ValueError("count arrays must be contiguous int64 with n entries")
+    _check(_lib_counts_async(sim, first, n, None if out_lr is None else _host_ptr(out_lr),
+                             None if out_tb is None else _host_ptr(out_tb)))
 
 
 def bml_read_lattice(sim: int, M: int, N: int, out: np.ndarray | None = None) -> np.ndarray:

@@ -625,6 +625,22 @@ extern "C" int bml_moved_counts(bml_sim *s, int64_t first, int64_t n, int64_t *o
   return BML_OK;
 }
 
+extern "C" int bml_moved_counts_async(bml_sim *s, int64_t first, int64_t n, int64_t *out_lr,
+                                      int64_t *out_tb) {
+  if (!s) return fail(BML_EINVAL, "sim is NULL");
+  if (first < 0 || n < 0 || first + n > s->steps_done)
+    return fail(BML_EINVAL, "count range [%lld, %lld) outside [0, %lld)", (long long)first,
+                (long long)(first + n), (long long)s->steps_done);
+  if (n == 0) return BML_OK;
+  if (out_lr)
+    CUDA_TRY(cudaMemcpyAsync(out_lr, cnt_lr(s) + first, (size_t)n * 8, cudaMemcpyDeviceToHost,
+                             s->st));
+  if (out_tb)
+    CUDA_TRY(cudaMemcpyAsync(out_tb, cnt_tb(s) + first, (size_t)n * 8, cudaMemcpyDeviceToHost,
+                             s->st));
+  return BML_OK;
+}
+
 // -------------------------------------------------------- lattice I/O --
 namespace {
 

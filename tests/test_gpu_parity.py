@@ -142,6 +142,27 @@ def test_count_range_errors(lib):
         assert tot.shape == (2,)
 
 
+def test_async_counts_equal_synchronous_counts(lib):
+    """Counts copied without waiting (into page-locked host memory, read
+    after a synchronise) equal the synchronous read, across history growth."""
+    import torch
+    M, N = 40, 300
+    with lib.Lattice(M, N, seed=2, density=0.3, kernel="tblock", block_k=4,
+                     reserve_steps=16) as sim:
+        lr = torch.zeros(200, dtype=torch.int64, pin_memory=True).numpy()
+        tb = torch.zeros(200, dtype=torch.int64, pin_memory=True).numpy()
+        for s in range(20):
+            sim.step(10)
+            lib.bml_moved_counts_async(sim.handle, 10 * s, 10, lr[10 * s:10 * s + 10],
+                                       tb[10 * s:10 * s + 10])
+        sim.synchronize()
+        tot, a, b = sim.moved_counts()
+        np.testing.assert_array_equal(lr, a)
+        np.testing.assert_array_equal(tb, b)
+        with pytest.raises(lib.BMLError):
+            lib.bml_moved_counts_async(sim.handle, 195, 10, lr[:10], tb[:10])
+
+
 def test_count_history_grows(lib):
     M, N = 24, 100
     with lib.Lattice(M, N, seed=4, density=0.3, kernel="tblock", block_k=8,
