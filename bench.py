@@ -179,14 +179,16 @@ def _cpu_sample(budget_s: float, threads: int):
     return rate, desc, dt
 
 
-def _ensemble_bench(bml, torch, stream, steps, seed_base=1):
+def _ensemble_bench(bml, torch, stream, steps, seed_base=1, tiling=None):
     """Batched ensemble of 4096 lattices (M, N uniform on {64..2048}, density
     uniform on [0.1, 0.6], LR fraction uniform on [0.3, 0.7]), autotuned,
     graph-replayed; `steps` steps timed with CUDA events after a warm-up."""
     from paper_1804_07981_b300.inputs import ensemble_params
     p = ensemble_params(4096, seed=1)
+    k, band = tiling if tiling else (0, 0)  # 0, 0: autotuned
     ens = bml.Ensemble(p["M"], p["N"], p["seed"] + np.uint64(seed_base - 1), p["p_lr"],
-                       p["p_tb"], stream=stream, reserve_steps=steps + 64)
+                       p["p_tb"], block_k=k, band_rows=band, stream=stream,
+                       reserve_steps=steps + 64)
     ens.step(32)
     ens.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -207,13 +209,17 @@ def _ensemble_bench(bml, torch, stream, steps, seed_base=1):
                         "LR fraction ~ U[0.3,0.7], seeds 1..4096"}
 
 
-def _model2_bench(bml, torch, stream, M, N, steps, sm_mhz, seed=1):
+def _model2_bench(bml, torch, stream, M, N, steps, sm_mhz, seed=1, tiling=None):
     """Model II on the bench lattice (same placement), autotuned, `steps`
     steps timed with CUDA events after a warm-up; the counts of the timed
     steps are checked for plausibility."""
-    with bml.Lattice(M, N, seed=seed, density=DENSITY, stream=stream,
-                     reserve_steps=steps + 64) as sim:
+    # explicit tiling: a TBLOCK object (no autotuning launches); else AUTO
+    kernel, bk = ("tblock", tiling[0]) if tiling else ("auto", 0)
+    with bml.Lattice(M, N, seed=seed, density=DENSITY, kernel=kernel, block_k=bk,
+                     stream=stream, reserve_steps=steps + 64) as sim:
         sim.set_model(bml.BML_MODEL_II, seed)
+        if tiling:
+            sim.set_tiling(*tiling)
         k, band, lw = sim.tiling
         sim.step(3 * k)
         sim.synchronize()
@@ -475,7 +481,8 @@ def run_ours(args):
 
     ens = None
     if not args.no_ensemble:
-        ens = _ensemble_bench(bml, torch, stream, args.ensemble_steps, seed_base=1 + 4096 * rank)
+        ens = _ensemble_bench(bml, torch, stream, args.ensemble_steps, seed_base=1 + 4096 * rank,
+                              tiling=_ints(args.ensemble_tiling))
         ens_max = max_over_ranks(ens["seconds"])
         ens["value"] = job_rate(world, ens["lattices"] * ens["steps"], ens_max)
 
@@ -491,7 +498,8 @@ def run_ours(args):
     m2 = None
     if not args.no_model2:
         m2 = _model2_bench(bml, torch, stream, M, N, args.model2_steps,
-                           (clk or {}).get("sm_mhz") or SM_MAX_MHZ, seed=1 + rank)
+                           (clk or {}).get("sm_mhz") or SM_MAX_MHZ, seed=1 + rank,
+                           tiling=_ints(args.model2_tiling))
         m2_max = max_over_ranks(m2["seconds"])
         m2["value"] = job_rate(world, M * N * m2["steps"], m2_max)
 
@@ -528,6 +536,10 @@ def run_ours(args):
     return 0
 
 
+def _ints(spec):
+    return tuple(int(x) for x in spec.split(",")) if spec else None
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -540,7 +552,11 @@ def main():
     ap.add_argument("--lane-words", type=int, default=1, help="1 or 2 (with --band)")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--ensemble-steps", type=int, default=1024)
+    ap.add_argument("--ensemble-tiling", default=None,
+                    help="K,BAND: explicit ensemble depth and band (default: autotuned)")
     ap.add_argument("--no-model2", action="store_true")
+    ap.add_argument("--model2-tiling", default=None,
+                    help="K,BAND,LANE_WORDS: explicit Model II tiling (default: autotuned)")
     ap.add_argument("--no-byte", action="store_true")
     ap.add_argument("--byte-steps", type=int, default=16)
     ap.add_argument("--no-configs", action="store_true")

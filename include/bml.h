@@ -190,9 +190,10 @@ int bml_get_tiling(const bml_sim *sim, int *block_k, int64_t *band_rows, int *la
  * count history are kept).  Model II runs on the streaming bitplane kernel
  * (k steps per launch, one 64-cell word per lane, any N): the object must
  * have been created with BML_KERNEL_TBLOCK or BML_KERNEL_AUTO, otherwise
- * BML_EINVAL.  Selecting a model autotunes its tiling (cached per shape,
- * model and device; bml_set_tiling_ex may override it).  Synchronises the
- * object's stream.  BML_EINVAL for an
+ * BML_EINVAL.  On a BML_KERNEL_AUTO object selecting a model autotunes the
+ * tiling for it (cached per shape, model and device); a BML_KERNEL_TBLOCK
+ * object keeps its tiling (bml_set_tiling_ex may change either).
+ * Synchronises the object's stream.  BML_EINVAL for an
  * unknown model; the object is unchanged on failure. */
 int bml_set_model(bml_sim *sim, int model, uint64_t tie_seed);
 

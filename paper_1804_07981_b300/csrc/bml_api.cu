@@ -578,7 +578,7 @@ extern "C" int bml_set_model(bml_sim *s, int model, uint64_t tie_seed) {
   s->model = model;
   s->tie_seed = tie_seed;
   int rc = BML_OK;
-  if (s->kernel == BML_KERNEL_AUTO || model == BML_MODEL_II) rc = autotune(s);
+  if (s->kernel == BML_KERNEL_AUTO) rc = autotune(s);  // TBLOCK keeps the caller's tiling
   if (!rc && cudaStreamSynchronize(s->st) != cudaSuccess)
     rc = fail(BML_ECUDA, "set_model: %s", cudaGetErrorString(cudaGetLastError()));
   if (rc) {

@@ -155,6 +155,9 @@ def test_model2_rejections(lib):
         assert sim.tiling == (2, 8, 1)
         sim.set_tiling(2, 8, lane_words=2)
         assert sim.tiling == (2, 8, 2)
+        sim.set_model(lib.BML_MODEL_I)          # a TBLOCK object keeps its tiling
+        sim.set_model(lib.BML_MODEL_II, 2)
+        assert sim.tiling == (2, 8, 2)
     with lib.Lattice(16, 100, seed=1, density=0.2, kernel="tblock", block_k=2) as sim:
         sim.set_model(lib.BML_MODEL_II, 1)
         with pytest.raises(lib.BMLError):       # N % 64 != 0: one word per lane only
