@@ -17,7 +17,8 @@ Sub-measurements on the same JSON line: "ensemble" (4096 lattices, the
 batched API), "model2" (the Sec. 2 Model II variant on the bench lattice,
 tie-break seed = placement seed, 1024 steps; --no-model2 skips it),
 "byte_kernel" (the plain byte-per-cell form on the bench lattice, 16 steps,
-against the HBM peak), "configs" (256^2 for 1024 steps; 4096^2 byte vs
+against the HBM peak), "one_pass" (one full step per DRAM pass on the bench
+lattice, 256 steps, against the HBM peak), "configs" (256^2 for 1024 steps; 4096^2 byte vs
 bit-packed over 3 densities x 3 seeds x 4096 steps; rank 0 of a 1-GPU run).
 
 --impl reference times the CPU oracle (test infrastructure) on the host
@@ -66,9 +67,10 @@ SMS = 148
 ALU_LANES_PER_SM_CLK = 64  # integer ALU pipe: 2 warp instructions per clock per SM
 SM_MAX_MHZ = 2032.0
 # DRAM bytes (read + write, as counted by ncu for one launch) per cell, from
-# the captures summarised in profiles/ (stream2_kernel<8>: 32768 x 32768;
-# fused_rows_kernel: 16384 x 32768); scaled by the cell count of the run
-TRAFFIC_PER_CELL = {"stream2_kernel<8>": 0.4700, "fused_rows_kernel": 0.4068}
+# the captures summarised in profiles/ (stream2_kernel<8> and <1>: 32768 x
+# 32768; fused_rows_kernel: 16384 x 32768); scaled by the cell count of the run
+TRAFFIC_PER_CELL = {"stream2_kernel<8>": 0.4700, "stream2_kernel<1>": 0.4517,
+                    "fused_rows_kernel": 0.4068}
 
 
 def _peaks():
@@ -273,6 +275,30 @@ def _byte_bench(bml, torch, stream, M, N, steps, hbm_peak, seed=1):
             "kernel": "byte_h + byte_v", "gpu_launches": 2 * steps,
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
                          "frac": gbs / hbm_peak, "bytes_per_cell_step": 4.0}}
+
+
+def _one_pass_bench(bml, torch, stream, M, N, steps, hbm_peak, seed=1):
+    """One full step per DRAM pass (depth 1) on the bench lattice: the
+    two-words-per-lane streaming kernel at depth 1 with 16-row bands (the
+    one-word kernel where N does not allow pairs); HBM-bound, 0.5 B per
+    cell-step of algorithmic traffic."""
+    lw = 2 if (N % 64 == 0 and (N // 64) % 2 == 0 and N // 64 > 32) else 1
+    with bml.Lattice(M, N, seed=seed, density=DENSITY, kernel="tblock", block_k=1,
+                     stream=stream, reserve_steps=steps + 8) as sim:
+        sim.set_tiling(1, 16, lane_words=lw)
+        sim.step(3)
+        ms = _timed_steps(torch, stream, sim, steps)
+    cells = M * N
+    gbs = BYTES_PER_CELL_STEP * cells * steps / (ms / 1e3) / 1e9
+    kname = "stream2_kernel<1>" if lw == 2 else "stream_kernel<1>"
+    traffic = TRAFFIC_PER_CELL.get(kname)
+    return {"metric": "cell-updates/s", "value": cells * steps / (ms / 1e3),
+            "unit": "cell-updates/s", "steps": steps, "seconds": ms / 1e3,
+            "kernel": kname, "temporal_depth": 1, "band_rows": 16, "lane_words": lw,
+            "gpu_launches": steps,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": gbs / hbm_peak, "bytes_per_cell_step": BYTES_PER_CELL_STEP,
+                         "traffic": traffic * cells if traffic else None}}
 
 
 def _config_benches(bml, torch, stream):
@@ -491,6 +517,12 @@ def run_ours(args):
         byte = _byte_bench(bml, torch, stream, M, N, args.byte_steps, hbm_peak, seed=1 + rank)
         byte["value"] = job_rate(world, M * N * byte["steps"], max_over_ranks(byte["seconds"]))
 
+    one = None
+    if not args.no_one_pass:
+        one = _one_pass_bench(bml, torch, stream, M, N, args.one_pass_steps, hbm_peak,
+                              seed=1 + rank)
+        one["value"] = job_rate(world, M * N * one["steps"], max_over_ranks(one["seconds"]))
+
     small = None
     if not args.no_configs and world == 1:
         small = _config_benches(bml, torch, stream)
@@ -526,7 +558,7 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (2 x 256 MB bitplanes)",
                        "parallelism": "replicas x%d" % world},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "ensemble": ens,
-            "model2": m2, "byte_kernel": byte, "configs": small,
+            "model2": m2, "byte_kernel": byte, "one_pass": one, "configs": small,
             "gpu_launches": gpu_launches, "clocks": clk,
         }
         print(json.dumps(line))
@@ -560,6 +592,8 @@ def main():
     ap.add_argument("--no-byte", action="store_true")
     ap.add_argument("--byte-steps", type=int, default=16)
     ap.add_argument("--no-configs", action="store_true")
+    ap.add_argument("--no-one-pass", action="store_true")
+    ap.add_argument("--one-pass-steps", type=int, default=256)
     ap.add_argument("--model2-steps", type=int, default=1024)
     ap.add_argument("--M", type=int, default=M_ROWS)
     ap.add_argument("--N", type=int, default=N_COLS)
