@@ -111,3 +111,34 @@ def test_32768_full_run_properties(lib):
     assert (int(tb.sum()) - (s_tb1 - s_tb0)) % M == 0
     n_lr, n_tb = int(per["0"][0].sum()), int(per["0"][1].sum())
     assert lr.min() >= 0 and lr.max() <= n_lr and tb.min() >= 0 and tb.max() <= n_tb
+
+
+def test_32768_one_pass_and_depth_8_agree_and_match_windows(lib):
+    """32768 x 32768, density 0.38, seed 1, 16 steps: the one-pass
+    configuration (depth 1, 16-row bands, two words per lane) and the
+    bench's depth-8 configuration give the same lattice and counts, and
+    sampled 33 x 33 windows match the oracle (8 steps at a time)."""
+    M = N = 32768
+    out = []
+    for k, band in ((1, 16), (8, 251)):
+        with lib.Lattice(M, N, seed=1, density=0.38, kernel="tblock", block_k=k) as sim:
+            sim.set_tiling(k, band, lane_words=2)
+            sim.step(8)
+            g8 = sim.read()
+            sim.step(8)
+            out.append((g8, sim.read(), sim.moved_counts()))
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+    for a, b in zip(out[0][2], out[1][2]):
+        np.testing.assert_array_equal(a, b)
+    t, S = 8, 33
+    rng = np.random.Generator(np.random.PCG64(9))
+    corners = rng.integers(0, M, size=(16, 2))
+    corners[0] = [0, N - 20]
+    for i0, j0 in corners:
+        rows = (np.arange(S) + i0) % M
+        cols = (np.arange(S) + j0) % N
+        w = out[0][0][np.ix_(rows, cols)]          # state after 8 steps
+        w_t, _, _ = oracle.run(w, t)
+        np.testing.assert_array_equal(out[0][1][np.ix_(rows[t:S - t], cols[t:S - t])],
+                                      w_t[t:S - t, t:S - t])
