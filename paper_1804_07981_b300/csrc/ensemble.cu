@@ -68,6 +68,7 @@ struct EnsCtrl {
   int err;               // set by a barrier that timed out
   unsigned bar_count;
   unsigned bar_gen;
+  unsigned tile_next;    // tile dispenser (0 between launches)
 };
 
 struct EnsParams {
@@ -287,15 +288,37 @@ template <int K>
 __global__ void __launch_bounds__(kEnsWarps * 32, K >= 8 ? 3 : 4) ens_kernel(EnsParams p) {
   const int lane = threadIdx.x & 31;
   const int nwarps = gridDim.x * kEnsWarps;
-  const int wid = blockIdx.x * kEnsWarps + (threadIdx.x >> 5);
   const long long base = __ldcg(&p.ctrl->steps);
   const long long last_depth = __ldcg(&p.ctrl->last_depth);
   const int par0 = *(volatile int *)&p.ctrl->parity;
+  // Every warp draws tickets until it gets one past the chunk's last tile, so
+  // chunk c draws exactly n_tiles + nwarps tickets: [c * stride, (c+1) * stride).
+  // The draw of the launch's last ticket resets the dispenser for the next
+  // launch (no later draw exists).
+  // (the host keeps n_chunks * stride below 2^32)
+  const unsigned stride = (unsigned)p.n_tiles + (unsigned)nwarps;
+  const unsigned last_ticket = stride * (unsigned)p.n_chunks - 1u;
   for (int c = 0; c < p.n_chunks; ++c) {
     const long long step0 = base + (long long)c * K;
     const int par = (par0 + c) & 1;
     const long long prev_depth = c == 0 ? last_depth : K;
-    for (int t = wid; t < p.n_tiles; t += nwarps) process_tile<K>(p, t, step0, par, prev_depth, lane);
+    // dynamic assignment: a warp takes the next tile (tiles are ordered
+    // longest first, so this is longest-processing-time-first list
+    // scheduling) until the dispenser passes the last tile
+    const unsigned cbase = (unsigned)c * stride;
+    for (;;) {
+      __shared__ unsigned s_ticket[kEnsWarps];
+      if (lane == 0) {
+        const unsigned v = atomicAdd(&p.ctrl->tile_next, 1u);
+        if (v == last_ticket) atomicExch(&p.ctrl->tile_next, 0u);
+        s_ticket[threadIdx.x >> 5] = v;
+      }
+      __syncwarp();
+      const unsigned t = s_ticket[threadIdx.x >> 5] - cbase;
+      __syncwarp();
+      if (t >= (unsigned)p.n_tiles) break;
+      process_tile<K>(p, (int)t, step0, par, prev_depth, lane);
+    }
     if (c + 1 < p.n_chunks) {
       if (!grid_barrier(p.ctrl, p.bar_target, p.timeout_ns)) return;
     }
@@ -606,7 +629,7 @@ void ens_free(bml_ens *e) {
 // Build tiles for target band height `band`: every lattice is cut into
 // round(M / band) bands (at least one) of near-equal length; groups of equal
 // word width are packed 32 / W to a warp tile, longest bands first, and the
-// tiles are ordered longest first for the round-robin assignment to warps.
+// tiles are ordered longest first for the kernel's dynamic assignment.
 int build_tiles(bml_ens *e, int64_t band) {
   // bands of every lattice, longest first
   struct Band {
@@ -765,8 +788,11 @@ int enqueue_steps_ens(bml_ens *e, int64_t k) {
   const int64_t full = k / e->block_k;
   int64_t left = k - full * e->block_k;
   int64_t done = 0;
+  // one launch draws n_chunks * (n_tiles + warps) 32-bit tickets
+  const int64_t per_chunk = (int64_t)e->n_tiles + 4ll * grid_for(e, e->block_k);
+  const int64_t max_chunks = std::max<int64_t>(1, std::min<int64_t>(1 << 20, 0xffffffffll / per_chunk));
   while (done < full) {
-    const int n = (int)std::min<int64_t>(full - done, 1 << 20);
+    const int n = (int)std::min<int64_t>(full - done, max_chunks);
     int rc = enqueue_ens(e, e->block_k, n, 1);
     if (rc) return rc;
     done += n;
