@@ -32,7 +32,9 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <functional>
 #include <map>
+#include <set>
 #include <string>
 #include <vector>
 
@@ -626,11 +628,16 @@ void ens_free(bml_ens *e) {
   cudaFree(e->flag);
 }
 
-// Build tiles for target band height `band`: every lattice is cut into
+struct TilePlan {
+  std::vector<EnsTile> tiles;
+  std::vector<EnsGroup> groups;
+};
+
+// Plan tiles for target band height `band`: every lattice is cut into
 // round(M / band) bands (at least one) of near-equal length; groups of equal
 // word width are packed 32 / W to a warp tile, longest bands first, and the
 // tiles are ordered longest first for the kernel's dynamic assignment.
-int build_tiles(bml_ens *e, int64_t band) {
+void plan_tiles(const bml_ens *e, int64_t band, TilePlan &plan) {
   // bands of every lattice, longest first
   struct Band {
     EnsGroup g;
@@ -657,26 +664,21 @@ int build_tiles(bml_ens *e, int64_t band) {
     if (a.W != b.W) return a.W > b.W;
     return a.g.lat != b.g.lat ? a.g.lat < b.g.lat : a.g.r0 < b.g.r0;
   });
-  // first fit into warps of 32 lanes: a band joins the first open warp with
-  // room for its W lanes; a warp closes once the bands reaching it are more
-  // than 1/8 shorter than its longest (every band runs the warp's longest
-  // band's rows), or when it is full
+  // first fit into warps of 32 lanes: a band joins the first open warp (in
+  // creation order) with room for its W lanes; a warp closes once the bands
+  // reaching it are more than 1/8 shorter than its longest (every band runs
+  // the warp's longest band's rows), or when it is full.  Open warps are kept
+  // in ordered sets by free lanes; since bands arrive longest first, the
+  // warps that have closed by age are the oldest of each set.
   std::vector<std::vector<EnsGroup>> tg;
   std::vector<int> used, maxlen, minlen;
-  std::vector<size_t> open;
+  std::vector<std::set<size_t>> open_by_room(33);
   for (const Band &x : all) {
     size_t chosen = SIZE_MAX;
-    for (size_t k = 0; k < open.size();) {
-      const size_t ti = open[k];
-      if ((int64_t)maxlen[ti] * 7 > (int64_t)x.g.len * 8) {
-        open.erase(open.begin() + (std::ptrdiff_t)k);
-        continue;
-      }
-      if (32 - used[ti] >= x.W) {
-        chosen = ti;
-        break;
-      }
-      ++k;
+    for (int r = x.W; r <= 32; ++r) {
+      std::set<size_t> &q = open_by_room[r];
+      while (!q.empty() && (int64_t)maxlen[*q.begin()] * 7 > (int64_t)x.g.len * 8) q.erase(q.begin());
+      if (!q.empty() && *q.begin() < chosen) chosen = *q.begin();
     }
     if (chosen == SIZE_MAX) {
       chosen = tg.size();
@@ -684,17 +686,20 @@ int build_tiles(bml_ens *e, int64_t band) {
       used.push_back(0);
       maxlen.push_back(x.g.len);
       minlen.push_back(x.g.len);
-      open.push_back(chosen);
+    } else {
+      open_by_room[32 - used[chosen]].erase(chosen);
     }
     EnsGroup g = x.g;
     g.lane0 = used[chosen];
     tg[chosen].push_back(g);
     used[chosen] += x.W;
     minlen[chosen] = std::min(minlen[chosen], x.g.len);
-    if (used[chosen] == 32) open.erase(std::find(open.begin(), open.end(), chosen));
+    if (used[chosen] < 32) open_by_room[32 - used[chosen]].insert(chosen);
   }
-  std::vector<EnsGroup> groups;
-  std::vector<EnsTile> tiles;
+  std::vector<EnsGroup> &groups = plan.groups;
+  std::vector<EnsTile> &tiles = plan.tiles;
+  groups.clear();
+  tiles.clear();
   for (size_t ti = 0; ti < tg.size(); ++ti) {
     EnsTile t{};
     t.G = (int)tg[ti].size();
@@ -711,6 +716,33 @@ int build_tiles(bml_ens *e, int64_t band) {
   }
   std::stable_sort(tiles.begin(), tiles.end(),
                    [](const EnsTile &a, const EnsTile &b) { return a.max_len > b.max_len; });
+}
+
+// Predicted time of one chunk of depth k for a plan, in rows per warp: a tile
+// costs its longest band plus the 2k halo rows; the score is the mean work
+// per warp plus the makespan of the kernel's longest-first assignment to
+// `warps` warps (list scheduling, simulated).  Measured chunk times of
+// mixed ensembles follow the sum of the two closely (a warp that runs alone
+// at the end of a chunk is faster than one among a full SM, so neither term
+// alone fits).
+double plan_score(const TilePlan &plan, int k, int warps) {
+  if (plan.tiles.empty() || warps < 1) return 0.0;
+  std::vector<long long> heap((size_t)warps, 0);  // min-heap of warp finish times
+  long long total = 0, makespan = 0;
+  for (const EnsTile &t : plan.tiles) {
+    const long long c = (long long)t.max_len + 2ll * k;
+    total += c;
+    std::pop_heap(heap.begin(), heap.end(), std::greater<long long>());
+    heap.back() += c;
+    makespan = std::max(makespan, heap.back());
+    std::push_heap(heap.begin(), heap.end(), std::greater<long long>());
+  }
+  return (double)total / warps + (double)makespan;
+}
+
+int upload_tiles(bml_ens *e, const TilePlan &plan, int64_t band) {
+  const std::vector<EnsTile> &tiles = plan.tiles;
+  const std::vector<EnsGroup> &groups = plan.groups;
   cudaFree(e->d_tiles);
   cudaFree(e->d_groups);
   e->d_tiles = nullptr;
@@ -726,6 +758,12 @@ int build_tiles(bml_ens *e, int64_t band) {
   e->band_rows = band;
   drop_graphs(e);
   return BML_OK;
+}
+
+int build_tiles(bml_ens *e, int64_t band) {
+  TilePlan plan;
+  plan_tiles(e, band, plan);
+  return upload_tiles(e, plan, band);
 }
 
 EnsParams make_params(bml_ens *e, int n_chunks, int commit) {
@@ -840,37 +878,77 @@ int check_err(bml_ens *e) {
   return BML_OK;
 }
 
+// Autotune (depth, band).  Every band height from 32 to 1024 rows in steps of
+// 16 (and powers of two up to the tallest lattice) is planned on the host
+// and scored for depth 8 (plan_score); the four best distinct plans are
+// timed at depth 8 and the best-scored one also at depths 1, 2 and 4.
 int autotune_ens(bml_ens *e) {
+  int max_m = 1;
+  for (const EnsLattice &l : e->lat) max_m = std::max(max_m, l.M);
+  std::vector<int64_t> bands;
+  for (int64_t b = 32; b <= 1024; b += 16) bands.push_back(b);
+  for (int64_t b = 2048; b / 2 < max_m; b *= 2) bands.push_back(b);
+  const int warps8 = grid_for(e, 8) * kEnsWarps;
+  struct Cand {
+    double score;
+    int64_t band;
+    size_t n_tiles;
+  };
+  std::vector<Cand> cands;
+  {
+    TilePlan plan;
+    for (int64_t b : bands) {
+      plan_tiles(e, b, plan);
+      cands.push_back(Cand{plan_score(plan, 8, warps8), b, plan.tiles.size()});
+    }
+  }
+  std::stable_sort(cands.begin(), cands.end(),
+                   [](const Cand &x, const Cand &y) { return x.score < y.score; });
+  // drop repeats of the same plan (bands above every lattice's height)
+  std::vector<Cand> top;
+  for (const Cand &c : cands) {
+    bool dup = false;
+    for (const Cand &t : top) dup = dup || (t.n_tiles == c.n_tiles && t.score == c.score);
+    if (!dup) top.push_back(c);
+    if (top.size() == 4) break;
+  }
+  std::vector<std::pair<int64_t, int>> trials;  // (band, depth)
+  for (const Cand &c : top) trials.emplace_back(c.band, 8);
+  for (int k : {4, 2, 1}) trials.emplace_back(top[0].band, k);
+
   cudaEvent_t a, b;
   ECUDA(cudaEventCreate(&a));
   ECUDA(cudaEventCreate(&b));
   double best = 1e30;
-  int best_k = 4;
-  int64_t best_b = 128;
+  int best_k = 8;
+  int64_t best_b = top[0].band;
+  int64_t built = -1;
   int rc = BML_OK;
-  for (int64_t band : {64, 128, 256, 512}) {
-    if ((rc = build_tiles(e, band))) break;
-    for (int k : {1, 2, 4, 8}) {
-      if ((rc = enqueue_ens(e, k, 1, 0))) break;  // warm-up, not committed
-      cudaEventRecord(a, e->st);
-      const int reps = 3;
-      for (int r = 0; r < reps && !rc; ++r) rc = enqueue_ens(e, k, 1, 0);
-      cudaEventRecord(b, e->st);
-      if (rc) break;
-      if (cudaEventSynchronize(b) != cudaSuccess) {
-        rc = efail(BML_ECUDA, "ensemble autotune: %s", cudaGetErrorString(cudaGetLastError()));
-        break;
-      }
-      float ms = 0;
-      cudaEventElapsedTime(&ms, a, b);
-      const double per = ms / (reps * k);
-      if (per < best) {
-        best = per;
-        best_k = k;
-        best_b = band;
-      }
+  for (const auto &tr : trials) {
+    const int64_t band = tr.first;
+    const int k = tr.second;
+    if (band != built) {
+      if ((rc = build_tiles(e, band))) break;
+      built = band;
     }
+    if ((rc = enqueue_ens(e, k, 1, 0))) break;  // warm-up, not committed
+    cudaEventRecord(a, e->st);
+    const int reps = 3;
+    for (int r = 0; r < reps && !rc; ++r) rc = enqueue_ens(e, k, 1, 0);
+    cudaEventRecord(b, e->st);
     if (rc) break;
+    if (cudaEventSynchronize(b) != cudaSuccess) {
+      rc = efail(BML_ECUDA, "ensemble autotune: %s", cudaGetErrorString(cudaGetLastError()));
+      break;
+    }
+    float ms = 0;
+    cudaEventElapsedTime(&ms, a, b);
+    const double per = ms / (reps * k);
+    if (per < best) {
+      best = per;
+      best_k = k;
+      best_b = band;
+    }
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
