@@ -54,68 +54,100 @@ __device__ __forceinline__ uint32_t popc_chunk(Chunk c) {
   return (uint32_t)(__popcll(c.lo) + __popcll(c.hi));
 }
 
+// A warp takes 32 consecutive chunks of one row (a row segment), one per lane;
+// the cells just past a chunk's ends come from the neighbouring lanes'
+// chunks by shuffle, and from memory only at the segment's and the row's ends.
 __global__ void byte_h_kernel(const uint8_t *__restrict__ cur, uint8_t *__restrict__ nxt, Geom g,
                               u64 *moved) {
-  const int64_t nq = g.PB / 16, total = g.M * nq;
+  const int nq = (int)(g.PB / 16), segs = (nq + 31) / 32;
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t di = nwarps / segs;
+  const int dseg = (int)(nwarps - di * segs);
+  // (row, segment) of this warp's first item, advanced by nwarps items a turn
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  int64_t i = w0 / segs;
+  int seg = (int)(w0 - i * segs);
   uint32_t cnt = 0;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = idx / nq, q = idx - i * nq;
+  for (; i < g.M; i += di, seg += dseg) {
+    if (seg >= segs) {
+      seg -= segs;
+      ++i;
+      if (i >= g.M) break;
+    }
+    const int q = seg * 32 + lane;
+    const bool on = q < nq;
     const uint8_t *row = cur + i * g.PB;
-    const int64_t c0 = 16 * q;
-    const int nv = (int)(g.N - c0 < 16 ? g.N - c0 : 16);
-    const Chunk x = load_chunk(row + c0);
-    const Chunk L = lr_mask(x), E = empty_mask(x, valid_bytes(nv));
-    // neighbours across the chunk edge, with wrap (column N-1 <-> column 0)
-    const uint8_t right = row[c0 + nv < g.N ? c0 + nv : 0];
-    const uint8_t left = row[c0 > 0 ? c0 - 1 : g.N - 1];
-    const u64 rE = right == 0 ? 1ull : 0ull;
-    const u64 lL = left == 1 ? 1ull : 0ull;
-    Chunk Er, Ll;
-    Er.lo = (E.lo >> 8) | (E.hi << 56);
-    Er.hi = E.hi >> 8;
-    if (nv > 8)
-      Er.hi |= rE << (8 * (nv - 9));
-    else
-      Er.lo |= rE << (8 * (nv - 1));
-    Ll.lo = (L.lo << 8) | lL;
-    Ll.hi = (L.hi << 8) | (L.lo >> 56);
-    const Chunk mv{L.lo & Er.lo, L.hi & Er.hi};
-    Chunk out;
-    out.lo = x.lo ^ (mv.lo | (Ll.lo & E.lo));
-    out.hi = x.hi ^ (mv.hi | (Ll.hi & E.hi));
-    store_chunk(nxt + i * g.PB + c0, out);
-    cnt += popc_chunk(mv);
+    const int64_t c0 = 16 * (int64_t)q;
+    const int nv = on ? (int)(g.N - c0 < 16 ? g.N - c0 : 16) : 16;
+    const Chunk x = on ? load_chunk(row + c0) : Chunk{0, 0};
+    // cell c0 + 16 is byte 0 of the next lane's chunk unless this chunk ends
+    // the row (wrap to column 0) or the segment; cell c0 - 1 is byte 15 of the
+    // previous lane's chunk (every chunk but a row's last is full)
+    const u64 nxt_lo = __shfl_down_sync(BML_FULL_MASK, x.lo, 1);
+    const u64 prv_hi = __shfl_up_sync(BML_FULL_MASK, x.hi, 1);
+    if (on) {
+      const bool row_end = c0 + nv >= g.N;
+      const uint8_t right = (lane < 31 && !row_end) ? (uint8_t)(nxt_lo & 0xffull)
+                                                    : row[row_end ? 0 : c0 + nv];
+      const uint8_t left = lane > 0 ? (uint8_t)(prv_hi >> 56) : row[c0 > 0 ? c0 - 1 : g.N - 1];
+      const Chunk L = lr_mask(x), E = empty_mask(x, valid_bytes(nv));
+      const u64 rE = right == 0 ? 1ull : 0ull;
+      const u64 lL = left == 1 ? 1ull : 0ull;
+      Chunk Er, Ll;
+      Er.lo = (E.lo >> 8) | (E.hi << 56);
+      Er.hi = E.hi >> 8;
+      if (nv > 8)
+        Er.hi |= rE << (8 * (nv - 9));
+      else
+        Er.lo |= rE << (8 * (nv - 1));
+      Ll.lo = (L.lo << 8) | lL;
+      Ll.hi = (L.hi << 8) | (L.lo >> 56);
+      const Chunk mv{L.lo & Er.lo, L.hi & Er.hi};
+      Chunk out;
+      out.lo = x.lo ^ (mv.lo | (Ll.lo & E.lo));
+      out.hi = x.hi ^ (mv.hi | (Ll.hi & E.hi));
+      store_chunk(nxt + i * g.PB + c0, out);
+      cnt += popc_chunk(mv);
+    }
   }
   block_count_add(cnt, moved);
 }
 
 // One thread per (band of rows, chunk column); marches down the band keeping
-// the upper row's TB mask and the current row's EMPTY mask.
-__global__ void byte_v_kernel(const uint8_t *__restrict__ cur, uint8_t *__restrict__ nxt, Geom g,
-                              int64_t band, u64 *moved) {
+// the upper row's TB mask and the current row's EMPTY mask.  Padding bytes
+// (columns N..PB-1) are 0 and hold no TB car, so no move involves them and
+// the vertical rule needs no column mask.
+__global__ void __launch_bounds__(256, 8)
+    byte_v_kernel(const uint8_t *__restrict__ cur, uint8_t *__restrict__ nxt, Geom g,
+                  int64_t band, u64 *moved) {
   const int64_t nq = g.PB / 16, nbands = (g.M + band - 1) / band, total = nbands * nq;
   uint32_t cnt = 0;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int64_t b = idx / nq, q = idx - b * nq;
-    const int64_t r0 = b * band, r1 = r0 + band < g.M ? r0 + band : g.M;
-    const int64_t c0 = 16 * q;
-    const int nv = (int)(g.N - c0 < 16 ? g.N - c0 : 16);
-    const Chunk valid = valid_bytes(nv);
-    const Chunk up = load_chunk(cur + (r0 > 0 ? r0 - 1 : g.M - 1) * g.PB + c0);
+    const int64_t r0 = b * band;
+    const int len = (int)(r0 + band < g.M ? band : g.M - r0);
+    const bool wraps = r0 + len == g.M;  // the band's last row reads row 0 below it
+    const uint8_t *col = cur + 16 * q;
+    const uint8_t *src = col + r0 * g.PB;
+    uint8_t *dst = nxt + r0 * g.PB + 16 * q;
+    const Chunk up = load_chunk(r0 > 0 ? src - g.PB : col + (g.M - 1) * g.PB);
     Chunk Tt = tb_mask(up);
-    Chunk x = load_chunk(cur + r0 * g.PB + c0);
-    Chunk E = empty_mask(x, valid);
-    for (int64_t i = r0; i < r1; ++i) {
-      const Chunk xn = load_chunk(cur + (i + 1 < g.M ? i + 1 : 0) * g.PB + c0);
-      const Chunk En = empty_mask(xn, valid);
+    Chunk x = load_chunk(src);
+    Chunk E = empty_mask(x, Chunk{kLsb, kLsb});
+#pragma unroll 1
+    for (int k = 0; k < len; ++k) {
+      src += g.PB;
+      const Chunk xn = load_chunk(k + 1 == len && wraps ? col : src);
+      const Chunk En = empty_mask(xn, Chunk{kLsb, kLsb});
       const Chunk T = tb_mask(x);
       const Chunk mv{T.lo & En.lo, T.hi & En.hi};
       Chunk out;
       out.lo = x.lo ^ ((mv.lo | (Tt.lo & E.lo)) << 1);
       out.hi = x.hi ^ ((mv.hi | (Tt.hi & E.hi)) << 1);
-      store_chunk(nxt + i * g.PB + c0, out);
+      store_chunk(dst, out);
+      dst += g.PB;
       cnt += popc_chunk(mv);
       Tt = T;
       x = xn;
@@ -140,7 +172,7 @@ int grid_cap(int64_t items, int threads) {
 
 cudaError_t launch_byte_h(const uint8_t *cur, uint8_t *nxt, const Geom &g, u64 *moved,
                           cudaStream_t st) {
-  const int64_t items = g.M * (g.PB / 16);
+  const int64_t items = g.M * ((g.PB / 16 + 31) / 32) * 32;
   byte_h_kernel<<<grid_cap(items, 256), 256, 0, st>>>(cur, nxt, g, moved);
   return cudaGetLastError();
 }
