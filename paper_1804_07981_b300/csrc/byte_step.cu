@@ -50,8 +50,10 @@ __device__ __forceinline__ Chunk empty_mask(Chunk x, Chunk valid) {
   return Chunk{~(x.lo | (x.lo >> 1)) & valid.lo, ~(x.hi | (x.hi >> 1)) & valid.hi};
 }
 
+// number of set bits of a chunk whose bits are all at bit 0 of bytes (the
+// high word's bits move to bit 1 of its bytes, so one 64-bit count suffices)
 __device__ __forceinline__ uint32_t popc_chunk(Chunk c) {
-  return (uint32_t)(__popcll(c.lo) + __popcll(c.hi));
+  return (uint32_t)__popcll(c.lo | (c.hi << 1));
 }
 
 // A warp takes 32 consecutive chunks of one row (a row segment), one per lane;
@@ -80,27 +82,39 @@ __global__ void byte_h_kernel(const uint8_t *__restrict__ cur, uint8_t *__restri
     const uint8_t *row = cur + i * g.PB;
     const int64_t c0 = 16 * (int64_t)q;
     const int nv = on ? (int)(g.N - c0 < 16 ? g.N - c0 : 16) : 16;
-    const Chunk x = on ? load_chunk(row + c0) : Chunk{0, 0};
     // cell c0 + 16 is byte 0 of the next lane's chunk unless this chunk ends
     // the row (wrap to column 0) or the segment; cell c0 - 1 is byte 15 of the
-    // previous lane's chunk (every chunk but a row's last is full)
-    const u64 nxt_lo = __shfl_down_sync(BML_FULL_MASK, x.lo, 1);
-    const u64 prv_hi = __shfl_up_sync(BML_FULL_MASK, x.hi, 1);
+    // previous lane's chunk (every chunk but a row's last is full).  The few
+    // cells read from memory are loaded together with the chunk.
+    const bool row_end = c0 + nv >= g.N;
+    const bool mem_r = on && (lane == 31 || row_end), mem_l = on && lane == 0;
+    Chunk x{0, 0};
+    uint8_t right = 0, left = 0;
+    if (on) x = load_chunk(row + c0);
+    if (mem_r) right = __ldg(row + (row_end ? 0 : c0 + nv));
+    if (mem_l) left = __ldg(row + (c0 > 0 ? c0 - 1 : g.N - 1));
+    const uint32_t nxt_b0 = __shfl_down_sync(BML_FULL_MASK, (uint32_t)x.lo, 1);
+    const uint32_t prv_b15 = __shfl_up_sync(BML_FULL_MASK, (uint32_t)(x.hi >> 32), 1);
     if (on) {
-      const bool row_end = c0 + nv >= g.N;
-      const uint8_t right = (lane < 31 && !row_end) ? (uint8_t)(nxt_lo & 0xffull)
-                                                    : row[row_end ? 0 : c0 + nv];
-      const uint8_t left = lane > 0 ? (uint8_t)(prv_hi >> 56) : row[c0 > 0 ? c0 - 1 : g.N - 1];
-      const Chunk L = lr_mask(x), E = empty_mask(x, valid_bytes(nv));
+      if (!mem_r) right = (uint8_t)(nxt_b0 & 0xffu);
+      if (!mem_l) left = (uint8_t)(prv_b15 >> 24);
+      const Chunk L = lr_mask(x);
       const u64 rE = right == 0 ? 1ull : 0ull;
       const u64 lL = left == 1 ? 1ull : 0ull;
-      Chunk Er, Ll;
-      Er.lo = (E.lo >> 8) | (E.hi << 56);
-      Er.hi = E.hi >> 8;
-      if (nv > 8)
-        Er.hi |= rE << (8 * (nv - 9));
-      else
-        Er.lo |= rE << (8 * (nv - 1));
+      Chunk E, Er, Ll;
+      if (nv == 16) {  // every chunk but a row's last
+        E = empty_mask(x, Chunk{kLsb, kLsb});
+        Er.lo = (E.lo >> 8) | (E.hi << 56);
+        Er.hi = (E.hi >> 8) | (rE << 56);
+      } else {
+        E = empty_mask(x, valid_bytes(nv));
+        Er.lo = (E.lo >> 8) | (E.hi << 56);
+        Er.hi = E.hi >> 8;
+        if (nv > 8)
+          Er.hi |= rE << (8 * (nv - 9));
+        else
+          Er.lo |= rE << (8 * (nv - 1));
+      }
       Ll.lo = (L.lo << 8) | lL;
       Ll.hi = (L.hi << 8) | (L.lo >> 56);
       const Chunk mv{L.lo & Er.lo, L.hi & Er.hi};
