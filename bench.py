@@ -19,7 +19,9 @@ tie-break seed = placement seed, 1024 steps; --no-model2 skips it),
 "byte_kernel" (the plain byte-per-cell form on the bench lattice, 16 steps,
 against the HBM peak), "one_pass" (one full step per DRAM pass on the bench
 lattice, 256 steps, against the HBM peak), "configs" (256^2 for 1024 steps; 4096^2 byte vs
-bit-packed over 3 densities x 3 seeds x 4096 steps; rank 0 of a 1-GPU run).
+bit-packed over 3 densities x 3 seeds x 4096 steps; rank 0 of a 1-GPU run), "mlp" (the
+surrogate network: AdamW step time at batch 1024, forward on 2624 samples, and its tcgen05
+GEMM kernel on a 2^22 x 128 x 128 product against the HBM peak; 1-GPU runs).
 
 --impl reference times the CPU oracle (test infrastructure) on the host
 cores on a bounded sample of the same workload.
@@ -301,6 +303,81 @@ def _one_pass_bench(bml, torch, stream, M, N, steps, hbm_peak, seed=1):
                          "traffic": traffic * cells if traffic else None}}
 
 
+def _mlp_bench(bml, torch, stream, hbm_peak, seed=1):
+    """The surrogate network (67 -> 3 x [128, ReLU] -> 2, BF16 on the tcgen05
+    GEMM): AdamW steps at batch 1024 (the sweep's training batch; enqueued
+    back to back, no loss read back), the forward pass on 2624 samples (the
+    sweep's inference batch; wall clock per call, which waits), and the GEMM
+    kernel alone on a 2^22 x 128 x 128 product (C fp32 = A bf16 . B^T): at
+    N <= 128 it moves 2 B of A and 4 B of C per 256 flops, far below the
+    tensor-core ridge, so its roof is HBM (algorithmic bytes: A + B + C)."""
+    from paper_1804_07981_b300.inputs import mlp_init_params
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    out = {}
+    with torch.cuda.stream(stream):
+        net = bml.MLP(stream=stream)
+        net.set_params(mlp_init_params(67, seed).astype(np.float32))
+        B = 1024
+        X = torch.rand((B, 67), device="cuda", generator=g)
+        V = torch.rand((B,), device="cuda", generator=g)
+        J = (torch.rand((B,), device="cuda", generator=g) > 0.5).float()
+        for _ in range(10):
+            net.train_step(X, V, J, lr=1e-3, weight_decay=1e-4, want_loss=False)
+        steps = 400
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        for _ in range(steps):
+            net.train_step(X, V, J, lr=1e-3, weight_decay=1e-4, want_loss=False)
+        e1.record(stream)
+        e1.synchronize()
+        host_s = time.perf_counter() - t0
+        out["train_step_us"] = e0.elapsed_time(e1) * 1e3 / steps
+        out["train_step_host_us"] = host_s * 1e6 / steps
+        out["train_batch"] = B
+        out["train_gpu_launches_per_step"] = 17
+        Xf = torch.rand((2624, 67), device="cuda", generator=g)
+        net.forward(Xf)
+        reps = 50
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            net.forward(Xf)
+        out["forward_2624_us"] = (time.perf_counter() - t0) * 1e6 / reps
+        net.close()
+        Mg, Ng, Kg = 1 << 22, 128, 128
+        A = (torch.rand((Mg, Kg), device="cuda", generator=g) - 0.5).to(torch.bfloat16)
+        Bw = (torch.rand((Ng, Kg), device="cuda", generator=g) - 0.5).to(torch.bfloat16)
+        C = torch.empty((Mg, Ng), device="cuda", dtype=torch.float32)
+        call = lambda: bml.bml_gemm_bf16(A.data_ptr(), Kg, Bw.data_ptr(), Kg, C.data_ptr(), Ng,
+                                         Mg, Ng, Kg, stream)
+        call()
+        ms = []
+        for _ in range(10):
+            stream.synchronize()
+            e0.record(stream)
+            call()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        ms = statistics.median(ms)
+        byts = Mg * Kg * 2 + Ng * Kg * 2 + Mg * Ng * 4
+        gbs = byts / (ms / 1e3) / 1e9
+        out["gemm"] = {"shape": [Mg, Ng, Kg], "ms": ms,
+                       "tflops": 2.0 * Mg * Ng * Kg / (ms / 1e3) / 1e12,
+                       "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak,
+                                    "unit": "GB/s", "frac": gbs / hbm_peak,
+                                    "bytes": byts,
+                                    "note": "event time of one call, including its flag reset "
+                                            "and read-back copies"}}
+        del A, Bw, C
+    out["metric"] = "AdamW steps/s"
+    out["value"] = 1e6 / out["train_step_us"]
+    out["unit"] = "steps/s"
+    out["bound"] = "latency (17 launches per step on 1024 samples)"
+    return out
+
+
 def _config_benches(bml, torch, stream):
     """The two smaller workloads: 256 x 256 at density 0.3 (seed 1, 1024
     steps; latency-bound) and 4096 x 4096 at densities 0.20/0.35/0.50,
@@ -527,6 +604,10 @@ def run_ours(args):
     if not args.no_configs and world == 1:
         small = _config_benches(bml, torch, stream)
 
+    mlp = None
+    if not args.no_mlp and world == 1:
+        mlp = _mlp_bench(bml, torch, stream, hbm_peak)
+
     m2 = None
     if not args.no_model2:
         m2 = _model2_bench(bml, torch, stream, M, N, args.model2_steps,
@@ -559,6 +640,7 @@ def run_ours(args):
                        "parallelism": "replicas x%d" % world},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "ensemble": ens,
             "model2": m2, "byte_kernel": byte, "one_pass": one, "configs": small,
+            "mlp": mlp,
             "gpu_launches": gpu_launches, "clocks": clk,
         }
         print(json.dumps(line))
@@ -592,6 +674,7 @@ def main():
     ap.add_argument("--no-byte", action="store_true")
     ap.add_argument("--byte-steps", type=int, default=16)
     ap.add_argument("--no-configs", action="store_true")
+    ap.add_argument("--no-mlp", action="store_true")
     ap.add_argument("--no-one-pass", action="store_true")
     ap.add_argument("--one-pass-steps", type=int, default=256)
     ap.add_argument("--model2-steps", type=int, default=1024)

@@ -221,7 +221,9 @@ const char *bml_last_error(void);
  * mean over the batch.  Parameters are a flat float array of
  * bml_mlp_num_params() entries: W1 (128 x 67), b1 (128), W2 (128 x 128), b2,
  * W3 (128 x 128), b3, W4 (2 x 128), b4 (2), each W row-major [out][in].
- * d_* pointers are device memory; the calls synchronise the stream.
+ * d_* pointers are device memory, read in stream order on the network's
+ * stream; the calls synchronise that stream, except bml_mlp_train_step
+ * without a loss to return.
  * ------------------------------------------------------------------------ */
 typedef struct bml_mlp bml_mlp;
 
@@ -234,7 +236,12 @@ int bml_mlp_get_params(bml_mlp *mlp, float *host_params);
 int bml_mlp_forward(bml_mlp *mlp, const float *d_x, int64_t batch, float *d_out);
 /* One AdamW step on the mean loss of the batch (d_v, d_jam: batch floats;
  * jam is 0 or 1).  *h_loss (host, may be NULL) receives the loss before the
- * update. */
+ * update; the call then waits for the gradients and returns BML_ETIMEOUT,
+ * with nothing updated, if a tensor-core wait timed out.  With h_loss NULL
+ * the step is only enqueued (d_x, d_v, d_jam must stay valid until the
+ * stream reaches it), and a timed-out wait inside it is reported by the
+ * next call that waits (forward, get_params, grads, a train step with a
+ * loss); the weights are then undefined. */
 int bml_mlp_train_step(bml_mlp *mlp, const float *d_x, const float *d_v, const float *d_jam,
                        int64_t batch, float lr, float weight_decay, float *h_loss);
 /* Gradients of the mean loss (host array in the parameter layout), no

@@ -9,23 +9,32 @@
 //
 // GEMM kernel.  C[M x N] = A[M x K] * B[N x K]^T with A, B BF16 and K
 // contiguous (K-major).  One CTA of 128 threads per 128-row tile of C and
-// all N <= 128 columns.  Per K chunk of 64 the threads copy A and B into
-// shared memory in the canonical no-swizzle K-major layout of tcgen05 (8-row
-// x 16-byte core matrices, stored contiguously: core (r/8, k/8) at
-// ((r/8) * 8 + k/8) * 128 bytes, so adjacent core matrices are 128 bytes
-// apart along K and 1024 bytes apart along M/N), make the writes visible to
-// the async proxy, and one thread issues 4 tcgen05.mma (M=128, N, K=16) into
-// the FP32 accumulator in tensor memory, then tcgen05.commit to an mbarrier
-// that all threads wait on (bounded by %globaltimer; on expiry an error flag
-// is set).  The epilogue reads the accumulator with tcgen05.ld (warp w owns
-// TMEM lanes 32w..32w+31 = rows) and applies bias / ReLU / conversion.
+// all N <= 128 columns, the FP32 accumulator in tensor memory.  Operands
+// reach shared memory by TMA (cp.async.bulk.tensor) through a ring of up to
+// four stages of one K chunk (64) each: thread 0 issues one copy per
+// operand and stage (a box of 64 elements = 128 bytes of K x rows, written
+// with the 128-byte swizzle: 8-row groups of 1024 bytes, the 16-byte chunks
+// of row r permuted by r mod 8) and arms the stage's full barrier with the
+// byte count; thread 32 waits for it, issues 4 tcgen05.mma (M=128, N, K=16;
+// the matrix descriptors in the same swizzled K-major layout, advanced 32
+// bytes per K step) and commits to the stage's empty
+// barrier, which releases the stage to the producer; a last commit marks
+// the accumulator complete.  Every wait is bounded by %globaltimer (on
+// expiry an error flag is set, copies still in flight are waited for, again
+// bounded, and the tensor memory is released).  The epilogue reads the
+// accumulator with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31 = rows),
+// applies bias / ReLU / conversion and stores row-major outputs through a
+// per-warp shared-memory transpose so that a warp writes whole row segments.
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <vector>
 
+#include <cuda.h>  // CUtensorMap and its enums (the encoder is fetched at run time)
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 
 #include "../../include/bml.h"
 #include "bml_internal.cuh"
@@ -36,8 +45,13 @@ namespace {
 typedef __nv_bfloat16 bf16;
 
 constexpr int kIn = 67, kInPad = 80, kHid = 128, kOut = 2, kOutPad = 16;
-constexpr int kKC = 64;                       // K per shared-memory chunk
-constexpr int kSmemBytes = 72 * 1024;         // caps residency at 3 CTAs per SM (TMEM)
+constexpr int kKC = 64;                       // K per shared-memory stage
+constexpr int kStageA = 128 * kKC * 2;        // A: 128 rows x 64 bf16
+constexpr int kStageBytes = 2 * kStageA;      // + B: up to 128 rows x 64 bf16
+constexpr int kMaxStages = 4;
+constexpr int kBarBytes = 1024;               // barriers, TMEM slot, flags after the ring
+constexpr int kMinSmem = 72 * 1024;           // caps residency at 3 CTAs per SM (TMEM)
+constexpr int kMaxSmem = kMaxStages * kStageBytes + kBarBytes;
 constexpr long long kWaitNs = 1000000000ll;   // 1 s bound on any wait
 
 enum EpiMode { EPI_F32 = 0, EPI_RELU_BF16 = 1, EPI_F32_T = 2 };
@@ -62,11 +76,14 @@ __device__ __forceinline__ long long gtimer() {
   return (long long)t;
 }
 
-// Shared-memory matrix descriptor: no swizzle, K-major, LBO = byte distance
-// of adjacent core matrices along K, SBO = along M/N; version field 1.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+// Shared-memory matrix descriptor of a K-major operand with the 128-byte
+// swizzle: start address, leading offset 16 bytes (unused within one
+// 128-byte swizzle row), stride 1024 bytes between 8-row groups, version
+// field 1, layout type 2 (128-byte swizzle).  The tile base is 1024-byte
+// aligned; a K step of 16 elements advances the start by 32 bytes.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         (1ull << 46) | (2ull << 61);
 }
 
 // Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major.
@@ -90,17 +107,51 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   }
 }
 
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+               :: "r"(bar), "r"(bytes) : "memory");
+}
+
+// 2-D tiled TMA load of box {64 elements (128 bytes) of K, rows} at (x = k,
+// y = row) into shared memory; completion is counted on the mbarrier in
+// bytes (the whole box, zero-filled where it passes the matrix edge)
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];"
+      :: "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+               :: "r"(bar) : "memory");
+}
+
 __global__ void __launch_bounds__(128, 1)
-    umma_gemm_kernel(const bf16 *__restrict__ A, int lda, const bf16 *__restrict__ B, int ldb,
-                     int M, int N, int K, Epi epi) {
+    umma_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
+                     const __grid_constant__ CUtensorMap mapB, int M, int N, int K, int stages,
+                     Epi epi) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  uint8_t *sA = smem;                    // 128 rows x 64 bf16 = 16 KB
-  uint8_t *sB = smem + 16384;            // N rows x 64 bf16 <= 16 KB
-  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 32768);
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + 32768 + 16);
+  uint8_t *ring = smem;  // stages x [A 16 KB | B 16 KB]
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + stages * kStageBytes);
+  // bars: full[kMaxStages], empty[kMaxStages], done; then the TMEM slot and flags
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * kMaxStages + 1);
+  volatile int *s_fail = reinterpret_cast<volatile int *>(tmem_slot + 1);
+  volatile int *s_issued = s_fail + 1, *s_consumed = s_fail + 2;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.x * 128;
+  const int nk = (K + kKC - 1) / kKC;
   const uint32_t ncols = N <= 32 ? 32u : (N <= 64 ? 64u : 128u);
+  const uint32_t bar0 = smem_u32(bars);
+  auto full = [&](int st) { return bar0 + 8u * (uint32_t)st; };
+  auto empty = [&](int st) { return bar0 + 8u * (uint32_t)(kMaxStages + st); };
+  const uint32_t done = bar0 + 8u * (uint32_t)(2 * kMaxStages);
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -108,58 +159,84 @@ __global__ void __launch_bounds__(128, 1)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(bar)) : "memory");
+    for (int st = 0; st < stages; ++st) {
+      mbar_init(full(st), 1);
+      mbar_init(empty(st), 1);
+    }
+    mbar_init(done, 1);
+    *s_fail = 0;
+    *s_issued = 0;
+    *s_consumed = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t taddr = *tmem_slot;
-  const uint32_t idesc = idesc_bf16(128, N);
-  uint32_t phase = 0;
-  bool ok = true;
 
-  for (int k0 = 0; k0 < K && ok; k0 += kKC) {
-    // stage A (128 x 64) and B (N x 64) chunks into the core-matrix layout
-    for (int c = tid; c < 128 * 8; c += 128) {
-      const int r = c >> 3, kc = c & 7, gk = k0 + kc * 8;
-      uint4 v = make_uint4(0, 0, 0, 0);
-      if (m0 + r < M && gk < K) v = *reinterpret_cast<const uint4 *>(A + (size_t)(m0 + r) * lda + gk);
-      *reinterpret_cast<uint4 *>(sA + ((r >> 3) * 8 + kc) * 128 + (r & 7) * 16) = v;
+  if (tid == 0) {  // (the other lanes of warps 0 and 1 wait at __syncwarp below)
+    // producer: stage c % stages takes K chunk c once the MMAs of chunk
+    // c - stages have released it
+    int c = 0;
+    for (; c < nk; ++c) {
+      const int st = c % stages;
+      if (c >= stages && !mbar_wait(empty(st), (uint32_t)((c / stages - 1) & 1))) {
+        *s_fail = 1;
+        break;
+      }
+      if (*s_fail) break;
+      const int k0 = c * kKC;
+      const uint32_t a = smem_u32(ring + st * kStageBytes), b = a + kStageA;
+      mbar_expect_tx(full(st), (uint32_t)((128 + N) * kKC * 2));
+      tma_load_2d(a, &mapA, k0, m0, full(st));
+      tma_load_2d(b, &mapB, k0, 0, full(st));
     }
-    for (int c = tid; c < N * 8; c += 128) {
-      const int r = c >> 3, kc = c & 7, gk = k0 + kc * 8;
-      uint4 v = make_uint4(0, 0, 0, 0);
-      if (gk < K) v = *reinterpret_cast<const uint4 *>(B + (size_t)r * ldb + gk);
-      *reinterpret_cast<uint4 *>(sB + ((r >> 3) * 8 + kc) * 128 + (r & 7) * 16) = v;
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
+    *s_issued = c;
+  } else if (tid == 32) {
+    // MMA issuer
+    const uint32_t idesc = idesc_bf16(128, N);
+    int c = 0;
+    for (; c < nk; ++c) {
+      const int st = c % stages;
+      if (!mbar_wait(full(st), (uint32_t)((c / stages) & 1))) {
+        *s_fail = 1;
+        break;
+      }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int ksteps = (K - k0) >= kKC ? kKC / 16 : (K - k0 + 15) / 16;
+      const int k0 = c * kKC;
+      const int ksteps = (K - k0) >= kKC ? kKC / 16 : (K - k0) / 16;
+      const uint32_t a = smem_u32(ring + st * kStageBytes), b = a + kStageA;
       for (int kk = 0; kk < ksteps; ++kk) {
-        const uint64_t ad = smem_desc(smem_u32(sA + kk * 256), 128, 1024);
-        const uint64_t bd = smem_desc(smem_u32(sB + kk * 256), 128, 1024);
-        const uint32_t acc = (k0 > 0 || kk > 0) ? 1u : 0u;
+        const uint64_t ad = smem_desc_sw128(a + (uint32_t)(kk * 32));
+        const uint64_t bd = smem_desc_sw128(b + (uint32_t)(kk * 32));
+        const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
             :: "r"(taddr), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                   :: "r"(smem_u32(bar)) : "memory");
+      umma_commit(empty(st));
     }
-    ok = mbar_wait(smem_u32(bar), phase);
-    phase ^= 1u;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    __syncthreads();
+    *s_consumed = c;
+    umma_commit(done);  // arrives once every MMA issued above has completed
   }
-  if (!ok) {
+  if (warp < 2) __syncwarp();
+  if (!mbar_wait(done, 0)) *s_fail = 1;
+  __syncthreads();
+  if (tid == 0) {
+    // copies of stages the MMA thread never consumed (after a failed wait)
+    for (int c = *s_consumed; c < *s_issued; ++c)
+      if (!mbar_wait(full(c % stages), (uint32_t)((c / stages) & 1))) *s_fail = 1;
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (*s_fail) {
     if (tid == 0) atomicExch(epi.err, 1);
   } else {
-    // epilogue: thread (warp w, lane l) owns row m0 + 32w + l
-    const int row = m0 + warp * 32 + lane;
+    // epilogue: thread (warp w, lane l) owns row m0 + 32w + l; row-major
+    // outputs go through this warp's 32 x 17 float tile in the (now idle) ring
+    const int row0 = m0 + warp * 32, row = row0 + lane;
+    float *stg = reinterpret_cast<float *>(ring) + warp * (32 * 17);
     for (int c0 = 0; c0 < N; c0 += 16) {
       uint32_t r[16];
       asm volatile(
@@ -170,22 +247,50 @@ __global__ void __launch_bounds__(128, 1)
             "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
           : "r"(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (row < M) {
+      float v[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int col = c0 + j;
-          float v = __uint_as_float(r[j]) + (epi.bias ? epi.bias[col] : 0.f);
-          if (epi.mode == EPI_F32) {
-            epi.out_f32[(size_t)row * epi.ldo + col] = v;
-          } else if (epi.mode == EPI_F32_T) {
-            epi.out_f32[(size_t)col * epi.ldo + row] = v;
-          } else {
-            const bf16 h = __float2bfloat16_rn(v > 0.f ? v : 0.f);
-            epi.out_bf16[(size_t)row * epi.ldo + col] = h;
-            if (epi.out_bf16_t) epi.out_bf16_t[(size_t)col * epi.ldt + row] = h;
+      for (int j = 0; j < 16; ++j) {
+        v[j] = __uint_as_float(r[j]) + (epi.bias ? epi.bias[c0 + j] : 0.f);
+        if (epi.mode == EPI_RELU_BF16) v[j] = v[j] > 0.f ? v[j] : 0.f;
+      }
+      if (epi.mode == EPI_F32_T) {
+        // transposed output: consecutive lanes write consecutive rows
+        if (row < M) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) epi.out_f32[(size_t)(c0 + j) * epi.ldo + row] = v[j];
+        }
+        continue;
+      }
+      if (epi.mode == EPI_RELU_BF16 && epi.out_bf16_t && row < M) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          epi.out_bf16_t[(size_t)(c0 + j) * epi.ldt + row] = __float2bfloat16_rn(v[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < 16; ++j) stg[lane * 17 + j] = v[j];
+      __syncwarp();
+      if (epi.mode == EPI_F32) {
+        // two rows of 16 floats per instruction
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int rr = 2 * i + (lane >> 4), cc = lane & 15;
+          if (row0 + rr < M) epi.out_f32[(size_t)(row0 + rr) * epi.ldo + c0 + cc] = stg[rr * 17 + cc];
+        }
+      } else {
+        // four rows of 16 bf16 per instruction, two columns per lane
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int rr = 4 * i + (lane >> 3), cc = (lane & 7) * 2;
+          if (row0 + rr < M) {
+            __nv_bfloat162 h;
+            h.x = __float2bfloat16_rn(stg[rr * 17 + cc]);
+            h.y = __float2bfloat16_rn(stg[rr * 17 + cc + 1]);
+            *reinterpret_cast<__nv_bfloat162 *>(epi.out_bf16 + (size_t)(row0 + rr) * epi.ldo +
+                                                c0 + cc) = h;
           }
         }
       }
+      __syncwarp();
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -359,17 +464,51 @@ int mfail(int code, const char *fmt, ...) {
   } while (0)
 
 bool g_attr_done = false;
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
+// Tensor map of a K-major bf16 matrix (rows x K, ld elements between rows)
+// with a box of 64 elements of K x box_rows rows, 128-byte swizzle.
+cudaError_t kmajor_map(CUtensorMap *map, const bf16 *p, int rows, int K, int ld, int box_rows) {
+  if (!g_encode) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    const cudaError_t e =
+        cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)kKC, (cuuint32_t)box_rows};
+  const cuuint32_t elem[2] = {1, 1};
+  const CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16 *>(p), dims,
+                              strides, box, elem, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// A: M rows x K (lda), B: N rows x K (ldb); 16-byte aligned, lda, ldb % 8 == 0.
 cudaError_t launch_gemm(const bf16 *A, int lda, const bf16 *B, int ldb, int M, int N, int K,
                         const Epi &epi, cudaStream_t st) {
   if (!g_attr_done) {
     cudaError_t e = cudaFuncSetAttribute(umma_gemm_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
     if (e != cudaSuccess) return e;
     g_attr_done = true;
   }
-  if (N < 16 || N > 128 || N % 16 || K % 16 || lda % 8 || ldb % 8) return cudaErrorInvalidValue;
-  umma_gemm_kernel<<<(M + 127) / 128, 128, kSmemBytes, st>>>(A, lda, B, ldb, M, N, K, epi);
+  if (M < 1 || N < 16 || N > 128 || N % 16 || K < 16 || K % 16 || lda % 8 || ldb % 8 ||
+      (uintptr_t)A % 16 || (uintptr_t)B % 16)
+    return cudaErrorInvalidValue;
+  CUtensorMap ma, mb;
+  cudaError_t e = kmajor_map(&ma, A, M, K, lda, 128);
+  if (e == cudaSuccess) e = kmajor_map(&mb, B, N, K, ldb, N);
+  if (e != cudaSuccess) return e;
+  const int nk = (K + kKC - 1) / kKC;
+  const int stages = nk < kMaxStages ? nk : kMaxStages;
+  int smem = stages * kStageBytes + kBarBytes;
+  if (smem < kMinSmem) smem = kMinSmem;
+  umma_gemm_kernel<<<(M + 127) / 128, 128, smem, st>>>(ma, mb, M, N, K, stages, epi);
   return cudaGetLastError();
 }
 
@@ -594,9 +733,10 @@ extern "C" int bml_mlp_forward(bml_mlp *p, const float *d_x, int64_t batch, floa
   return check_mlp_err(p);
 }
 
-// Gradients of the mean loss on a batch into gW / gb (no update).
+// Gradients of the mean loss on a batch into gW / gb (no update).  wait:
+// synchronise and report a timed-out tensor-core wait before returning.
 static int compute_grads(bml_mlp *p, const float *d_x, const float *d_v, const float *d_jam,
-                         int B, float *h_loss) {
+                         int B, float *h_loss, bool wait) {
   const int Bp = (B + 127) / 128 * 128;
   int rc = ensure_batch(p, Bp);
   if (rc) return rc;
@@ -647,7 +787,7 @@ static int compute_grads(bml_mlp *p, const float *d_x, const float *d_v, const f
   if (h_loss) {
     MCUDA(cudaMemcpyAsync(h_loss, p->loss, 4, cudaMemcpyDeviceToHost, p->st));
   }
-  return check_mlp_err(p);
+  return wait ? check_mlp_err(p) : BML_OK;
 }
 
 static int adamw(bml_mlp *p, float lr, float wd, const float *d_ext) {
@@ -669,18 +809,21 @@ extern "C" int bml_mlp_train_step(bml_mlp *p, const float *d_x, const float *d_v
   if (!p || !d_x || !d_v || !d_jam) return mfail(BML_EINVAL, "NULL argument");
   if (batch < 1 || batch > (1 << 24)) return mfail(BML_EINVAL, "batch must be in [1, 2^24]");
   if (!(lr >= 0.f) || !(weight_decay >= 0.f)) return mfail(BML_EINVAL, "bad lr / weight_decay");
-  int rc = compute_grads(p, d_x, d_v, d_jam, (int)batch, h_loss);
+  // with a loss to return, the step waits for the gradients (and reports a
+  // timed-out wait before anything is updated); without one it only enqueues
+  // (the error flag is sticky: a failure in an enqueued step is reported by
+  // the next call that waits)
+  const bool wait = h_loss != nullptr;
+  int rc = compute_grads(p, d_x, d_v, d_jam, (int)batch, h_loss, wait);
   if (rc) return rc;
-  if ((rc = adamw(p, lr, weight_decay, nullptr))) return rc;
-  MCUDA(cudaStreamSynchronize(p->st));
-  return BML_OK;
+  return adamw(p, lr, weight_decay, nullptr);
 }
 
 extern "C" int bml_mlp_grads(bml_mlp *p, const float *d_x, const float *d_v, const float *d_jam,
                              int64_t batch, float *host_grads, float *h_loss) {
   if (!p || !d_x || !d_v || !d_jam || !host_grads) return mfail(BML_EINVAL, "NULL argument");
   if (batch < 1 || batch > (1 << 24)) return mfail(BML_EINVAL, "batch must be in [1, 2^24]");
-  int rc = compute_grads(p, d_x, d_v, d_jam, (int)batch, h_loss);
+  int rc = compute_grads(p, d_x, d_v, d_jam, (int)batch, h_loss, true);
   if (rc) return rc;
   // gather the padded gradient buffers into the flat parameter layout
   for (int l = 0; l < 4; ++l) {
@@ -717,8 +860,14 @@ extern "C" int bml_gemm_bf16(const void *A, int64_t lda, const void *B, int64_t 
     return mfail(BML_EINVAL, "bml_gemm_bf16: need 16 <= N <= 128, N % 16 == 0, K % 16 == 0, "
                  "lda, ldb >= K and multiples of 8, ldc >= N");
   if ((uintptr_t)A % 16 || (uintptr_t)B % 16) return mfail(BML_EINVAL, "A, B not 16-byte aligned");
-  int *err = nullptr;
-  MCUDA(cudaMalloc(&err, 4));
+  // one completion-wait error flag per calling thread and device, allocated
+  // on first use (the call waits for the stream, so a thread has at most one
+  // call in flight)
+  thread_local std::map<int, int *> flags;
+  int dev = 0;
+  MCUDA(cudaGetDevice(&dev));
+  int *&err = flags[dev];
+  if (!err) MCUDA(cudaMalloc(&err, 4));
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = cudaMemsetAsync(err, 0, 4, st);
   Epi ep{};
@@ -732,7 +881,6 @@ extern "C" int bml_gemm_bf16(const void *A, int64_t lda, const void *B, int64_t 
   int h = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&h, err, 4, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  cudaFree(err);
   if (e != cudaSuccess) return mfail(BML_ECUDA, "gemm: %s", cudaGetErrorString(e));
   if (h) return mfail(BML_ETIMEOUT, "a tensor-core completion wait timed out");
   return BML_OK;

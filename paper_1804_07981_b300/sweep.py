@@ -65,6 +65,11 @@ def training_set(count, T, window, seed, lo=64, hi=2048, stream=None):
     return X, v, jam, secs
 
 
+def _nullctx():
+    import contextlib
+    return contextlib.nullcontext()
+
+
 def train(X, v, jam, steps=2000, batch=1024, lr=1e-3, wd=1e-4, seed=0, stream=None,
           loss_tail=50):
     """AdamW on random mini-batches; returns the network and the losses of
@@ -77,12 +82,17 @@ def train(X, v, jam, steps=2000, batch=1024, lr=1e-3, wd=1e-4, seed=0, stream=No
     g = torch.Generator(device="cuda").manual_seed(seed)
     n = X.shape[0]
     losses = []
-    for s in range(steps):
-        idx = torch.randint(0, n, (min(batch, n),), device="cuda", generator=g)
-        want = s == 0 or s >= steps - loss_tail
-        loss = net.train_step(X[idx], v[idx], jam[idx], lr=lr, weight_decay=wd, want_loss=want)
-        if want:
-            losses.append(loss)
+    # the batches are gathered on the network's stream: steps that report no
+    # loss are only enqueued, and their inputs must be read before reuse
+    ctx = torch.cuda.stream(stream) if isinstance(stream, torch.cuda.Stream) else _nullctx()
+    with ctx:
+        for s in range(steps):
+            idx = torch.randint(0, n, (min(batch, n),), device="cuda", generator=g)
+            want = s == 0 or s >= steps - loss_tail
+            loss = net.train_step(X[idx], v[idx], jam[idx], lr=lr, weight_decay=wd,
+                                  want_loss=want)
+            if want:
+                losses.append(loss)
     return net, losses
 
 

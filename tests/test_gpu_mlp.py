@@ -26,6 +26,23 @@ def test_gemm_matches_matmul(lib, M, N, K):
     assert torch.allclose(C.double().cpu(), want, rtol=1e-4, atol=1e-3 * np.sqrt(K))
 
 
+def test_gemm_padded_leading_dims_and_many_tiles(lib):
+    """Row strides above K (lda, ldb, ldc), a ragged last row tile and K
+    not a multiple of the 64-element stage; then 1100 row tiles."""
+    import torch
+    for M, N, K, lda, ldb, ldc in [(300, 32, 96, 120, 104, 37), (140800, 128, 128, 128, 128, 128)]:
+        g = torch.Generator().manual_seed(M + N + K)
+        A = torch.randn(M, lda, generator=g).to(torch.bfloat16).cuda()
+        B = torch.randn(N, ldb, generator=g).to(torch.bfloat16).cuda()
+        C = torch.full((M, ldc), float("nan"), dtype=torch.float32, device="cuda")
+        lib.bml_gemm_bf16(A.data_ptr(), lda, B.data_ptr(), ldb, C.data_ptr(), ldc, M, N, K)
+        want = A[:, :K].double() @ B[:, :K].double().T
+        got = C[:, :N].double()
+        assert torch.allclose(got, want, rtol=1e-4, atol=1e-3 * np.sqrt(K))
+        if ldc > N:
+            assert torch.isnan(C[:, N:]).all()  # nothing written past column N
+
+
 def _batch(B, seed):
     rng = np.random.Generator(np.random.PCG64(seed))
     x = rng.uniform(0, 1, size=(B, IN))
