@@ -244,6 +244,20 @@ int bml_mlp_forward(bml_mlp *mlp, const float *d_x, int64_t batch, float *d_out)
  * loss); the weights are then undefined. */
 int bml_mlp_train_step(bml_mlp *mlp, const float *d_x, const float *d_v, const float *d_jam,
                        int64_t batch, float lr, float weight_decay, float *h_loss);
+/* `steps` AdamW steps, each on a mini-batch of `batch` samples drawn with
+ * replacement from the n training samples (d_x: n x 67 floats, d_v, d_jam: n
+ * floats, device memory): sample i of the network's training step t (t =
+ * AdamW steps taken so far) is row floor(u * n / 2^64), u = SplitMix64 of
+ * (seed, t * batch + i + 1), the generator of the seeded placement.  The
+ * draw, the gather and every step run on the device, enqueued on the
+ * network's stream; the call waits at the end.  h_losses (host, NULL or
+ * `steps` floats) receives each step's loss before its update.  Errors:
+ * BML_EINVAL (NULL pointer, n < 1, steps < 0, batch outside [1, 2^24], bad
+ * lr / weight_decay), BML_ENOMEM / BML_ECUDA, BML_ETIMEOUT (a tensor-core
+ * wait timed out; the weights are then undefined). */
+int bml_mlp_train(bml_mlp *mlp, const float *d_x, const float *d_v, const float *d_jam,
+                  int64_t n, int64_t steps, int64_t batch, float lr, float weight_decay,
+                  uint64_t seed, float *h_losses);
 /* Gradients of the mean loss (host array in the parameter layout), no
  * update. */
 int bml_mlp_grads(bml_mlp *mlp, const float *d_x, const float *d_v, const float *d_jam,

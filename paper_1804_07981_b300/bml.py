@@ -339,6 +339,8 @@ _lib_mlp_fwd = _sig("bml_mlp_forward", [_vp, _vp, _i64, _vp])
 _lib_mlp_train = _sig("bml_mlp_train_step", [_vp, _vp, _vp, _vp, _i64, ctypes.c_float,
                                               ctypes.c_float, _vp])
 _lib_mlp_grads = _sig("bml_mlp_grads", [_vp, _vp, _vp, _vp, _i64, _vp, _vp])
+_lib_mlp_fit = _sig("bml_mlp_train", [_vp, _vp, _vp, _vp, _i64, _i64, _i64, ctypes.c_float,
+                                      ctypes.c_float, ctypes.c_uint64, _vp])
 _lib_mlp_apply = _sig("bml_mlp_apply_grads", [_vp, _vp, ctypes.c_float, ctypes.c_float])
 _lib_mlp_destroy = _sig("bml_mlp_destroy", [_vp], None)
 _lib_gemm = _sig("bml_gemm_bf16", [_vp, _i64, _vp, _i64, _vp, _i64, _i64, _i64, _i64, _vp])
@@ -385,6 +387,18 @@ class MLP:
                               jam.contiguous().data_ptr(), x.shape[0], lr, weight_decay,
                               ctypes.byref(loss) if want_loss else None))
         return loss.value if want_loss else None
+
+    def train(self, x, v, jam, steps: int, batch: int, lr: float, weight_decay: float = 0.0,
+              seed: int = 0, want_losses: bool = True):
+        """`steps` AdamW steps on mini-batches drawn on the device from the
+        rows of (x, v, jam) (bml_mlp_train); returns every step's loss (numpy
+        float32) or None."""
+        n = x.shape[0]
+        losses = np.empty(max(steps, 0), dtype=np.float32) if want_losses else None
+        _check(_lib_mlp_fit(self._h, x.contiguous().data_ptr(), v.contiguous().data_ptr(),
+                            jam.contiguous().data_ptr(), n, steps, batch, lr, weight_decay,
+                            seed, _host_ptr(losses) if want_losses else None))
+        return losses
 
     def grads(self, x, v, jam):
         g = np.empty(self.n, dtype=np.float32)

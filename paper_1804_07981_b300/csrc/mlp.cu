@@ -38,6 +38,7 @@
 
 #include "../../include/bml.h"
 #include "bml_internal.cuh"
+#include "device_common.cuh"
 
 namespace bml {
 namespace {
@@ -351,6 +352,24 @@ __global__ void loss_grad_kernel(const float *__restrict__ out, const float *__r
   }
 }
 
+// Mini-batch draw for bml_mlp_train: sample i of training step t takes row
+// floor(u * n / 2^64) of the training set, u = SplitMix64(seed, t * B + i + 1)
+// (uniform, with replacement); its features and labels are copied into xb,
+// vb, jb.
+__global__ void gather_batch_kernel(const float *__restrict__ x, const float *__restrict__ v,
+                                    const float *__restrict__ jam, long long n, u64 seed,
+                                    long long t, int B, float *xb, float *vb, float *jb) {
+  for (int i = blockIdx.x; i < B; i += gridDim.x) {
+    const u64 u = splitmix64_at(seed, (u64)t * (u64)B + (u64)i + 1ull);
+    const long long r = (long long)__umul64hi(u, (u64)n);
+    for (int c = threadIdx.x; c < kIn; c += blockDim.x) xb[(size_t)i * kIn + c] = x[r * kIn + c];
+    if (threadIdx.x == 0) {
+      vb[i] = v[r];
+      jb[i] = jam[r];
+    }
+  }
+}
+
 // dZ = dH * (H > 0): bf16 [Bp][128] and transpose [128][Bp]; bias gradient
 // = column sums (atomics), over the first B rows.
 __global__ void relu_bwd_kernel(const float *__restrict__ dH, const bf16 *__restrict__ H, int B,
@@ -531,6 +550,11 @@ struct bml_mlp {
   float *out = nullptr, *dH = nullptr, *loss = nullptr;
   float *bias4 = nullptr;  // padded output bias [16]
   int *err = nullptr;
+  // bml_mlp_train: gathered mini-batch (features, labels) and per-step losses
+  int train_cap = 0;
+  float *xb = nullptr, *vb = nullptr, *jb = nullptr;
+  long long loss_cap = 0;
+  float *losses = nullptr;
 };
 
 namespace {
@@ -687,6 +711,10 @@ extern "C" void bml_mlp_destroy(bml_mlp *p) {
   cudaFree(p->err);
   cudaFree(p->loss);
   cudaFree(p->bias4);
+  cudaFree(p->xb);
+  cudaFree(p->vb);
+  cudaFree(p->jb);
+  cudaFree(p->losses);
   for (int l = 0; l < 4; ++l) {
     cudaFree(p->W[l]);
     cudaFree(p->WT[l]);
@@ -817,6 +845,50 @@ extern "C" int bml_mlp_train_step(bml_mlp *p, const float *d_x, const float *d_v
   int rc = compute_grads(p, d_x, d_v, d_jam, (int)batch, h_loss, wait);
   if (rc) return rc;
   return adamw(p, lr, weight_decay, nullptr);
+}
+
+extern "C" int bml_mlp_train(bml_mlp *p, const float *d_x, const float *d_v, const float *d_jam,
+                             int64_t n, int64_t steps, int64_t batch, float lr,
+                             float weight_decay, uint64_t seed, float *h_losses) {
+  if (!p || !d_x || !d_v || !d_jam) return mfail(BML_EINVAL, "NULL argument");
+  if (n < 1 || n > (1ll << 40)) return mfail(BML_EINVAL, "n must be in [1, 2^40]");
+  if (steps < 0 || steps > (1 << 30)) return mfail(BML_EINVAL, "steps must be in [0, 2^30]");
+  if (batch < 1 || batch > (1 << 24)) return mfail(BML_EINVAL, "batch must be in [1, 2^24]");
+  if (!(lr >= 0.f) || !(weight_decay >= 0.f)) return mfail(BML_EINVAL, "bad lr / weight_decay");
+  if (steps == 0) return BML_OK;
+  const int B = (int)batch;
+  if (B > p->train_cap) {
+    cudaFree(p->xb);
+    cudaFree(p->vb);
+    cudaFree(p->jb);
+    p->xb = p->vb = p->jb = nullptr;
+    p->train_cap = 0;
+    MCUDA(cudaMalloc(&p->xb, (size_t)B * kIn * 4));
+    MCUDA(cudaMalloc(&p->vb, (size_t)B * 4));
+    MCUDA(cudaMalloc(&p->jb, (size_t)B * 4));
+    p->train_cap = B;
+  }
+  if (h_losses && steps > p->loss_cap) {
+    cudaFree(p->losses);
+    p->losses = nullptr;
+    p->loss_cap = 0;
+    MCUDA(cudaMalloc(&p->losses, (size_t)steps * 4));
+    p->loss_cap = steps;
+  }
+  const int gblocks = B < 1024 ? B : 1024;
+  for (int64_t s = 0; s < steps; ++s) {
+    gather_batch_kernel<<<gblocks, 64, 0, p->st>>>(d_x, d_v, d_jam, (long long)n, seed, p->t, B,
+                                                   p->xb, p->vb, p->jb);
+    MCUDA(cudaGetLastError());
+    int rc = compute_grads(p, p->xb, p->vb, p->jb, B, nullptr, false);
+    if (rc) return rc;
+    if (h_losses)
+      MCUDA(cudaMemcpyAsync(p->losses + s, p->loss, 4, cudaMemcpyDeviceToDevice, p->st));
+    if ((rc = adamw(p, lr, weight_decay, nullptr))) return rc;
+  }
+  if (h_losses)
+    MCUDA(cudaMemcpyAsync(h_losses, p->losses, (size_t)steps * 4, cudaMemcpyDeviceToHost, p->st));
+  return check_mlp_err(p);
 }
 
 extern "C" int bml_mlp_grads(bml_mlp *p, const float *d_x, const float *d_v, const float *d_jam,

@@ -65,35 +65,18 @@ def training_set(count, T, window, seed, lo=64, hi=2048, stream=None):
     return X, v, jam, secs
 
 
-def _nullctx():
-    import contextlib
-    return contextlib.nullcontext()
-
-
 def train(X, v, jam, steps=2000, batch=1024, lr=1e-3, wd=1e-4, seed=0, stream=None,
           loss_tail=50):
-    """AdamW on random mini-batches; returns the network and the losses of
-    the first step and of the last `loss_tail` steps (only those steps wait
-    for the device to report their loss)."""
-    import torch
+    """AdamW on mini-batches drawn on the device (bml_mlp_train: one call,
+    the draw, gather and steps all enqueued on the network's stream);
+    returns the network and the losses of the first step and of the last
+    `loss_tail` steps."""
     from .inputs import mlp_init_params
     net = bml.MLP(stream=stream)
     net.set_params(mlp_init_params(X.shape[1], seed).astype(np.float32))
-    g = torch.Generator(device="cuda").manual_seed(seed)
-    n = X.shape[0]
-    losses = []
-    # the batches are gathered on the network's stream: steps that report no
-    # loss are only enqueued, and their inputs must be read before reuse
-    ctx = torch.cuda.stream(stream) if isinstance(stream, torch.cuda.Stream) else _nullctx()
-    with ctx:
-        for s in range(steps):
-            idx = torch.randint(0, n, (min(batch, n),), device="cuda", generator=g)
-            want = s == 0 or s >= steps - loss_tail
-            loss = net.train_step(X[idx], v[idx], jam[idx], lr=lr, weight_decay=wd,
-                                  want_loss=want)
-            if want:
-                losses.append(loss)
-    return net, losses
+    losses = net.train(X, v, jam, steps, min(batch, X.shape[0]), lr=lr, weight_decay=wd,
+                       seed=seed + 1)
+    return net, [float(losses[0])] + [float(x) for x in losses[-loss_tail:]]
 
 
 def sweep_runs(densities, n_seeds, L):

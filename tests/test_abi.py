@@ -111,3 +111,14 @@ def test_set_allocator_needs_both_functions(lib):
         return None
     with pytest.raises(lib.BMLError):
         lib._check(lib._lib_set_allocator(a, lib.FREE_FN(), None))
+
+
+def test_mlp_train_rejects_bad_arguments_before_any_cuda_call(lib):
+    so = ctypes.CDLL(lib.LIB_PATH)
+    f = so.bml_mlp_train
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                  ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_float,
+                  ctypes.c_float, ctypes.c_uint64, ctypes.c_void_p]
+    assert f(None, 1, 1, 1, 10, 1, 8, 1e-3, 0.0, 1, None) == lib.BML_EINVAL
+    assert f(1, None, 1, 1, 10, 1, 8, 1e-3, 0.0, 1, None) == lib.BML_EINVAL

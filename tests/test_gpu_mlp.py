@@ -155,3 +155,52 @@ def test_training_without_loss_readback_updates_identically(lib):
         params.append(net.get_params())
         net.close()
     np.testing.assert_allclose(params[0], params[1], rtol=1e-5, atol=1e-8)
+
+
+def _drawn_rows(seed, t, B, n):
+    """Rows of training step t's mini-batch, restated from the documented
+    draw: u = SplitMix64(seed, t * B + i + 1), row = floor(u * n / 2^64)."""
+    M64 = (1 << 64) - 1
+    rows = []
+    for i in range(B):
+        z = (seed + (t * B + i + 1) * 0x9E3779B97F4A7C15) & M64
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M64
+        z ^= z >> 31
+        rows.append((z * n) >> 64)
+    return np.array(rows, dtype=np.int64)
+
+
+def test_native_training_equals_train_steps_on_the_drawn_batches(lib):
+    """bml_mlp_train (draw, gather and steps on the device) gives the losses
+    and weights of the same steps taken one by one on the batches the
+    documented draw selects (up to the rounding order of float atomics)."""
+    import torch
+    n, B, steps, seed = 700, 128, 12, 99
+    rng = np.random.Generator(np.random.PCG64(5))
+    x = rng.uniform(0, 1, size=(n, IN))
+    v = 0.3 * x[:, 0] + 0.2 * x[:, 5]
+    jam = (x[:, 7] > 0.6).astype(np.float64)
+    t = lambda a: torch.tensor(a, dtype=torch.float32, device="cuda")
+    X, V, J = t(x), t(v), t(jam)
+    p0 = mlp_init_params(IN, 3).astype(np.float32)
+    a = lib.MLP()
+    a.set_params(p0)
+    losses = a.train(X, V, J, steps, B, lr=2e-3, weight_decay=1e-4, seed=seed)
+    b = lib.MLP()
+    b.set_params(p0)
+    want = []
+    for s in range(steps):
+        idx = torch.tensor(_drawn_rows(seed, s, B, n), device="cuda")
+        want.append(b.train_step(X[idx], V[idx], J[idx], lr=2e-3, weight_decay=1e-4))
+    np.testing.assert_allclose(losses, np.array(want, dtype=np.float32), rtol=1e-5)
+    np.testing.assert_allclose(a.get_params(), b.get_params(), rtol=1e-5, atol=1e-7)
+    # a second call continues the step index (new batches)
+    more = a.train(X, V, J, 3, B, lr=2e-3, weight_decay=1e-4, seed=seed)
+    for s in range(3):
+        idx = torch.tensor(_drawn_rows(seed, steps + s, B, n), device="cuda")
+        got = b.train_step(X[idx], V[idx], J[idx], lr=2e-3, weight_decay=1e-4)
+        assert abs(got - more[s]) <= 1e-5 * abs(got)
+    assert a.train(X, V, J, 0, B, lr=1e-3) is not None
+    a.close()
+    b.close()
