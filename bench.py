@@ -183,10 +183,13 @@ def _cpu_sample(budget_s: float, threads: int):
     return rate, desc, dt
 
 
-def _ensemble_bench(bml, torch, stream, steps, seed_base=1, tiling=None):
+def _ensemble_bench(bml, torch, stream, steps, seed_base=1, tiling=None, sm_mhz=SM_MAX_MHZ):
     """Batched ensemble of 4096 lattices (M, N uniform on {64..2048}, density
     uniform on [0.1, 0.6], LR fraction uniform on [0.3, 0.7]), autotuned,
-    graph-replayed; `steps` steps timed with CUDA events after a warm-up."""
+    graph-replayed; `steps` steps timed with CUDA events after a warm-up.
+    Roofline: the integer ALU pipe, the bitplane step's algorithmic
+    operations (ALU_OPS_PER_CELL_STEP) against 148 SMs x 64 lanes x the SM
+    clock."""
     from paper_1804_07981_b300.inputs import ensemble_params
     p = ensemble_params(4096, seed=1)
     k, band = tiling if tiling else (0, 0)  # 0, 0: autotuned
@@ -205,9 +208,15 @@ def _ensemble_bench(bml, torch, stream, steps, seed_base=1, tiling=None):
     cells = int((p["M"] * p["N"]).sum())
     k, band, graphs = ens.config
     ens.close()
+    cu = cells * steps / (ms / 1e3)
+    ops = cu * ALU_OPS_PER_CELL_STEP / 1e12
+    peak = SMS * ALU_LANES_PER_SM_CLK * sm_mhz * 1e6 / 1e12
     return {"metric": "ensemble lattice-steps/s", "lattices": 4096, "steps": steps,
             "seconds": ms / 1e3, "unit": "lattice-steps/s",
-            "cell_updates_per_s": cells * steps / (ms / 1e3), "cells": cells,
+            "cell_updates_per_s": cu, "cells": cells,
+            "roofline": {"bound": "alu", "kernel": "ens_kernel<%d>" % k, "achieved": ops,
+                         "peak": peak, "unit": "Tops/s", "frac": ops / peak,
+                         "ops_per_cell_step": ALU_OPS_PER_CELL_STEP},
             "temporal_depth": k, "band_rows": band, "graph": graphs,
             "workload": "4096 lattices, M,N ~ U{64..2048}, rho ~ U[0.1,0.6], "
                         "LR fraction ~ U[0.3,0.7], seeds 1..4096"}
@@ -586,7 +595,8 @@ def run_ours(args):
     ens = None
     if not args.no_ensemble:
         ens = _ensemble_bench(bml, torch, stream, args.ensemble_steps, seed_base=1 + 4096 * rank,
-                              tiling=_ints(args.ensemble_tiling))
+                              tiling=_ints(args.ensemble_tiling),
+                              sm_mhz=(clk or {}).get("sm_mhz") or SM_MAX_MHZ)
         ens_max = max_over_ranks(ens["seconds"])
         ens["value"] = job_rate(world, ens["lattices"] * ens["steps"], ens_max)
 
