@@ -56,10 +56,15 @@ __device__ __forceinline__ u64 mk64(uint32_t lo, uint32_t hi) {
 // copied).  FULL: every word of the row holds 64 cells.
 //
 // Words with fewer cells (the last word of a row whose N is not a multiple of
-// 64): the right neighbour's first cell enters at this word's last cell as
-// rr * ins (a product on the FMA pipe); the higher bits of that product fall
-// outside the row and stay out of mvH because L is zero there.  The last
-// cell sent to the left neighbour is placed at bit 31 by two multiply-adds.
+// 64): E is masked to the valid cells and the right neighbour's first cell
+// (bit 0 of its E) enters at this word's last cell as a multiply-add on the
+// FMA pipe (the shifted E is zero at that bit), so Er is zero past the row's
+// end and no car moves there.  The last cell sent to the left neighbour is
+// placed at bit 31 by two multiply-adds.  `in` also shifts the row's last
+// cell one bit past the end (the left shuffle carries it to the row's first
+// cell); that bit is never read by a valid cell, never counted and never
+// moves again, so the caller clears it once, when it stores the emitted row
+// (mask `valid`), instead of at every stage.
 template <bool FULL>
 __device__ __forceinline__ void stage_step_pp(u64 &inL, u64 &inT, const u64 curT, const u64 curLh,
                                               const u64 prevMv, u64 &nT, u64 &nLh, u64 &nMv,
@@ -70,14 +75,14 @@ __device__ __forceinline__ void stage_step_pp(u64 &inL, u64 &inT, const u64 curT
   if (FULL) {
     Er = mk64(__funnelshift_r(lo32(E), hi32(E), 1), __funnelshift_r(hi32(E), rr, 1));
   } else {
-    Er = mk64(__funnelshift_r(lo32(E), hi32(E), 1) | (rr * lw.ins_lo),
-              (hi32(E) >> 1) | (rr * lw.ins_hi));
+    const uint32_t r0 = rr & 1u;
+    Er = mk64(__funnelshift_r(lo32(E), hi32(E), 1) + r0 * lw.ins_lo,
+              (hi32(E) >> 1) + r0 * lw.ins_hi);
   }
   mvH = inL & Er;
   const uint32_t send_l = FULL ? hi32(mvH) : hi32(mvH) * lw.mul_hi + lo32(mvH) * lw.mul_lo;
   const uint32_t rl = __shfl_sync(BML_FULL_MASK, send_l, lw.src_l);
-  u64 in = mk64(__funnelshift_l(rl, lo32(mvH), 1), __funnelshift_l(lo32(mvH), hi32(mvH), 1));
-  if (!FULL) in &= lw.valid;
+  const u64 in = mk64(__funnelshift_l(rl, lo32(mvH), 1), __funnelshift_l(lo32(mvH), hi32(mvH), 1));
   nLh = inL ^ mvH ^ in;
   mvV = curT & ~(nLh | inT);
   nT = inT;
