@@ -70,23 +70,74 @@ __device__ __forceinline__ HPair h_pair(const u64 *__restrict__ Lr, const u64 *_
   return r;
 }
 
-// One thread per (row, pair of words): 128-bit loads of L and T.
+// A warp takes 32 consecutive word pairs of one row (a row segment), one pair
+// per lane, with 128-bit loads of L and T.  The left neighbour's last L cell
+// and the right neighbour's first E cell come from the adjacent lanes by
+// shuffle, and from memory (loaded beside the pair) only at the segment's
+// ends and at the row's wrap.  The (row, segment) of a warp advances by the
+// number of warps in the grid, without a division per item.
 __global__ void __launch_bounds__(256) plane_h_kernel(const u64 *__restrict__ L,
                                                       const u64 *__restrict__ T,
                                                       u64 *__restrict__ Lh, Geom g, u64 *moved) {
-  const int64_t np = g.P / 2, total = g.M * np;
+  const int np = (int)(g.P / 2), segs = (np + 31) / 32;
+  const int W = (int)g.W;
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t di = nwarps / segs;
+  const int dseg = (int)(nwarps - di * segs);
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  int64_t i = w0 / segs;
+  int seg = (int)(w0 - i * segs);
   uint32_t cnt = 0;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = idx / np, p = idx - i * np;
-    const int64_t a = 2 * p;
+  for (; i < g.M; i += di, seg += dseg) {
+    if (seg >= segs) {
+      seg -= segs;
+      ++i;
+      if (i >= g.M) break;
+    }
+    const int q = seg * 32 + lane;
+    const bool on = q < np;
+    const int a = 2 * q, b = a + 1;
+    const bool a_last = a == W - 1, b_last = b == W - 1;
+    // word whose first E cell is right of b (or of a when a ends the row),
+    // and word whose last L cell is left of a, when they are not in the
+    // neighbouring lanes
+    const bool mem_r = on && (a_last || b_last || lane == 31);
+    const bool mem_l = on && lane == 0;
+    const int wr = (a_last || b_last) ? 0 : b + 1;
+    const int wl = a == 0 ? W - 1 : a - 1;
     const u64 *Lr = L + i * g.P, *Tr = T + i * g.P;
-    u64 La, Lb, Ta, Tb;
-    ld2(Lr + a, La, Lb);
-    ld2(Tr + a, Ta, Tb);
-    const HPair h = h_pair(Lr, Tr, a, g, La, Lb, Ta, Tb);
-    st2(Lh + i * g.P + a, h.La, h.Lb);
-    cnt += h.moved;
+    u64 La = 0, Lb = 0, Ta = 0, Tb = 0, Lrr = 0, Trr = 0, Lll = 0;
+    if (on) {
+      ld2(Lr + a, La, Lb);
+      ld2(Tr + a, Ta, Tb);
+    }
+    if (mem_r) {
+      Lrr = __ldg(Lr + wr);
+      Trr = __ldg(Tr + wr);
+    }
+    if (mem_l) Lll = __ldg(Lr + wl);
+    const u64 Ea = ~(La | Ta) & word_valid(a, g);
+    const u64 Eb = ~(Lb | Tb) & word_valid(b, g);
+    const uint32_t nxt_e = __shfl_down_sync(BML_FULL_MASK, (uint32_t)Ea, 1);
+    const uint32_t prv_l = __shfl_up_sync(BML_FULL_MASK, (uint32_t)(Lb >> 32), 1);
+    if (on) {
+      const u64 e0 = mem_r ? (~(Lrr | Trr) & 1ull) : (u64)(nxt_e & 1u);
+      const u64 lbit = mem_l ? ((Lll >> word_top(wl, g)) & 1ull) : (u64)(prv_l >> 31);
+      u64 Era, Erb, Llb;
+      if (!a_last) {
+        Era = funnel_r1(Ea, Eb);
+        Erb = (Eb >> 1) | (e0 << word_top(b, g));
+        Llb = funnel_l1(La, Lb);
+      } else {  // a ends the row, b is padding
+        Era = (Ea >> 1) | (e0 << word_top(a, g));
+        Erb = 0;
+        Llb = 0;
+      }
+      const u64 Lla = (La << 1) | lbit;
+      st2(Lh + i * g.P + a, (La & ~Era) | (Lla & Ea), (Lb & ~Erb) | (Llb & Eb));
+      cnt += (uint32_t)(__popcll(La & Era) + __popcll(Lb & Erb));
+    }
   }
   block_count_add(cnt, moved);
 }
@@ -151,32 +202,41 @@ __global__ void __launch_bounds__(128) fused_rows_kernel(const u64 *__restrict__
 }
 
 // One thread per (band of rows, pair of words): marches down the band with
-// the previous row's T and the current row's E in registers.
+// the previous row's T and the current row's E in registers.  Padding words
+// (past column N) hold no TB car, so no move involves them and the vertical
+// rule needs no column mask.
 __global__ void __launch_bounds__(256) plane_v_kernel(const u64 *__restrict__ Lh,
-                                                      const u64 *__restrict__ T,
-                                                      u64 *__restrict__ Tv, Geom g,
-                                                      int64_t band, u64 *moved) {
+                                                         const u64 *__restrict__ T,
+                                                         u64 *__restrict__ Tv, Geom g,
+                                                         int64_t band, u64 *moved) {
   const int64_t np = g.P / 2, nbands = (g.M + band - 1) / band, total = nbands * np;
   uint32_t cnt = 0;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int64_t bnd = idx / np, p = idx - bnd * np;
-    const int64_t a = 2 * p;
-    const u64 va = word_valid(a, g), vb = word_valid(a + 1, g);
-    const int64_t r0 = bnd * band, r1 = r0 + band < g.M ? r0 + band : g.M;
+    const int64_t r0 = bnd * band;
+    const int len = (int)(r0 + band < g.M ? band : g.M - r0);
+    const bool wraps = r0 + len == g.M;  // the band's last row reads row 0 below it
+    const int64_t off0 = 2 * p;
+    const u64 *lp = Lh + r0 * g.P + off0, *tp = T + r0 * g.P + off0;
+    u64 *op = Tv + r0 * g.P + off0;
     u64 Tpa, Tpb, x0, x1, Ta, Tb;
-    ld2(T + (r0 > 0 ? r0 - 1 : g.M - 1) * g.P + a, Tpa, Tpb);
-    ld2(Lh + r0 * g.P + a, x0, x1);
-    ld2(T + r0 * g.P + a, Ta, Tb);
-    u64 Ea = ~(x0 | Ta) & va, Eb = ~(x1 | Tb) & vb;
-    for (int64_t i = r0; i < r1; ++i) {
-      const int64_t n = i + 1 < g.M ? i + 1 : 0;
+    ld2(r0 > 0 ? tp - g.P : T + (g.M - 1) * g.P + off0, Tpa, Tpb);
+    ld2(lp, x0, x1);
+    ld2(tp, Ta, Tb);
+    u64 Ea = ~(x0 | Ta), Eb = ~(x1 | Tb);
+#pragma unroll 1
+    for (int k = 0; k < len; ++k) {
+      lp += g.P;
+      tp += g.P;
+      const bool w = k + 1 == len && wraps;
       u64 Lna, Lnb, Tna, Tnb;
-      ld2(Lh + n * g.P + a, Lna, Lnb);
-      ld2(T + n * g.P + a, Tna, Tnb);
-      const u64 Ena = ~(Lna | Tna) & va, Enb = ~(Lnb | Tnb) & vb;
+      ld2(w ? Lh + off0 : lp, Lna, Lnb);
+      ld2(w ? T + off0 : tp, Tna, Tnb);
+      const u64 Ena = ~(Lna | Tna), Enb = ~(Lnb | Tnb);
       const u64 mva = Ta & Ena, mvb = Tb & Enb;
-      st2(Tv + i * g.P + a, (Ta & ~Ena) | (Tpa & Ea), (Tb & ~Enb) | (Tpb & Eb));
+      st2(op, (Ta & ~Ena) | (Tpa & Ea), (Tb & ~Enb) | (Tpb & Eb));
+      op += g.P;
       cnt += (uint32_t)(__popcll(mva) + __popcll(mvb));
       Tpa = Ta;
       Tpb = Tb;
@@ -197,12 +257,26 @@ int grid_cap(int64_t items, int threads, int per_sm) {
   return (int)blocks;
 }
 
+// Blocks of `threads` threads of kernel f resident per SM (at least 1): the
+// grid-stride kernels launch exactly one wave of them, so that every block's
+// equal share of the items runs concurrently.
+template <typename F>
+int resident_per_sm(F f, int threads) {
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, threads, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return b > 0 ? b : 1;
+}
+
 }  // namespace
 
 cudaError_t launch_plane_h(const u64 *L, const u64 *T, u64 *Lh, const Geom &g, u64 *moved,
                            cudaStream_t st) {
-  const int64_t items = g.M * (g.P / 2);
-  plane_h_kernel<<<grid_cap(items, 256, 8), 256, 0, st>>>(L, T, Lh, g, moved);
+  const int64_t items = g.M * ((g.P / 2 + 31) / 32) * 32;
+  static const int per_sm = resident_per_sm(plane_h_kernel, 256);
+  plane_h_kernel<<<grid_cap(items, 256, per_sm), 256, 0, st>>>(L, T, Lh, g, moved);
   return cudaGetLastError();
 }
 
@@ -220,7 +294,8 @@ cudaError_t launch_plane_v(const u64 *Lh, const u64 *T, u64 *Tv, const Geom &g, 
                            cudaStream_t st) {
   const int64_t band = 16;
   const int64_t items = ((g.M + band - 1) / band) * (g.P / 2);
-  plane_v_kernel<<<grid_cap(items, 256, 8), 256, 0, st>>>(Lh, T, Tv, g, band, moved);
+  static const int per_sm = resident_per_sm(plane_v_kernel, 256);
+  plane_v_kernel<<<grid_cap(items, 256, per_sm), 256, 0, st>>>(Lh, T, Tv, g, band, moved);
   return cudaGetLastError();
 }
 
