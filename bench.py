@@ -17,8 +17,10 @@ Sub-measurements on the same JSON line: "ensemble" (4096 lattices, the
 batched API), "model2" (the Sec. 2 Model II variant on the bench lattice,
 tie-break seed = placement seed, 1024 steps; --no-model2 skips it),
 "byte_kernel" (the plain byte-per-cell form on the bench lattice, 16 steps,
-against the HBM peak), "one_pass" (one full step per DRAM pass on the bench
-lattice, 256 steps, against the HBM peak), "configs" (256^2 for 1024 steps; 4096^2 byte vs
+against the HBM peak), "two_phase" (the two-phase bitplane form, a horizontal and
+a vertical kernel per step, 64 steps, against the HBM peak), "one_pass" (one full step
+per DRAM pass on the bench lattice, 256 steps, against the HBM peak), "configs" (256^2
+for 1024 steps; 4096^2 byte vs
 bit-packed over 3 densities x 3 seeds x 4096 steps; rank 0 of a 1-GPU run), "mlp" (the
 surrogate network: AdamW step time at batch 1024, forward on 2624 samples, and its tcgen05
 GEMM kernel on a 2^22 x 128 x 128 product against the HBM peak; 1-GPU runs).
@@ -286,6 +288,24 @@ def _byte_bench(bml, torch, stream, M, N, steps, hbm_peak, seed=1):
             "kernel": "byte_h + byte_v", "gpu_launches": 2 * steps,
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
                          "frac": gbs / hbm_peak, "bytes_per_cell_step": 4.0}}
+
+
+def _two_phase_bench(bml, torch, stream, M, N, steps, hbm_peak, seed=1):
+    """The two-phase bitplane form on the bench lattice: a horizontal-phase
+    kernel (reads L and T, writes L') and a vertical-phase kernel (reads L'
+    and T, writes T') per step, 3 + 3 bitplane passes = 0.75 B of DRAM
+    traffic per cell-step."""
+    with bml.Lattice(M, N, seed=seed, density=DENSITY, kernel="bitplane", stream=stream,
+                     reserve_steps=steps + 8) as sim:
+        sim.step(2)
+        ms = _timed_steps(torch, stream, sim, steps)
+    cells = M * N
+    gbs = 0.75 * cells * steps / (ms / 1e3) / 1e9
+    return {"metric": "cell-updates/s", "value": cells * steps / (ms / 1e3),
+            "unit": "cell-updates/s", "steps": steps, "seconds": ms / 1e3,
+            "kernel": "plane_h + plane_v", "gpu_launches": 2 * steps,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": gbs / hbm_peak, "bytes_per_cell_step": 0.75}}
 
 
 def _one_pass_bench(bml, torch, stream, M, N, steps, hbm_peak, seed=1):
@@ -605,6 +625,12 @@ def run_ours(args):
         byte = _byte_bench(bml, torch, stream, M, N, args.byte_steps, hbm_peak, seed=1 + rank)
         byte["value"] = job_rate(world, M * N * byte["steps"], max_over_ranks(byte["seconds"]))
 
+    two = None
+    if not args.no_two_phase:
+        two = _two_phase_bench(bml, torch, stream, M, N, args.two_phase_steps, hbm_peak,
+                               seed=1 + rank)
+        two["value"] = job_rate(world, M * N * two["steps"], max_over_ranks(two["seconds"]))
+
     one = None
     if not args.no_one_pass:
         one = _one_pass_bench(bml, torch, stream, M, N, args.one_pass_steps, hbm_peak,
@@ -650,7 +676,8 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (2 x 256 MB bitplanes)",
                        "parallelism": "replicas x%d" % world},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "ensemble": ens,
-            "model2": m2, "byte_kernel": byte, "one_pass": one, "configs": small,
+            "model2": m2, "byte_kernel": byte, "two_phase": two, "one_pass": one,
+            "configs": small,
             "mlp": mlp,
             "gpu_launches": gpu_launches, "clocks": clk,
         }
@@ -689,6 +716,8 @@ def main():
     ap.add_argument("--mlp-gemm-rows", type=int, default=1 << 22,
                     help="rows of the GEMM-kernel measurement in the mlp entry")
     ap.add_argument("--no-one-pass", action="store_true")
+    ap.add_argument("--no-two-phase", action="store_true")
+    ap.add_argument("--two-phase-steps", type=int, default=64)
     ap.add_argument("--one-pass-steps", type=int, default=256)
     ap.add_argument("--model2-steps", type=int, default=1024)
     ap.add_argument("--M", type=int, default=M_ROWS)

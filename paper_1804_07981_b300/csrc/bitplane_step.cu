@@ -117,20 +117,26 @@ __global__ void __launch_bounds__(256) plane_h_kernel(const u64 *__restrict__ L,
       Trr = __ldg(Tr + wr);
     }
     if (mem_l) Lll = __ldg(Lr + wl);
-    const u64 Ea = ~(La | Ta) & word_valid(a, g);
-    const u64 Eb = ~(Lb | Tb) & word_valid(b, g);
+    // only the pair holding the row's last word has cells to mask
+    const bool full = b < W - 1;
+    const u64 Ea = full ? ~(La | Ta) : (~(La | Ta) & word_valid(a, g));
+    const u64 Eb = full ? ~(Lb | Tb) : (~(Lb | Tb) & word_valid(b, g));
     const uint32_t nxt_e = __shfl_down_sync(BML_FULL_MASK, (uint32_t)Ea, 1);
     const uint32_t prv_l = __shfl_up_sync(BML_FULL_MASK, (uint32_t)(Lb >> 32), 1);
     if (on) {
       const u64 e0 = mem_r ? (~(Lrr | Trr) & 1ull) : (u64)(nxt_e & 1u);
-      const u64 lbit = mem_l ? ((Lll >> word_top(wl, g)) & 1ull) : (u64)(prv_l >> 31);
+      const u64 lbit = mem_l ? ((Lll >> (a == 0 ? g.nb - 1 : 63)) & 1ull) : (u64)(prv_l >> 31);
       u64 Era, Erb, Llb;
-      if (!a_last) {
+      if (full) {
         Era = funnel_r1(Ea, Eb);
-        Erb = (Eb >> 1) | (e0 << word_top(b, g));
+        Erb = (Eb >> 1) | (e0 << 63);
+        Llb = funnel_l1(La, Lb);
+      } else if (!a_last) {  // b ends the row
+        Era = funnel_r1(Ea, Eb);
+        Erb = (Eb >> 1) | (e0 << (g.nb - 1));
         Llb = funnel_l1(La, Lb);
       } else {  // a ends the row, b is padding
-        Era = (Ea >> 1) | (e0 << word_top(a, g));
+        Era = (Ea >> 1) | (e0 << (g.nb - 1));
         Erb = 0;
         Llb = 0;
       }
