@@ -89,6 +89,7 @@ __global__ void __launch_bounds__(256) plane_h_kernel(const u64 *__restrict__ L,
   int64_t i = w0 / segs;
   int seg = (int)(w0 - i * segs);
   uint32_t cnt = 0;
+  pdl_wait();
   for (; i < g.M; i += di, seg += dseg) {
     if (seg >= segs) {
       seg -= segs;
@@ -145,6 +146,7 @@ __global__ void __launch_bounds__(256) plane_h_kernel(const u64 *__restrict__ L,
       cnt += (uint32_t)(__popcll(La & Era) + __popcll(Lb & Erb));
     }
   }
+  pdl_release();  // this block's lattice work is done
   block_count_add(cnt, moved);
 }
 
@@ -217,6 +219,7 @@ __global__ void __launch_bounds__(256) plane_v_kernel(const u64 *__restrict__ Lh
                                                          int64_t band, u64 *moved) {
   const int64_t np = g.P / 2, nbands = (g.M + band - 1) / band, total = nbands * np;
   uint32_t cnt = 0;
+  pdl_wait();
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int64_t bnd = idx / np, p = idx - bnd * np;
@@ -252,6 +255,7 @@ __global__ void __launch_bounds__(256) plane_v_kernel(const u64 *__restrict__ Lh
       Eb = Enb;
     }
   }
+  pdl_release();  // this block's lattice work is done
   block_count_add(cnt, moved);
 }
 
@@ -282,8 +286,8 @@ cudaError_t launch_plane_h(const u64 *L, const u64 *T, u64 *Lh, const Geom &g, u
                            cudaStream_t st) {
   const int64_t items = g.M * ((g.P / 2 + 31) / 32) * 32;
   static const int per_sm = resident_per_sm(plane_h_kernel, 256);
-  plane_h_kernel<<<grid_cap(items, 256, per_sm), 256, 0, st>>>(L, T, Lh, g, moved);
-  return cudaGetLastError();
+  return launch_pdl(plane_h_kernel, dim3(grid_cap(items, 256, per_sm)), dim3(256), 0, st, L, T,
+                    Lh, g, moved);
 }
 
 cudaError_t launch_fused_direct(const u64 *L, const u64 *T, u64 *Lo, u64 *To, const Geom &g,
@@ -301,8 +305,8 @@ cudaError_t launch_plane_v(const u64 *Lh, const u64 *T, u64 *Tv, const Geom &g, 
   const int64_t band = 16;
   const int64_t items = ((g.M + band - 1) / band) * (g.P / 2);
   static const int per_sm = resident_per_sm(plane_v_kernel, 256);
-  plane_v_kernel<<<grid_cap(items, 256, per_sm), 256, 0, st>>>(Lh, T, Tv, g, band, moved);
-  return cudaGetLastError();
+  return launch_pdl(plane_v_kernel, dim3(grid_cap(items, 256, per_sm)), dim3(256), 0, st, Lh, T,
+                    Tv, g, band, moved);
 }
 
 }  // namespace bml

@@ -115,4 +115,23 @@ cudaError_t launch_stream2(const u64 *Lin, const u64 *Tin, u64 *Lout, u64 *Tout,
                            int k, int64_t band_rows, u64 *moved_lr, u64 *moved_tb,
                            cudaStream_t st, int model = 1, u64 tie_seed = 0, u64 t0 = 0);
 
+// Launch `kern` with programmatic stream serialization: it may be scheduled
+// while the previous kernel on the stream finishes; the kernel calls
+// pdl_wait() before its first global memory access.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 }  // namespace bml

@@ -71,6 +71,7 @@ __global__ void byte_h_kernel(const uint8_t *__restrict__ cur, uint8_t *__restri
   int64_t i = w0 / segs;
   int seg = (int)(w0 - i * segs);
   uint32_t cnt = 0;
+  pdl_wait();
   for (; i < g.M; i += di, seg += dseg) {
     if (seg >= segs) {
       seg -= segs;
@@ -125,6 +126,7 @@ __global__ void byte_h_kernel(const uint8_t *__restrict__ cur, uint8_t *__restri
       cnt += popc_chunk(mv);
     }
   }
+  pdl_release();  // this block's lattice work is done
   block_count_add(cnt, moved);
 }
 
@@ -137,6 +139,7 @@ __global__ void __launch_bounds__(256, 8)
                   int64_t band, u64 *moved) {
   const int64_t nq = g.PB / 16, nbands = (g.M + band - 1) / band, total = nbands * nq;
   uint32_t cnt = 0;
+  pdl_wait();
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int64_t b = idx / nq, q = idx - b * nq;
@@ -168,6 +171,7 @@ __global__ void __launch_bounds__(256, 8)
       E = En;
     }
   }
+  pdl_release();  // this block's lattice work is done
   block_count_add(cnt, moved);
 }
 
@@ -187,16 +191,16 @@ int grid_cap(int64_t items, int threads) {
 cudaError_t launch_byte_h(const uint8_t *cur, uint8_t *nxt, const Geom &g, u64 *moved,
                           cudaStream_t st) {
   const int64_t items = g.M * ((g.PB / 16 + 31) / 32) * 32;
-  byte_h_kernel<<<grid_cap(items, 256), 256, 0, st>>>(cur, nxt, g, moved);
-  return cudaGetLastError();
+  return launch_pdl(byte_h_kernel, dim3(grid_cap(items, 256)), dim3(256), 0, st, cur, nxt, g,
+                    moved);
 }
 
 cudaError_t launch_byte_v(const uint8_t *cur, uint8_t *nxt, const Geom &g, u64 *moved,
                           cudaStream_t st) {
   const int64_t band = 32;
   const int64_t items = ((g.M + band - 1) / band) * (g.PB / 16);
-  byte_v_kernel<<<grid_cap(items, 256), 256, 0, st>>>(cur, nxt, g, band, moved);
-  return cudaGetLastError();
+  return launch_pdl(byte_v_kernel, dim3(grid_cap(items, 256)), dim3(256), 0, st, cur, nxt, g,
+                    band, moved);
 }
 
 }  // namespace bml

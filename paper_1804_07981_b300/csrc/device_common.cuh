@@ -21,6 +21,20 @@ __device__ __forceinline__ int word_top(int64_t w, const Geom &g) {
   return w == g.W - 1 ? g.nb - 1 : 63;
 }
 
+// Programmatic dependent launch: a kernel launched with launch_pdl may start
+// (and run its set-up) while the previous kernel on the stream finishes;
+// pdl_wait() returns once that kernel has completed and its memory writes are
+// visible, so it comes before the first global access (the ping-pong buffers
+// the previous kernel read are written after it).  pdl_release(), once a
+// block's lattice work is done, lets the next kernel launch when every block
+// has released or exited (releasing at the start let the next kernel's
+// waiting blocks take the free slots of a partial wave and unbalance it).
+// Both are no-ops for a normal launch.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // n-th output (n >= 1) of SplitMix64 (Steele, Lea, Flood 2014) started from
 // state `seed`: the placement's and the Model II tie-break's generator.
 __device__ __forceinline__ u64 splitmix64_at(u64 seed, u64 n) {

@@ -135,6 +135,7 @@ __global__ void __launch_bounds__(kWarps2 * 32, K >= 8 ? 2 : 3)
   __shared__ unsigned long long s_cnt[2 * K];
   __shared__ __align__(16) ulonglong2 s_ring[kWarps2][kRing][2][32];  // [warp][slot][plane][lane]
   for (int t = threadIdx.x; t < 2 * K; t += blockDim.x) s_cnt[t] = 0;
+  pdl_wait();
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int tile = blockIdx.x * kWarps2 + (threadIdx.x >> 5);
@@ -240,6 +241,7 @@ __global__ void __launch_bounds__(kWarps2 * 32, K >= 8 ? 2 : 3)
       }
     }
   }
+  pdl_release();  // this block's lattice work is done
   flush_counts<K>(cnt, own, lane, s_cnt);
   __syncthreads();
   if (threadIdx.x < K) {
@@ -261,10 +263,9 @@ cudaError_t launch2_k(const u64 *Lin, const u64 *Tin, u64 *Lout, u64 *Tout, cons
   const int64_t tiles = n_strips * n_bands;
   if (tiles > INT32_MAX - kWarps2) return cudaErrorInvalidValue;
   const int64_t blocks = (tiles + kWarps2 - 1) / kWarps2;
-  stream2_kernel<K, MODEL><<<(unsigned)blocks, kWarps2 * 32, 0, st>>>(
-      Lin, Tin, Lout, Tout, g, (int)n_strips, base, rem, (int)band_rows, (int)n_bands,
-      moved_lr, moved_tb, tie_seed, t0);
-  return cudaGetLastError();
+  return launch_pdl(stream2_kernel<K, MODEL>, dim3((unsigned)blocks), dim3(kWarps2 * 32), 0, st,
+                    Lin, Tin, Lout, Tout, g, (int)n_strips, base, rem, (int)band_rows,
+                    (int)n_bands, moved_lr, moved_tb, tie_seed, t0);
 }
 
 template <int K, int MODEL>
