@@ -166,6 +166,7 @@ __global__ void __launch_bounds__(128) fused_rows_kernel(const u64 *__restrict__
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   const int groups = (int)((g.M + R - 1) / R);
   uint32_t clr = 0, ctb = 0;
+  pdl_wait();
   if (p < np) {
     const int64_t a = 2 * (int64_t)p;
     const u64 va = word_valid(a, g), vb = word_valid(a + 1, g);
@@ -205,6 +206,7 @@ __global__ void __launch_bounds__(128) fused_rows_kernel(const u64 *__restrict__
       }
     }
   }
+  pdl_release();  // this block's lattice work is done
   block_count_add(clr, moved_lr);
   block_count_add(ctb, moved_tb);
 }
@@ -296,8 +298,8 @@ cudaError_t launch_fused_direct(const u64 *L, const u64 *T, u64 *Lo, u64 *To, co
   const int64_t np = g.P / 2;
   const int64_t groups = (g.M + R - 1) / R;
   dim3 grid((unsigned)((np + 127) / 128), (unsigned)(groups < 65535 ? groups : 65535));
-  fused_rows_kernel<R><<<grid, 128, 0, st>>>(L, T, Lo, To, g, moved_lr, moved_tb);
-  return cudaGetLastError();
+  return launch_pdl(fused_rows_kernel<R>, grid, dim3(128), 0, st, L, T, Lo, To, g, moved_lr,
+                    moved_tb);
 }
 
 cudaError_t launch_plane_v(const u64 *Lh, const u64 *T, u64 *Tv, const Geom &g, u64 *moved,

@@ -98,6 +98,7 @@ __global__ void __launch_bounds__(kWarpsM2 * 32, K >= 8 ? 2 : (K >= 4 ? 3 : 4))
   constexpr int P = 2;  // rows per unrolled chunk (the state sets alternate by row)
   __shared__ unsigned long long s_cnt[2 * K];
   for (int t = threadIdx.x; t < 2 * K; t += blockDim.x) s_cnt[t] = 0;
+  pdl_wait();
   __syncthreads();
 
   const int lane = threadIdx.x & 31;
@@ -219,6 +220,7 @@ __global__ void __launch_bounds__(kWarpsM2 * 32, K >= 8 ? 2 : (K >= 4 ? 3 : 4))
     }
   }
 
+  pdl_release();  // this block's lattice work is done
 #pragma unroll
   for (int s = 0; s < K; ++s) {
     const uint32_t a = __reduce_add_sync(BML_FULL_MASK, c_lr[s]);
@@ -247,14 +249,12 @@ cudaError_t launch_m2_k(const u64 *Lin, const u64 *Tin, u64 *Lout, u64 *Tout, co
   if (tiles > INT32_MAX - kWarpsM2) return cudaErrorInvalidValue;
   const int64_t blocks = (tiles + kWarpsM2 - 1) / kWarpsM2;
   if (g.nb == 64)
-    model2_kernel<K, true><<<(unsigned)blocks, kWarpsM2 * 32, 0, st>>>(
-        Lin, Tin, Lout, Tout, g, sp, (int)band_rows, (int)n_bands, tie_seed, t0, moved_lr,
-        moved_tb);
-  else
-    model2_kernel<K, false><<<(unsigned)blocks, kWarpsM2 * 32, 0, st>>>(
-        Lin, Tin, Lout, Tout, g, sp, (int)band_rows, (int)n_bands, tie_seed, t0, moved_lr,
-        moved_tb);
-  return cudaGetLastError();
+    return launch_pdl(model2_kernel<K, true>, dim3((unsigned)blocks), dim3(kWarpsM2 * 32), 0, st,
+                      Lin, Tin, Lout, Tout, g, sp, (int)band_rows, (int)n_bands, tie_seed, t0,
+                      moved_lr, moved_tb);
+  return launch_pdl(model2_kernel<K, false>, dim3((unsigned)blocks), dim3(kWarpsM2 * 32), 0, st,
+                    Lin, Tin, Lout, Tout, g, sp, (int)band_rows, (int)n_bands, tie_seed, t0,
+                    moved_lr, moved_tb);
 }
 
 template <int K, bool FULL>

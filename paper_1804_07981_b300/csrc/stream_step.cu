@@ -87,6 +87,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, K >= 8 ? 3 : 4)
   constexpr int P = PF<K>::value;
   __shared__ unsigned long long s_cnt[2 * K];
   for (int t = threadIdx.x; t < 2 * K; t += blockDim.x) s_cnt[t] = 0;
+  pdl_wait();
   __syncthreads();
 
   const int lane = threadIdx.x & 31;
@@ -208,6 +209,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, K >= 8 ? 3 : 4)
   }
 
   // ---- counts: warp -> block (shared) -> global ----
+  pdl_release();  // this block's lattice work is done
 #pragma unroll
   for (int s = 0; s < K; ++s) {
     const uint32_t a = __reduce_add_sync(BML_FULL_MASK, c_lr[s]);
@@ -235,12 +237,12 @@ cudaError_t launch_k(const u64 *Lin, const u64 *Tin, u64 *Lout, u64 *Tout, const
   if (tiles > INT32_MAX - kWarpsPerBlock) return cudaErrorInvalidValue;
   const int64_t blocks = (tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
   if (g.nb == 64)
-    stream_kernel<K, true><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, st>>>(
-        Lin, Tin, Lout, Tout, g, sp, (int)band_rows, (int)n_bands, moved_lr, moved_tb);
-  else
-    stream_kernel<K, false><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, st>>>(
-        Lin, Tin, Lout, Tout, g, sp, (int)band_rows, (int)n_bands, moved_lr, moved_tb);
-  return cudaGetLastError();
+    return launch_pdl(stream_kernel<K, true>, dim3((unsigned)blocks), dim3(kWarpsPerBlock * 32), 0,
+                      st, Lin, Tin, Lout, Tout, g, sp, (int)band_rows, (int)n_bands, moved_lr,
+                      moved_tb);
+  return launch_pdl(stream_kernel<K, false>, dim3((unsigned)blocks), dim3(kWarpsPerBlock * 32), 0,
+                    st, Lin, Tin, Lout, Tout, g, sp, (int)band_rows, (int)n_bands, moved_lr,
+                    moved_tb);
 }
 
 template <int K, bool FULL>
