@@ -72,9 +72,9 @@ ALU_LANES_PER_SM_CLK = 64  # integer ALU pipe: 2 warp instructions per clock per
 SM_MAX_MHZ = 2032.0
 # DRAM bytes (read + write, as counted by ncu for one launch) per cell, from
 # the captures summarised in profiles/ (stream2_kernel<8> and <1>: 32768 x
-# 32768; fused_rows_kernel: 16384 x 32768); scaled by the cell count of the run
-TRAFFIC_PER_CELL = {"stream2_kernel<8>": 0.4700, "stream2_kernel<1>": 0.4517,
-                    "fused_rows_kernel": 0.4068}
+# 32768, the kernels as they are now); scaled by the cell count of the run.
+# A kernel without an entry reports traffic null.
+TRAFFIC_PER_CELL = {"stream2_kernel<8>": 0.4671, "stream2_kernel<1>": 0.4492}
 
 
 def _peaks():
