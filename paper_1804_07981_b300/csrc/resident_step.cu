@@ -19,8 +19,10 @@
 // neighbours computed once.  The horizontal phase reads the neighbours' L, T
 // and writes Lh to the other L buffer; the vertical phase reads the
 // neighbours' Lh, T and writes T' to the other T buffer; a block barrier
-// separates the phases.  Moved counts of step t are summed per warp (redux)
-// and per block (shared-memory atomics) and written once at the end.
+// separates the phases.  Moved counts of a phase are summed per warp (redux)
+// into a per-warp slot; after the phase's barrier warp 0 adds the slots into
+// the step's counter (no atomics), and the counters are written once at the
+// end.
 #include "device_common.cuh"
 
 namespace bml {
@@ -44,6 +46,7 @@ __global__ void __launch_bounds__(kResThreads, 1)
   u64 *sL[2] = {sm, sm + words};
   u64 *sT[2] = {sm + 2 * words, sm + 3 * words};
   unsigned int *cnt = (unsigned int *)(sm + 4 * words);  // [2][K]
+  __shared__ unsigned int s_part[2][kResThreads / 32];   // per-warp partial counts, by phase
   for (int x = threadIdx.x; x < words; x += blockDim.x) {
     sL[0][x] = Lin[x];
     sT[0][x] = Tin[x];
@@ -100,8 +103,13 @@ __global__ void __launch_bounds__(kResThreads, 1)
       }
     }
     c = __reduce_add_sync(BML_FULL_MASK, c);
-    if (lane == 0 && c) atomicAdd(&cnt[t], c);
+    if (lane == 0) s_part[0][threadIdx.x >> 5] = c;
     __syncthreads();
+    if (threadIdx.x < 32) {  // the previous step's vertical slots were read before this barrier
+      const uint32_t v = threadIdx.x < (blockDim.x >> 5) ? s_part[0][threadIdx.x] : 0u;
+      const uint32_t tot = __reduce_add_sync(BML_FULL_MASK, v);
+      if (threadIdx.x == 0) cnt[t] = tot;
+    }
     // ---- vertical phase: (L[a^1], T[a]) -> T[a^1] ----
     c = 0;
 #pragma unroll
@@ -118,10 +126,16 @@ __global__ void __launch_bounds__(kResThreads, 1)
       }
     }
     c = __reduce_add_sync(BML_FULL_MASK, c);
-    if (lane == 0 && c) atomicAdd(&cnt[K + t], c);
+    if (lane == 0) s_part[1][threadIdx.x >> 5] = c;
     __syncthreads();
+    if (threadIdx.x < 32) {
+      const uint32_t v = threadIdx.x < (blockDim.x >> 5) ? s_part[1][threadIdx.x] : 0u;
+      const uint32_t tot = __reduce_add_sync(BML_FULL_MASK, v);
+      if (threadIdx.x == 0) cnt[K + t] = tot;
+    }
     a ^= 1;
   }
+  __syncthreads();  // the last step's counters
   for (int x = threadIdx.x; x < words; x += blockDim.x) {
     Lout[x] = sL[a][x];
     Tout[x] = sT[a][x];
