@@ -165,3 +165,63 @@ def test_32768_full_job_byte_kernel_agrees(lib):
         np.testing.assert_array_equal(a, b)
     tot = out[1][1][0]
     assert tot.shape == (K,) and tot.min() > 0  # flows at 0.38 at this size
+
+
+def _byte_runs(lib, M, N, seeds, plr, ptb, K):
+    """Each lattice alone through the byte-per-cell kernels (K steps)."""
+    outs, lrs, tbs = [], [], []
+    for m, n, s, a, b in zip(M, N, seeds, plr, ptb):
+        with lib.Lattice(int(m), int(n), seed=int(s), p_lr=float(a), p_tb=float(b),
+                         kernel="byte", reserve_steps=K) as sim:
+            sim.step(K)
+            outs.append(sim.read())
+            _, lr, tb = sim.moved_counts()
+            lrs.append(lr)
+            tbs.append(tb)
+    return outs, np.stack(lrs), np.stack(tbs)
+
+
+def test_ensemble_workload_all_lattices_512_steps_against_byte_kernel(lib):
+    """The batched-ensemble workload (4096 lattices, M, N uniform on
+    {64..2048}, density in [0.1, 0.6], LR fraction in [0.3, 0.7]), autotuned
+    as the bench runs it, 512 steps: every lattice and every count equals the
+    lattice run alone through the byte-per-cell kernels (an independent GPU
+    path)."""
+    from paper_1804_07981_b300.inputs import ensemble_params
+    p = ensemble_params(4096, seed=1)
+    K = 512
+    with lib.Ensemble(p["M"], p["N"], p["seed"], p["p_lr"], p["p_tb"],
+                      reserve_steps=K) as ens:
+        ens.step(K)
+        got = ens.read_all()
+        lr, tb = ens.traces()
+    want, wlr, wtb = _byte_runs(lib, p["M"], p["N"], p["seed"], p["p_lr"], p["p_tb"], K)
+    for l in range(len(want)):
+        assert np.array_equal(got[l], want[l]), l
+    np.testing.assert_array_equal(lr, wlr)
+    np.testing.assert_array_equal(tb, wtb)
+
+
+def test_ensemble_workload_256_lattices_full_10000_steps_against_byte_kernel(lib):
+    """A seeded 256-lattice subset of the ensemble workload (every 16th
+    lattice) for the full 10^4 steps, with the jam early exit: lattices,
+    counts and jam steps equal the byte kernels' runs."""
+    from paper_1804_07981_b300.inputs import ensemble_params
+    p = ensemble_params(4096, seed=1)
+    idx = np.arange(0, 4096, 16)
+    M, N, s, a, b = p["M"][idx], p["N"][idx], p["seed"][idx], p["p_lr"][idx], p["p_tb"][idx]
+    K = 10000
+    with lib.Ensemble(M, N, s, a, b, flags=lib.BML_ENS_EARLY_EXIT, reserve_steps=K) as ens:
+        ens.step(K)
+        got = ens.read_all()
+        lr, tb = ens.traces()
+        jam = ens.jam_steps()
+    want, wlr, wtb = _byte_runs(lib, M, N, s, a, b, K)
+    for l in range(len(want)):
+        assert np.array_equal(got[l], want[l]), l
+    np.testing.assert_array_equal(lr, wlr)
+    np.testing.assert_array_equal(tb, wtb)
+    tot = wlr + wtb
+    want_jam = np.array([np.flatnonzero(t == 0)[0] if np.any(t == 0) else -1 for t in tot])
+    np.testing.assert_array_equal(jam, want_jam)
+    assert (want_jam >= 0).any() and (want_jam < 0).any()
