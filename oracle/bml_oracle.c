@@ -9,8 +9,8 @@
  * Model (Biham-Middleton-Levine Model I, Marzolla 2018, Sec. 2):
  *   - a periodic M x N lattice of cells, each EMPTY, LR (moves right) or
  *     TB (moves down);
- *   - one step = a horizontal phase then a vertical phase (Sec. 2, Fig. 1
- *     caption: "each step includes a horizontal and vertical phase");
+ *   - one step = a horizontal phase then a vertical phase (Sec. 2; the
+ *     Fig. 1 caption counts both phases as one step);
  *   - horizontal rule (Sec. 2, first case analysis):
  *       center' = LR     if left == LR and center == EMPTY
  *                 EMPTY  if center == LR and right == EMPTY

@@ -3,8 +3,9 @@
 // launch per step, each reading and writing one byte per cell.
 //
 // A thread handles a 16-byte chunk (16 cells) with one 128-bit load and
-// computes the rules branch-free on byte lanes, the selection-and-masking
-// idea of Sec. 5 ("a = (C & x) | (~C & y)"): with per-byte bit masks of
+// computes the rules branch-free on byte lanes, the selection-by-mask idea
+// of Sec. 5 (pick one of two values per lane through a condition mask and its
+// complement instead of a branch): with per-byte bit masks of
 // LR, TB and EMPTY (1 in bit 0 of a byte), a moving LR car and the cell it
 // enters both flip bit 0, a moving TB car and its destination flip bit 1.
 //   horizontal: out = x ^ ((L & Er) | (Ll & E))          (Sec. 2 rule 1)
