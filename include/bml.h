@@ -273,6 +273,15 @@ void bml_mlp_destroy(bml_mlp *mlp);
 int bml_gemm_bf16(const void *A, int64_t lda, const void *B, int64_t ldb, float *C, int64_t ldc,
                   int64_t M, int64_t N, int64_t K, void *stream);
 
+/* bml_gemm_bf16 with flags.  BML_GEMM_TEST_STALL (test hook): no operand copy
+ * is issued, so the kernel's first completion wait runs out after its 1 s
+ * bound; the kernel sets its error flag, releases its tensor memory and
+ * returns, and the call reports BML_ETIMEOUT (C is then undefined; the
+ * context stays usable).  Unknown flags: BML_EINVAL. */
+#define BML_GEMM_TEST_STALL 1u
+int bml_gemm_bf16_ex(const void *A, int64_t lda, const void *B, int64_t ldb, float *C,
+                     int64_t ldc, int64_t M, int64_t N, int64_t K, unsigned flags, void *stream);
+
 /* ------------------------------------------------------------------------
  * Byte-per-cell step that allocates nothing (no counterpart in the paper).
  *

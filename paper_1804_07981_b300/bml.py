@@ -344,11 +344,19 @@ _lib_mlp_fit = _sig("bml_mlp_train", [_vp, _vp, _vp, _vp, _i64, _i64, _i64, ctyp
 _lib_mlp_apply = _sig("bml_mlp_apply_grads", [_vp, _vp, ctypes.c_float, ctypes.c_float])
 _lib_mlp_destroy = _sig("bml_mlp_destroy", [_vp], None)
 _lib_gemm = _sig("bml_gemm_bf16", [_vp, _i64, _vp, _i64, _vp, _i64, _i64, _i64, _i64, _vp])
+_lib_gemm_ex = _sig("bml_gemm_bf16_ex", [_vp, _i64, _vp, _i64, _vp, _i64, _i64, _i64, _i64,
+                                         ctypes.c_uint, _vp])
+BML_GEMM_TEST_STALL = 1
 
 
 def bml_gemm_bf16(A: int, lda: int, B: int, ldb: int, C: int, ldc: int, M: int, N: int, K: int,
                   stream=None) -> None:
     _check(_lib_gemm(A, lda, B, ldb, C, ldc, M, N, K, _stream_handle(stream)))
+
+
+def bml_gemm_bf16_ex(A: int, lda: int, B: int, ldb: int, C: int, ldc: int, M: int, N: int,
+                     K: int, flags: int, stream=None) -> None:
+    _check(_lib_gemm_ex(A, lda, B, ldb, C, ldc, M, N, K, flags, _stream_handle(stream)))
 
 
 class MLP:

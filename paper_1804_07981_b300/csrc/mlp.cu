@@ -65,6 +65,7 @@ struct Epi {
   bf16 *out_bf16_t;   // EPI_RELU_BF16: optional [N][ldt] transposed copy
   int ldo, ldt;
   int *err;
+  int test_stall;  // test hook: the producer issues no copy, so the first wait runs out
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -179,7 +180,7 @@ __global__ void __launch_bounds__(128, 1)
     // producer: stage c % stages takes K chunk c once the MMAs of chunk
     // c - stages have released it
     int c = 0;
-    for (; c < nk; ++c) {
+    for (; c < nk && !epi.test_stall; ++c) {
       const int st = c % stages;
       if (c >= stages && !mbar_wait(empty(st), (uint32_t)((c / stages - 1) & 1))) {
         *s_fail = 1;
@@ -926,7 +927,14 @@ extern "C" int bml_mlp_apply_grads(bml_mlp *p, const float *host_grads, float lr
 
 extern "C" int bml_gemm_bf16(const void *A, int64_t lda, const void *B, int64_t ldb, float *C,
                              int64_t ldc, int64_t M, int64_t N, int64_t K, void *stream) {
+  return bml_gemm_bf16_ex(A, lda, B, ldb, C, ldc, M, N, K, 0u, stream);
+}
+
+extern "C" int bml_gemm_bf16_ex(const void *A, int64_t lda, const void *B, int64_t ldb, float *C,
+                                int64_t ldc, int64_t M, int64_t N, int64_t K, unsigned flags,
+                                void *stream) {
   if (!A || !B || !C) return mfail(BML_EINVAL, "NULL argument");
+  if (flags & ~BML_GEMM_TEST_STALL) return mfail(BML_EINVAL, "unknown flags");
   if (M < 1 || M > (1 << 24) || N < 16 || N > 128 || N % 16 || K < 16 || K % 16 ||
       K > (1 << 24) || lda < K || ldb < K || ldc < N || lda % 8 || ldb % 8)
     return mfail(BML_EINVAL, "bml_gemm_bf16: need 16 <= N <= 128, N % 16 == 0, K % 16 == 0, "
@@ -935,10 +943,10 @@ extern "C" int bml_gemm_bf16(const void *A, int64_t lda, const void *B, int64_t 
   // one completion-wait error flag per calling thread and device, allocated
   // on first use (the call waits for the stream, so a thread has at most one
   // call in flight)
-  thread_local std::map<int, int *> flags;
+  thread_local std::map<int, int *> err_flags;
   int dev = 0;
   MCUDA(cudaGetDevice(&dev));
-  int *&err = flags[dev];
+  int *&err = err_flags[dev];
   if (!err) MCUDA(cudaMalloc(&err, 4));
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = cudaMemsetAsync(err, 0, 4, st);
@@ -947,6 +955,7 @@ extern "C" int bml_gemm_bf16(const void *A, int64_t lda, const void *B, int64_t 
   ep.out_f32 = C;
   ep.ldo = (int)ldc;
   ep.err = err;
+  ep.test_stall = (flags & BML_GEMM_TEST_STALL) ? 1 : 0;
   if (e == cudaSuccess)
     e = launch_gemm((const bf16 *)A, (int)lda, (const bf16 *)B, (int)ldb, (int)M, (int)N, (int)K,
                     ep, st);

@@ -122,3 +122,9 @@ def test_mlp_train_rejects_bad_arguments_before_any_cuda_call(lib):
                   ctypes.c_float, ctypes.c_uint64, ctypes.c_void_p]
     assert f(None, 1, 1, 1, 10, 1, 8, 1e-3, 0.0, 1, None) == lib.BML_EINVAL
     assert f(1, None, 1, 1, 10, 1, 8, 1e-3, 0.0, 1, None) == lib.BML_EINVAL
+
+
+def test_gemm_rejects_unknown_flags_before_any_cuda_call(lib):
+    with pytest.raises(lib.BMLError) as e:
+        lib.bml_gemm_bf16_ex(16, 64, 16, 64, 16, 32, 256, 32, 64, 1 << 7)
+    assert e.value.code == lib.BML_EINVAL

@@ -204,3 +204,21 @@ def test_native_training_equals_train_steps_on_the_drawn_batches(lib):
     assert a.train(X, V, J, 0, B, lr=1e-3) is not None
     a.close()
     b.close()
+
+
+def test_gemm_completion_wait_runs_out_and_reports_timeout(lib):
+    """Test hook: no operand copy is issued, so the kernel's first
+    completion wait gives up after its bound; the call returns BML_ETIMEOUT
+    and the context stays usable (the next GEMM is exact)."""
+    import torch
+    g = torch.Generator().manual_seed(3)
+    A = torch.randn(256, 64, generator=g).to(torch.bfloat16).cuda()
+    B = torch.randn(32, 64, generator=g).to(torch.bfloat16).cuda()
+    C = torch.zeros((256, 32), dtype=torch.float32, device="cuda")
+    with pytest.raises(lib.BMLError) as e:
+        lib.bml_gemm_bf16_ex(A.data_ptr(), 64, B.data_ptr(), 64, C.data_ptr(), 32, 256, 32, 64,
+                             lib.BML_GEMM_TEST_STALL)
+    assert e.value.code == lib.BML_ETIMEOUT
+    lib.bml_gemm_bf16(A.data_ptr(), 64, B.data_ptr(), 64, C.data_ptr(), 32, 256, 32, 64)
+    want = A.double().cpu() @ B.double().cpu().T
+    assert torch.allclose(C.double().cpu(), want, rtol=1e-4, atol=1e-2)
