@@ -398,6 +398,17 @@ int bml_ensemble_features(bml_ens *ens, int64_t first, int64_t n, int points, fl
  * a fixed point), else 0 (device arrays of count floats).  Synchronises. */
 int bml_ensemble_labels(bml_ens *ens, int64_t window, float *d_v, float *d_jam);
 
+/* Stop advancing the n listed lattices (host array of indices; repeats and
+ * lattices already retired or jammed are allowed): from the next step on
+ * they keep their current state, their per-step counts are 0 and their
+ * tiles cost the kernel nothing, while the other lattices go on.  Their jam
+ * steps and labels are computed over the steps before the retirement.  For
+ * budget allocation: runs that have had their budget stop, the others
+ * continue in the same ensemble.  bml_ensemble_write_lattices makes every
+ * lattice active again.  Synchronises.  Errors: BML_EINVAL (NULL with n > 0,
+ * an index outside [0, count)), BML_ESTATE (the ensemble failed earlier). */
+int bml_ensemble_retire(bml_ens *ens, int64_t n, const int64_t *lattices);
+
 /* Temporal depth, band height and whether graph replay is in use. */
 int bml_ensemble_get_config(const bml_ens *ens, int *block_k, int64_t *band_rows, int *graphs);
 

@@ -465,6 +465,7 @@ _lib_ens_write = _sig("bml_ensemble_write_lattices", [_vp, _vp])
 _lib_ens_steps = _sig("bml_ensemble_steps_done", [_vp], _i64)
 _lib_ens_cfg = _sig("bml_ensemble_get_config", [_vp, ctypes.POINTER(_int), _i64p,
                                                  ctypes.POINTER(_int)])
+_lib_ens_retire = _sig("bml_ensemble_retire", [_vp, _i64, _vp])
 _lib_ens_sync = _sig("bml_ensemble_synchronize", [_vp])
 _lib_ens_cars = _sig("bml_ensemble_car_counts", [_vp, _vp])
 _lib_ens_feat = _sig("bml_ensemble_features", [_vp, _i64, _i64, _int, _vp])
@@ -608,6 +609,11 @@ class Ensemble:
     @property
     def config(self):
         return bml_ensemble_get_config(self._h)
+
+    def retire(self, lattices) -> None:
+        """Stop advancing the given lattices (bml_ensemble_retire)."""
+        idx = np.ascontiguousarray(lattices, dtype=np.int64)
+        _check(_lib_ens_retire(self._h, idx.size, _host_ptr(idx) if idx.size else None))
 
     def car_counts(self) -> np.ndarray:
         out = np.zeros(self.count, dtype=np.int64)

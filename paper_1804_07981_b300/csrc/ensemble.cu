@@ -160,9 +160,9 @@ __device__ void process_tile(const EnsParams &p, int t, long long step0, int par
   }
   const int W = on ? L.W : 1;           // words per row of this lane's lattice
   const int wi = on ? lane - gr.lane0 : 0;  // this lane's word of the row
-  if (on && p.early_exit) {
+  if (on) {  // frozen: jammed (early exit) or retired
     long long fz = __ldcg(p.frozen + gr.lat);
-    if (fz < 0 && step0 > 0) {
+    if (p.early_exit && fz < 0 && step0 > 0) {
       const u64 *a = p.tr_lr + (long long)gr.lat * p.cap, *b = p.tr_tb + (long long)gr.lat * p.cap;
       for (long long s = step0 - prev_depth; s < step0; ++s) {
         if (s >= 0 && __ldcg(a + s) + __ldcg(b + s) == 0ull) {
@@ -423,11 +423,13 @@ __global__ void ens_unpack_kernel(const EnsLattice *lat, int count, const long l
 
 // first step (0-based entry) with no move, per lattice, over [0, steps)
 __global__ void ens_first_zero_kernel(const u64 *tr_lr, const u64 *tr_tb, long long cap,
-                                      int count, long long steps, long long *out) {
+                                      int count, long long steps, const long long *retired,
+                                      long long *out) {
   for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < count; l += gridDim.x * blockDim.x) {
     long long r = -1;
     const u64 *a = tr_lr + (long long)l * cap, *b = tr_tb + (long long)l * cap;
-    for (long long s = 0; s < steps; ++s)
+    const long long end = retired[l] >= 0 && retired[l] < steps ? retired[l] : steps;
+    for (long long s = 0; s < end; ++s)
       if (a[s] + b[s] == 0ull) {
         r = s;
         break;
@@ -493,18 +495,21 @@ __global__ void ens_features_kernel(const EnsLattice *lat, const long long *cars
 // step in 0 .. steps-1 moved no car.
 __global__ void ens_labels_kernel(const long long *cars, const u64 *tr_lr, const u64 *tr_tb,
                                   long long cap, int count, long long steps, long long window,
-                                  float *v, float *jam) {
+                                  const long long *retired, float *v, float *jam) {
   for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < count; l += gridDim.x * blockDim.x) {
     const u64 *a = tr_lr + (long long)l * cap, *b = tr_tb + (long long)l * cap;
+    // a retired lattice's trajectory ends at its retirement
+    const long long end = retired[l] >= 0 && retired[l] < steps ? retired[l] : steps;
+    const long long win = window < end ? window : end;
     double sum = 0.0;
     int j = 0;
-    for (long long t = 0; t < steps; ++t) {
+    for (long long t = 0; t < end; ++t) {
       const u64 m = a[t] + b[t];
       if (m == 0) j = 1;
-      if (t >= steps - window) sum += (double)m;
+      if (t >= end - win) sum += (double)m;
     }
     const double c = (double)cars[l];
-    v[l] = c > 0 ? (float)(sum / (c * (double)window)) : 0.f;
+    v[l] = c > 0 && win > 0 ? (float)(sum / (c * (double)win)) : 0.f;
     jam[l] = (float)j;
   }
 }
@@ -512,6 +517,22 @@ __global__ void ens_labels_kernel(const long long *cars, const u64 *tr_lr, const
 __global__ void ens_fill_kernel(long long *a, int count, long long v) {
   for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < count; l += gridDim.x * blockDim.x)
     a[l] = v;
+}
+
+// Stream-ordered after the steps taken so far: freeze the listed lattices
+// where they are (a jammed lattice is frozen already) and record the step.
+__global__ void ens_retire_kernel(const long long *idx, int n, const EnsCtrl *ctrl,
+                                  long long *frozen, int *frozen_buf, long long *retired) {
+  const long long now = ctrl->steps;
+  const int par = ctrl->parity;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const long long l = idx[i];
+    if (retired[l] < 0) retired[l] = now;
+    if (frozen[l] < 0) {
+      frozen[l] = now;
+      frozen_buf[l] = par;
+    }
+  }
 }
 
 template <int K>
@@ -585,6 +606,7 @@ struct bml_ens {
   u64 *tr = nullptr;  // lr then tb, count * cap each
   long long cap = 0;
   long long *frozen = nullptr;
+  long long *retired = nullptr;  // step at which a lattice was retired, else -1
   long long *cars = nullptr;
   int *frozen_buf = nullptr;
   int *buf_of = nullptr;
@@ -619,6 +641,7 @@ void ens_free(bml_ens *e) {
   cudaFree(e->pool);
   cudaFree(e->tr);
   cudaFree(e->frozen);
+  cudaFree(e->retired);
   cudaFree(e->cars);
   cudaFree(e->frozen_buf);
   cudaFree(e->buf_of);
@@ -1031,6 +1054,7 @@ extern "C" int bml_ensemble_create_ex(int64_t count, const int64_t *M, const int
   ETRY(cudaMalloc(&e->d_lat, count * sizeof(EnsLattice)));
   ETRY(cudaMalloc(&e->pool, words * sizeof(u64)));
   ETRY(cudaMalloc(&e->frozen, count * sizeof(long long)));
+  ETRY(cudaMalloc(&e->retired, count * sizeof(long long)));
   ETRY(cudaMalloc(&e->cars, count * sizeof(long long)));
   ETRY(cudaMalloc(&e->frozen_buf, count * sizeof(int)));
   ETRY(cudaMalloc(&e->buf_of, count * sizeof(int)));
@@ -1053,6 +1077,7 @@ extern "C" int bml_ensemble_create_ex(int64_t count, const int64_t *M, const int
   ETRY(cudaMemsetAsync(e->scratch, 0, 16 * sizeof(u64), e->st));
   ETRY(cudaMemsetAsync(e->frozen_buf, 0, count * sizeof(int), e->st));
   ens_fill_kernel<<<256, 256, 0, e->st>>>(e->frozen, (int)count, -1);
+  ens_fill_kernel<<<256, 256, 0, e->st>>>(e->retired, (int)count, -1);
   ETRY(cudaGetLastError());
   ens_init_kernel<<<(unsigned)std::min<int64_t>(count, 148 * 16), 256, 0, e->st>>>(
       e->d_lat, (int)count, d_seed, d_tl, d_tt, e->pool);
@@ -1144,6 +1169,30 @@ extern "C" int bml_ensemble_synchronize(bml_ens *e) {
 
 extern "C" int64_t bml_ensemble_steps_done(const bml_ens *e) { return e ? e->steps_done : -1; }
 
+extern "C" int bml_ensemble_retire(bml_ens *e, int64_t n, const int64_t *lattices) {
+  if (!e || (n > 0 && !lattices)) return efail(BML_EINVAL, "NULL argument");
+  if (n < 0 || n > INT32_MAX) return efail(BML_EINVAL, "n outside [0, 2^31)");
+  if (e->failed) return efail(BML_ESTATE, "ensemble failed earlier (barrier timeout)");
+  for (int64_t i = 0; i < n; ++i)
+    if (lattices[i] < 0 || lattices[i] >= e->count)
+      return efail(BML_EINVAL, "lattice index %lld out of range", (long long)lattices[i]);
+  if (n == 0) return BML_OK;
+  long long *d = nullptr;
+  ECUDA(cudaMalloc(&d, (size_t)n * sizeof(long long)));
+  cudaError_t r = cudaMemcpyAsync(d, lattices, (size_t)n * sizeof(long long),
+                                  cudaMemcpyHostToDevice, e->st);
+  if (r == cudaSuccess) {
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 1024);
+    ens_retire_kernel<<<blocks, 256, 0, e->st>>>(d, (int)n, e->ctrl, e->frozen, e->frozen_buf,
+                                                 e->retired);
+    r = cudaGetLastError();
+  }
+  if (r == cudaSuccess) r = cudaStreamSynchronize(e->st);
+  cudaFree(d);
+  if (r != cudaSuccess) return efail(BML_ECUDA, "retire: %s", cudaGetErrorString(r));
+  return check_err(e);
+}
+
 extern "C" int bml_ensemble_get_config(const bml_ens *e, int *block_k, int64_t *band_rows,
                                        int *graphs) {
   if (!e) return efail(BML_EINVAL, "ensemble is NULL");
@@ -1203,7 +1252,7 @@ extern "C" int bml_ensemble_jam_steps(bml_ens *e, int64_t *out) {
   long long *d = nullptr;
   ECUDA(cudaMalloc(&d, (size_t)e->count * 8));
   ens_first_zero_kernel<<<(e->count + 255) / 256, 256, 0, e->st>>>(
-      e->tr, e->tr + (size_t)e->count * e->cap, e->cap, e->count, e->steps_done, d);
+      e->tr, e->tr + (size_t)e->count * e->cap, e->cap, e->count, e->steps_done, e->retired, d);
   cudaError_t r = cudaGetLastError();
   if (r == cudaSuccess)
     r = cudaMemcpyAsync(out, d, (size_t)e->count * 8, cudaMemcpyDeviceToHost, e->st);
@@ -1274,6 +1323,7 @@ extern "C" int bml_ensemble_write_lattices(bml_ens *e, const uint8_t *in) {
       r = cudaMemsetAsync(e->tr, 0, (size_t)e->count * e->cap * 2 * sizeof(u64), e->st);
     if (r == cudaSuccess) {
       ens_fill_kernel<<<256, 256, 0, e->st>>>(e->frozen, e->count, -1);
+      ens_fill_kernel<<<256, 256, 0, e->st>>>(e->retired, e->count, -1);
       r = cudaGetLastError();
     }
     if (r == cudaSuccess) {
@@ -1321,7 +1371,7 @@ extern "C" int bml_ensemble_labels(bml_ens *e, int64_t window, float *d_v, float
   if (rc) return rc;
   ens_labels_kernel<<<(e->count + 255) / 256, 256, 0, e->st>>>(
       e->cars, e->tr, e->tr + (size_t)e->count * e->cap, e->cap, e->count, e->steps_done, window,
-      d_v, d_jam);
+      e->retired, d_v, d_jam);
   ECUDA(cudaGetLastError());
   ECUDA(cudaStreamSynchronize(e->st));
   return BML_OK;

@@ -123,16 +123,11 @@ def surrogate_arm(runs, net, T_long, B0, window, tau, v_free=0.99, stream=None, 
     v, jam = np.where(jammed, 0.0, v0), jam0.copy()
     idx = np.flatnonzero(extend)
     if idx.size:
-        states = ens.read_all()
-        ext = bml.Ensemble(M[idx], N[idx], seeds[idx], plr[idx], ptb[idx],
-                           flags=bml.BML_ENS_EARLY_EXIT, stream=stream,
-                           block_k=ens.config[0], band_rows=ens.config[1],
-                           reserve_steps=T_long - B0)
-        ext.write_all([states[i] for i in idx])
-        ext.step(T_long - B0)
-        ve, je = (t.cpu().numpy().astype(np.float64) for t in ext.labels(window))
-        v[idx], jam[idx] = ve, je
-        ext.close()
+        # the other runs stop here; the extended ones go on in the same ensemble
+        ens.retire(np.flatnonzero(~extend))
+        ens.step(T_long - B0)
+        ve, je = (t.cpu().numpy().astype(np.float64) for t in ens.labels(window))
+        v[idx], jam[idx] = ve[idx], je[idx]
     _sync(torch)
     secs = time.perf_counter() - t0
     ens.close()

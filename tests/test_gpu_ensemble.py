@@ -224,3 +224,44 @@ def test_features_and_labels_match_oracle(lib):
     np.testing.assert_allclose(f, wf, rtol=1e-6, atol=1e-7)
     np.testing.assert_allclose(v, wv, rtol=1e-6, atol=1e-7)
     np.testing.assert_array_equal(jam, wj)
+
+
+@pytest.mark.parametrize("early_exit", [False, True])
+def test_ensemble_retire_stops_lattices_and_others_continue(lib, early_exit):
+    """Retired lattices keep the state they had at the retirement step and
+    count 0 afterwards; jam steps and labels of a retired lattice are those
+    of its trajectory before the retirement; the others match the oracle
+    over the whole run."""
+    M, N, seeds, plr, ptb = mixed_shapes(24, 17)
+    K1, K2 = 37, 29
+    w1, l1, t1 = oracle_ensemble(M, N, seeds, plr, ptb, K1)
+    w2, l2, t2 = oracle_ensemble(M, N, seeds, plr, ptb, K1 + K2)
+    gone = np.array([0, 3, 4, 11, 23, 3])  # with a repeat
+    flags = lib.BML_ENS_EARLY_EXIT if early_exit else 0
+    with lib.Ensemble(M, N, seeds, plr, ptb, block_k=4, band_rows=16, flags=flags,
+                      reserve_steps=K1 + K2) as ens:
+        ens.step(K1)
+        ens.retire(gone)
+        ens.retire([])
+        ens.step(K2)
+        got = ens.read_all()
+        lr, tb = ens.traces()
+        jam = ens.jam_steps()
+        v, jf = (t.cpu().numpy() for t in ens.labels(8))
+        with pytest.raises(lib.BMLError):
+            ens.retire([len(M)])
+    for l in range(len(M)):
+        if l in gone:
+            np.testing.assert_array_equal(got[l], w1[l])
+            np.testing.assert_array_equal(lr[l], np.concatenate([l1[l], np.zeros(K2, np.int64)]))
+            np.testing.assert_array_equal(tb[l], np.concatenate([t1[l], np.zeros(K2, np.int64)]))
+            tot = l1[l] + t1[l]
+            zero = np.flatnonzero(tot == 0)
+            assert jam[l] == (zero[0] if zero.size else -1)
+            cars = np.count_nonzero(w1[l])
+            want_v = tot[-8:].sum() / (8 * cars) if cars else 0.0
+            assert abs(v[l] - want_v) < 1e-6 and jf[l] == float(zero.size > 0)
+        else:
+            np.testing.assert_array_equal(got[l], w2[l])
+            np.testing.assert_array_equal(lr[l], l2[l])
+            np.testing.assert_array_equal(tb[l], t2[l])
