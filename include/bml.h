@@ -348,7 +348,8 @@ int bml_ensemble_create(int64_t count, const int64_t *M, const int64_t *N, const
 
 /* Full form: block_k in {1, 2, 4, 8} and band_rows >= 1 fix the temporal
  * depth and the target band height; both 0 autotune them on this ensemble
- * (the lattices are not advanced).  reserve_steps preallocates the traces
+ * (the lattices are not advanced; the choice is kept per device and multiset
+ * of lattice shapes, and a later ensemble of the same shapes reuses it).  reserve_steps preallocates the traces
  * (0 picks 1024; they grow on demand). */
 int bml_ensemble_create_ex(int64_t count, const int64_t *M, const int64_t *N,
                            const uint64_t *seed, const double *p_lr, const double *p_tb,

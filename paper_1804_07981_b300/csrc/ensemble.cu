@@ -34,6 +34,7 @@
 #include <cstdio>
 #include <functional>
 #include <map>
+#include <mutex>
 #include <set>
 #include <string>
 #include <vector>
@@ -981,6 +982,60 @@ int autotune_ens(bml_ens *e) {
   return build_tiles(e, best_b);
 }
 
+// Autotuned (depth, band) per device and multiset of lattice shapes: an
+// ensemble of the same shapes (another seed set or density mix, say) reuses
+// the choice instead of timing the candidates again.
+struct EnsTuneKey {
+  int dev;
+  int count;
+  unsigned long long shapes;  // FNV-1a hash of the sorted (M, N) pairs
+  bool operator<(const EnsTuneKey &o) const {
+    if (dev != o.dev) return dev < o.dev;
+    if (count != o.count) return count < o.count;
+    return shapes < o.shapes;
+  }
+};
+std::mutex g_ens_tune_mu;
+std::map<EnsTuneKey, std::pair<int, int64_t>> g_ens_tune;
+
+EnsTuneKey tune_key(const bml_ens *e) {
+  std::vector<std::pair<int, int>> sh;
+  sh.reserve(e->lat.size());
+  for (const EnsLattice &l : e->lat) sh.emplace_back(l.M, l.N);
+  std::sort(sh.begin(), sh.end());
+  unsigned long long h = 1469598103934665603ull;
+  auto mix = [&h](unsigned long long v) {
+    for (int b = 0; b < 8; ++b) {
+      h ^= (v >> (8 * b)) & 0xffull;
+      h *= 1099511628211ull;
+    }
+  };
+  for (const auto &x : sh) {
+    mix((unsigned long long)x.first);
+    mix((unsigned long long)x.second);
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return EnsTuneKey{dev, e->count, h};
+}
+
+int tune_or_reuse(bml_ens *e) {
+  const EnsTuneKey key = tune_key(e);
+  {
+    std::lock_guard<std::mutex> lock(g_ens_tune_mu);
+    auto it = g_ens_tune.find(key);
+    if (it != g_ens_tune.end()) {
+      e->block_k = it->second.first;
+      return build_tiles(e, it->second.second);
+    }
+  }
+  int rc = autotune_ens(e);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lock(g_ens_tune_mu);
+  g_ens_tune[key] = std::make_pair(e->block_k, e->band_rows);
+  return BML_OK;
+}
+
 }  // namespace
 
 extern "C" int bml_ensemble_create_ex(int64_t count, const int64_t *M, const int64_t *N,
@@ -1092,7 +1147,7 @@ extern "C" int bml_ensemble_create_ex(int64_t count, const int64_t *M, const int
   d_seed = d_tl = d_tt = nullptr;
   if ((rc = grow_traces(e, reserve_steps > 0 ? reserve_steps : 1024))) goto fail_;
   if (block_k == 0) {
-    if ((rc = autotune_ens(e))) goto fail_;
+    if ((rc = tune_or_reuse(e))) goto fail_;
   } else {
     e->block_k = block_k;
     if ((rc = build_tiles(e, band_rows))) goto fail_;
