@@ -19,8 +19,8 @@ rho/2), seeds 1..S per density, T steps:
   interpolation between the grid densities).
 
 Lattices up to `ensemble_max_n` columns run as one batched ensemble per size
-(jam early exit); larger ones run one by one on the single-lattice kernels,
-stopping at the first step with no move.  Every step, count and trace comes
+(jam early exit); larger ones run on the single-lattice kernels, several at
+a time on their own streams, each stopping at its first step with no move.  Every step, count and trace comes
 from the CUDA library; this module orders the calls and averages integers.
 """
 from __future__ import annotations
@@ -79,30 +79,51 @@ def _runs_ensemble(N, densities, seeds, T, window, stream):
     return rho, v, jam
 
 
-def _runs_single(N, densities, seeds, T, window, stream, chunk=1024):
-    rho, v, jam = [], [], []
-    for r in densities:
-        for s in range(1, seeds + 1):
-            with bml.Lattice(N, N, seed=s, density=r, stream=stream, reserve_steps=T) as sim:
-                cars = int(np.count_nonzero(sim.read()))
-                done, jammed = 0, False
-                while done < T and not jammed:
-                    n = min(chunk, T - done)
-                    sim.step(n)
-                    tot, _, _ = sim.moved_counts(done, n)
-                    done += n
-                    jammed = bool(np.any(tot == 0))
-                # steps not run (after a jam) move nothing
-                start = T - window
-                moved = 0
-                if done > start:
-                    tot, _, _ = sim.moved_counts(start, done - start)
-                    moved = int(tot.sum())
-                vel = moved / (window * cars) if cars else 0.0
-            rho.append(r)
-            v.append(vel)
-            jam.append(jammed)
-    return np.array(rho), np.array(v), np.array(jam)
+def _runs_single(N, densities, seeds, T, window, stream, chunk=1024, lanes=6):
+    """Lattices too wide for the ensemble, each through the autotuned
+    single-lattice kernel, `lanes` of them at a time on their own streams (one
+    lattice of this size occupies only part of the GPU): every `chunk` steps
+    the counts are read and a run stops at its first step with no move."""
+    import torch
+    jobs = [(r, s) for r in densities for s in range(1, seeds + 1)]
+    out = [None] * len(jobs)
+    streams = [torch.cuda.Stream() for _ in range(lanes)]
+    active = []  # [job, sim, cars, done, jammed, stream slot]
+    nxt = 0
+    free = list(range(lanes))
+    while nxt < len(jobs) or active:
+        while free and nxt < len(jobs):
+            r, s = jobs[nxt]
+            slot = free.pop()
+            sim = bml.Lattice(N, N, seed=s, density=r, stream=streams[slot], reserve_steps=T)
+            active.append([nxt, sim, int(np.count_nonzero(sim.read())), 0, False, slot])
+            nxt += 1
+        for a in active:  # enqueue one chunk of every run, then read them
+            a[1].step(min(chunk, T - a[3]))
+        still = []
+        for a in active:
+            job, sim, cars, done, _, slot = a
+            n = min(chunk, T - done)
+            tot, _, _ = sim.moved_counts(done, n)
+            done += n
+            jammed = bool(np.any(tot == 0))
+            if done < T and not jammed:
+                a[3] = done
+                still.append(a)
+                continue
+            # steps not run (after a jam) move nothing
+            start = T - window
+            moved = 0
+            if done > start:
+                tot, _, _ = sim.moved_counts(start, done - start)
+                moved = int(tot.sum())
+            out[job] = (jobs[job][0], moved / (window * cars) if cars else 0.0, jammed)
+            sim.close()
+            free.append(slot)
+        active = still
+    torch.cuda.synchronize()
+    return (np.array([o[0] for o in out]), np.array([o[1] for o in out]),
+            np.array([o[2] for o in out]))
 
 
 def phase_diagram(sizes, densities, seeds, T, window, ensemble_max_n=2048, stream=None,
