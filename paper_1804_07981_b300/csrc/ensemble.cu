@@ -7,12 +7,15 @@
 // moved-count traces are [lattice][step] int64 arrays (LR and TB).
 //
 // Tiles.  Every lattice row fits one warp (N <= 2048, W <= 32 words).  A
-// lattice is cut into row bands; a warp tile packs G = 32 / W bands of
-// lattices with the same W side by side (lane group g = lanes
-// [gW, gW + W) is one whole periodic row of its band), so narrow lattices do
-// not leave lanes idle.  Each group streams its band through the same k-stage
-// register pipeline as the single-lattice streaming kernel (the stage math is
-// shared), with k-row halos read modulo M.
+// lattice is cut into row bands; a warp tile packs bands of any word widths
+// side by side (first fit over the bands sorted by length; a band of W words
+// takes W consecutive lanes, one whole periodic row), so narrow lattices do
+// not leave lanes idle.  Each band streams through the same k-stage register
+// pipeline as the single-lattice streaming kernel (the stage math is
+// shared), with k-row halos read modulo M.  Tiles are ordered longest first
+// and warps draw them from a dispenser (one atomic per tile), so the work is
+// spread by longest-processing-time-first list scheduling; the band height
+// is chosen on the host by a model of that schedule and confirmed by timing.
 //
 // Chunks.  One launch runs n chunks of k steps; between chunks every block
 // meets at a grid barrier whose waits are bounded by %globaltimer (on expiry
@@ -27,7 +30,8 @@
 // start of each chunk a group checks the previous chunk's counts of its
 // lattice; after a zero-move step the lattice is frozen: its buffer index is
 // recorded and its tiles are skipped.  Later counts stay zero, which is what
-// the automaton would produce.
+// the automaton would produce.  A retired lattice (bml_ensemble_retire) is
+// frozen the same way at the step of its retirement.
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
