@@ -14,14 +14,16 @@ rank runs an independent replica (weak scaling); there is no data-path
 collective.
 
 Sub-measurements on the same JSON line: "ensemble" (4096 lattices, the
-batched API), "model2" (the Sec. 2 Model II variant on the bench lattice,
+batched API; with "cpu_oracle", the oracle on all host cores on a subset of
+the lattices, extrapolated), "model2" (the Sec. 2 Model II variant on the bench lattice,
 tie-break seed = placement seed, 1024 steps; --no-model2 skips it),
 "byte_kernel" (the plain byte-per-cell form on the bench lattice, 16 steps,
 against the HBM peak), "two_phase" (the two-phase bitplane form, a horizontal and
 a vertical kernel per step, 64 steps, against the HBM peak), "one_pass" (one full step
 per DRAM pass on the bench lattice, 256 steps, against the HBM peak), "configs" (256^2
 for 1024 steps; 4096^2 byte vs
-bit-packed over 3 densities x 3 seeds x 4096 steps; rank 0 of a 1-GPU run), "mlp" (the
+bit-packed over 3 densities x 3 seeds x 4096 steps, with the oracle's one-core time per run
+estimated from a bounded sample; rank 0 of a 1-GPU run), "mlp" (the
 surrogate network: AdamW step time at batch 1024, forward on 2624 samples, and its tcgen05
 GEMM kernel on a 2^22 x 128 x 128 product against the HBM peak; 1-GPU runs).
 
@@ -183,6 +185,53 @@ def _cpu_sample(budget_s: float, threads: int):
     desc = ("oracle (C, OpenMP rows, %d threads) on a %d x %d periodic band of the workload "
             "(density %.2f), %d steps in %.1f s" % (threads, rows, N_COLS, DENSITY, done, dt))
     return rate, desc, dt
+
+
+def _oracle_ensemble_sample(budget_s: float, threads: int):
+    """The oracle, as it stands, on a subset of the ensemble workload (every
+    64th lattice; 8-step runs per lattice, row-parallel on `threads` cores,
+    repeated until about `budget_s` seconds), extrapolated to the whole
+    ensemble: lattice-steps/s at the workload's mean lattice size."""
+    import oracle
+    from paper_1804_07981_b300.inputs import ensemble_params
+    p = ensemble_params(4096, seed=1)
+    idx = np.arange(0, 4096, 64)
+    gs = [oracle.init(int(p["M"][l]), int(p["N"][l]), int(p["seed"][l]), float(p["p_lr"][l]),
+                      float(p["p_tb"][l])) for l in idx]
+    cells = 0
+    t0 = time.perf_counter()
+    while True:
+        for j, g in enumerate(gs):
+            gs[j], _, _ = oracle.run(g, 8, threads=threads)
+            cells += g.size * 8
+        dt = time.perf_counter() - t0
+        if dt >= budget_s:
+            break
+    rate = cells / dt
+    mean_cells = float((p["M"] * p["N"]).sum()) / 4096
+    return {"value": rate / mean_cells, "unit": "lattice-steps/s", "cores": threads,
+            "kind": "oracle", "cell_updates_per_s": rate,
+            "sample": "64 lattices of the workload (every 64th), 8-step runs, %.1f s; "
+                      "extrapolated at the mean lattice size" % dt}
+
+
+def _oracle_1core_4096(budget_s: float):
+    """The oracle on one core, one 4096 x 4096 run (density 0.35, seed 1),
+    timed over whole 8-step runs for about `budget_s` seconds and scaled to the
+    4096 steps of a run."""
+    import oracle
+    g = oracle.init(4096, 4096, 1, 0.175, 0.175)
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        g, _, _ = oracle.run(g, 8, threads=1)
+        steps += 8
+        dt = time.perf_counter() - t0
+        if dt >= budget_s:
+            break
+    return {"cell_updates_per_s": 4096 * 4096 * steps / dt,
+            "seconds_per_run_estimate": dt / steps * 4096, "cores": 1,
+            "sample": "%d steps of one 4096^2 run in %.1f s" % (steps, dt)}
 
 
 def _ensemble_bench(bml, torch, stream, steps, seed_base=1, tiling=None, sm_mhz=SM_MAX_MHZ):
@@ -659,6 +708,11 @@ def run_ours(args):
         rate, desc, _ = _cpu_sample(args.cpu_seconds, threads)
         cpu = {"value": rate, "unit": "cell-updates/s", "cores": threads, "kind": "oracle",
                "sample": desc}
+        if ens is not None:
+            ens["cpu_oracle"] = _oracle_ensemble_sample(4.0, threads)
+        if small is not None:
+            small["4096x4096_rho0.20-0.50_seeds1-3_4096steps"]["oracle_1core"] = \
+                _oracle_1core_4096(4.0)
 
     if rank == 0:
         line = {
