@@ -225,3 +225,23 @@ def test_ensemble_workload_256_lattices_full_10000_steps_against_byte_kernel(lib
     want_jam = np.array([np.flatnonzero(t == 0)[0] if np.any(t == 0) else -1 for t in tot])
     np.testing.assert_array_equal(jam, want_jam)
     assert (want_jam >= 0).any() and (want_jam < 0).any()
+
+
+def test_ensemble_extreme_shapes_against_byte_kernel(lib):
+    """An ensemble holding a 4M-row single-column lattice, a one-row lattice
+    of 2048 cells, a 2048-wide lattice of 40000 rows and small ones,
+    autotuned: every lattice and count equals the byte kernels' runs."""
+    M = np.array([(1 << 22) + 7, 1, 40000, 3, 64, 129])
+    N = np.array([1, 2048, 2048, 5, 64, 1000])
+    seeds = np.arange(1, 7, dtype=np.uint64)
+    plr, ptb = np.full(6, 0.2), np.full(6, 0.15)
+    K = 20
+    with lib.Ensemble(M, N, seeds, plr, ptb, reserve_steps=K) as ens:
+        ens.step(K)
+        got = ens.read_all()
+        lr, tb = ens.traces()
+    want, wlr, wtb = _byte_runs(lib, M, N, seeds, plr, ptb, K)
+    for l in range(len(M)):
+        assert np.array_equal(got[l], want[l]), l
+    np.testing.assert_array_equal(lr, wlr)
+    np.testing.assert_array_equal(tb, wtb)

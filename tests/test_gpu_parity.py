@@ -351,3 +351,23 @@ def test_allocation_failure_mid_creation_frees_everything(lib, fail_at):
         lib.use_torch_allocator(False)
     with make(lib, 64, 300, "tblock", 2) as sim:
         sim.step(3)
+
+
+@pytest.mark.parametrize("M,N", [(1, (1 << 22) + 37), ((1 << 22) + 5, 1), (2, (1 << 21) + 64),
+                                 ((1 << 20) + 3, 3), (3, 128 * 1024)])
+def test_extreme_aspect_ratios_every_kernel(lib, M, N):
+    """A single row of 4M cells (ragged tail), a single column of 4M rows,
+    and near-degenerate widths: every kernel and depth against the oracle
+    (lattice and every count), 9 steps in calls of 4 and 5."""
+    g0 = random_lattice(M, N, M + 3 * N, 0.2, 0.2)
+    K = 9
+    want, mlr, mtb = oracle.run(g0, K)
+    for kernel, block_k in KERNEL_CASES:
+        if kernel == "resident":
+            continue  # larger than one block's shared memory
+        with make(lib, M, N, kernel, block_k) as sim:
+            sim.write(g0)
+            sim.step(4)
+            sim.step(5)
+            np.testing.assert_array_equal(sim.read(), want, err_msg=str((kernel, block_k)))
+            oracle_counts_equal(sim.moved_counts(), mlr, mtb)
