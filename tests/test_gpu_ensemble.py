@@ -265,3 +265,25 @@ def test_ensemble_retire_stops_lattices_and_others_continue(lib, early_exit):
             np.testing.assert_array_equal(got[l], w2[l])
             np.testing.assert_array_equal(lr[l], l2[l])
             np.testing.assert_array_equal(tb[l], t2[l])
+
+
+@pytest.mark.parametrize("block_k,band", [(1, 16), (4, 64), (8, 21), (0, 0)])
+def test_ensemble_full_word_tiles_match_oracle(lib, block_k, band):
+    """Lattices whose rows are whole 64-cell words only (every tile takes the
+    stage form without ragged terms), mixed widths and heights."""
+    rng = np.random.Generator(np.random.PCG64(21))
+    count = 30
+    N = 64 * rng.integers(1, 33, size=count)
+    M = rng.integers(1, 150, size=count)
+    rho = rng.uniform(0.1, 0.7, size=count)
+    seeds = np.arange(50, 50 + count, dtype=np.uint64)
+    K = 33
+    want, wlr, wtb = oracle_ensemble(M, N, seeds, rho / 2, rho / 2, K)
+    with lib.Ensemble(M, N, seeds, rho / 2, rho / 2, block_k=block_k, band_rows=band) as ens:
+        ens.step(K)
+        got = ens.read_all()
+        lr, tb = ens.traces()
+    for l in range(count):
+        np.testing.assert_array_equal(got[l], want[l], err_msg="lattice %d" % l)
+    np.testing.assert_array_equal(lr, wlr)
+    np.testing.assert_array_equal(tb, wtb)
