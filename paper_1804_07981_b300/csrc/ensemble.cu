@@ -258,7 +258,7 @@ __device__ void process_tile(const EnsParams &p, int t, long long step0, int par
         }
         if (on && i >= 2 * K && i - 2 * K < len) {
           const size_t off = (size_t)(i - 2 * K) * pitch;
-          __stcg(Lo + off, inL & lw.valid);  // clears a car shifted past the row's end
+          __stcg(Lo + off, inL);
           __stcg(Lo + off + plane, inT);
         }
       }

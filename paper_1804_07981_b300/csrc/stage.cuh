@@ -55,35 +55,38 @@ __device__ __forceinline__ u64 mk64(uint32_t lo, uint32_t hi) {
 // another (callers alternate two sets from row to row, so no value is
 // copied).  FULL: every word of the row holds 64 cells.
 //
+// The horizontal rule in the "who enters" form: Ll = L shifted one column
+// right (the left neighbour's last cell enters bit 0), in = Ll & E (the cells
+// an LR car enters), Lh = (L & ~Er) | in (cars that stay, plus cars that
+// enter).  Every moving car enters exactly one cell, so the row's LR move
+// count is the popcount of `in` (returned as mvIn).  The left shuffle needs
+// only L, so both shuffles issue at the start of the stage.
+//
 // Words with fewer cells (the last word of a row whose N is not a multiple of
-// 64): E is masked to the valid cells and the right neighbour's first cell
-// (bit 0 of its E) enters at this word's last cell as a multiply-add on the
-// FMA pipe (the shifted E is zero at that bit), so Er is zero past the row's
-// end and no car moves there.  The last cell sent to the left neighbour is
-// placed at bit 31 by two multiply-adds.  `in` also shifts the row's last
-// cell one bit past the end (the left shuffle carries it to the row's first
-// cell); that bit is never read by a valid cell, never counted and never
-// moves again, so the caller clears it once, when it stores the emitted row
-// (mask `valid`), instead of at every stage.
+// 64): E is masked to the valid cells, so `in` never sets a cell past the
+// row's end; the right neighbour's E enters at this word's last cell as a
+// multiply-add on the FMA pipe (the shifted E is zero from that bit on, so
+// the add carries nothing; the neighbour's higher bits land past the end,
+// where L is zero and Er is not read); the last cell sent to the left
+// neighbour is placed at bit 31 by two multiply-adds.
 template <bool FULL>
 __device__ __forceinline__ void stage_step_pp(u64 &inL, u64 &inT, const u64 curT, const u64 curLh,
                                               const u64 prevMv, u64 &nT, u64 &nLh, u64 &nMv,
-                                              const LaneWord &lw, u64 &mvH, u64 &mvV) {
+                                              const LaneWord &lw, u64 &mvIn, u64 &mvV) {
   const u64 E = FULL ? ~(inL | inT) : (~(inL | inT) & lw.valid);
+  const uint32_t send_l = FULL ? hi32(inL) : hi32(inL) * lw.mul_hi + lo32(inL) * lw.mul_lo;
+  const uint32_t rl = __shfl_sync(BML_FULL_MASK, send_l, lw.src_l);
   const uint32_t rr = __shfl_sync(BML_FULL_MASK, lo32(E), lw.src_r);
   u64 Er;
   if (FULL) {
     Er = mk64(__funnelshift_r(lo32(E), hi32(E), 1), __funnelshift_r(hi32(E), rr, 1));
   } else {
-    const uint32_t r0 = rr & 1u;
-    Er = mk64(__funnelshift_r(lo32(E), hi32(E), 1) + r0 * lw.ins_lo,
-              (hi32(E) >> 1) + r0 * lw.ins_hi);
+    Er = mk64(__funnelshift_r(lo32(E), hi32(E), 1) + rr * lw.ins_lo,
+              (hi32(E) >> 1) + rr * lw.ins_hi);
   }
-  mvH = inL & Er;
-  const uint32_t send_l = FULL ? hi32(mvH) : hi32(mvH) * lw.mul_hi + lo32(mvH) * lw.mul_lo;
-  const uint32_t rl = __shfl_sync(BML_FULL_MASK, send_l, lw.src_l);
-  const u64 in = mk64(__funnelshift_l(rl, lo32(mvH), 1), __funnelshift_l(lo32(mvH), hi32(mvH), 1));
-  nLh = inL ^ mvH ^ in;
+  const u64 Ll = mk64(__funnelshift_l(rl, lo32(inL), 1), __funnelshift_l(lo32(inL), hi32(inL), 1));
+  mvIn = Ll & E;
+  nLh = (inL & ~Er) | mvIn;
   mvV = curT & ~(nLh | inT);
   nT = inT;
   nMv = mvV;

@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, K >= 8 ? 3 : 4)
           // row i - 2K of the band leaves the last stage
           if ((steady || i >= 2 * K) && own) {
             const size_t off = (size_t)(i - 2 * K) * pitch;
-            __stcs(Lo + off, FULL ? inL : (inL & lw.valid));  // see stage_step_pp
+            __stcs(Lo + off, inL);
             __stcs(To + off, inT);
           }
         }
