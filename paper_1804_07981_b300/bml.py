@@ -466,6 +466,8 @@ _lib_ens_steps = _sig("bml_ensemble_steps_done", [_vp], _i64)
 _lib_ens_cfg = _sig("bml_ensemble_get_config", [_vp, ctypes.POINTER(_int), _i64p,
                                                  ctypes.POINTER(_int)])
 _lib_ens_retire = _sig("bml_ensemble_retire", [_vp, _i64, _vp])
+_lib_ens_plan = _sig("bml_ensemble_plan", [_i64, _vp, _vp, _i64, _int, _int, _i64p,
+                                           ctypes.POINTER(ctypes.c_double), _vp])
 _lib_ens_sync = _sig("bml_ensemble_synchronize", [_vp])
 _lib_ens_cars = _sig("bml_ensemble_car_counts", [_vp, _vp])
 _lib_ens_feat = _sig("bml_ensemble_features", [_vp, _i64, _i64, _int, _vp])
@@ -546,6 +548,19 @@ def bml_ensemble_get_config(ens: int):
     b = _i64()
     _check(_lib_ens_cfg(ens, ctypes.byref(k), ctypes.byref(b), ctypes.byref(g)))
     return k.value, b.value, bool(g.value)
+
+
+def bml_ensemble_plan(M, N, band: int, depth: int, warps: int):
+    """Host-side tile plan of an ensemble (no CUDA call): (tiles, score, rows
+    covered per lattice)."""
+    Ma = np.ascontiguousarray(M, dtype=np.int64)
+    Na = np.ascontiguousarray(N, dtype=np.int64)
+    tiles = _i64()
+    score = ctypes.c_double()
+    rows = np.zeros(Ma.size, dtype=np.int64)
+    _check(_lib_ens_plan(Ma.size, _host_ptr(Ma), _host_ptr(Na), band, depth, warps,
+                         ctypes.byref(tiles), ctypes.byref(score), _host_ptr(rows)))
+    return tiles.value, score.value, rows
 
 
 def bml_ensemble_synchronize(ens: int) -> None:

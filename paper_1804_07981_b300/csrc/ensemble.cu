@@ -1228,6 +1228,48 @@ extern "C" int bml_ensemble_synchronize(bml_ens *e) {
 
 extern "C" int64_t bml_ensemble_steps_done(const bml_ens *e) { return e ? e->steps_done : -1; }
 
+extern "C" int bml_ensemble_plan(int64_t count, const int64_t *M, const int64_t *N,
+                                 int64_t band, int depth, int warps, int64_t *out_tiles,
+                                 double *out_score, int64_t *out_rows) {
+  if (!M || !N || !out_tiles || !out_score) return efail(BML_EINVAL, "NULL argument");
+  if (count < 1 || count > (1 << 30)) return efail(BML_EINVAL, "count must be in [1, 2^30]");
+  if (band < 1 || depth < 1 || depth > 64 || warps < 1)
+    return efail(BML_EINVAL, "need band >= 1, 1 <= depth <= 64, warps >= 1");
+  bml_ens e;  // host fields only: no device memory is touched
+  e.count = (int)count;
+  e.lat.resize((size_t)count);
+  for (int64_t l = 0; l < count; ++l) {
+    if (M[l] < 1 || N[l] < 1 || N[l] > 2048 || M[l] > (1 << 24))
+      return efail(BML_EINVAL, "lattice %lld: need 1 <= N <= 2048 and 1 <= M <= 2^24",
+                   (long long)l);
+    EnsLattice &L = e.lat[(size_t)l];
+    L.M = (int)M[l];
+    L.N = (int)N[l];
+    L.W = (L.N + 63) / 64;
+    L.P = L.W + (L.W & 1);
+    L.nb = L.N - 64 * (L.W - 1);
+  }
+  TilePlan plan;
+  plan_tiles(&e, band, plan);
+  *out_tiles = (int64_t)plan.tiles.size();
+  *out_score = plan_score(plan, depth, warps);
+  if (out_rows) {
+    for (int64_t l = 0; l < count; ++l) out_rows[l] = 0;
+    for (const EnsTile &t : plan.tiles)
+      for (int j = 0; j < t.G; ++j) {
+        const EnsGroup &g = plan.groups[(size_t)(t.first_group + j)];
+        // a group's lanes must lie inside the warp and match the lattice's width
+        int lanes = 0;
+        for (int l = 0; l < 32; ++l) lanes += t.lane_grp[l] == j;
+        if (g.lane0 + e.lat[(size_t)g.lat].W > 32 || lanes != e.lat[(size_t)g.lat].W ||
+            g.len > t.max_len || g.len < t.min_len)
+          return efail(BML_ESTATE, "inconsistent tile plan");
+        out_rows[g.lat] += g.len;
+      }
+  }
+  return BML_OK;
+}
+
 extern "C" int bml_ensemble_retire(bml_ens *e, int64_t n, const int64_t *lattices) {
   if (!e || (n > 0 && !lattices)) return efail(BML_EINVAL, "NULL argument");
   if (n < 0 || n > INT32_MAX) return efail(BML_EINVAL, "n outside [0, 2^31)");
