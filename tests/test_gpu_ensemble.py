@@ -287,3 +287,24 @@ def test_ensemble_full_word_tiles_match_oracle(lib, block_k, band):
         np.testing.assert_array_equal(got[l], want[l], err_msg="lattice %d" % l)
     np.testing.assert_array_equal(lr, wlr)
     np.testing.assert_array_equal(tb, wtb)
+
+
+def test_ensemble_write_makes_retired_lattices_active_again(lib):
+    M, N, seeds, plr, ptb = mixed_shapes(10, 23)
+    K = 17
+    with lib.Ensemble(M, N, seeds, plr, ptb, block_k=2, band_rows=8, reserve_steps=64) as ens:
+        ens.step(5)
+        start = ens.read_all()
+        ens.retire(np.arange(10))
+        ens.step(3)
+        for a, b in zip(ens.read_all(), start):   # nothing moved
+            np.testing.assert_array_equal(a, b)
+        ens.write_all(start)                        # restart: every lattice active
+        ens.step(K)
+        got = ens.read_all()
+        lr, tb = ens.traces()
+    for l in range(10):
+        want, wlr, wtb = oracle.run(start[l], K)
+        np.testing.assert_array_equal(got[l], want)
+        np.testing.assert_array_equal(lr[l], wlr)
+        np.testing.assert_array_equal(tb[l], wtb)
