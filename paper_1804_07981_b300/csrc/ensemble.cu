@@ -250,10 +250,10 @@ __device__ void process_tile(const EnsParams &p, int t, long long step0, int par
         const int a = u & 1, b = a ^ 1;
 #pragma unroll
         for (int s = 0; s < K; ++s) {
-          u64 mvH, mvV;
+          u64 mvIn, mvV;
           stage_step_pp<false>(inL, inT, curT[a][s], curLh[a][s], prevMv[a][s], curT[b][s],
-                               curLh[b][s], prevMv[b][s], lw, mvH, mvV);
-          if (steady || (unsigned)(i - K - s) < (unsigned)len) c_lr[s] += popc64(mvH);
+                               curLh[b][s], prevMv[b][s], lw, mvIn, mvV);
+          if (steady || (unsigned)(i - K - s) < (unsigned)len) c_lr[s] += popc64(mvIn);
           if (steady || (unsigned)(i - K - s - 1) < (unsigned)len) c_tb[s] += popc64(mvV);
         }
         if (on && i >= 2 * K && i - 2 * K < len) {

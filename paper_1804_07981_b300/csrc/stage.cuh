@@ -2,19 +2,22 @@
 // single-lattice streaming kernel and the ensemble kernel.
 //
 // With E = EMPTY before the horizontal phase (Sec. 2 rules):
-//   mvH_x = L_x & Er_x            LR cars that leave (Er[j] = E[j+1])
-//   in_x  = mvH_x shifted one column right (the cells they enter)
-//   Lh_x  = L_x ^ mvH_x ^ in_x     horizontal rule on row x
+//   Er_x  = E_x shifted one column left (Er[j] = E[j+1], the cell ahead)
+//   in_x  = (L_x shifted one column right) & E_x   the cells LR cars enter
+//   Lh_x  = (L_x & ~Er_x) | in_x   horizontal rule on row x (cars that stay,
+//                                  plus cars that enter)
 //   E'_x  = ~(Lh_x | T_x)          EMPTY after the horizontal phase (TB cars
 //                                  do not move in it)
 //   mvV_{x-1} = T_{x-1} & E'_x     TB cars of row x-1 that move down
 //   emitted row x-1: L = Lh_{x-1}, T = (T_{x-1} & ~mvV_{x-1}) | mvV_{x-2}
 // (the cars entering row x-1 from above are mvV_{x-2}, computed one row
 // earlier).  Written this way E' is never formed: mvV and the emitted T are
-// one three-input logic operation each.  Horizontal neighbours come from two 32-bit warp shuffles: the
-// right neighbour's low half of E (bit 0 = the cell right of this word) and
-// the left neighbour's half of mvH holding its last cell, pre-aligned to bit
-// 31.
+// one three-input logic operation each.  Every LR car that moves enters
+// exactly one cell, so the row's LR count is the popcount of in.  Horizontal
+// neighbours come from two 32-bit warp shuffles, both issued at the start of
+// the stage: the right neighbour's low half of E (bit 0 = the cell right of
+// this word) and the left neighbour's half of L holding its last cell,
+// pre-aligned to bit 31.
 #pragma once
 
 #include "device_common.cuh"

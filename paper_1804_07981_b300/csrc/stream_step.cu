@@ -9,9 +9,8 @@
 // rows that stage s-1 emits.  With E = EMPTY before the horizontal phase:
 //
 //   receive row x (L_x, T_x) of state s:
-//     mvH_x = L_x & Er_x            LR cars that leave (Er[j] = E[j+1])
-//     in_x  = mvH_x shifted one column right (the cells they enter)
-//     Lh_x  = L_x ^ mvH_x ^ in_x     horizontal rule on row x
+//     in_x  = (L_x shifted one column right) & E_x   cells LR cars enter
+//     Lh_x  = (L_x & ~Er_x) | in_x   horizontal rule on row x (Er[j] = E[j+1])
 //     E'_x  = ~(Lh_x | T_x)          EMPTY after the horizontal phase
 //     mvV_{x-1} = T_{x-1} & E'_x     TB cars of row x-1 that move down
 //   emit row x-1 of state s+1:
@@ -20,10 +19,10 @@
 // since the cars entering row x-1 from above are exactly mvV_{x-2}, computed
 // one row earlier.  Each stage lags one row behind the previous one and keeps
 // three words per lane (T_{x-1}, Lh_{x-1}, mvV_{x-2}).  The only horizontal
-// communication per stage and row is two 32-bit warp shuffles: the right
-// neighbour's low half of E (its bit 0 is the cell right of this word) and
-// the left neighbour's half of mvH holding its last cell, pre-aligned to bit
-// 31; the receiver funnel-shifts them in.
+// communication per stage and row is two 32-bit warp shuffles, both issued at
+// the start of the stage: the right neighbour's low half of E (its bit 0 is
+// the cell right of this word) and the left neighbour's half of L holding its
+// last cell, pre-aligned to bit 31; the receiver funnel-shifts them in.
 //
 // Halos.  Each step widens the dependency cone by one row up and down and one
 // column left and right.  A band [r0, r1) therefore reads rows
@@ -70,10 +69,10 @@ __device__ __forceinline__ void row_through(u64 &inL, u64 &inT, const Pipe<K> &s
                                             uint32_t (&c_lr)[K], uint32_t (&c_tb)[K]) {
 #pragma unroll
   for (int s = 0; s < K; ++s) {
-    u64 mvH, mvV;
+    u64 mvIn, mvV;
     stage_step_pp<FULL>(inL, inT, src.curT[s], src.curLh[s], src.prevMv[s], dst.curT[s],
-                        dst.curLh[s], dst.prevMv[s], lw, mvH, mvV);
-    if (!PRED || (unsigned)(i - K - s) < (unsigned)B) c_lr[s] += popc64(mvH);
+                        dst.curLh[s], dst.prevMv[s], lw, mvIn, mvV);
+    if (!PRED || (unsigned)(i - K - s) < (unsigned)B) c_lr[s] += popc64(mvIn);
     if (!PRED || (unsigned)(i - K - s - 1) < (unsigned)B) c_tb[s] += popc64(mvV);
   }
 }
