@@ -145,14 +145,29 @@ __device__ bool grid_barrier(EnsCtrl *ctrl, unsigned target, long long timeout_n
   return s_ok != 0;
 }
 
+// Rows per unrolled chunk of the row loop (even: the stage state sets
+// alternate by row).
 template <int K>
 struct PFE {
   static constexpr int value = K >= 4 ? 2 : 4;
 };
 
+// Input rows reach a warp through a ring of kEnsRing row slots in shared
+// memory, filled kEnsAhead rows ahead with cp.async.cg (through L2, so the
+// words other blocks wrote in the previous chunk are seen).  A lane copies the
+// aligned 16-byte pair of words that holds its own word (rows start 16-byte
+// aligned, since P is even) and reads back only its own half; the two lanes
+// of a pair request the same bytes, so the warp's requests cover the same
+// sectors as one word per lane.  A slot is refilled two rows after it was
+// last read.
+constexpr int kEnsRing = 8;
+constexpr int kEnsAhead = 6;
+static_assert(kEnsAhead <= kEnsRing - 2 && (kEnsRing & (kEnsRing - 1)) == 0, "ring layout");
+using EnsRing = ulonglong2[kEnsRing][2][32];  // [slot][plane][lane]
+
 template <int K>
 __device__ void process_tile(const EnsParams &p, int t, long long step0, int par,
-                             long long prev_depth, int lane) {
+                             long long prev_depth, int lane, EnsRing &ring) {
   constexpr int PF = PFE<K>::value;
   const EnsTile &tile = p.tiles[t];
   const int grp = tile.lane_grp[lane];
@@ -196,13 +211,15 @@ __device__ void process_tile(const EnsParams &p, int t, long long step0, int par
   const int M = on ? L.M : 1;
   const size_t pitch = on ? (size_t)L.P : 0;
   const size_t plane = (size_t)M * pitch;
-  const u64 *inbase = p.pool + (on ? L.off[par] : 0) + wi;
+  // the 16-byte word pair that holds this lane's word
+  const u64 *inbase = p.pool + (on ? L.off[par] : 0) + (wi & ~1);
   u64 *outbase = p.pool + (on ? L.off[par ^ 1] : 0) + wi;
   const int len = gr.len, n_in = len + 2 * K;
   int ld_row = on ? (gr.r0 - K) % M : 0;
   if (ld_row < 0) ld_row += M;
   const u64 *Lp = inbase + (size_t)ld_row * pitch;
   u64 *Lo = outbase + (size_t)gr.r0 * pitch;
+  const int half = wi & 1;
 
   // two state sets, alternated row by row (PF is even), so no value is copied
   u64 curT[2][K], curLh[2][K], prevMv[2][K];
@@ -214,13 +231,12 @@ __device__ void process_tile(const EnsParams &p, int t, long long step0, int par
     c_lr[s] = c_tb[s] = 0;
   }
 
-  u64 bufL[PF], bufT[PF];
+  // rows 0 .. kEnsAhead-1 in flight, one commit group per row (empty past n_in)
 #pragma unroll
-  for (int u = 0; u < PF; ++u) {
-    bufL[u] = bufT[u] = 0;
+  for (int u = 0; u < kEnsAhead; ++u) {
     if (on && u < n_in) {
-      bufL[u] = __ldcg(Lp);
-      bufT[u] = __ldcg(Lp + plane);
+      cp_async16(&ring[u][0][lane], Lp);
+      cp_async16(&ring[u][1][lane], Lp + plane);
       if (++ld_row == M) {
         ld_row = 0;
         Lp = inbase;
@@ -228,6 +244,7 @@ __device__ void process_tile(const EnsParams &p, int t, long long step0, int par
         Lp += pitch;
       }
     }
+    cp_async_commit();
   }
   const int n_max = tile.max_len + 2 * K;
   for (int i0 = 0; i0 < n_max; i0 += PF) {
@@ -236,10 +253,10 @@ __device__ void process_tile(const EnsParams &p, int t, long long step0, int par
     for (int u = 0; u < PF; ++u) {
       const int i = i0 + u;
       if (i < n_max) {  // warp-uniform
-        u64 inL = bufL[u], inT = bufT[u];
-        if (on && i + PF < n_in) {
-          bufL[u] = __ldcg(Lp);
-          bufT[u] = __ldcg(Lp + plane);
+        if (on && i + kEnsAhead < n_in) {
+          const int sl = (i + kEnsAhead) & (kEnsRing - 1);
+          cp_async16(&ring[sl][0][lane], Lp);
+          cp_async16(&ring[sl][1][lane], Lp + plane);
           if (++ld_row == M) {
             ld_row = 0;
             Lp = inbase;
@@ -247,6 +264,12 @@ __device__ void process_tile(const EnsParams &p, int t, long long step0, int par
             Lp += pitch;
           }
         }
+        cp_async_commit();
+        cp_async_wait<kEnsAhead>();  // row i has landed (this lane's own copies)
+        // lanes past their band's input rows (or off) read stale slots: those
+        // rows are neither stored nor counted
+        const u64 *q = reinterpret_cast<const u64 *>(&ring[i & (kEnsRing - 1)][0][lane]) + half;
+        u64 inL = q[0], inT = q[64];
         const int a = u & 1, b = a ^ 1;
 #pragma unroll
         for (int s = 0; s < K; ++s) {
@@ -293,6 +316,7 @@ __device__ void process_tile(const EnsParams &p, int t, long long step0, int par
 
 template <int K>
 __global__ void __launch_bounds__(kEnsWarps * 32, K >= 8 ? 3 : 4) ens_kernel(EnsParams p) {
+  __shared__ __align__(16) EnsRing s_ring[kEnsWarps];
   const int lane = threadIdx.x & 31;
   const int nwarps = gridDim.x * kEnsWarps;
   const long long base = __ldcg(&p.ctrl->steps);
@@ -324,7 +348,7 @@ __global__ void __launch_bounds__(kEnsWarps * 32, K >= 8 ? 3 : 4) ens_kernel(Ens
       const unsigned t = s_ticket[threadIdx.x >> 5] - cbase;
       __syncwarp();
       if (t >= (unsigned)p.n_tiles) break;
-      process_tile<K>(p, (int)t, step0, par, prev_depth, lane);
+      process_tile<K>(p, (int)t, step0, par, prev_depth, lane, s_ring[threadIdx.x >> 5]);
     }
     if (c + 1 < p.n_chunks) {
       if (!grid_barrier(p.ctrl, p.bar_target, p.timeout_ns)) return;
