@@ -33,9 +33,15 @@
 // the row).  Rows that fit in one warp (W <= 32) are whole periodic rings:
 // lane W-1's right neighbour is lane 0.
 //
-// The row loop runs in chunks of PF rows (the prefetch depth).  Chunks that
-// lie entirely in the steady part of the band (every stage counts its row and
-// the last stage stores) run without per-row predicates.
+// Input rows reach a warp through a ring of row slots in shared memory, filled
+// a few rows ahead with cp.async: a lane copies the aligned 16-byte
+// pair of words that holds its own word (rows start 16-byte aligned, since P
+// is even) and reads back only its own half, so the warp's requests cover the
+// same sectors as one word per lane.  A slot is refilled two rows after it
+// was last read.  The row loop runs in chunks of PF rows (PF even: the stage
+// state sets alternate by row).  Chunks that lie entirely in the steady part
+// of the band (every stage counts its row and the last stage stores) run
+// without per-row predicates.
 //
 // Counts.  Sub-step s counts LR moves of its row x and TB moves of its
 // emitted row x-1, only for owned rows and words, in per-lane registers; at
@@ -49,10 +55,19 @@ namespace {
 
 constexpr int kWarpsPerBlock = 4;
 
-// rows prefetched per warp: deeper when a row costs little compute
+// rows per unrolled chunk of the row loop
 template <int K>
 struct PF {
   static constexpr int value = K >= 4 ? 2 : 4;
+};
+
+// Row slots per warp and rows in flight ahead of the row being consumed.  At
+// depth 1 a smaller ring keeps more blocks resident (shared memory would
+// otherwise bound the occupancy, not registers).
+template <int K>
+struct RingGeom {
+  static constexpr int slots = K >= 2 ? 8 : 4;
+  static constexpr int ahead = slots - 2;
 };
 
 template <int K>
@@ -84,7 +99,10 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, K >= 8 ? 3 : 4)
                   int band_rows, int n_bands, u64 *__restrict__ moved_lr,
                   u64 *__restrict__ moved_tb) {
   constexpr int P = PF<K>::value;
+  constexpr int kRing = RingGeom<K>::slots, kAhead = RingGeom<K>::ahead;
+  static_assert(kAhead <= kRing - 2 && (kRing & (kRing - 1)) == 0, "ring layout");
   __shared__ unsigned long long s_cnt[2 * K];
+  __shared__ __align__(16) ulonglong2 s_ring[kWarpsPerBlock][kRing][2][32];  // [warp][slot][plane][lane]
   for (int t = threadIdx.x; t < 2 * K; t += blockDim.x) s_cnt[t] = 0;
   pdl_wait();
   __syncthreads();
@@ -133,9 +151,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, K >= 8 ? 3 : 4)
     int ld_row = (r0 - K) % (int)g.M;
     if (ld_row < 0) ld_row += (int)g.M;
     const size_t pitch = (size_t)g.P;
-    const u64 *Lp = Lin + w + (size_t)ld_row * pitch;
-    const u64 *Tp = Tin + w + (size_t)ld_row * pitch;
-    const u64 *Lbase = Lin + w, *Tbase = Tin + w;
+    // the 16-byte word pair that holds this lane's word
+    const u64 *Lbase = Lin + (w & ~1), *Tbase = Tin + (w & ~1);
+    const u64 *Lp = Lbase + (size_t)ld_row * pitch;
+    const u64 *Tp = Tbase + (size_t)ld_row * pitch;
+    const int half = w & 1;
     const int M = (int)g.M;
     u64 *Lo = Lout + w + (size_t)r0 * pitch;
     u64 *To = Tout + w + (size_t)r0 * pitch;
@@ -158,17 +178,18 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, K >= 8 ? 3 : 4)
       }
     };
 
-    u64 bufL[P], bufT[P];
+    ulonglong2 (*ring)[2][32] = s_ring[threadIdx.x >> 5];
+    // rows 0 .. kAhead-1 in flight, one commit group per row (empty past n_in)
 #pragma unroll
-    for (int u = 0; u < P; ++u) {
-      bufL[u] = bufT[u] = 0;
+    for (int u = 0; u < kAhead; ++u) {
       if (u < n_in) {
         if (on) {
-          bufL[u] = __ldg(Lp);
-          bufT[u] = __ldg(Tp);
+          cp_async16(&ring[u][0][lane], Lp);
+          cp_async16(&ring[u][1][lane], Tp);
         }
         advance();
       }
+      cp_async_commit();
     }
 
     for (int i0 = 0; i0 < n_in; i0 += P) {
@@ -178,14 +199,20 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, K >= 8 ? 3 : 4)
       for (int u = 0; u < P; ++u) {
         const int i = i0 + u;
         if (steady || i < n_in) {  // warp-uniform
-          u64 inL = bufL[u], inT = bufT[u];
-          if (i + P < n_in) {
+          if (i + kAhead < n_in) {
             if (on) {
-              bufL[u] = __ldg(Lp);
-              bufT[u] = __ldg(Tp);
+              const int sl = (i + kAhead) & (kRing - 1);
+              cp_async16(&ring[sl][0][lane], Lp);
+              cp_async16(&ring[sl][1][lane], Tp);
             }
             advance();
           }
+          cp_async_commit();
+          cp_async_wait<kAhead>();  // row i has landed (this lane's own copies)
+          // lanes that are off read a stale slot: they are neither stored
+          // nor counted, and no lane that is on reads their words
+          const u64 *q = reinterpret_cast<const u64 *>(&ring[i & (kRing - 1)][0][lane]) + half;
+          u64 inL = q[0], inT = q[64];
           if (steady)
             row_through<K, FULL, false>(inL, inT, pp[u & 1], pp[(u & 1) ^ 1], lw, i, B, c_lr,
                                         c_tb);
