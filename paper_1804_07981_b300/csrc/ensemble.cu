@@ -153,17 +153,13 @@ struct PFE {
 };
 
 // Input rows reach a warp through a ring of kEnsRing row slots in shared
-// memory, filled kEnsAhead rows ahead with cp.async.cg (through L2, so the
-// words other blocks wrote in the previous chunk are seen).  A lane copies the
-// aligned 16-byte pair of words that holds its own word (rows start 16-byte
-// aligned, since P is even) and reads back only its own half; the two lanes
-// of a pair request the same bytes, so the warp's requests cover the same
-// sectors as one word per lane.  A slot is refilled two rows after it was
-// last read.
+// memory (stage.cuh), filled kEnsAhead rows ahead with cp.async.cg: through
+// L2, so the words other blocks wrote in the previous chunk are seen.  A slot
+// is refilled two rows after it was last read.
 constexpr int kEnsRing = 8;
 constexpr int kEnsAhead = 6;
 static_assert(kEnsAhead <= kEnsRing - 2 && (kEnsRing & (kEnsRing - 1)) == 0, "ring layout");
-using EnsRing = ulonglong2[kEnsRing][2][32];  // [slot][plane][lane]
+using EnsRing = RingSlot[kEnsRing];
 
 template <int K>
 __device__ void process_tile(const EnsParams &p, int t, long long step0, int par,
@@ -235,8 +231,7 @@ __device__ void process_tile(const EnsParams &p, int t, long long step0, int par
 #pragma unroll
   for (int u = 0; u < kEnsAhead; ++u) {
     if (on && u < n_in) {
-      cp_async16(&ring[u][0][lane], Lp);
-      cp_async16(&ring[u][1][lane], Lp + plane);
+      ring_fill(ring, u, lane, Lp, Lp + plane);
       if (++ld_row == M) {
         ld_row = 0;
         Lp = inbase;
@@ -254,9 +249,7 @@ __device__ void process_tile(const EnsParams &p, int t, long long step0, int par
       const int i = i0 + u;
       if (i < n_max) {  // warp-uniform
         if (on && i + kEnsAhead < n_in) {
-          const int sl = (i + kEnsAhead) & (kEnsRing - 1);
-          cp_async16(&ring[sl][0][lane], Lp);
-          cp_async16(&ring[sl][1][lane], Lp + plane);
+          ring_fill(ring, (i + kEnsAhead) & (kEnsRing - 1), lane, Lp, Lp + plane);
           if (++ld_row == M) {
             ld_row = 0;
             Lp = inbase;
@@ -268,8 +261,8 @@ __device__ void process_tile(const EnsParams &p, int t, long long step0, int par
         cp_async_wait<kEnsAhead>();  // row i has landed (this lane's own copies)
         // lanes past their band's input rows (or off) read stale slots: those
         // rows are neither stored nor counted
-        const u64 *q = reinterpret_cast<const u64 *>(&ring[i & (kEnsRing - 1)][0][lane]) + half;
-        u64 inL = q[0], inT = q[64];
+        u64 inL, inT;
+        ring_read(ring, i & (kEnsRing - 1), lane, half, inL, inT);
         const int a = u & 1, b = a ^ 1;
 #pragma unroll
         for (int s = 0; s < K; ++s) {

@@ -97,6 +97,27 @@ __device__ __forceinline__ void stage_step_pp(u64 &inL, u64 &inT, const u64 curT
   inL = curLh;
 }
 
+// Input-row ring of a warp in shared memory, [slot][plane][lane], 16 bytes
+// per lane and plane.  A lane copies (cp.async, through L2) the aligned
+// 16-byte pair of words that holds its own word (rows start 16-byte aligned:
+// the pitch is even) and reads back only its own half (half = word & 1); the
+// two lanes of a pair request the same bytes, so a warp's requests cover the
+// same sectors as one word per lane.
+using RingSlot = ulonglong2[2][32];
+
+__device__ __forceinline__ void ring_fill(RingSlot *ring, int slot, int lane, const u64 *Lpair,
+                                          const u64 *Tpair) {
+  cp_async16(&ring[slot][0][lane], Lpair);
+  cp_async16(&ring[slot][1][lane], Tpair);
+}
+
+__device__ __forceinline__ void ring_read(const RingSlot *ring, int slot, int lane, int half,
+                                          u64 &L, u64 &T) {
+  const u64 *q = reinterpret_cast<const u64 *>(&ring[slot][0][lane]) + half;
+  L = q[0];
+  T = q[64];  // the same lane's entry of plane 1
+}
+
 __device__ __forceinline__ uint32_t popc64(u64 x) {
   return (uint32_t)(__popc(lo32(x)) + __popc(hi32(x)));
 }

@@ -34,11 +34,9 @@
 // lane W-1's right neighbour is lane 0.
 //
 // Input rows reach a warp through a ring of row slots in shared memory, filled
-// a few rows ahead with cp.async: a lane copies the aligned 16-byte
-// pair of words that holds its own word (rows start 16-byte aligned, since P
-// is even) and reads back only its own half, so the warp's requests cover the
-// same sectors as one word per lane.  A slot is refilled two rows after it
-// was last read.  The row loop runs in chunks of PF rows (PF even: the stage
+// a few rows ahead with cp.async (stage.cuh: a lane copies the aligned
+// 16-byte word pair that holds its word and reads back its own half).  A
+// slot is refilled two rows after it was last read.  The row loop runs in chunks of PF rows (PF even: the stage
 // state sets alternate by row).  Chunks that lie entirely in the steady part
 // of the band (every stage counts its row and the last stage stores) run
 // without per-row predicates.
@@ -102,7 +100,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, K >= 8 ? 3 : 4)
   constexpr int kRing = RingGeom<K>::slots, kAhead = RingGeom<K>::ahead;
   static_assert(kAhead <= kRing - 2 && (kRing & (kRing - 1)) == 0, "ring layout");
   __shared__ unsigned long long s_cnt[2 * K];
-  __shared__ __align__(16) ulonglong2 s_ring[kWarpsPerBlock][kRing][2][32];  // [warp][slot][plane][lane]
+  __shared__ __align__(16) RingSlot s_ring[kWarpsPerBlock][kRing];
   for (int t = threadIdx.x; t < 2 * K; t += blockDim.x) s_cnt[t] = 0;
   pdl_wait();
   __syncthreads();
@@ -178,15 +176,12 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, K >= 8 ? 3 : 4)
       }
     };
 
-    ulonglong2 (*ring)[2][32] = s_ring[threadIdx.x >> 5];
+    RingSlot *ring = s_ring[threadIdx.x >> 5];
     // rows 0 .. kAhead-1 in flight, one commit group per row (empty past n_in)
 #pragma unroll
     for (int u = 0; u < kAhead; ++u) {
       if (u < n_in) {
-        if (on) {
-          cp_async16(&ring[u][0][lane], Lp);
-          cp_async16(&ring[u][1][lane], Tp);
-        }
+        if (on) ring_fill(ring, u, lane, Lp, Tp);
         advance();
       }
       cp_async_commit();
@@ -200,19 +195,15 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, K >= 8 ? 3 : 4)
         const int i = i0 + u;
         if (steady || i < n_in) {  // warp-uniform
           if (i + kAhead < n_in) {
-            if (on) {
-              const int sl = (i + kAhead) & (kRing - 1);
-              cp_async16(&ring[sl][0][lane], Lp);
-              cp_async16(&ring[sl][1][lane], Tp);
-            }
+            if (on) ring_fill(ring, (i + kAhead) & (kRing - 1), lane, Lp, Tp);
             advance();
           }
           cp_async_commit();
           cp_async_wait<kAhead>();  // row i has landed (this lane's own copies)
           // lanes that are off read a stale slot: they are neither stored
           // nor counted, and no lane that is on reads their words
-          const u64 *q = reinterpret_cast<const u64 *>(&ring[i & (kRing - 1)][0][lane]) + half;
-          u64 inL = q[0], inT = q[64];
+          u64 inL, inT;
+          ring_read(ring, i & (kRing - 1), lane, half, inL, inT);
           if (steady)
             row_through<K, FULL, false>(inL, inT, pp[u & 1], pp[(u & 1) ^ 1], lw, i, B, c_lr,
                                         c_tb);
