@@ -46,6 +46,17 @@ namespace {
 typedef __nv_bfloat16 bf16;
 
 constexpr int kIn = 67, kInPad = 80, kHid = 128, kOut = 2, kOutPad = 16;
+// Blocks of the loss and bias-gradient kernels (grid-stride over the batch):
+// few enough that the last block's ordered sum over their partials is short.
+constexpr int kReluBlocks = 256, kLossBlocks = 256;
+inline int relu_blocks(int Bp) {
+  const int b = Bp / 8;
+  return b < 1 ? 1 : (b > kReluBlocks ? kReluBlocks : b);
+}
+inline int loss_blocks(int Bp) {
+  const int b = (Bp + 255) / 256;
+  return b > kLossBlocks ? kLossBlocks : b;
+}
 constexpr int kKC = 64;                       // K per shared-memory stage
 constexpr int kStageA = 128 * kKC * 2;        // A: 128 rows x 64 bf16
 constexpr int kStageBytes = 2 * kStageA;      // + B: up to 128 rows x 64 bf16
@@ -316,11 +327,51 @@ __global__ void prep_x_kernel(const float *__restrict__ x, int B, int Bp, bf16 *
   }
 }
 
+// Sums over the blocks of a grid in a fixed order: block b has stored its n
+// partial sums at part[b * n, (b + 1) * n) (and fenced them); the block that
+// arrives last at the counter adds them up in a fixed association (ACC
+// interleaved running sums, then those in order), so every sum is formed the
+// same way whatever the blocks' timing (float atomics would make training
+// runs differ from one another).  Returns true in that block, whose
+// threads j < n then hold the total of entry j in *total; the counter is
+// re-armed for the next launch on the stream.
+template <int ACC>
+__device__ __forceinline__ bool grid_sum_last(const float *part, int n, unsigned *count,
+                                              float *total) {
+  __shared__ bool s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(count, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return false;
+  if ((int)threadIdx.x < n) {
+    // ACC running sums (block b into sum b % ACC), added in order at the end:
+    // a fixed association with ACC loads in flight
+    float t[ACC];
+#pragma unroll
+    for (int k = 0; k < ACC; ++k) t[k] = 0.f;
+    const unsigned G = gridDim.x;
+    for (unsigned b = 0; b < G; b += ACC) {
+#pragma unroll
+      for (int k = 0; k < ACC; ++k)
+        if (b + k < G) t[k] += __ldcg(part + (size_t)(b + k) * n + threadIdx.x);
+    }
+    float sum = 0.f;
+#pragma unroll
+    for (int k = 0; k < ACC; ++k) sum += t[k];
+    *total = sum;
+  }
+  if (threadIdx.x == 0) *count = 0u;
+  return true;
+}
+
 // outputs fp32 [Bp][16] -> loss (sum / B), dOut bf16 [Bp][16] and its
-// transpose [16][Bp], and the output-bias gradient (atomics on db4[0..1]).
+// transpose [16][Bp], and the output-bias gradient db4[0..1]; loss and db4
+// are sums over the batch formed in a fixed order (per-warp shuffles, warps
+// in order, blocks in order by the last block).  256 threads per block.
 __global__ void loss_grad_kernel(const float *__restrict__ out, const float *__restrict__ v,
                                  const float *__restrict__ jam, int B, int Bp, bf16 *G,
-                                 bf16 *GT, float *loss, float *db4) {
+                                 bf16 *GT, float *loss, float *db4, float *part,
+                                 unsigned *count) {
   float l_sum = 0.f, g0 = 0.f, g1 = 0.f;
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < Bp; b += gridDim.x * blockDim.x) {
     float d0 = 0.f, d1 = 0.f;
@@ -346,10 +397,25 @@ __global__ void loss_grad_kernel(const float *__restrict__ out, const float *__r
     g0 += __shfl_down_sync(0xffffffffu, g0, o);
     g1 += __shfl_down_sync(0xffffffffu, g1, o);
   }
+  __shared__ float s_w[8][3];
+  const int warp = threadIdx.x >> 5;
   if ((threadIdx.x & 31) == 0) {
-    atomicAdd(loss, l_sum / (float)B);
-    atomicAdd(db4 + 0, g0);
-    atomicAdd(db4 + 1, g1);
+    s_w[warp][0] = l_sum;
+    s_w[warp][1] = g0;
+    s_w[warp][2] = g1;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    float t = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_w[w][threadIdx.x];
+    part[(size_t)blockIdx.x * 3 + threadIdx.x] = t;
+    __threadfence();
+  }
+  float total = 0.f;
+  if (grid_sum_last<8>(part, 3, count, &total)) {
+    if (threadIdx.x == 0) *loss = total / (float)B;
+    if (threadIdx.x == 1) db4[0] = total;
+    if (threadIdx.x == 2) db4[1] = total;
   }
 }
 
@@ -372,11 +438,16 @@ __global__ void gather_batch_kernel(const float *__restrict__ x, const float *__
 }
 
 // dZ = dH * (H > 0): bf16 [Bp][128] and transpose [128][Bp]; bias gradient
-// = column sums (atomics), over the first B rows.
+// db = column sums over the first B rows, formed in a fixed order (rows in
+// order within a block, blocks in order by the last block).  128 threads per
+// block, one per column.
 __global__ void relu_bwd_kernel(const float *__restrict__ dH, const bf16 *__restrict__ H, int B,
-                                int Bp, bf16 *dZ, bf16 *dZT, float *db) {
-  const int col = threadIdx.x;  // 128 threads = 128 columns
+                                int Bp, bf16 *__restrict__ dZ, bf16 *__restrict__ dZT,
+                                float *__restrict__ db, float *__restrict__ part,
+                                unsigned *count) {
+  const int col = threadIdx.x;
   float s = 0.f;
+#pragma unroll 8
   for (int b = blockIdx.x; b < Bp; b += gridDim.x) {
     const size_t i = (size_t)b * kHid + col;
     const float g = (b < B && __bfloat162float(H[i]) > 0.f) ? dH[i] : 0.f;
@@ -385,7 +456,10 @@ __global__ void relu_bwd_kernel(const float *__restrict__ dH, const bf16 *__rest
     dZ[i] = h;
     dZT[(size_t)col * Bp + b] = h;
   }
-  atomicAdd(db + col, s);
+  part[(size_t)blockIdx.x * kHid + col] = s;
+  __threadfence();
+  float total = 0.f;
+  if (grid_sum_last<32>(part, kHid, count, &total)) db[col] = total;
 }
 
 // column sums of a bf16-free fp32 gradient are not needed for layer 4 (done
@@ -549,6 +623,10 @@ struct bml_mlp {
   bf16 *X = nullptr, *XT = nullptr, *H[3] = {}, *HT[3] = {}, *G = nullptr, *GT = nullptr;
   bf16 *dZ = nullptr, *dZT = nullptr;
   float *out = nullptr, *dH = nullptr, *loss = nullptr;
+  // fixed-order reductions: per-block partial sums and two arrival counters
+  // (loss kernel, bias-gradient kernel)
+  float *part = nullptr;
+  unsigned *red_count = nullptr;
   float *bias4 = nullptr;  // padded output bias [16]
   int *err = nullptr;
   // bml_mlp_train: gathered mini-batch (features, labels) and per-step losses
@@ -579,8 +657,9 @@ void mlp_free_batch(bml_mlp *p) {
   cudaFree(p->dZT);
   cudaFree(p->out);
   cudaFree(p->dH);
+  cudaFree(p->part);
   p->X = p->XT = p->G = p->GT = p->dZ = p->dZT = nullptr;
-  p->out = p->dH = nullptr;
+  p->out = p->dH = p->part = nullptr;
   p->cap = 0;
 }
 
@@ -599,6 +678,7 @@ int ensure_batch(bml_mlp *p, int Bp) {
   MCUDA(cudaMalloc(&p->dZT, (size_t)Bp * kHid * 2));
   MCUDA(cudaMalloc(&p->out, (size_t)Bp * kOutPad * 4));
   MCUDA(cudaMalloc(&p->dH, (size_t)Bp * kHid * 4));
+  MCUDA(cudaMalloc(&p->part, (size_t)(kReluBlocks * kHid + kLossBlocks * 3) * 4));
   p->cap = Bp;
   return BML_OK;
 }
@@ -668,6 +748,7 @@ extern "C" int bml_mlp_create(void *stream, bml_mlp **out) {
   MTRY(cudaMalloc(&p->v, p->n * 4));
   MTRY(cudaMalloc(&p->err, 256));
   MTRY(cudaMalloc(&p->loss, 256));
+  MTRY(cudaMalloc(&p->red_count, 256));
   MTRY(cudaMalloc(&p->bias4, kOutPad * 4));
   for (int l = 0; l < 4; ++l) {
     Layer &ly = p->layers.l[l];
@@ -688,6 +769,7 @@ extern "C" int bml_mlp_create(void *stream, bml_mlp **out) {
   MTRY(cudaMemsetAsync(p->m, 0, p->n * 4, p->st));
   MTRY(cudaMemsetAsync(p->v, 0, p->n * 4, p->st));
   MTRY(cudaMemsetAsync(p->err, 0, 256, p->st));
+  MTRY(cudaMemsetAsync(p->red_count, 0, 256, p->st));
   MTRY(cudaMemsetAsync(p->bias4, 0, kOutPad * 4, p->st));
   MTRY(cudaStreamSynchronize(p->st));
 #undef MTRY
@@ -711,6 +793,7 @@ extern "C" void bml_mlp_destroy(bml_mlp *p) {
   cudaFree(p->v);
   cudaFree(p->err);
   cudaFree(p->loss);
+  cudaFree(p->red_count);
   cudaFree(p->bias4);
   cudaFree(p->xb);
   cudaFree(p->vb);
@@ -769,14 +852,13 @@ static int compute_grads(bml_mlp *p, const float *d_x, const float *d_v, const f
   const int Bp = (B + 127) / 128 * 128;
   int rc = ensure_batch(p, Bp);
   if (rc) return rc;
-  MCUDA(cudaMemsetAsync(p->loss, 0, 4, p->st));
-  for (int l = 0; l < 4; ++l)
-    MCUDA(cudaMemsetAsync(p->gb[l], 0, p->layers.l[l].out * 4, p->st));
+  // the loss and every bias gradient are written (not accumulated) below
   prep_x_kernel<<<256, 256, 0, p->st>>>(d_x, B, Bp, p->X, p->XT);
   MCUDA(cudaGetLastError());
   if ((rc = forward_staged(p, Bp, true))) return rc;
-  loss_grad_kernel<<<(Bp + 255) / 256, 256, 0, p->st>>>(p->out, d_v, d_jam, B, Bp, p->G, p->GT,
-                                                        p->loss, p->gb[3]);
+  loss_grad_kernel<<<loss_blocks(Bp), 256, 0, p->st>>>(p->out, d_v, d_jam, B, Bp, p->G, p->GT,
+                                                       p->loss, p->gb[3], p->part,
+                                                       p->red_count);
   MCUDA(cudaGetLastError());
   // layer 4: dW4^T [128][16] = H3^T (128 x Bp) . G^T (16 x Bp)^T, stored transposed
   {
@@ -794,7 +876,8 @@ static int compute_grads(bml_mlp *p, const float *d_x, const float *d_v, const f
     MCUDA(launch_gemm(p->G, kOutPad, p->WT[3], kOutPad, Bp, kHid, kOutPad, d, p->st));
   }
   for (int l = 2; l >= 0; --l) {
-    relu_bwd_kernel<<<256, kHid, 0, p->st>>>(p->dH, p->H[l], B, Bp, p->dZ, p->dZT, p->gb[l]);
+    relu_bwd_kernel<<<relu_blocks(Bp), kHid, 0, p->st>>>(p->dH, p->H[l], B, Bp, p->dZ, p->dZT,
+                                                         p->gb[l], p->part, p->red_count + 1);
     MCUDA(cudaGetLastError());
     const bf16 *prevT = l > 0 ? p->HT[l - 1] : p->XT;
     const int in_pad = kInPads[l];
