@@ -472,18 +472,22 @@ def _config_benches(bml, torch, stream):
                                         "cell_updates_per_s": 65536 * 1024 / (ms / 1e3),
                                         "tiling": [k, band, lw]}
     tot = {"byte": 0.0, "auto": 0.0}
+    tilings = set()
     for rho in (0.20, 0.35, 0.50):
         for seed in (1, 2, 3):
             for kernel in ("byte", "auto"):
                 with bml.Lattice(4096, 4096, seed=seed, density=rho, kernel=kernel,
                                  stream=stream, reserve_steps=4096 + 64) as sim:
                     tot[kernel] += _timed_steps(torch, stream, sim, 4096) / 1e3
+                    if kernel == "auto":
+                        tilings.add(tuple(sim.tiling))
     cs = 9 * 4096 * 4096 * 4096
     out["4096x4096_rho0.20-0.50_seeds1-3_4096steps"] = {
         "byte_seconds": tot["byte"], "bitplane_seconds": tot["auto"],
         "byte_cell_updates_per_s": cs / tot["byte"],
         "bitplane_cell_updates_per_s": cs / tot["auto"],
-        "bitplane_over_byte": tot["byte"] / tot["auto"]}
+        "bitplane_over_byte": tot["byte"] / tot["auto"],
+        "bitplane_tilings": sorted(list(t) for t in tilings)}
     return out
 
 

@@ -33,10 +33,13 @@
 // the row).  Rows that fit in one warp (W <= 32) are whole periodic rings:
 // lane W-1's right neighbour is lane 0.
 //
-// Input rows reach a warp through a ring of row slots in shared memory, filled
-// a few rows ahead with cp.async (stage.cuh: a lane copies the aligned
-// 16-byte word pair that holds its word and reads back its own half).  A
-// slot is refilled two rows after it was last read.  The row loop runs in chunks of PF rows (PF even: the stage
+// Input rows of a lattice larger than half of L2 reach a warp through a ring
+// of row slots in shared memory, filled a few rows ahead with cp.async
+// (stage.cuh: a lane copies the aligned 16-byte word pair that holds its word
+// and reads back its own half); a slot is refilled two rows after it was
+// last read.  Rows of a smaller lattice come from L2, whose latency a
+// prefetch of P rows into registers already hides, so the ring's extra
+// instructions per row would only cost time there.  The row loop runs in chunks of PF rows (PF even: the stage
 // state sets alternate by row).  Chunks that lie entirely in the steady part
 // of the band (every stage counts its row and the last stage stores) run
 // without per-row predicates.
@@ -90,15 +93,16 @@ __device__ __forceinline__ void row_through(u64 &inL, u64 &inT, const Pipe<K> &s
   }
 }
 
-template <int K, bool FULL>
+// RING: input rows through the shared-memory ring, else a register prefetch.
+template <int K, bool FULL, bool RING>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, K >= 8 ? 3 : 4)
     stream_kernel(const u64 *__restrict__ Lin, const u64 *__restrict__ Tin,
                   u64 *__restrict__ Lout, u64 *__restrict__ Tout, Geom g, StripPlan sp,
                   int band_rows, int n_bands, u64 *__restrict__ moved_lr,
                   u64 *__restrict__ moved_tb) {
   constexpr int P = PF<K>::value;
-  constexpr int kRing = RingGeom<K>::slots, kAhead = RingGeom<K>::ahead;
-  static_assert(kAhead <= kRing - 2 && (kRing & (kRing - 1)) == 0, "ring layout");
+  constexpr int kRing = RING ? RingGeom<K>::slots : 1, kAhead = RingGeom<K>::ahead;
+  static_assert(!RING || (kAhead <= kRing - 2 && (kRing & (kRing - 1)) == 0), "ring layout");
   __shared__ unsigned long long s_cnt[2 * K];
   __shared__ __align__(16) RingSlot s_ring[kWarpsPerBlock][kRing];
   for (int t = threadIdx.x; t < 2 * K; t += blockDim.x) s_cnt[t] = 0;
@@ -149,8 +153,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, K >= 8 ? 3 : 4)
     int ld_row = (r0 - K) % (int)g.M;
     if (ld_row < 0) ld_row += (int)g.M;
     const size_t pitch = (size_t)g.P;
-    // the 16-byte word pair that holds this lane's word
-    const u64 *Lbase = Lin + (w & ~1), *Tbase = Tin + (w & ~1);
+    // ring: the 16-byte word pair that holds this lane's word
+    const int pw = RING ? (w & ~1) : w;
+    const u64 *Lbase = Lin + pw, *Tbase = Tin + pw;
     const u64 *Lp = Lbase + (size_t)ld_row * pitch;
     const u64 *Tp = Tbase + (size_t)ld_row * pitch;
     const int half = w & 1;
@@ -177,14 +182,29 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, K >= 8 ? 3 : 4)
     };
 
     RingSlot *ring = s_ring[threadIdx.x >> 5];
-    // rows 0 .. kAhead-1 in flight, one commit group per row (empty past n_in)
+    u64 bufL[P], bufT[P];  // register prefetch (no ring)
+    if constexpr (RING) {
+      // rows 0 .. kAhead-1 in flight, one commit group per row (empty past n_in)
 #pragma unroll
-    for (int u = 0; u < kAhead; ++u) {
-      if (u < n_in) {
-        if (on) ring_fill(ring, u, lane, Lp, Tp);
-        advance();
+      for (int u = 0; u < kAhead; ++u) {
+        if (u < n_in) {
+          if (on) ring_fill(ring, u, lane, Lp, Tp);
+          advance();
+        }
+        cp_async_commit();
       }
-      cp_async_commit();
+    } else {
+#pragma unroll
+      for (int u = 0; u < P; ++u) {
+        bufL[u] = bufT[u] = 0;
+        if (u < n_in) {
+          if (on) {
+            bufL[u] = __ldg(Lp);
+            bufT[u] = __ldg(Tp);
+          }
+          advance();
+        }
+      }
     }
 
     for (int i0 = 0; i0 < n_in; i0 += P) {
@@ -194,16 +214,28 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, K >= 8 ? 3 : 4)
       for (int u = 0; u < P; ++u) {
         const int i = i0 + u;
         if (steady || i < n_in) {  // warp-uniform
-          if (i + kAhead < n_in) {
-            if (on) ring_fill(ring, (i + kAhead) & (kRing - 1), lane, Lp, Tp);
-            advance();
-          }
-          cp_async_commit();
-          cp_async_wait<kAhead>();  // row i has landed (this lane's own copies)
-          // lanes that are off read a stale slot: they are neither stored
-          // nor counted, and no lane that is on reads their words
           u64 inL, inT;
-          ring_read(ring, i & (kRing - 1), lane, half, inL, inT);
+          if constexpr (RING) {
+            if (i + kAhead < n_in) {
+              if (on) ring_fill(ring, (i + kAhead) & (kRing - 1), lane, Lp, Tp);
+              advance();
+            }
+            cp_async_commit();
+            cp_async_wait<kAhead>();  // row i has landed (this lane's own copies)
+            // lanes that are off read a stale slot: they are neither stored
+            // nor counted, and no lane that is on reads their words
+            ring_read(ring, i & (kRing - 1), lane, half, inL, inT);
+          } else {
+            inL = bufL[u];
+            inT = bufT[u];
+            if (i + P < n_in) {
+              if (on) {
+                bufL[u] = __ldg(Lp);
+                bufT[u] = __ldg(Tp);
+              }
+              advance();
+            }
+          }
           if (steady)
             row_through<K, FULL, false>(inL, inT, pp[u & 1], pp[(u & 1) ^ 1], lw, i, B, c_lr,
                                         c_tb);
@@ -245,6 +277,32 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, K >= 8 ? 3 : 4)
   }
 }
 
+// The ring pays off when the step's rows come from DRAM: both buffers of the
+// lattice (2 planes each) take more than half of L2.
+bool use_ring(const Geom &g) {
+  static int l2_bytes = -1;
+  if (l2_bytes < 0) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&v, cudaDevAttrL2CacheSize, dev) != cudaSuccess) {
+      cudaGetLastError();
+      v = 126 << 20;
+    }
+    l2_bytes = v;
+  }
+  const double footprint = 2.0 * 2.0 * (double)g.M * (double)g.P * 8.0;
+  return footprint > 0.5 * (double)l2_bytes;
+}
+
+template <int K, bool FULL, bool RING>
+cudaError_t launch_kfr(const u64 *Lin, const u64 *Tin, u64 *Lout, u64 *Tout, const Geom &g,
+                       const StripPlan &sp, int64_t band_rows, int64_t n_bands, int64_t blocks,
+                       u64 *moved_lr, u64 *moved_tb, cudaStream_t st) {
+  return launch_pdl(stream_kernel<K, FULL, RING>, dim3((unsigned)blocks),
+                    dim3(kWarpsPerBlock * 32), 0, st, Lin, Tin, Lout, Tout, g, sp,
+                    (int)band_rows, (int)n_bands, moved_lr, moved_tb);
+}
+
 template <int K>
 cudaError_t launch_k(const u64 *Lin, const u64 *Tin, u64 *Lout, u64 *Tout, const Geom &g,
                      int64_t band_rows, u64 *moved_lr, u64 *moved_tb, cudaStream_t st) {
@@ -253,19 +311,24 @@ cudaError_t launch_k(const u64 *Lin, const u64 *Tin, u64 *Lout, u64 *Tout, const
   const int64_t tiles = (int64_t)sp.n_strips * n_bands;
   if (tiles > INT32_MAX - kWarpsPerBlock) return cudaErrorInvalidValue;
   const int64_t blocks = (tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
-  if (g.nb == 64)
-    return launch_pdl(stream_kernel<K, true>, dim3((unsigned)blocks), dim3(kWarpsPerBlock * 32), 0,
-                      st, Lin, Tin, Lout, Tout, g, sp, (int)band_rows, (int)n_bands, moved_lr,
-                      moved_tb);
-  return launch_pdl(stream_kernel<K, false>, dim3((unsigned)blocks), dim3(kWarpsPerBlock * 32), 0,
-                    st, Lin, Tin, Lout, Tout, g, sp, (int)band_rows, (int)n_bands, moved_lr,
-                    moved_tb);
+  const bool full = g.nb == 64, ring = use_ring(g);
+  if (full && ring)
+    return launch_kfr<K, true, true>(Lin, Tin, Lout, Tout, g, sp, band_rows, n_bands, blocks,
+                                     moved_lr, moved_tb, st);
+  if (full)
+    return launch_kfr<K, true, false>(Lin, Tin, Lout, Tout, g, sp, band_rows, n_bands, blocks,
+                                      moved_lr, moved_tb, st);
+  if (ring)
+    return launch_kfr<K, false, true>(Lin, Tin, Lout, Tout, g, sp, band_rows, n_bands, blocks,
+                                      moved_lr, moved_tb, st);
+  return launch_kfr<K, false, false>(Lin, Tin, Lout, Tout, g, sp, band_rows, n_bands, blocks,
+                                     moved_lr, moved_tb, st);
 }
 
-template <int K, bool FULL>
+template <int K, bool FULL, bool RING>
 int occupancy_of() {
   int blocks = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, stream_kernel<K, FULL>,
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, stream_kernel<K, FULL, RING>,
                                                     kWarpsPerBlock * 32, 0) != cudaSuccess) {
     cudaGetLastError();
     return 1;
@@ -273,16 +336,22 @@ int occupancy_of() {
   return blocks > 0 ? blocks : 1;
 }
 
+template <int K>
+int occupancy_k(const Geom &g) {
+  const bool full = g.nb == 64, ring = use_ring(g);
+  if (full) return ring ? occupancy_of<K, true, true>() : occupancy_of<K, true, false>();
+  return ring ? occupancy_of<K, false, true>() : occupancy_of<K, false, false>();
+}
+
 }  // namespace
 
 int stream_occupancy(const Geom &g, int k, int *warps_per_block) {
   if (warps_per_block) *warps_per_block = kWarpsPerBlock;
-  const bool full = g.nb == 64;
   switch (k) {
-    case 1: return full ? occupancy_of<1, true>() : occupancy_of<1, false>();
-    case 2: return full ? occupancy_of<2, true>() : occupancy_of<2, false>();
-    case 4: return full ? occupancy_of<4, true>() : occupancy_of<4, false>();
-    default: return full ? occupancy_of<8, true>() : occupancy_of<8, false>();
+    case 1: return occupancy_k<1>(g);
+    case 2: return occupancy_k<2>(g);
+    case 4: return occupancy_k<4>(g);
+    default: return occupancy_k<8>(g);
   }
 }
 
