@@ -21,9 +21,9 @@
 // meets at a grid barrier whose waits are bounded by %globaltimer (on expiry
 // the kernel sets an error flag and returns; the host reports BML_ETIMEOUT).
 // The launch is cooperative, so all blocks are co-resident.  Data written in
-// one chunk is read by other blocks in the next, so the kernel loads and
-// stores lattice words through L2 (ld/st .cg), never through the
-// non-coherent read-only path.
+// one chunk is read by other blocks in the next, so lattice words move
+// through L2 only (cp.async.cg into a per-warp shared-memory ring, st.cg),
+// never through L1 or the non-coherent read-only path.
 //
 // Jam early exit (optional).  A step in which no car moves leaves the lattice
 // unchanged, so every later step does too (an absorbing fixed point).  At the
