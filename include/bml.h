@@ -123,8 +123,12 @@ int bml_moved_counts(bml_sim *sim, int64_t first, int64_t n, int64_t *out_total,
  * is their sum) on the object's stream and return without waiting: a
  * caller can read every step's result while the steps run.  The values are
  * valid once the stream has been synchronised (bml_synchronize, or any call
- * documented to synchronise).  The host arrays should be page-locked, or the
- * copy waits for the stream.  Same range rule as bml_moved_counts. */
+ * documented to synchronise).  Page-locked arrays that the current device
+ * can address (cudaHostAlloc / pinned tensors under unified addressing) are
+ * written by a small kernel ordered after the steps, so no copy-engine round
+ * trip sits between two step launches; other page-locked arrays take
+ * cudaMemcpyAsync; pageable arrays make the copy wait for the stream.  Same
+ * range rule as bml_moved_counts. */
 int bml_moved_counts_async(bml_sim *sim, int64_t first, int64_t n, int64_t *out_lr,
                            int64_t *out_tb);
 

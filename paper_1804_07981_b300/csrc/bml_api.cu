@@ -625,6 +625,22 @@ extern "C" int bml_moved_counts(bml_sim *s, int64_t first, int64_t n, int64_t *o
   return BML_OK;
 }
 
+namespace {
+// Device address of page-locked host memory that was allocated or registered
+// on the current device and is mapped into its address space, else NULL
+// (pageable memory, device memory, memory of another device's context).
+int64_t *device_view(int64_t *host) {
+  cudaPointerAttributes a;
+  int dev = 0;
+  if (cudaPointerGetAttributes(&a, host) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || !a.devicePointer || a.device != dev) return nullptr;
+  return (int64_t *)a.devicePointer;
+}
+}  // namespace
+
 extern "C" int bml_moved_counts_async(bml_sim *s, int64_t first, int64_t n, int64_t *out_lr,
                                       int64_t *out_tb) {
   if (!s) return fail(BML_EINVAL, "sim is NULL");
@@ -632,6 +648,16 @@ extern "C" int bml_moved_counts_async(bml_sim *s, int64_t first, int64_t n, int6
     return fail(BML_EINVAL, "count range [%lld, %lld) outside [0, %lld)", (long long)first,
                 (long long)(first + n), (long long)s->steps_done);
   if (n == 0) return BML_OK;
+  // Page-locked host arrays that the device can address are written by a
+  // small dependent kernel (no copy-engine round trip between two step
+  // kernels); other host memory goes through cudaMemcpyAsync.
+  int64_t *d_lr = nullptr, *d_tb = nullptr;
+  const bool mapped = (!out_lr || (d_lr = device_view(out_lr))) &&
+                      (!out_tb || (d_tb = device_view(out_tb)));
+  if (mapped) {
+    CUDA_TRY(launch_copy_counts(cnt_lr(s) + first, cnt_tb(s) + first, n, d_lr, d_tb, s->st));
+    return BML_OK;
+  }
   if (out_lr)
     CUDA_TRY(cudaMemcpyAsync(out_lr, cnt_lr(s) + first, (size_t)n * 8, cudaMemcpyDeviceToHost,
                              s->st));

@@ -63,6 +63,10 @@ cudaError_t launch_unpack(const u64 *L, const u64 *T, uint8_t *c, const Geom &g,
                           cudaStream_t st);
 // bytes (pitch PB) -> validity check only.
 cudaError_t launch_check_bytes(const uint8_t *c, const Geom &g, int *bad, cudaStream_t st);
+// n moved counts (device) -> host arrays given by their device-mapped
+// addresses (either may be NULL)
+cudaError_t launch_copy_counts(const u64 *lr, const u64 *tb, int64_t n, int64_t *dlr,
+                               int64_t *dtb, cudaStream_t st);
 
 // Byte-per-cell phases: cur -> nxt, moved cars added to *moved.
 cudaError_t launch_byte_h(const uint8_t *cur, uint8_t *nxt, const Geom &g, u64 *moved,

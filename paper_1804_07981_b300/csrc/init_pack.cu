@@ -1,4 +1,5 @@
-// Lattice set-up kernels: seeded placement, byte <-> bitplane conversion.
+// Lattice set-up and I/O kernels: seeded placement, byte <-> bitplane
+// conversion, the copy of moved counts into host-mapped memory.
 //
 // Placement (Sec. 2 of the paper only says vehicles are placed at random):
 // cell (i, j) draws u = SplitMix64 output n = i*N + j + 1 from state `seed`
@@ -176,6 +177,32 @@ cudaError_t launch_unpack(const u64 *L, const u64 *T, uint8_t *c, const Geom &g,
 cudaError_t launch_check_bytes(const uint8_t *c, const Geom &g, int *bad, cudaStream_t st) {
   check_bytes_kernel<<<grid_for(g.M * (g.PB / 16), 256), 256, 0, st>>>(c, g, bad);
   return cudaGetLastError();
+}
+
+namespace {
+
+// Moved counts of n steps -> page-locked host arrays reached through their
+// device mapping (PCIe writes from the kernel).  Launched as a dependent of
+// the step kernels (waits for them to complete), so the next step kernel's
+// launch still overlaps this one's.
+__global__ void copy_counts_kernel(const u64 *__restrict__ lr, const u64 *__restrict__ tb,
+                                   int64_t n, int64_t *dlr, int64_t *dtb) {
+  pdl_wait();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (dlr) dlr[i] = (int64_t)lr[i];
+    if (dtb) dtb[i] = (int64_t)tb[i];
+  }
+  pdl_release();
+}
+
+}  // namespace
+
+cudaError_t launch_copy_counts(const u64 *lr, const u64 *tb, int64_t n, int64_t *dlr,
+                               int64_t *dtb, cudaStream_t st) {
+  const int64_t blocks64 = (n + 255) / 256;
+  const unsigned blocks = (unsigned)(blocks64 < 1 ? 1 : (blocks64 > 148 ? 148 : blocks64));
+  return launch_pdl(copy_counts_kernel, dim3(blocks), dim3(256), 0, st, lr, tb, n, dlr, dtb);
 }
 
 }  // namespace bml

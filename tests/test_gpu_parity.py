@@ -163,6 +163,34 @@ def test_async_counts_equal_synchronous_counts(lib):
             lib.bml_moved_counts_async(sim.handle, 195, 10, lr[:10], tb[:10])
 
 
+@pytest.mark.parametrize("memory", ["pinned", "pageable", "pinned_lr_only"])
+def test_async_counts_every_host_memory_kind(lib, memory):
+    """Page-locked arrays are written by the dependent copy kernel, pageable
+    ones by cudaMemcpyAsync; both give the synchronous counts, with either
+    output omitted as well."""
+    import torch
+    M, N = 64, 640
+    with lib.Lattice(M, N, seed=3, density=0.35, kernel="tblock", block_k=8,
+                     reserve_steps=400) as sim:
+        if memory == "pageable":
+            lr = np.zeros(320, dtype=np.int64)
+            tb = np.zeros(320, dtype=np.int64)
+        else:
+            lr = torch.zeros(320, dtype=torch.int64, pin_memory=True).numpy()
+            tb = torch.zeros(320, dtype=torch.int64, pin_memory=True).numpy()
+        for s in range(40):
+            sim.step(8)
+            lib.bml_moved_counts_async(sim.handle, 8 * s, 8, lr[8 * s:8 * s + 8],
+                                       None if memory == "pinned_lr_only" else tb[8 * s:8 * s + 8])
+        sim.synchronize()
+        _, a, b = sim.moved_counts()
+        np.testing.assert_array_equal(lr, a)
+        if memory == "pinned_lr_only":
+            assert not tb.any()
+        else:
+            np.testing.assert_array_equal(tb, b)
+
+
 def test_count_history_grows(lib):
     M, N = 24, 100
     with lib.Lattice(M, N, seed=4, density=0.3, kernel="tblock", block_k=8,
