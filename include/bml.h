@@ -170,6 +170,15 @@ int bml_set_tiling(bml_sim *sim, int block_k, int64_t band_rows);
  * selects 1. */
 int bml_set_tiling_ex(bml_sim *sim, int block_k, int64_t band_rows, int lane_words);
 
+/* For an object that runs the resident kernel (created with
+ * BML_KERNEL_RESIDENT, or BML_KERNEL_AUTO when the autotuner chose it): hold
+ * the lattice in `blocks` thread blocks of one cluster (1, 2, 4 or 8; at most
+ * M), each keeping ceil(M / blocks) rows in its shared memory and reading
+ * the rows next to its band from its neighbours' shared memory; 1 keeps the
+ * whole lattice in one block.  The choice is reported by bml_get_tiling as
+ * band_rows = ceil(M / blocks).  BML_EINVAL for other objects or values. */
+int bml_set_resident_blocks(bml_sim *sim, int blocks);
+
 /* Current tiling of the bitplane kernels (band_rows 0: one-pass kernel;
  * lane_words 0 with block_k 0: the resident kernel). */
 int bml_get_tiling(const bml_sim *sim, int *block_k, int64_t *band_rows, int *lane_words);

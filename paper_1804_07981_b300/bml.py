@@ -82,6 +82,7 @@ _lib_get_config = _sig("bml_get_config", [_vp, ctypes.POINTER(_int), ctypes.POIN
 _lib_set_tiling = _sig("bml_set_tiling", [_vp, _int, _i64])
 _lib_set_tiling_ex = _sig("bml_set_tiling_ex", [_vp, _int, _i64, _int])
 _lib_get_tiling = _sig("bml_get_tiling", [_vp, ctypes.POINTER(_int), _i64p, ctypes.POINTER(_int)])
+_lib_set_resident_blocks = _sig("bml_set_resident_blocks", [_vp, _int])
 _lib_set_model = _sig("bml_set_model", [_vp, _int, _u64])
 _lib_get_model = _sig("bml_get_model", [_vp, ctypes.POINTER(_int), ctypes.POINTER(_u64)])
 _lib_sync = _sig("bml_synchronize", [_vp])
@@ -222,6 +223,10 @@ def bml_set_tiling_ex(sim: int, block_k: int, band_rows: int, lane_words: int) -
     _check(_lib_set_tiling_ex(sim, block_k, band_rows, lane_words))
 
 
+def bml_set_resident_blocks(sim: int, blocks: int) -> None:
+    _check(_lib_set_resident_blocks(sim, blocks))
+
+
 def bml_get_tiling(sim: int):
     k, lw = _int(), _int()
     b = _i64()
@@ -295,6 +300,9 @@ class Lattice:
             bml_set_tiling(self._h, block_k, band_rows)
         else:
             bml_set_tiling_ex(self._h, block_k, band_rows, lane_words)
+
+    def set_resident_blocks(self, blocks: int) -> None:
+        bml_set_resident_blocks(self._h, blocks)
 
     @property
     def tiling(self):

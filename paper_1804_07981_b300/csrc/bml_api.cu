@@ -226,7 +226,7 @@ int enqueue_steps(bml_sim *s, int64_t k, u64 *lr, u64 *tb, bool commit, int64_t 
       const int d = (int)std::min<int64_t>(k - done, resident_max_steps());
       const int a = s->cur, b = 1 - s->cur;
       CUDA_TRY(launch_resident(plane_L(s, a), plane_T(s, a), plane_L(s, b), plane_T(s, b), g, d,
-                               lr + done, tb + done, s->st));
+                               s->band_rows, lr + done, tb + done, s->st));
       if (commit) s->cur = b;
       done += d;
     }
@@ -301,8 +301,14 @@ int autotune(bml_sim *s) {
   const bool m2 = s->model == BML_MODEL_II;
   std::vector<Tiling> cands;
   if (!m2) cands.push_back({1, 0, 1});  // Model II has no one-pass kernel
-  // the resident kernel, timed on 64-step launches (a call runs all its steps in one)
-  if (!m2 && resident_applies(s->g)) cands.push_back({kTuneSteps, s->g.M, 0});
+  // the resident kernel, timed on 64-step launches (a call runs all its steps in one):
+  // the lattice in one block, or split over a cluster of 2, 4 or 8 blocks
+  if (!m2 && resident_applies(s->g)) {
+    for (int64_t blocks : {1, 2, 4, 8}) {
+      if (blocks > s->g.M) break;
+      cands.push_back({kTuneSteps, (s->g.M + blocks - 1) / blocks, 0});
+    }
+  }
   for (int lw : {1, 2}) {
     if (lw == 2 && !stream2_applies(s->g)) continue;
     for (int k : {1, 2, 4, 8}) {
@@ -563,6 +569,19 @@ extern "C" int bml_set_tiling(bml_sim *s, int block_k, int64_t band_rows) {
   s->block_k = block_k;
   s->band_rows = band_rows;
   s->lane_words = 1;
+  return BML_OK;
+}
+
+extern "C" int bml_set_resident_blocks(bml_sim *s, int blocks) {
+  if (!s) return fail(BML_EINVAL, "sim is NULL");
+  if (s->lane_words != 0)
+    return fail(BML_EINVAL, "the object does not run the resident kernel");
+  if (blocks != 1 && blocks != 2 && blocks != 4 && blocks != 8)
+    return fail(BML_EINVAL, "blocks must be 1, 2, 4 or 8 (got %d)", blocks);
+  if (blocks > s->g.M)
+    return fail(BML_EINVAL, "%d blocks need at least as many rows (M = %lld)", blocks,
+                (long long)s->g.M);
+  s->band_rows = (s->g.M + blocks - 1) / blocks;
   return BML_OK;
 }
 

@@ -102,12 +102,16 @@ cudaError_t launch_model2(const u64 *Lin, const u64 *Tin, u64 *Lout, u64 *Tout, 
                           int k, int64_t band_rows, u64 tie_seed, u64 t0, u64 *moved_lr,
                           u64 *moved_tb, cudaStream_t st);
 
-// Resident kernel: the whole lattice in one block's shared memory, k <=
-// resident_max_steps() steps per launch.
+// Resident kernel: the whole lattice in shared memory, k <=
+// resident_max_steps() steps per launch; band_rows >= M: one block holds it,
+// else the rows are split into bands of band_rows over the blocks of one
+// thread-block cluster (resident_blocks of them, at most 8).
 bool resident_applies(const Geom &g);
 int resident_max_steps();
+int resident_blocks(const Geom &g, int64_t band_rows);
 cudaError_t launch_resident(const u64 *Lin, const u64 *Tin, u64 *Lout, u64 *Tout, const Geom &g,
-                            int k, u64 *moved_lr, u64 *moved_tb, cudaStream_t st);
+                            int k, int64_t band_rows, u64 *moved_lr, u64 *moved_tb,
+                            cudaStream_t st);
 
 // Two-words-per-lane streaming kernel (rows of full words, W even, W > 32);
 // model 1 (the paper's model) or 2 (Model II, with tie_seed and the index

@@ -284,6 +284,58 @@ def test_resident_kernel_long_calls(lib):
             sim.set_tiling(1, 16)
 
 
+RESIDENT_CLUSTER_SHAPES = [(2, 64), (3, 3), (8, 65), (9, 70), (33, 127), (100, 300),
+                           (256, 256), (64, 2000), (17, 2048)]
+
+
+@pytest.mark.parametrize("blocks", [2, 4, 8])
+@pytest.mark.parametrize("M,N", RESIDENT_CLUSTER_SHAPES)
+def test_resident_cluster_matches_oracle(lib, M, N, blocks):
+    """The resident kernel with the rows split over a cluster of 2, 4 or 8
+    blocks (bands of ceil(M / blocks) rows, the last one shorter, rows next
+    to a band read from the neighbouring block's shared memory) gives the
+    oracle's lattices and counts; more blocks than rows are refused."""
+    with make(lib, M, N, "resident", 0) as sim:
+        if blocks > M:
+            with pytest.raises(lib.BMLError):
+                sim.set_resident_blocks(blocks)
+            return
+        sim.set_resident_blocks(blocks)
+        assert sim.tiling == (0, -(-M // blocks), 0)
+        for seed, rho in [(M * 31 + N, 0.3), (M + 5 * N, 0.7)]:
+            g0 = random_lattice(M, N, seed, rho / 2, rho / 2)
+            sim.write(g0)
+            sim.step(37)
+            sim.step(5)
+            want, mlr, mtb = oracle.run(g0, 42)
+            np.testing.assert_array_equal(sim.read(), want)
+            oracle_counts_equal(sim.moved_counts(), mlr, mtb)
+
+
+def test_resident_cluster_long_calls_and_rejections(lib):
+    """5003 steps over a cluster of 4 blocks (two launches); the call is
+    refused for objects that do not run the resident kernel and for block
+    counts other than 1, 2, 4, 8."""
+    M, N = 48, 200
+    g0 = random_lattice(M, N, 6, 0.2, 0.2)
+    want, mlr, mtb = oracle.run(g0, 5003)
+    with make(lib, M, N, "resident", 0) as sim:
+        sim.set_resident_blocks(4)
+        sim.write(g0)
+        sim.step(5000)
+        sim.step(3)
+        np.testing.assert_array_equal(sim.read(), want)
+        oracle_counts_equal(sim.moved_counts(), mlr, mtb)
+        for bad in (0, 3, 16, -1):
+            with pytest.raises(lib.BMLError):
+                sim.set_resident_blocks(bad)
+        sim.set_resident_blocks(1)
+        assert sim.tiling == (0, M, 0)
+    with make(lib, M, N, "tblock", 4) as sim:
+        with pytest.raises(lib.BMLError):
+            sim.set_resident_blocks(2)
+
+
 def test_set_tiling_rejects_bad_values(lib):
     with make(lib, 32, 64, "tblock", 2) as sim:
         for k, band in [(3, 16), (2, 0), (1, -1), (16, 8)]:
