@@ -280,15 +280,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, K >= 8 ? 3 : 4)
 // The ring pays off when the step's rows come from DRAM: both buffers of the
 // lattice (2 planes each) take more than half of L2.
 bool use_ring(const Geom &g) {
-  static int l2_bytes = -1;
-  if (l2_bytes < 0) {
-    int dev = 0, v = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&v, cudaDevAttrL2CacheSize, dev) != cudaSuccess) {
-      cudaGetLastError();
-      v = 126 << 20;
-    }
-    l2_bytes = v;
+  int dev = 0, l2_bytes = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&l2_bytes, cudaDevAttrL2CacheSize, dev) != cudaSuccess) {
+    cudaGetLastError();
+    l2_bytes = 126 << 20;
   }
   const double footprint = 2.0 * 2.0 * (double)g.M * (double)g.P * 8.0;
   return footprint > 0.5 * (double)l2_bytes;
