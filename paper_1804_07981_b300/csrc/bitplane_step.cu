@@ -303,9 +303,16 @@ cudaError_t launch_fused_direct(const u64 *L, const u64 *T, u64 *Lo, u64 *To, co
 
 cudaError_t launch_plane_v(const u64 *Lh, const u64 *T, u64 *Tv, const Geom &g, u64 *moved,
                            cudaStream_t st) {
-  const int64_t band = 16;
-  const int64_t items = ((g.M + band - 1) / band) * (g.P / 2);
+  // Band height: as short as one resident wave of threads allows, so that
+  // every thread marches down exactly one band (no tail of threads doing one
+  // band more than the others) and the re-read row above each band is 1/band
+  // of the traffic; at least 8 rows, at most 1024.
   static const int per_sm = resident_per_sm(plane_v_kernel, 256);
+  const int64_t np = g.P / 2;
+  const int64_t threads = (int64_t)sm_count() * per_sm * 256;
+  int64_t band = (g.M * np + threads - 1) / threads;
+  band = band < 8 ? 8 : (band > 1024 ? 1024 : band);
+  const int64_t items = ((g.M + band - 1) / band) * np;
   return launch_pdl(plane_v_kernel, dim3(grid_cap(items, 256, per_sm)), dim3(256), 0, st, Lh, T,
                     Tv, g, band, moved);
 }
