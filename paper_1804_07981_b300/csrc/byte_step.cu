@@ -198,8 +198,20 @@ cudaError_t launch_byte_h(const uint8_t *cur, uint8_t *nxt, const Geom &g, u64 *
 
 cudaError_t launch_byte_v(const uint8_t *cur, uint8_t *nxt, const Geom &g, u64 *moved,
                           cudaStream_t st) {
-  const int64_t band = 32;
-  const int64_t items = ((g.M + band - 1) / band) * (g.PB / 16);
+  // Band height: as short as one wave of the launched threads allows (every
+  // thread marches down one band; the rows re-read above and below a band
+  // are 2/band of the traffic), at least 32 rows, at most 4096.
+  const int64_t nq = g.PB / 16;
+  int dev = 0, sms = 148;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    sms = 148;
+  }
+  const int64_t threads = (int64_t)sms * 8 * 256;
+  int64_t band = (g.M * nq + threads - 1) / threads;
+  band = band < 32 ? 32 : (band > 4096 ? 4096 : band);
+  const int64_t items = ((g.M + band - 1) / band) * nq;
   return launch_pdl(byte_v_kernel, dim3(grid_cap(items, 256)), dim3(256), 0, st, cur, nxt, g,
                     band, moved);
 }
