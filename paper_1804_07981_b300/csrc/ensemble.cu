@@ -207,9 +207,12 @@ __device__ void process_tile(const EnsParams &p, int t, long long step0, int par
   const int M = on ? L.M : 1;
   const size_t pitch = on ? (size_t)L.P : 0;
   const size_t plane = (size_t)M * pitch;
-  // the 16-byte word pair that holds this lane's word
-  const u64 *inbase = p.pool + (on ? L.off[par] : 0) + (wi & ~1);
-  u64 *outbase = p.pool + (on ? L.off[par ^ 1] : 0) + wi;
+  // the 16-byte word pair that holds this lane's word (buffers picked by a
+  // select: a runtime index into the copied lattice record would put it in
+  // local memory)
+  const u64 off_in = par ? L.off[1] : L.off[0], off_out = par ? L.off[0] : L.off[1];
+  const u64 *inbase = p.pool + (on ? off_in : 0) + (wi & ~1);
+  u64 *outbase = p.pool + (on ? off_out : 0) + wi;
   const int len = gr.len, n_in = len + 2 * K;
   int ld_row = on ? (gr.r0 - K) % M : 0;
   if (ld_row < 0) ld_row += M;
