@@ -277,6 +277,16 @@ int bml_mlp_grads(bml_mlp *mlp, const float *d_x, const float *d_v, const float 
                   int64_t batch, float *host_grads, float *h_loss);
 /* One AdamW step with caller-supplied gradients (host array). */
 int bml_mlp_apply_grads(bml_mlp *mlp, const float *host_grads, float lr, float weight_decay);
+/* Inspection of one layer's device buffers in their padded layouts (layer
+ * 0..3; out_pad x in_pad = 128 x 80, 128 x 128, 128 x 128, 16 x 128): host_W
+ * receives the BF16 forward copy of W [out_pad][in_pad] (as floats),
+ * host_WT its transposed copy [in_pad][out_pad], host_gW the weight gradient
+ * of the last gradient computation [out_pad][in_pad] (fp32).  Any of the
+ * three may be NULL.  Entries outside [out][in] are padding: the forward and
+ * transposed copies keep them 0, and so does every gradient computation.
+ * Synchronises the network's stream.  Errors: BML_EINVAL (NULL mlp, layer
+ * out of range), BML_ECUDA. */
+int bml_mlp_get_layer(bml_mlp *mlp, int layer, float *host_W, float *host_WT, float *host_gW);
 void bml_mlp_destroy(bml_mlp *mlp);
 
 /* The tensor-core GEMM the network runs on: C (M x N, fp32, row-major, ldc)
@@ -309,7 +319,9 @@ int bml_gemm_bf16_ex(const void *A, int64_t lda, const void *B, int64_t ldb, flo
  *
  * d_cells: device pointer, 16-byte aligned, M rows of PB bytes each, PB = N
  *   rounded up to a multiple of 16; cell (i, j) is byte i*PB + j (0/1/2);
- *   bytes j >= N of a row are left untouched.  Stepped k times in place.
+ *   bytes j >= N of a row (the row padding) may hold any value: they are
+ *   not cells, take no part in any move or count, and are left exactly as
+ *   they were.  Stepped k times in place.
  * d_moved_lr, d_moved_tb: device arrays of k int64; set to the counts of the
  *   k steps (they are cleared first).
  * stream: cudaStream_t (NULL = legacy default stream); the call only
@@ -319,8 +331,10 @@ int bml_gemm_bf16_ex(const void *A, int64_t lda, const void *B, int64_t ldb, flo
  *   or a misaligned d_cells give BML_EINVAL.  No cudaMalloc, cudaFree or any
  *   other allocating routine is called.
  * The first call on a device looks up the device address of the built-in
- *   array (cudaGetSymbolAddress); make that first call before any stream
- *   capture.  All calls share the one array: calls whose work overlaps on
+ *   array (cudaGetSymbolAddress) and keeps it for the life of the process;
+ *   make that first call before any stream capture.  A device reset
+ *   (cudaDeviceReset) between calls is not supported: the array may be
+ *   reloaded at another address while the kept one stays in use.  All calls share the one array: calls whose work overlaps on
  *   the GPU (different streams, or other threads) race and corrupt each
  *   other; order them on one stream.
  * ------------------------------------------------------------------------ */

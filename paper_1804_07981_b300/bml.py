@@ -350,6 +350,7 @@ _lib_mlp_grads = _sig("bml_mlp_grads", [_vp, _vp, _vp, _vp, _i64, _vp, _vp])
 _lib_mlp_fit = _sig("bml_mlp_train", [_vp, _vp, _vp, _vp, _i64, _i64, _i64, ctypes.c_float,
                                       ctypes.c_float, ctypes.c_uint64, _vp])
 _lib_mlp_apply = _sig("bml_mlp_apply_grads", [_vp, _vp, ctypes.c_float, ctypes.c_float])
+_lib_mlp_layer = _sig("bml_mlp_get_layer", [_vp, _int, _vp, _vp, _vp])
 _lib_mlp_destroy = _sig("bml_mlp_destroy", [_vp], None)
 _lib_gemm = _sig("bml_gemm_bf16", [_vp, _i64, _vp, _i64, _vp, _i64, _i64, _i64, _i64, _vp])
 _lib_gemm_ex = _sig("bml_gemm_bf16_ex", [_vp, _i64, _vp, _i64, _vp, _i64, _i64, _i64, _i64,
@@ -427,6 +428,20 @@ class MLP:
     def apply_grads(self, grads: np.ndarray, lr: float, weight_decay: float = 0.0) -> None:
         a = np.ascontiguousarray(grads, dtype=np.float32)
         _check(_lib_mlp_apply(self._h, _host_ptr(a), lr, weight_decay))
+
+    # padded (rows, columns) of each layer's device weight buffers
+    PADDED = ((128, 80), (128, 128), (128, 128), (16, 128))
+
+    def layer(self, layer: int):
+        """Padded device buffers of one layer (bml_mlp_get_layer): the BF16
+        forward copy of W [out_pad][in_pad], its transposed copy and the last
+        weight gradient [out_pad][in_pad], as float32 arrays."""
+        r, c = self.PADDED[layer]
+        W = np.empty((r, c), dtype=np.float32)
+        WT = np.empty((c, r), dtype=np.float32)
+        gW = np.empty((r, c), dtype=np.float32)
+        _check(_lib_mlp_layer(self._h, layer, _host_ptr(W), _host_ptr(WT), _host_ptr(gW)))
+        return W, WT, gW
 
     def close(self) -> None:
         if self._h:

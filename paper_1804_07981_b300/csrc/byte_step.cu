@@ -132,9 +132,11 @@ __global__ void byte_h_kernel(const uint8_t *__restrict__ cur, uint8_t *__restri
 }
 
 // One thread per (band of rows, chunk column); marches down the band keeping
-// the upper row's TB mask and the current row's EMPTY mask.  Padding bytes
-// (columns N..PB-1) are 0 and hold no TB car, so no move involves them and
-// the vertical rule needs no column mask.
+// the upper row's TB mask and the current row's EMPTY mask.  The EMPTY mask
+// of the row's last chunk is limited to the columns < N: padding bytes
+// (columns N..PB-1) may hold anything (the allocation-free entry point steps
+// caller-owned rows), and with no EMPTY bit there no TB move involves them,
+// so they are copied unchanged and never counted.
 __global__ void __launch_bounds__(256, 8)
     byte_v_kernel(const uint8_t *__restrict__ cur, uint8_t *__restrict__ nxt, Geom g,
                   int64_t band, u64 *moved) {
@@ -150,15 +152,17 @@ __global__ void __launch_bounds__(256, 8)
     const uint8_t *col = cur + 16 * q;
     const uint8_t *src = col + r0 * g.PB;
     uint8_t *dst = nxt + r0 * g.PB + 16 * q;
+    const int64_t nv = g.N - 16 * q;  // valid cells of this chunk column
+    const Chunk vm = nv >= 16 ? Chunk{kLsb, kLsb} : valid_bytes((int)nv);
     const Chunk up = load_chunk(r0 > 0 ? src - g.PB : col + (g.M - 1) * g.PB);
     Chunk Tt = tb_mask(up);
     Chunk x = load_chunk(src);
-    Chunk E = empty_mask(x, Chunk{kLsb, kLsb});
+    Chunk E = empty_mask(x, vm);
 #pragma unroll 1
     for (int k = 0; k < len; ++k) {
       src += g.PB;
       const Chunk xn = load_chunk(k + 1 == len && wraps ? col : src);
-      const Chunk En = empty_mask(xn, Chunk{kLsb, kLsb});
+      const Chunk En = empty_mask(xn, vm);
       const Chunk T = tb_mask(x);
       const Chunk mv{T.lo & En.lo, T.hi & En.hi};
       Chunk out;

@@ -1008,6 +1008,31 @@ extern "C" int bml_mlp_apply_grads(bml_mlp *p, const float *host_grads, float lr
   return rc;
 }
 
+extern "C" int bml_mlp_get_layer(bml_mlp *p, int layer, float *host_W, float *host_WT,
+                                 float *host_gW) {
+  if (!p) return mfail(BML_EINVAL, "NULL argument");
+  if (layer < 0 || layer > 3) return mfail(BML_EINVAL, "layer must be in [0, 3]");
+  const Layer &ly = p->layers.l[layer];
+  const size_t n = (size_t)ly.out_pad * ly.in_pad;
+  std::vector<uint16_t> h(n);
+  const bf16 *src[2] = {p->W[layer], p->WT[layer]};
+  float *dst[2] = {host_W, host_WT};
+  for (int k = 0; k < 2; ++k) {
+    if (!dst[k]) continue;
+    MCUDA(cudaMemcpyAsync(h.data(), src[k], n * 2, cudaMemcpyDeviceToHost, p->st));
+    MCUDA(cudaStreamSynchronize(p->st));
+    for (size_t i = 0; i < n; ++i) {  // a bf16 value is the top half of its float
+      const uint32_t u = (uint32_t)h[i] << 16;
+      std::memcpy(dst[k] + i, &u, 4);
+    }
+  }
+  if (host_gW) {
+    MCUDA(cudaMemcpyAsync(host_gW, p->gW[layer], n * 4, cudaMemcpyDeviceToHost, p->st));
+    MCUDA(cudaStreamSynchronize(p->st));
+  }
+  return BML_OK;
+}
+
 extern "C" int bml_gemm_bf16(const void *A, int64_t lda, const void *B, int64_t ldb, float *C,
                              int64_t ldc, int64_t M, int64_t N, int64_t K, void *stream) {
   return bml_gemm_bf16_ex(A, lda, B, ldb, C, ldc, M, N, K, 0u, stream);

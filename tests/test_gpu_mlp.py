@@ -72,6 +72,9 @@ def test_forward_matches_oracle(lib, B):
     want, _ = ref.forward(ref.unflatten(flat, IN), xr)
     err = np.abs(out - want).max() / np.abs(want).max()
     assert err <= 1e-2, err
+    # every element, not only the largest deviation (activations are BF16
+    # between layers on the device, fp64 in the oracle)
+    np.testing.assert_allclose(out, want, rtol=2e-2, atol=2e-2 * np.abs(want).max())
     net.close()
 
 
@@ -90,10 +93,54 @@ def test_gradients_match_oracle(lib, B):
     assert abs(loss - want_loss) <= 1e-2 * abs(want_loss)
     gs = ref.unflatten(g.astype(np.float64), IN)
     for i, (a, w) in enumerate(zip(gs, want)):
+        # every element of every tensor ...
+        np.testing.assert_allclose(a, w, rtol=3e-2, atol=3e-2 * np.abs(w).max(),
+                                   err_msg="tensor %d" % i)
+        # ... and the tensor as a whole
         a, w = a.ravel(), w.ravel()
         cos = a @ w / (np.linalg.norm(a) * np.linalg.norm(w) + 1e-30)
         rel = np.linalg.norm(a - w) / (np.linalg.norm(w) + 1e-30)
         assert cos >= 0.999 and rel <= 2e-2, (i, cos, rel)
+    # the padded device gradients hold the same values, and zeros in the
+    # padding (input columns 67..79 of layer 0, output rows 2..15 of layer 3)
+    for l in range(4):
+        _, _, gW = net.layer(l)
+        o, k = want[2 * l].shape
+        np.testing.assert_array_equal(gW[:o, :k], gs[2 * l].astype(np.float32))
+        assert not gW[o:, :].any() and not gW[:, k:].any(), l
+    net.close()
+
+
+def _check_padded_weights(net, flat):
+    """The BF16 forward and transposed weight copies equal the master
+    weights rounded to BF16, and every padding entry is exactly 0."""
+    ps = ref.unflatten(flat.astype(np.float64), IN)
+    for l in range(4):
+        W, WT, _ = net.layer(l)
+        o, k = ps[2 * l].shape
+        np.testing.assert_array_equal(W[:o, :k], ref.bf16_round(ps[2 * l]).astype(np.float32))
+        np.testing.assert_array_equal(WT, W.T)
+        assert not W[o:, :].any() and not W[:, k:].any(), l
+
+
+def test_padding_stays_zero_through_updates(lib):
+    """After set_params, after AdamW steps with caller gradients and after
+    on-device training, the padded weight copies hold BF16(master) in their
+    [out][in] corner and 0 elsewhere."""
+    import torch
+    flat = _rounded_params(51)
+    net = lib.MLP()
+    net.set_params(flat.astype(np.float32))
+    _check_padded_weights(net, net.get_params())
+    rng = np.random.Generator(np.random.PCG64(52))
+    for _ in range(3):
+        net.apply_grads(rng.normal(0, 1e-2, size=flat.size).astype(np.float32), lr=1e-2,
+                        weight_decay=0.01)
+    _check_padded_weights(net, net.get_params())
+    x, v, jam = _batch(300, 53)
+    t = lambda a: torch.tensor(a, dtype=torch.float32, device="cuda")
+    net.train(t(x), t(v), t(jam), 25, 128, lr=1e-2, weight_decay=1e-3, seed=7)
+    _check_padded_weights(net, net.get_params())
     net.close()
 
 

@@ -39,12 +39,16 @@ def test_phase_runs_match_oracle(lib):
         np.testing.assert_array_equal(got[0], want[0])
         np.testing.assert_allclose(got[1], want[1], rtol=1e-12, atol=0)
         np.testing.assert_array_equal(got[2], want[2])
-        if N > 64:  # the same runs with a given tiling for the concurrent lattices
-            got = phase._runs_single(N, dens, seeds, T, window, None, chunk=300,
-                                     tiling=(8, 16, 1))
-            np.testing.assert_array_equal(got[0], want[0])
-            np.testing.assert_allclose(got[1], want[1], rtol=1e-12, atol=0)
-            np.testing.assert_array_equal(got[2], want[2])
+        if N > 64:
+            # the same runs with a given tiling for the concurrent lattices,
+            # the shipped one of the full diagram included (depth 8, 64-row
+            # bands: a 96-row lattice is cut into two bands)
+            for tiling in [(8, 16, 1), tuple(phase.FULL["single_tiling"])]:
+                got = phase._runs_single(N, dens, seeds, T, window, None, chunk=300,
+                                         tiling=tiling)
+                np.testing.assert_array_equal(got[0], want[0])
+                np.testing.assert_allclose(got[1], want[1], rtol=1e-12, atol=0)
+                np.testing.assert_array_equal(got[2], want[2])
     curves = phase.phase_diagram([32, 96], dens, 4, T, window, ensemble_max_n=64,
                                  single_seeds=2)
     for N, S in [(32, 4), (96, 2)]:
