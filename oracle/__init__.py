@@ -55,6 +55,9 @@ def _load():
             lib.oracle_threshold.restype = u64
             lib.oracle_init.argtypes = [vp, i64, i64, u64, dbl, dbl]
             lib.oracle_init.restype = ctypes.c_int
+            lib.oracle_init_window.argtypes = [vp, i64, i64, i64, i64, i64, i64, u64, dbl,
+                                               dbl]
+            lib.oracle_init_window.restype = ctypes.c_int
             lib.oracle_run.argtypes = [vp, i64, i64, i64, vp, vp, ctypes.c_int]
             lib.oracle_run.restype = ctypes.c_int
             lib.oracle_phase.argtypes = [vp, vp, i64, i64, ctypes.c_int]
@@ -89,6 +92,17 @@ def init(M: int, N: int, seed: int, p_lr: float, p_tb: float) -> np.ndarray:
     if rc != 0:
         raise ValueError("oracle_init rejected its arguments")
     return g
+
+
+def init_window(i0: int, j0: int, R: int, C: int, M: int, N: int, seed: int, p_lr: float,
+                p_tb: float) -> np.ndarray:
+    """Rows i0..i0+R-1 and columns j0..j0+C-1 (mod M, N) of the seeded
+    placement of an M x N lattice, uint8 (R, C)."""
+    w = np.empty((R, C), dtype=np.uint8)
+    rc = _load().oracle_init_window(_ptr(w), R, C, i0, j0, M, N, seed, p_lr, p_tb)
+    if rc != 0:
+        raise ValueError("oracle_init_window rejected its arguments")
+    return w
 
 
 def run(g: np.ndarray, K: int, threads: int = 1):

@@ -98,6 +98,35 @@ int oracle_init(uint8_t *g, int64_t M, int64_t N, uint64_t seed,
     return 0;
 }
 
+/* Fill w (R*C bytes, row-major) with the cells of rows i0..i0+R-1 and
+ * columns j0..j0+C-1 (both mod M, N) of the seeded placement of an M x N
+ * lattice: the same cells oracle_init would write there, for a window of a
+ * lattice too large to hold whole. */
+int oracle_init_window(uint8_t *w, int64_t R, int64_t C, int64_t i0, int64_t j0,
+                       int64_t M, int64_t N, uint64_t seed, double p_lr, double p_tb)
+{
+    if (!w || M <= 0 || N <= 0 || R <= 0 || C <= 0 || i0 < 0 || j0 < 0) return -1;
+    if (!(p_lr >= 0.0 && p_tb >= 0.0 && p_lr + p_tb <= 1.0)) return -1;
+    const uint64_t t_lr = oracle_threshold(p_lr);
+    const uint64_t t_tb = oracle_threshold(p_tb);
+    for (int64_t a = 0; a < R; a++) {
+        const int64_t i = (i0 + a) % M;
+        for (int64_t b = 0; b < C; b++) {
+            const int64_t j = (j0 + b) % N;
+            const uint64_t u = oracle_splitmix64(seed, (uint64_t)(i * N + j) + 1);
+            uint8_t c;
+            if (u < t_lr)
+                c = LR;
+            else if (u - t_lr < t_tb)
+                c = TB;
+            else
+                c = EMPTY;
+            w[a * C + b] = c;
+        }
+    }
+    return 0;
+}
+
 /* Horizontal phase over all rows: next = H(cur); returns LR cars moved. */
 static int64_t horizontal_phase(const uint8_t *cur, uint8_t *next,
                                 int64_t M, int64_t N, int threads)

@@ -1,0 +1,158 @@
+"""Write the oracle's results for the full-size workloads into tests/golden/.
+
+Calls only the oracle (and the shared seeded input generators, which hold
+none of the automaton's arithmetic); nothing here runs or reads the CUDA
+library.  The GPU tests compare their full-length runs with these files.
+The lattices themselves are too large to store, so each run is recorded by
+the SHA-256 of its final lattice (M*N bytes, row-major, 0/1/2) and of its
+count traces (moved_lr then moved_tb, int64 little-endian), plus a few plain
+numbers for diagnostics.
+
+    python tests/golden/make_oracle_refs.py [4096] [windows] [ensemble]
+
+With no argument all three files are written.  On 8 host threads the 4096^2
+runs take about 30 minutes, the windows about 2 and the ensemble subset
+about 20.
+
+- oracle_4096_runs.json: the single-lattice workload 4096 x 4096, densities
+  0.20, 0.35, 0.50 split evenly between LR and TB, seeds 1-3, 4096 steps,
+  placement by the seeded rule (every cell independently LR w.p. rho/2, TB
+  w.p. rho/2).
+- oracle_32768_windows.json: the 32768 x 32768 lattice at density 0.38,
+  seed 1, after t = 1024 steps, sampled through windows: the state of a
+  cell after t steps depends only on the cells within t rows and t columns
+  of it (one cell per phase at most), so the oracle run for t steps on a
+  (2t + 33) x (2t + 33) window of the initial lattice, wrapped as its own
+  torus, gives the exact state of the window's 33 x 33 centre.  Eight
+  windows; the first straddles both wrap seams.
+- oracle_ensemble_subset.json: 32 lattices of the batched-ensemble workload
+  (4096 lattices, M, N uniform on {64..2048}, density uniform on [0.1, 0.6],
+  LR fraction uniform on [0.3, 0.7], numpy PCG64 seed 1; lattice l uses
+  placement seed l + 1), one at each of 32 evenly spaced quantiles of the
+  cell count, run for the full 10^4 steps; with the first step index at
+  which no car moved (-1 if none).
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import oracle  # noqa: E402
+from paper_1804_07981_b300.inputs import ensemble_params  # noqa: E402
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+THREADS = os.cpu_count() or 1
+
+
+def digest(a: np.ndarray) -> str:
+    return hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()
+
+
+def count_digest(lr: np.ndarray, tb: np.ndarray) -> str:
+    return digest(np.concatenate([lr.astype("<i8"), tb.astype("<i8")]))
+
+
+def record(g, lr, tb) -> dict:
+    tot = lr + tb
+    zero = np.flatnonzero(tot == 0)
+    return {"lattice_sha256": digest(g), "counts_sha256": count_digest(lr, tb),
+            "lr_sum": int(lr.sum()), "tb_sum": int(tb.sum()),
+            "lr_last": int(lr[-1]), "tb_last": int(tb[-1]),
+            "first_zero_step": int(zero[0]) if zero.size else -1}
+
+
+def runs_4096(path):
+    M = N = 4096
+    K = 4096
+    out = {"M": M, "N": N, "steps": K, "runs": []}
+    for rho in (0.20, 0.35, 0.50):
+        for seed in (1, 2, 3):
+            t = time.time()
+            g0 = oracle.init(M, N, seed, rho / 2, rho / 2)
+            g, lr, tb = oracle.run(g0, K, threads=THREADS)
+            rec = {"rho": rho, "seed": seed}
+            rec.update(record(g, lr, tb))
+            out["runs"].append(rec)
+            print("4096^2 rho %.2f seed %d: %.0f s" % (rho, seed, time.time() - t), flush=True)
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1)
+
+
+WINDOW_T = 1024
+WINDOW_CORE = 33
+
+
+def window_corners(M, N):
+    rng = np.random.Generator(np.random.PCG64(1024))
+    corners = rng.integers(0, M, size=(8, 2))
+    half = WINDOW_T + WINDOW_CORE // 2
+    corners[0] = [M - half, N - half]  # the centre sits on both wrap seams
+    return [(int(i), int(j)) for i, j in corners]
+
+
+def windows_32768(path):
+    M = N = 32768
+    t, c = WINDOW_T, WINDOW_CORE
+    S = 2 * t + c
+    out = {"M": M, "N": N, "rho": 0.38, "seed": 1, "steps": t, "window": S, "centre": c,
+           "windows": []}
+    for i0, j0 in window_corners(M, N):
+        tic = time.time()
+        w = oracle.init_window(i0, j0, S, S, M, N, 1, 0.19, 0.19)
+        w_t, _, _ = oracle.run(w, t, threads=THREADS)
+        core = w_t[t:t + c, t:t + c]
+        out["windows"].append({"i0": i0, "j0": j0,
+                               "centre_rows": ["".join(str(int(v)) for v in r) for r in core]})
+        print("window (%d, %d): %.0f s" % (i0, j0, time.time() - tic), flush=True)
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1)
+
+
+ENS_STEPS = 10000
+
+
+def ensemble_subset_indices(p, count=32):
+    cells = p["M"] * p["N"]
+    order = np.argsort(cells, kind="stable")
+    q = ((np.arange(count) + 0.5) / count * len(order)).astype(np.int64)
+    return sorted(int(order[k]) for k in q)
+
+
+def ensemble_subset(path):
+    p = ensemble_params(4096, seed=1)
+    idx = ensemble_subset_indices(p)
+    out = {"workload": "ensemble_params(4096, seed=1)", "steps": ENS_STEPS, "lattices": []}
+    for l in idx:
+        tic = time.time()
+        M, N = int(p["M"][l]), int(p["N"][l])
+        g0 = oracle.init(M, N, int(p["seed"][l]), float(p["p_lr"][l]), float(p["p_tb"][l]))
+        g, lr, tb = oracle.run(g0, ENS_STEPS, threads=THREADS)
+        rec = {"index": l, "M": M, "N": N}
+        rec.update(record(g, lr, tb))
+        out["lattices"].append(rec)
+        print("lattice %d (%d x %d): %.0f s" % (l, M, N, time.time() - tic), flush=True)
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1)
+
+
+def main(argv):
+    which = set(argv) or {"4096", "windows", "ensemble"}
+    if "windows" in which:
+        windows_32768(os.path.join(HERE, "oracle_32768_windows.json"))
+    if "ensemble" in which:
+        ensemble_subset(os.path.join(HERE, "oracle_ensemble_subset.json"))
+    if "4096" in which:
+        runs_4096(os.path.join(HERE, "oracle_4096_runs.json"))
+
+
+if __name__ == "__main__":
+    main(sys.argv[1:])
