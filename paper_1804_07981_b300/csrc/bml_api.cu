@@ -93,6 +93,7 @@ struct bml_sim {
   DevBuf planes[2];  // each: L then T, M*P words apiece
   DevBuf bytes[2];
   int cur = 0;
+  bool pair_layout = false;  // planes[cur] in the pair-interleaved layout (else plain)
   DevBuf counts;  // cap u64 LR counts, then cap u64 TB counts
   int64_t cap = 0;
   int64_t steps_done = 0;
@@ -179,10 +180,26 @@ int grow_counts(bml_sim *s, int64_t need) {
   return BML_OK;
 }
 
+// Bring the current planes into the layout the next kernel reads: the
+// pair-interleaved one for the two-words-per-lane Model I kernel, the plain
+// one for every other kernel and for unpacking (one in-place pass).
+int set_layout(bml_sim *s, bool pair) {
+  if (s->pair_layout == pair) return BML_OK;
+  CUDA_TRY(launch_pair_layout(plane_L(s, s->cur), plane_T(s, s->cur), s->g, pair, s->st));
+  s->pair_layout = pair;
+  return BML_OK;
+}
+
 // Enqueue `k` steps with the configured model and kernel.  lr/tb point at
 // the count slots of the first step, whose index is t0 (Model II tie-breaks).
 int enqueue_steps(bml_sim *s, int64_t k, u64 *lr, u64 *tb, bool commit, int64_t t0 = 0) {
   const Geom &g = s->g;
+  if (uses_planes(s->kernel)) {
+    const bool pair = s->model == BML_MODEL_I && s->lane_words == 2 && s->band_rows != 0 &&
+                      s->kernel != BML_KERNEL_BITPLANE;
+    int rc = set_layout(s, pair);
+    if (rc) return rc;
+  }
   if (s->model == BML_MODEL_II) {
     int64_t done = 0;
     while (done < k) {
@@ -692,6 +709,8 @@ namespace {
 // Enqueue: current state -> bytes with pitch PB in `dst` (device).
 int state_to_pitched(bml_sim *s, uint8_t *dst) {
   if (uses_planes(s->kernel)) {
+    int rc = set_layout(s, false);
+    if (rc) return rc;
     CUDA_TRY(launch_unpack(plane_L(s, s->cur), plane_T(s, s->cur), dst, s->g, s->st));
   } else {
     CUDA_TRY(cudaMemcpyAsync(dst, s->bytes[0].ptr, (size_t)(s->g.M * s->g.PB),
@@ -760,6 +779,7 @@ int write_impl(bml_sim *s, const uint8_t *in, cudaMemcpyKind kind) {
   }
   if (uses_planes(s->kernel)) {
     s->cur = other;
+    s->pair_layout = false;  // packed in the plain layout
   } else {
     void *t = s->bytes[0].ptr;
     s->bytes[0].ptr = s->bytes[1].ptr;

@@ -5,11 +5,15 @@
 // per stage, the TB cars entering a row being the previous row's TB move
 // mask), but lane l of a warp holds one aligned pair of ring words: pair
 // first-1+l of the W/2 pairs of the row (W even), read and written with
-// 128-bit accesses.  The shift between the two words of a lane is an
-// in-register funnel shift; lanes 0 and owned+1 hold halo pairs (a 128-column
-// cone), lanes 1..owned are stored and counted (up to 30 pairs per warp).
-// Per stage and row a lane makes two 32-bit shuffles for two words: the right
-// lane's low half of E and the left lane's high half of the LR move mask.
+// 128-bit accesses.  For the paper's model the planes are kept in the
+// pair-interleaved layout (launch_pair_layout: the pair's even columns in
+// its first word, the odd columns in its second), so that a cell's right
+// neighbour is mostly the same bit of the other word and the horizontal rule
+// needs half the shifts of the plain layout; lanes 0 and owned+1 hold halo
+// pairs (a 128-column cone), lanes 1..owned are stored and counted (up to 30
+// pairs per warp).  Per stage and row a lane makes two 32-bit shuffles for
+// two words: the right lane's low half of E (even columns) and the left
+// lane's high half of the odd columns' LR move mask.
 //
 // Moved-car counts: one 32-bit register per stage and lane holds the LR moves
 // in its low 16 bits and the TB moves in its high 16 bits (a lane moves at
@@ -24,7 +28,7 @@
 //
 // MODEL = 2 runs the Model II rule of model2_step.cu (one synchronous phase,
 // tie-break words from the step, row and word indices) on the same
-// structure: per stage and row a lane draws the two tie-break words of its
+// structure, in the plain layout: per stage and row a lane draws the two tie-break words of its
 // pair, shuffles the left lane's last L cell and bit 0 of the right lane's
 // inLR, and the state word handed on is inTB instead of mvV.
 #include "stage.cuh"
@@ -48,20 +52,29 @@ struct PairState {
 __device__ __forceinline__ uint32_t fsr(uint32_t lo, uint32_t hi) { return __funnelshift_r(lo, hi, 1); }
 __device__ __forceinline__ uint32_t fsl(uint32_t lo, uint32_t hi) { return __funnelshift_l(lo, hi, 1); }
 
-// One stage on the word pair (a, b) of this lane; see stage.cuh for the rule.
+// One stage on the word pair (a, b) of this lane in the column-interleaved
+// layout of the pair (word a holds the pair's even columns, bit i = column
+// 2i of the pair's 128; word b the odd ones, bit i = column 2i + 1); see
+// stage.cuh for the rule.  The right neighbour of even column 2i is odd
+// column 2i + 1, the same bit of b, so the even cells' move mask needs no
+// shift: mHa = La & ~(Lb | Tb), and the cars entering the odd cells are
+// exactly mHa.  Only the odd cells' right neighbours (a shifted one bit, the
+// right lane's column 0 entering at bit 63) and the even cells' entering
+// cars (mHb shifted one bit, the left lane's column 127 entering at bit 0)
+// need shifts: 4 funnel shifts per pair and stage instead of 8 in the plain
+// layout.
 __device__ __forceinline__ void stage_pair(u64 &La, u64 &Lb, u64 &Ta, u64 &Tb,
                                            const PairState &st, PairState &nx, int src_l,
                                            int src_r, uint32_t &cnt, bool cnt_h,
                                            bool cnt_v) {
-  const u64 Ea = ~(La | Ta), Eb = ~(Lb | Tb);
+  const u64 Ea = ~(La | Ta);
   const uint32_t rr = __shfl_sync(BML_FULL_MASK, lo32(Ea), src_r);
-  const u64 Era = mk64(fsr(lo32(Ea), hi32(Ea)), fsr(hi32(Ea), lo32(Eb)));
-  const u64 Erb = mk64(fsr(lo32(Eb), hi32(Eb)), fsr(hi32(Eb), rr));
-  const u64 mHa = La & Era, mHb = Lb & Erb;
+  const u64 mHa = La & ~(Lb | Tb);
+  const u64 Erb = mk64(fsr(lo32(Ea), hi32(Ea)), fsr(hi32(Ea), rr));
+  const u64 mHb = Lb & Erb;
   const uint32_t rl = __shfl_sync(BML_FULL_MASK, hi32(mHb), src_l);
-  const u64 ina = mk64(fsl(rl, lo32(mHa)), fsl(lo32(mHa), hi32(mHa)));
-  const u64 inb = mk64(fsl(hi32(mHa), lo32(mHb)), fsl(lo32(mHb), hi32(mHb)));
-  const u64 Lha = La ^ mHa ^ ina, Lhb = Lb ^ mHb ^ inb;
+  const u64 ina = mk64(fsl(rl, lo32(mHb)), fsl(lo32(mHb), hi32(mHb)));
+  const u64 Lha = La ^ mHa ^ ina, Lhb = Lb ^ mHb ^ mHa;
   const u64 mVa = st.Ta & ~(Lha | Ta), mVb = st.Tb & ~(Lhb | Tb);
   const u64 oTa = (st.Ta & ~mVa) | st.Ma, oTb = (st.Tb & ~mVb) | st.Mb;
   if (cnt_h) cnt += popc64(mHa) + popc64(mHb);
@@ -125,13 +138,79 @@ __device__ __forceinline__ void flush_counts(uint32_t (&cnt)[K], bool own, int l
   }
 }
 
+// Per-warp constants and running positions of a tile.
+struct PairTile {
+  const u64 *Lin, *Tin;
+  u64 *Lout, *Tout;
+  size_t pitch, roff;  // row pitch in words, offset of the next row to fetch
+  int ld_row, M;       // lattice row of the next row to fetch
+  int wa;              // first word of this lane's pair
+  int r0, B, n_in;     // band start, band rows, input rows (B + 2K)
+  int src_l, src_r;
+  bool own;
+  u64 W64, MW, nbase, tie_seed;  // Model II tie-break counters
+  int x0;                        // lattice row of the current input row (Model II)
+};
+
+// Input row i of the tile through the K stages: prefetch row i + kAhead into
+// the ring, read row i, run the stages, store the emitted row.  GUARD: rows
+// near the band's ends, where a stage's row may lie outside the band (not
+// counted), no row may be emitted yet, or the input may be exhausted.  In the
+// steady part of a band (GUARD false) every stage counts and a row is stored.
+template <int K, int MODEL, bool GUARD, int U>
+__device__ __forceinline__ void pair_row(PairTile &t, RingSlot *ring, int lane, int i,
+                                         PairState (&st)[2][K], uint32_t (&cnt)[K]) {
+  if (GUARD && i >= t.n_in) return;
+  // unguarded rows lie below B + K, so row i + kAhead exists when K >= kAhead
+  if ((!GUARD && K >= kAhead) || i + kAhead < t.n_in) {
+    const int sl = (i + kAhead) & (kRing - 1);
+    cp_async16(&ring[sl][0][lane], t.Lin + t.roff + t.wa);
+    cp_async16(&ring[sl][1][lane], t.Tin + t.roff + t.wa);
+    if (++t.ld_row == t.M) {
+      t.ld_row = 0;
+      t.roff = 0;
+    } else {
+      t.roff += t.pitch;
+    }
+  }
+  cp_async_commit();
+  cp_async_wait<kAhead>();  // row i has landed
+  const ulonglong2 vL = ring[i & (kRing - 1)][0][lane];
+  const ulonglong2 vT = ring[i & (kRing - 1)][1][lane];
+  u64 La = vL.x, Lb = vL.y, Ta = vT.x, Tb = vT.y;
+#pragma unroll
+  for (int s = 0; s < K; ++s) {
+    const bool ch = !GUARD || (unsigned)(i - K - s) < (unsigned)t.B;
+    const bool cv = !GUARD || (unsigned)(i - K - s - 1) < (unsigned)t.B;
+    if constexpr (MODEL == 2) {
+      int x = t.x0 - s;  // lattice row of this stage's row
+      while (x < 0) x += t.M;
+      const u64 n = t.nbase + (u64)s * t.MW + (u64)x * t.W64;
+      stage_pair_m2(La, Lb, Ta, Tb, st[U][s], st[U ^ 1][s], t.src_l, t.src_r, cnt[s], ch, cv,
+                    splitmix64_at(t.tie_seed, n), splitmix64_at(t.tie_seed, n + 1));
+    } else {
+      stage_pair(La, Lb, Ta, Tb, st[U][s], st[U ^ 1][s], t.src_l, t.src_r, cnt[s], ch, cv);
+    }
+  }
+  if constexpr (MODEL == 2) {
+    if (++t.x0 == t.M) t.x0 = 0;
+  }
+  if (!GUARD || i >= 2 * K) {
+    const size_t off = (size_t)(t.r0 + i - 2 * K) * t.pitch;
+    if (t.own) {
+      st2(t.Lout + off + t.wa, La, Lb);
+      st2(t.Tout + off + t.wa, Ta, Tb);
+    }
+  }
+}
+
 template <int K, int MODEL>
 __global__ void __launch_bounds__(kWarps2 * 32, K >= 8 ? 2 : 3)
     stream2_kernel(const u64 *__restrict__ Lin, const u64 *__restrict__ Tin,
                    u64 *__restrict__ Lout, u64 *__restrict__ Tout, Geom g, int n_strips,
                    int base, int rem, int band_rows, int n_bands, u64 *__restrict__ moved_lr,
                    u64 *__restrict__ moved_tb, u64 tie_seed, u64 t0) {
-  constexpr int P = kChunk;
+  static_assert(kChunk == 2, "the row loops take two rows per turn");
   __shared__ unsigned long long s_cnt[2 * K];
   __shared__ __align__(16) ulonglong2 s_ring[kWarps2][kRing][2][32];  // [warp][slot][plane][lane]
   for (int t = threadIdx.x; t < 2 * K; t += blockDim.x) s_cnt[t] = 0;
@@ -151,94 +230,70 @@ __global__ void __launch_bounds__(kWarps2 * 32, K >= 8 ? 2 : 3)
     const int WP = (int)(g.W / 2);
     int pw = (first - 1 + lane) % WP;
     if (pw < 0) pw += WP;
-    const int wa = 2 * pw;
+    PairTile t;
+    t.Lin = Lin;
+    t.Tin = Tin;
+    t.Lout = Lout;
+    t.Tout = Tout;
+    t.wa = 2 * pw;
     own = lane >= 1 && lane <= owned;
-    const int src_l = lane > 0 ? lane - 1 : 0, src_r = lane < 31 ? lane + 1 : 31;
-
-    const int r0 = band * band_rows;
-    const int B = r0 + band_rows < g.M ? band_rows : (int)g.M - r0;
-    const int n_in = B + 2 * K;
-    const int M = (int)g.M;
-    int ld_row = (r0 - K) % M;
-    if (ld_row < 0) ld_row += M;
-    const size_t pitch = (size_t)g.P;
-    size_t roff = (size_t)ld_row * pitch;
+    t.own = own;
+    t.src_l = lane > 0 ? lane - 1 : 0;
+    t.src_r = lane < 31 ? lane + 1 : 31;
+    t.r0 = band * band_rows;
+    t.B = t.r0 + band_rows < g.M ? band_rows : (int)g.M - t.r0;
+    t.n_in = t.B + 2 * K;
+    t.M = (int)g.M;
+    t.ld_row = (t.r0 - K) % t.M;
+    if (t.ld_row < 0) t.ld_row += t.M;
+    t.pitch = (size_t)g.P;
+    t.roff = (size_t)t.ld_row * t.pitch;
     // Model II tie-break counters: n = t*M*W + x*W + w + 1 for word w of row x
-    const u64 W64 = (u64)g.W, MW = (u64)g.M * W64;
-    const u64 nbase = t0 * MW + (u64)wa + 1;
-    int x0 = ld_row;  // lattice row of input row i (stage 0)
+    t.W64 = (u64)g.W;
+    t.MW = (u64)g.M * t.W64;
+    t.nbase = t0 * t.MW + (u64)t.wa + 1;
+    t.tie_seed = tie_seed;
+    t.x0 = t.ld_row;  // lattice row of input row i (stage 0)
 
-    PairState st[2][K];  // state sets, alternated row by row (P is even)
+    PairState st[2][K];  // state sets, alternated row by row
 #pragma unroll
     for (int s = 0; s < K; ++s) st[0][s] = st[1][s] = PairState{0, 0, 0, 0, 0, 0};
 
-    ulonglong2 (*ring)[2][32] = s_ring[threadIdx.x >> 5];
+    RingSlot *ring = s_ring[threadIdx.x >> 5];
     // rows 0 .. kAhead-1 in flight, one commit group per row (empty past n_in)
 #pragma unroll
     for (int u = 0; u < kAhead; ++u) {
-      if (u < n_in) {
-        cp_async16(&ring[u][0][lane], Lin + roff + wa);
-        cp_async16(&ring[u][1][lane], Tin + roff + wa);
-        if (++ld_row == M) {
-          ld_row = 0;
-          roff = 0;
+      if (u < t.n_in) {
+        cp_async16(&ring[u][0][lane], Lin + t.roff + t.wa);
+        cp_async16(&ring[u][1][lane], Tin + t.roff + t.wa);
+        if (++t.ld_row == t.M) {
+          t.ld_row = 0;
+          t.roff = 0;
         } else {
-          roff += pitch;
+          t.roff += t.pitch;
         }
       }
       cp_async_commit();
     }
-    for (int i0 = 0; i0 < n_in; i0 += P) {
-      if ((i0 & 255) == 0 && i0 > 0) flush_counts<K>(cnt, own, lane, s_cnt);
-      const bool steady = i0 >= 2 * K && i0 + P <= B + K;
-#pragma unroll
-      for (int u = 0; u < P; ++u) {
-        const int i = i0 + u;
-        if (steady || i < n_in) {
-          if (i + kAhead < n_in) {
-            const int sl = (i + kAhead) & (kRing - 1);
-            cp_async16(&ring[sl][0][lane], Lin + roff + wa);
-            cp_async16(&ring[sl][1][lane], Tin + roff + wa);
-            if (++ld_row == M) {
-              ld_row = 0;
-              roff = 0;
-            } else {
-              roff += pitch;
-            }
-          }
-          cp_async_commit();
-          cp_async_wait<kAhead>();  // row i has landed
-          const ulonglong2 vL = ring[i & (kRing - 1)][0][lane];
-          const ulonglong2 vT = ring[i & (kRing - 1)][1][lane];
-          u64 La = vL.x, Lb = vL.y, Ta = vT.x, Tb = vT.y;
-#pragma unroll
-          for (int s = 0; s < K; ++s) {
-            if constexpr (MODEL == 2) {
-              int x = x0 - s;  // lattice row of this stage's row
-              while (x < 0) x += M;
-              const u64 n = nbase + (u64)s * MW + (u64)x * W64;
-              stage_pair_m2(La, Lb, Ta, Tb, st[u & 1][s], st[(u & 1) ^ 1][s], src_l, src_r,
-                            cnt[s], steady || (unsigned)(i - K - s) < (unsigned)B,
-                            steady || (unsigned)(i - K - s - 1) < (unsigned)B,
-                            splitmix64_at(tie_seed, n), splitmix64_at(tie_seed, n + 1));
-            } else {
-              stage_pair(La, Lb, Ta, Tb, st[u & 1][s], st[(u & 1) ^ 1][s], src_l, src_r, cnt[s],
-                         steady || (unsigned)(i - K - s) < (unsigned)B,
-                         steady || (unsigned)(i - K - s - 1) < (unsigned)B);
-            }
-          }
-          if constexpr (MODEL == 2) {
-            if (++x0 == M) x0 = 0;
-          }
-          if (steady || i >= 2 * K) {
-            const size_t off = (size_t)(r0 + i - 2 * K) * pitch;
-            if (own) {
-              st2(Lout + off + wa, La, Lb);
-              st2(Tout + off + wa, Ta, Tb);
-            }
-          }
-        }
-      }
+    // rows [0, 2K): the pipeline fills (guarded); rows [2K, B + K): every
+    // stage's row lies in the band and a row is emitted (unguarded); the
+    // rest: the pipeline drains (guarded).  Counts are flushed every 256
+    // rows (a 16-bit field holds at most 511 rows of moves).
+    int i = 0;
+    for (; i < 2 * K; i += 2) {
+      pair_row<K, MODEL, true, 0>(t, ring, lane, i, st, cnt);
+      pair_row<K, MODEL, true, 1>(t, ring, lane, i + 1, st, cnt);
+    }
+    const int steady_end = t.B + K;
+    for (; i + 2 <= steady_end; i += 2) {
+      if ((i & 255) == 0) flush_counts<K>(cnt, own, lane, s_cnt);
+      pair_row<K, MODEL, false, 0>(t, ring, lane, i, st, cnt);
+      pair_row<K, MODEL, false, 1>(t, ring, lane, i + 1, st, cnt);
+    }
+    for (; i < t.n_in; i += 2) {
+      if ((i & 255) == 0) flush_counts<K>(cnt, own, lane, s_cnt);
+      pair_row<K, MODEL, true, 0>(t, ring, lane, i, st, cnt);
+      pair_row<K, MODEL, true, 1>(t, ring, lane, i + 1, st, cnt);
     }
   }
   pdl_release();  // this block's lattice work is done
@@ -279,7 +334,66 @@ int occupancy2() {
   return b > 0 ? b : 1;
 }
 
+// Even bits of x to bits 0..31, odd bits to bits 32..63 (the outer perfect
+// unshuffle by five delta swaps, Warren, Hacker's Delight, Sec. 7-2), and
+// its inverse.
+__device__ __forceinline__ u64 delta_swap(u64 x, u64 m, int s) {
+  const u64 t = (x ^ (x >> s)) & m;
+  return x ^ t ^ (t << s);
+}
+__device__ __forceinline__ u64 unshuffle64(u64 x) {
+  x = delta_swap(x, 0x2222222222222222ull, 1);
+  x = delta_swap(x, 0x0C0C0C0C0C0C0C0Cull, 2);
+  x = delta_swap(x, 0x00F000F000F000F0ull, 4);
+  x = delta_swap(x, 0x0000FF000000FF00ull, 8);
+  return delta_swap(x, 0x00000000FFFF0000ull, 16);
+}
+__device__ __forceinline__ u64 shuffle64(u64 x) {
+  x = delta_swap(x, 0x00000000FFFF0000ull, 16);
+  x = delta_swap(x, 0x0000FF000000FF00ull, 8);
+  x = delta_swap(x, 0x00F000F000F000F0ull, 4);
+  x = delta_swap(x, 0x0C0C0C0C0C0C0C0Cull, 2);
+  return delta_swap(x, 0x2222222222222222ull, 1);
+}
+
+// In place, every aligned word pair (A, B) of both planes (columns
+// 128p .. 128p + 127 of a row): plain -> interleaved (to_pair) sets
+// a = even columns, b = odd columns; interleaved -> plain undoes it.
+__global__ void pair_layout_kernel(u64 *__restrict__ L, u64 *__restrict__ T, int64_t pairs,
+                                   int to_pair) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < 2 * pairs;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    u64 *p = (q < pairs ? L : T) + 2 * (q < pairs ? q : q - pairs);
+    const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(p);
+    ulonglong2 o;
+    if (to_pair) {
+      const u64 ua = unshuffle64(v.x), ub = unshuffle64(v.y);
+      o.x = (ua & 0xFFFFFFFFull) | (ub << 32);
+      o.y = (ua >> 32) | (ub & 0xFFFFFFFF00000000ull);
+    } else {
+      o.x = shuffle64((v.x & 0xFFFFFFFFull) | (v.y << 32));
+      o.y = shuffle64((v.x >> 32) | (v.y & 0xFFFFFFFF00000000ull));
+    }
+    *reinterpret_cast<ulonglong2 *>(p) = o;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_pair_layout(u64 *L, u64 *T, const Geom &g, bool to_pair, cudaStream_t st) {
+  if (!stream2_applies(g)) return cudaErrorInvalidValue;
+  const int64_t pairs = g.M * g.P / 2;
+  int dev = 0, sms = 148;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    sms = 148;
+  }
+  int64_t blocks = (2 * pairs + 255) / 256;
+  if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
+  pair_layout_kernel<<<(unsigned)blocks, 256, 0, st>>>(L, T, pairs, to_pair ? 1 : 0);
+  return cudaGetLastError();
+}
 
 bool stream2_applies(const Geom &g) { return g.nb == 64 && g.W % 2 == 0 && g.W > 32; }
 
