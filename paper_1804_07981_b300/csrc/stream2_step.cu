@@ -155,10 +155,12 @@ __device__ __forceinline__ void st_quad(u64 *p, const Quad &v) {
 
 // Per-warp constants and running positions of a tile.
 struct PairTile {
-  const u64 *Lin, *Tin;
-  u64 *Lout, *Tout;
-  size_t pitch, roff;  // row pitch in words, offset of the next row to fetch
-  int ld_row, M;       // lattice row of the next row to fetch
+  const u64 *Lin, *Tin;  // this lane's pair in row 0 of the input planes
+  const u64 *fL;         // this lane's pair in the next row to fetch (L plane)
+  int64_t dT;            // T plane minus L plane, in words (input and output)
+  u64 *sL;               // this lane's pair in the next row to store (L plane)
+  size_t pitch;          // row pitch in words
+  int ld_row, M;         // lattice row of the next row to fetch
   int wa;              // first word of this lane's pair
   int r0, B, n_in;     // band start, band rows, input rows (B + 2K)
   int src_l, src_r;
@@ -169,13 +171,13 @@ struct PairTile {
 
 // Fetch the next input row into ring slot `slot` (one commit group).
 __device__ __forceinline__ void fetch_row(PairTile &t, RingSlot *ring, int lane, int slot) {
-  cp_async16(&ring[slot][0][lane], t.Lin + t.roff + t.wa);
-  cp_async16(&ring[slot][1][lane], t.Tin + t.roff + t.wa);
+  cp_async16(&ring[slot][0][lane], t.fL);
+  cp_async16(&ring[slot][1][lane], t.fL + t.dT);
   if (++t.ld_row == t.M) {
     t.ld_row = 0;
-    t.roff = 0;
+    t.fL = t.Lin;
   } else {
-    t.roff += t.pitch;
+    t.fL += t.pitch;
   }
 }
 
@@ -213,14 +215,13 @@ __device__ __forceinline__ void run_stages(PairTile &t, int i, int x0, Quad &L, 
   }
 }
 
-// Store the row emitted at input row i (band row i - 2K).
-__device__ __forceinline__ void store_row(const PairTile &t, int i2k, const Quad &L,
-                                          const Quad &T) {
-  const size_t off = (size_t)(t.r0 + i2k) * t.pitch;
+// Store the next emitted row (band rows in order).
+__device__ __forceinline__ void store_row(PairTile &t, const Quad &L, const Quad &T) {
   if (t.own) {
-    st_quad(t.Lout + off + t.wa, L);
-    st_quad(t.Tout + off + t.wa, T);
+    st_quad(t.sL, L);
+    st_quad(t.sL + t.dT, T);
   }
+  t.sL += t.pitch;
 }
 
 // One input row near the band's ends (pipeline fill and drain): rows past
@@ -237,7 +238,7 @@ __device__ __forceinline__ void guarded_row(PairTile &t, RingSlot *ring, int lan
   read_row(ring, lane, i, L, T);
   run_stages<K, MODEL, true, U>(t, i, t.x0, L, T, st, cnt);
   if (++t.x0 == t.M) t.x0 = 0;
-  if (i >= 2 * K) store_row(t, i - 2 * K, L, T);
+  if (i >= 2 * K) store_row(t, L, T);
 }
 
 // One input row of the band's steady part (below B + K): every stage's row
@@ -252,7 +253,7 @@ __device__ __forceinline__ void steady_row1(PairTile &t, RingSlot *ring, int lan
   read_row(ring, lane, i, L, T);
   run_stages<K, MODEL, false, U>(t, i, t.x0, L, T, st, cnt);
   if (++t.x0 == t.M) t.x0 = 0;
-  store_row(t, i - 2 * K, L, T);
+  store_row(t, L, T);
 }
 
 // Two input rows i, i + 1 of the band's steady part (both below B + K):
@@ -286,8 +287,8 @@ __device__ __forceinline__ void steady_rows(PairTile &t, RingSlot *ring, int lan
   run_stages<K, MODEL, false, 0>(t, i, x0, L0, T0, st, cnt);
   run_stages<K, MODEL, false, 1>(t, i + 1, x1, L1, T1, st, cnt);
   t.x0 = x1 + 1 == t.M ? 0 : x1 + 1;
-  store_row(t, i - 2 * K, L0, T0);
-  store_row(t, i + 1 - 2 * K, L1, T1);
+  store_row(t, L0, T0);
+  store_row(t, L1, T1);
 }
 
 template <int K, int MODEL>
@@ -317,10 +318,6 @@ __global__ void __launch_bounds__(kWarps2 * 32, K >= 8 ? 2 : 3)
     int pw = (first - 1 + lane) % WP;
     if (pw < 0) pw += WP;
     PairTile t;
-    t.Lin = Lin;
-    t.Tin = Tin;
-    t.Lout = Lout;
-    t.Tout = Tout;
     t.wa = 2 * pw;
     own = lane >= 1 && lane <= owned;
     t.own = own;
@@ -333,7 +330,12 @@ __global__ void __launch_bounds__(kWarps2 * 32, K >= 8 ? 2 : 3)
     t.ld_row = (t.r0 - K) % t.M;
     if (t.ld_row < 0) t.ld_row += t.M;
     t.pitch = (size_t)g.P;
-    t.roff = (size_t)t.ld_row * t.pitch;
+    // the T planes follow the L planes at the same distance in both buffers
+    t.dT = Tin - Lin;
+    t.Lin = Lin + t.wa;
+    t.Tin = Tin + t.wa;
+    t.fL = t.Lin + (size_t)t.ld_row * t.pitch;
+    t.sL = Lout + (size_t)t.r0 * t.pitch + t.wa;
     // Model II tie-break counters: n = t*M*W + x*W + w + 1 for word w of row x
     t.W64 = (u64)g.W;
     t.MW = (u64)g.M * t.W64;
@@ -495,7 +497,8 @@ int stream2_occupancy(int k, int model) {
 cudaError_t launch_stream2(const u64 *Lin, const u64 *Tin, u64 *Lout, u64 *Tout, const Geom &g,
                            int k, int64_t band_rows, u64 *moved_lr, u64 *moved_tb,
                            cudaStream_t st, int model, u64 tie_seed, u64 t0) {
-  if (!stream2_applies(g) || band_rows < 1 || band_rows > INT32_MAX) return cudaErrorInvalidValue;
+  if (!stream2_applies(g) || band_rows < 1 || band_rows > INT32_MAX || Tin - Lin != Tout - Lout)
+    return cudaErrorInvalidValue;
   if (model == 2) {
     switch (k) {
       case 1: return launch2_k<1, 2>(Lin, Tin, Lout, Tout, g, band_rows, moved_lr, moved_tb, tie_seed, t0, st);
