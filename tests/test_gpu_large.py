@@ -1,7 +1,18 @@
-"""Parity at the workloads' full sizes, where the oracle cannot run the whole
-job: exact cross-checks between independent GPU paths, oracle runs on
-sampled windows whose dependency cone fits inside them, and properties that
-hold at any size."""
+"""Parity at the workloads' full sizes.
+
+Against the oracle's own full-length results (tests/golden/oracle_*.json,
+written by tests/golden/make_oracle_refs.py, which runs only the oracle and
+records each final lattice and count trace by its SHA-256): all nine
+4096^2 x 4096-step runs through both the byte-per-cell and the bit-packed
+kernels, the 32768^2 lattice after 1024 steps through eight (2t + 33)^2
+windows in the benchmark's launch configuration, and 32 lattices of the
+ensemble workload for the full 10^4 steps.  Beside them: oracle runs on
+sampled windows computed here, exact cross-checks between independent GPU
+paths, and properties that hold at any size."""
+import hashlib
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -10,6 +21,91 @@ import oracle
 pytestmark = pytest.mark.gpu
 
 EMPTY, LR, TB = 0, 1, 2
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _golden(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+def _digest(a):
+    return hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()
+
+
+def _count_digest(lr, tb):
+    return _digest(np.concatenate([np.asarray(lr).astype("<i8"), np.asarray(tb).astype("<i8")]))
+
+
+@pytest.mark.parametrize("kernel", ["byte", "auto"])
+def test_4096_nine_full_runs_against_oracle(lib, kernel):
+    """Single lattice 4096 x 4096, densities {0.20, 0.35, 0.50} split evenly,
+    seeds 1-3, 4096 steps, placement by the seeded rule: every final lattice
+    and the whole LR / TB count trace of each run equal the oracle's."""
+    ref = _golden("oracle_4096_runs.json")
+    assert len(ref["runs"]) == 9 and ref["steps"] == 4096
+    for r in ref["runs"]:
+        with lib.Lattice(4096, 4096, seed=r["seed"], density=r["rho"], kernel=kernel,
+                         reserve_steps=4096) as sim:
+            sim.step(4096)
+            g = sim.read()
+            _, lr, tb = sim.moved_counts()
+        what = (kernel, r["rho"], r["seed"])
+        assert int(lr.sum()) == r["lr_sum"] and int(tb.sum()) == r["tb_sum"], what
+        assert int(lr[-1]) == r["lr_last"] and int(tb[-1]) == r["tb_last"], what
+        assert _count_digest(lr, tb) == r["counts_sha256"], what
+        assert _digest(g) == r["lattice_sha256"], what
+
+
+@pytest.mark.parametrize("config", ["auto", "depth 8, 251-row bands, two words per lane"])
+def test_32768_windows_after_1024_steps_against_oracle(lib, config):
+    """32768 x 32768, density 0.38, seed 1, 1024 steps in the benchmark's
+    launch configuration (autotuned, and the tiling it picks on a B300 given
+    explicitly): the 33 x 33 centres of eight (2t + 33)^2 windows, one across
+    both wrap seams, equal the oracle's run of each window as its own torus."""
+    ref = _golden("oracle_32768_windows.json")
+    M, N, t, c = ref["M"], ref["N"], ref["steps"], ref["centre"]
+    kw = {} if config == "auto" else {"kernel": "tblock", "block_k": 8}
+    with lib.Lattice(M, N, seed=ref["seed"], density=ref["rho"], reserve_steps=t, **kw) as sim:
+        if config != "auto":
+            sim.set_tiling(8, 251, lane_words=2)
+        sim.step(t)
+        got = sim.read()
+    assert len(ref["windows"]) == 8
+    for w in ref["windows"]:
+        rows = (np.arange(t, t + c) + w["i0"]) % M
+        cols = (np.arange(t, t + c) + w["j0"]) % N
+        want = np.array([[int(ch) for ch in r] for r in w["centre_rows"]], dtype=np.uint8)
+        np.testing.assert_array_equal(got[np.ix_(rows, cols)], want, err_msg=str(w["i0"]))
+
+
+def test_ensemble_workload_32_lattices_full_10000_steps_against_oracle(lib):
+    """The batched-ensemble workload (4096 lattices), autotuned as the
+    benchmark runs it, 10^4 steps: 32 lattices spread over the range of
+    sizes (N mod 64 != 0 included) end with the oracle's lattice and count
+    trace, and the jam steps of the early-exit ensemble equal the oracle's
+    first step with no move."""
+    from paper_1804_07981_b300.inputs import ensemble_params
+    ref = _golden("oracle_ensemble_subset.json")
+    K = ref["steps"]
+    p = ensemble_params(4096, seed=1)
+    recs = ref["lattices"]
+    assert len(recs) == 32 and any(r["N"] % 64 for r in recs)
+    for flags in (0, lib.BML_ENS_EARLY_EXIT):
+        with lib.Ensemble(p["M"], p["N"], p["seed"], p["p_lr"], p["p_tb"], flags=flags,
+                          reserve_steps=K) as ens:
+            ens.step(K)
+            jam = ens.jam_steps()
+            for r in recs:
+                l = r["index"]
+                assert (int(p["M"][l]), int(p["N"][l])) == (r["M"], r["N"])
+                _, lr, tb = ens.moved_counts(l)
+                assert _count_digest(lr, tb) == r["counts_sha256"], (flags, l)
+                assert _digest(ens.read(l)) == r["lattice_sha256"], (flags, l)
+                if flags:
+                    assert jam[l] == r["first_zero_step"], l
+    assert any(r["first_zero_step"] >= 0 for r in recs)
+    assert any(r["first_zero_step"] < 0 for r in recs)
 
 
 @pytest.mark.parametrize("rho", [0.20, 0.35, 0.50])

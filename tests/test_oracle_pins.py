@@ -309,6 +309,28 @@ def test_init_definition_and_frequencies():
     assert not np.any(oracle.init(8, 8, 3, 0.0, 0.0))
 
 
+def test_init_window_is_the_wrapped_slice_of_the_placement():
+    """A window of the seeded placement (used for lattices too large to hold)
+    equals the wrapped slice of the whole lattice, across both seams; cells
+    re-derived one by one from the rule agree."""
+    M, N, seed, p_lr, p_tb = 37, 53, 5, 0.2, 0.3
+    g = oracle.init(M, N, seed, p_lr, p_tb)
+    for i0, j0, R, C in [(30, 40, 20, 25), (0, 0, M, N), (36, 52, 3, 4), (5, 7, 80, 120)]:
+        w = oracle.init_window(i0, j0, R, C, M, N, seed, p_lr, p_tb)
+        rows = (np.arange(R) + i0) % M
+        cols = (np.arange(C) + j0) % N
+        np.testing.assert_array_equal(w, g[np.ix_(rows, cols)])
+    # a window of a lattice too large to build: cells from the rule directly
+    M, N = 1 << 20, 1 << 20
+    t_lr, t_tb = oracle.threshold(p_lr), oracle.threshold(p_tb)
+    w = oracle.init_window(M - 2, N - 3, 4, 5, M, N, seed, p_lr, p_tb)
+    for a in range(4):
+        for b in range(5):
+            i, j = (M - 2 + a) % M, (N - 3 + b) % N
+            u = oracle.splitmix64(seed, i * N + j + 1)
+            assert w[a, b] == (LR if u < t_lr else (TB if u - t_lr < t_tb else EMPTY))
+
+
 def test_threaded_oracle_identical():
     g = random_lattice(257, 300, 5, 0.19, 0.19)
     a, alr, atb = oracle.run(g, 25, threads=1)

@@ -1,0 +1,60 @@
+"""The stored full-length oracle results (tests/golden/oracle_*.json) are
+what the committed script computes from the oracle: their layout is
+checked, and the cheapest record (the smallest lattice of the ensemble
+subset, 10^4 steps) is recomputed here from the oracle alone."""
+import importlib.util
+import json
+import os
+
+import numpy as np
+
+import oracle
+from paper_1804_07981_b300.inputs import ensemble_params
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _script():
+    spec = importlib.util.spec_from_file_location(
+        "make_oracle_refs", os.path.join(GOLDEN, "make_oracle_refs.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def _load(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+def test_golden_files_cover_the_workloads():
+    runs = _load("oracle_4096_runs.json")
+    assert sorted((r["rho"], r["seed"]) for r in runs["runs"]) == \
+        [(rho, s) for rho in (0.20, 0.35, 0.50) for s in (1, 2, 3)]
+    win = _load("oracle_32768_windows.json")
+    t, c, M = win["steps"], win["centre"], win["M"]
+    assert (t, c, win["window"]) == (1024, 33, 2 * 1024 + 33) and len(win["windows"]) == 8
+    w0 = win["windows"][0]
+    # the first window's centre crosses both wrap seams
+    assert w0["i0"] + t < M <= w0["i0"] + t + c - 1 and w0["j0"] + t < M <= w0["j0"] + t + c - 1
+    for w in win["windows"]:
+        assert len(w["centre_rows"]) == c and all(len(r) == c for r in w["centre_rows"])
+    ens = _load("oracle_ensemble_subset.json")
+    mod = _script()
+    p = ensemble_params(4096, seed=1)
+    assert [r["index"] for r in ens["lattices"]] == mod.ensemble_subset_indices(p)
+
+
+def test_smallest_ensemble_record_recomputes_from_the_oracle():
+    mod = _script()
+    ens = _load("oracle_ensemble_subset.json")
+    rec = min(ens["lattices"], key=lambda r: r["M"] * r["N"])
+    p = ensemble_params(4096, seed=1)
+    l = rec["index"]
+    g0 = oracle.init(rec["M"], rec["N"], int(p["seed"][l]), float(p["p_lr"][l]),
+                     float(p["p_tb"][l]))
+    g, lr, tb = oracle.run(g0, ens["steps"], threads=os.cpu_count() or 1)
+    got = mod.record(g, lr, tb)
+    for key, val in got.items():
+        assert rec[key] == val, key
+    assert isinstance(rec["first_zero_step"], int) and np.all(lr >= 0)
