@@ -41,6 +41,7 @@
 #include <mutex>
 #include <set>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/bml.h"
@@ -145,26 +146,64 @@ __device__ bool grid_barrier(EnsCtrl *ctrl, unsigned target, long long timeout_n
   return s_ok != 0;
 }
 
-// Rows per unrolled chunk of the row loop (even: the stage state sets
-// alternate by row).
-template <int K>
-struct PFE {
-  static constexpr int value = K >= 4 ? 2 : 4;
-};
-
 // Input rows reach a warp through a ring of kEnsRing row slots in shared
 // memory (stage.cuh), filled kEnsAhead rows ahead with cp.async.cg: through
 // L2, so the words other blocks wrote in the previous chunk are seen.  A slot
 // is refilled two rows after it was last read.
 constexpr int kEnsRing = 8;
-constexpr int kEnsAhead = 6;
-static_assert(kEnsAhead <= kEnsRing - 2 && (kEnsRing & (kEnsRing - 1)) == 0, "ring layout");
+constexpr int kEnsAhead = 5;
+// a slot is refilled at least two rows after it was last read, also when the
+// steady loop fetches two rows at once
+static_assert(kEnsAhead + 1 <= kEnsRing - 2 && (kEnsRing & (kEnsRing - 1)) == 0, "ring layout");
 using EnsRing = RingSlot[kEnsRing];
+
+// Running position of a lane in its band: the next input row to fetch (with
+// wrap-around at the lattice's last row) and the next output row to store.
+struct EnsCursor {
+  const u64 *Lp;     // next row to fetch (L plane; T plane at + plane)
+  const u64 *inbase; // row 0
+  u64 *Lo;           // next row to store (L plane)
+  size_t pitch, plane;
+  int ld_row, M;
+};
+
+__device__ __forceinline__ void ens_fetch(EnsCursor &c, EnsRing &ring, int slot, int lane) {
+  ring_fill(ring, slot, lane, c.Lp, c.Lp + c.plane);
+  if (++c.ld_row == c.M) {
+    c.ld_row = 0;
+    c.Lp = c.inbase;
+  } else {
+    c.Lp += c.pitch;
+  }
+}
+
+__device__ __forceinline__ void ens_store(EnsCursor &c, u64 L, u64 T) {
+  __stcg(c.Lo, L);
+  __stcg(c.Lo + c.plane, T);
+  c.Lo += c.pitch;
+}
+
+// The K stages on one input row i (already read); A selects the state set
+// the row reads.  GUARD: a stage's row may lie outside the band.
+template <int K, bool GUARD, int A>
+__device__ __forceinline__ void ens_stages(u64 &inL, u64 &inT, u64 (&curT)[2][K],
+                                           u64 (&curLh)[2][K], u64 (&prevMv)[2][K],
+                                           uint32_t (&c_lr)[K], uint32_t (&c_tb)[K],
+                                           const LaneWord &lw, int i, int len) {
+  constexpr int B = A ^ 1;
+#pragma unroll
+  for (int s = 0; s < K; ++s) {
+    u64 mvIn, mvV;
+    stage_step_pp<false>(inL, inT, curT[A][s], curLh[A][s], prevMv[A][s], curT[B][s],
+                         curLh[B][s], prevMv[B][s], lw, mvIn, mvV);
+    if (!GUARD || (unsigned)(i - K - s) < (unsigned)len) c_lr[s] += popc64(mvIn);
+    if (!GUARD || (unsigned)(i - K - s - 1) < (unsigned)len) c_tb[s] += popc64(mvV);
+  }
+}
 
 template <int K>
 __device__ void process_tile(const EnsParams &p, int t, long long step0, int par,
                              long long prev_depth, int lane, EnsRing &ring) {
-  constexpr int PF = PFE<K>::value;
   const EnsTile &tile = p.tiles[t];
   const int grp = tile.lane_grp[lane];
   bool on = grp != 0xff;
@@ -206,21 +245,23 @@ __device__ void process_tile(const EnsParams &p, int t, long long step0, int par
 
   const int M = on ? L.M : 1;
   const size_t pitch = on ? (size_t)L.P : 0;
-  const size_t plane = (size_t)M * pitch;
   // the 16-byte word pair that holds this lane's word (buffers picked by a
   // select: a runtime index into the copied lattice record would put it in
   // local memory)
   const u64 off_in = par ? L.off[1] : L.off[0], off_out = par ? L.off[0] : L.off[1];
-  const u64 *inbase = p.pool + (on ? off_in : 0) + (wi & ~1);
-  u64 *outbase = p.pool + (on ? off_out : 0) + wi;
+  EnsCursor cur;
+  cur.inbase = p.pool + (on ? off_in : 0) + (wi & ~1);
+  cur.pitch = pitch;
+  cur.plane = (size_t)M * pitch;
+  cur.M = M;
   const int len = gr.len, n_in = len + 2 * K;
-  int ld_row = on ? (gr.r0 - K) % M : 0;
-  if (ld_row < 0) ld_row += M;
-  const u64 *Lp = inbase + (size_t)ld_row * pitch;
-  u64 *Lo = outbase + (size_t)gr.r0 * pitch;
+  cur.ld_row = on ? (gr.r0 - K) % M : 0;
+  if (cur.ld_row < 0) cur.ld_row += M;
+  cur.Lp = cur.inbase + (size_t)cur.ld_row * pitch;
+  cur.Lo = p.pool + (on ? off_out : 0) + wi + (size_t)gr.r0 * pitch;
   const int half = wi & 1;
 
-  // two state sets, alternated row by row (PF is even), so no value is copied
+  // two state sets, alternated row by row, so no value is copied
   u64 curT[2][K], curLh[2][K], prevMv[2][K];
   uint32_t c_lr[K], c_tb[K];
 #pragma unroll
@@ -233,55 +274,56 @@ __device__ void process_tile(const EnsParams &p, int t, long long step0, int par
   // rows 0 .. kEnsAhead-1 in flight, one commit group per row (empty past n_in)
 #pragma unroll
   for (int u = 0; u < kEnsAhead; ++u) {
-    if (on && u < n_in) {
-      ring_fill(ring, u, lane, Lp, Lp + plane);
-      if (++ld_row == M) {
-        ld_row = 0;
-        Lp = inbase;
-      } else {
-        Lp += pitch;
-      }
-    }
+    if (on && u < n_in) ens_fetch(cur, ring, u, lane);
     cp_async_commit();
   }
+  // One input row near the band ends (guarded: rows past a lane's input,
+  // stages outside its band and rows before 2K are neither counted nor
+  // stored; lanes past their band's input rows, or off, read stale slots).
+  auto guarded_row = [&](int i, auto a_tag) {
+    constexpr int A = decltype(a_tag)::value;
+    if (on && i + kEnsAhead < n_in) ens_fetch(cur, ring, (i + kEnsAhead) & (kEnsRing - 1), lane);
+    cp_async_commit();
+    cp_async_wait<kEnsAhead>();  // row i has landed (this lane's own copies)
+    u64 inL, inT;
+    ring_read(ring, i & (kEnsRing - 1), lane, half, inL, inT);
+    ens_stages<K, true, A>(inL, inT, curT, curLh, prevMv, c_lr, c_tb, lw, i, len);
+    if (on && i >= 2 * K && i - 2 * K < len) ens_store(cur, inL, inT);
+  };
+  using A0 = std::integral_constant<int, 0>;
+  using A1 = std::integral_constant<int, 1>;
   const int n_max = tile.max_len + 2 * K;
-  for (int i0 = 0; i0 < n_max; i0 += PF) {
-    const bool steady = i0 >= 2 * K && i0 + PF <= tile.min_len + K;
-#pragma unroll
-    for (int u = 0; u < PF; ++u) {
-      const int i = i0 + u;
-      if (i < n_max) {  // warp-uniform
-        if (on && i + kEnsAhead < n_in) {
-          ring_fill(ring, (i + kEnsAhead) & (kEnsRing - 1), lane, Lp, Lp + plane);
-          if (++ld_row == M) {
-            ld_row = 0;
-            Lp = inbase;
-          } else {
-            Lp += pitch;
-          }
-        }
-        cp_async_commit();
-        cp_async_wait<kEnsAhead>();  // row i has landed (this lane's own copies)
-        // lanes past their band's input rows (or off) read stale slots: those
-        // rows are neither stored nor counted
-        u64 inL, inT;
-        ring_read(ring, i & (kEnsRing - 1), lane, half, inL, inT);
-        const int a = u & 1, b = a ^ 1;
-#pragma unroll
-        for (int s = 0; s < K; ++s) {
-          u64 mvIn, mvV;
-          stage_step_pp<false>(inL, inT, curT[a][s], curLh[a][s], prevMv[a][s], curT[b][s],
-                               curLh[b][s], prevMv[b][s], lw, mvIn, mvV);
-          if (steady || (unsigned)(i - K - s) < (unsigned)len) c_lr[s] += popc64(mvIn);
-          if (steady || (unsigned)(i - K - s - 1) < (unsigned)len) c_tb[s] += popc64(mvV);
-        }
-        if (on && i >= 2 * K && i - 2 * K < len) {
-          const size_t off = (size_t)(i - 2 * K) * pitch;
-          __stcg(Lo + off, inL);
-          __stcg(Lo + off + plane, inT);
-        }
-      }
+  // rows [0, 2K): the pipeline fills; rows [2K, min_len + K): every lane's
+  // stage rows lie in its band and every on-lane stores (two rows a turn,
+  // both read from the ring before either runs its stages); the rest drains
+  int i = 0;
+  for (; i < 2 * K; i += 2) {
+    guarded_row(i, A0{});
+    guarded_row(i + 1, A1{});
+  }
+  const int steady_end = tile.min_len + K;
+  for (; i + 2 <= steady_end; i += 2) {
+    // rows i + kEnsAhead (+1) exist when K > kEnsAhead (i + 1 < min_len + K)
+    if (on && (K > kEnsAhead || i + kEnsAhead < n_in))
+      ens_fetch(cur, ring, (i + kEnsAhead) & (kEnsRing - 1), lane);
+    cp_async_commit();
+    if (on && (K > kEnsAhead || i + kEnsAhead + 1 < n_in))
+      ens_fetch(cur, ring, (i + kEnsAhead + 1) & (kEnsRing - 1), lane);
+    cp_async_commit();
+    cp_async_wait<kEnsAhead>();  // rows i and i + 1 have landed
+    u64 L0, T0, L1, T1;
+    ring_read(ring, i & (kEnsRing - 1), lane, half, L0, T0);
+    ring_read(ring, (i + 1) & (kEnsRing - 1), lane, half, L1, T1);
+    ens_stages<K, false, 0>(L0, T0, curT, curLh, prevMv, c_lr, c_tb, lw, i, len);
+    ens_stages<K, false, 1>(L1, T1, curT, curLh, prevMv, c_lr, c_tb, lw, i + 1, len);
+    if (on) {
+      ens_store(cur, L0, T0);
+      ens_store(cur, L1, T1);
     }
+  }
+  for (; i < n_max; i += 2) {
+    guarded_row(i, A0{});
+    if (i + 1 < n_max) guarded_row(i + 1, A1{});  // warp-uniform
   }
   // per-group reduction of the counts, then one atomic per group and step
 #pragma unroll
@@ -443,6 +485,22 @@ __global__ void ens_unpack_kernel(const EnsLattice *lat, int count, const long l
       const int b = j & 63;
       dst[idx] = (uint8_t)(((Lp[wi] >> b) & 1ull) | (((Tp[wi] >> b) & 1ull) << 1));
     }
+  }
+}
+
+// one lattice's bitplanes -> its bytes (the whole grid on one lattice)
+__global__ void ens_unpack_one_kernel(const EnsLattice *lat, int l, const int *buf_of,
+                                      const u64 *pool, uint8_t *dst) {
+  const EnsLattice L = lat[l];
+  const long long words = (long long)L.M * L.P;
+  const u64 *Lp = pool + L.off[buf_of[l]], *Tp = Lp + words;
+  const long long cells = (long long)L.M * L.N;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < cells;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / L.N), j = (int)(idx - (long long)i * L.N);
+    const long long wi = (long long)i * L.P + (j >> 6);
+    const int b = j & 63;
+    dst[idx] = (uint8_t)(((Lp[wi] >> b) & 1ull) | (((Tp[wi] >> b) & 1ull) << 1));
   }
 }
 
@@ -1405,12 +1463,24 @@ extern "C" int bml_ensemble_read_lattices(bml_ens *e, uint8_t *out) {
 extern "C" int bml_ensemble_read_lattice(bml_ens *e, int64_t lattice, uint8_t *out) {
   if (!e || !out) return efail(BML_EINVAL, "NULL argument");
   if (lattice < 0 || lattice >= e->count) return efail(BML_EINVAL, "lattice out of range");
-  std::vector<uint8_t> all((size_t)e->total_bytes);
-  int rc = bml_ensemble_read_lattices(e, all.data());
+  int rc = check_err(e);
   if (rc) return rc;
+  // unpack only this lattice (reading every lattice would move the whole
+  // ensemble for one of them)
   const EnsLattice &L = e->lat[(size_t)lattice];
-  std::copy(all.begin() + e->byte_off[(size_t)lattice],
-            all.begin() + e->byte_off[(size_t)lattice] + (long long)L.M * L.N, out);
+  const size_t cells = (size_t)L.M * (size_t)L.N;
+  uint8_t *d = nullptr;
+  ECUDA(cudaMalloc(&d, std::max<size_t>(1, cells)));
+  ens_buf_of_kernel<<<(e->count + 255) / 256, 256, 0, e->st>>>(e->frozen, e->frozen_buf, e->ctrl,
+                                                              e->count, e->buf_of);
+  const size_t blocks = std::min<size_t>((cells + 255) / 256, 148 * 8);
+  ens_unpack_one_kernel<<<(unsigned)std::max<size_t>(1, blocks), 256, 0, e->st>>>(
+      e->d_lat, (int)lattice, e->buf_of, e->pool, d);
+  cudaError_t r = cudaGetLastError();
+  if (r == cudaSuccess) r = cudaMemcpyAsync(out, d, cells, cudaMemcpyDeviceToHost, e->st);
+  if (r == cudaSuccess) r = cudaStreamSynchronize(e->st);
+  cudaFree(d);
+  if (r != cudaSuccess) return efail(BML_ECUDA, "read lattice: %s", cudaGetErrorString(r));
   return BML_OK;
 }
 
