@@ -71,8 +71,10 @@ cudaError_t launch_copy_counts(const u64 *lr, const u64 *tb, int64_t n, int64_t 
 // Byte-per-cell phases: cur -> nxt, moved cars added to *moved.
 cudaError_t launch_byte_h(const uint8_t *cur, uint8_t *nxt, const Geom &g, u64 *moved,
                           cudaStream_t st);
+// pad_any: the padding bytes of a row may hold any value (caller-owned
+// rows); they are then excluded from the rule and left unchanged.
 cudaError_t launch_byte_v(const uint8_t *cur, uint8_t *nxt, const Geom &g, u64 *moved,
-                          cudaStream_t st);
+                          cudaStream_t st, bool pad_any = false);
 
 // Bitplane phases.  H: (L, T) -> Lh; V: (Lh, T) -> Tv.  Moved cars added to
 // *moved.

@@ -132,11 +132,14 @@ __global__ void byte_h_kernel(const uint8_t *__restrict__ cur, uint8_t *__restri
 }
 
 // One thread per (band of rows, chunk column); marches down the band keeping
-// the upper row's TB mask and the current row's EMPTY mask.  The EMPTY mask
-// of the row's last chunk is limited to the columns < N: padding bytes
-// (columns N..PB-1) may hold anything (the allocation-free entry point steps
-// caller-owned rows), and with no EMPTY bit there no TB move involves them,
-// so they are copied unchanged and never counted.
+// the upper row's TB mask and the current row's EMPTY mask.  The library's
+// own byte lattices keep their padding bytes (columns N..PB-1) at 0, so no
+// move involves them and the rule needs no column mask.  PAD_ANY (the
+// allocation-free entry point, which steps caller-owned rows whose padding
+// may hold anything): the EMPTY mask of a row's last chunk is limited to the
+// columns < N, so no TB move involves a padding byte, and padding bytes are
+// copied unchanged and never counted.
+template <bool PAD_ANY>
 __global__ void __launch_bounds__(256, 8)
     byte_v_kernel(const uint8_t *__restrict__ cur, uint8_t *__restrict__ nxt, Geom g,
                   int64_t band, u64 *moved) {
@@ -152,8 +155,8 @@ __global__ void __launch_bounds__(256, 8)
     const uint8_t *col = cur + 16 * q;
     const uint8_t *src = col + r0 * g.PB;
     uint8_t *dst = nxt + r0 * g.PB + 16 * q;
-    const int64_t nv = g.N - 16 * q;  // valid cells of this chunk column
-    const Chunk vm = nv >= 16 ? Chunk{kLsb, kLsb} : valid_bytes((int)nv);
+    Chunk vm{kLsb, kLsb};
+    if (PAD_ANY && g.N - 16 * q < 16) vm = valid_bytes((int)(g.N - 16 * q));
     const Chunk up = load_chunk(r0 > 0 ? src - g.PB : col + (g.M - 1) * g.PB);
     Chunk Tt = tb_mask(up);
     Chunk x = load_chunk(src);
@@ -201,7 +204,7 @@ cudaError_t launch_byte_h(const uint8_t *cur, uint8_t *nxt, const Geom &g, u64 *
 }
 
 cudaError_t launch_byte_v(const uint8_t *cur, uint8_t *nxt, const Geom &g, u64 *moved,
-                          cudaStream_t st) {
+                          cudaStream_t st, bool pad_any) {
   // Band height: as short as one wave of the launched threads allows (every
   // thread marches down one band; the rows re-read above and below a band
   // are 2/band of the traffic), at least 32 rows, at most 4096.
@@ -216,8 +219,11 @@ cudaError_t launch_byte_v(const uint8_t *cur, uint8_t *nxt, const Geom &g, u64 *
   int64_t band = (g.M * nq + threads - 1) / threads;
   band = band < 32 ? 32 : (band > 4096 ? 4096 : band);
   const int64_t items = ((g.M + band - 1) / band) * nq;
-  return launch_pdl(byte_v_kernel, dim3(grid_cap(items, 256)), dim3(256), 0, st, cur, nxt, g,
-                    band, moved);
+  if (pad_any)
+    return launch_pdl(byte_v_kernel<true>, dim3(grid_cap(items, 256)), dim3(256), 0, st, cur,
+                      nxt, g, band, moved);
+  return launch_pdl(byte_v_kernel<false>, dim3(grid_cap(items, 256)), dim3(256), 0, st, cur,
+                    nxt, g, band, moved);
 }
 
 }  // namespace bml

@@ -86,7 +86,7 @@ extern "C" int bml_step_bytes_noalloc(uint8_t *d_cells, int64_t M, int64_t N, in
     // earlier call is ever read
     e = bml::launch_byte_h(d_cells, scratch, g, (bml::u64 *)(d_moved_lr + t), st);
     if (e == cudaSuccess)
-      e = bml::launch_byte_v(scratch, d_cells, g, (bml::u64 *)(d_moved_tb + t), st);
+      e = bml::launch_byte_v(scratch, d_cells, g, (bml::u64 *)(d_moved_tb + t), st, true);
   }
   if (e != cudaSuccess) return noalloc_fail(BML_ECUDA, cudaGetErrorString(e));
   return BML_OK;
