@@ -14,8 +14,8 @@ rank runs an independent replica (weak scaling); there is no data-path
 collective.
 
 Sub-measurements on the same JSON line: "ensemble" (4096 lattices, the
-batched API; with "cpu_oracle", the oracle on all host cores on a subset of
-the lattices, extrapolated), "model2" (the Sec. 2 Model II variant on the bench lattice,
+batched API, the workload's full 10^4 steps timed; with "cpu_oracle", the
+oracle on all host cores on a subset of the lattices, extrapolated), "model2" (the Sec. 2 Model II variant on the bench lattice,
 tie-break seed = placement seed, 1024 steps; --no-model2 skips it),
 "byte_kernel" (the plain byte-per-cell form on the bench lattice, 16 steps,
 against the HBM peak), "two_phase" (the two-phase bitplane form, a horizontal and
@@ -26,6 +26,7 @@ bit-packed over 3 densities x 3 seeds x 4096 steps, with the oracle's one-core t
 estimated from a bounded sample; rank 0 of a 1-GPU run), "mlp" (the
 surrogate network: AdamW step time at batch 1024, forward on 2624 samples, and its tcgen05
 GEMM kernel on a 2^22 x 128 x 128 product against the HBM peak; 1-GPU runs).
+The line ends with "summary", the headline number of each of them again.
 
 --impl reference times the CPU oracle (test infrastructure) on the host
 cores on a bounded sample of the same workload.
@@ -73,10 +74,10 @@ SMS = 148
 ALU_LANES_PER_SM_CLK = 64  # integer ALU pipe: 2 warp instructions per clock per SM
 SM_MAX_MHZ = 2032.0
 # DRAM bytes (read + write, as counted by ncu for one launch) per cell, from
-# the captures summarised in profiles/ (stream2_kernel<8> and <1>: 32768 x
-# 32768, the kernels as they are now); scaled by the cell count of the run.
-# A kernel without an entry reports traffic null.
-TRAFFIC_PER_CELL = {"stream2_kernel<8>": 0.4671, "stream2_kernel<1>": 0.4492}
+# the captures summarised in profiles/ (32768 x 32768, the kernels as they are
+# now); scaled by the cell count of the run.  A kernel without an entry (or
+# changed since its capture) reports traffic null.
+TRAFFIC_PER_CELL = {}
 
 
 def _peaks():
@@ -739,11 +740,53 @@ def run_ours(args):
             "mlp": mlp,
             "gpu_launches": gpu_launches, "clocks": clk,
         }
+        # the headline figures of every sub-measurement again, last on the
+        # line, where a reader that keeps only the end of the output sees them
+        line["summary"] = _summary(line)
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def _summary(line):
+    """Compact copy of the sub-measurements' headline numbers."""
+    def pick(d, *keys):
+        return {k: d[k] for k in keys if d is not None and k in d}
+
+    out = {"value": line["value"], "roofline_frac": line["roofline"]["frac"],
+           "roofline_kernel": line["roofline"].get("kernel")}
+    if line.get("e2e"):
+        out["e2e"] = line["e2e"]["value"]
+    if line.get("cpu_baseline"):
+        out["cpu_baseline"] = line["cpu_baseline"]["value"]
+    ens = line.get("ensemble")
+    if ens:
+        out["ensemble"] = pick(ens, "value", "unit", "steps", "seconds", "temporal_depth",
+                               "band_rows", "cell_updates_per_s")
+        out["ensemble"]["roofline_frac"] = ens["roofline"]["frac"]
+        if ens.get("cpu_oracle"):
+            out["ensemble"]["cpu_oracle"] = ens["cpu_oracle"]["value"]
+    for key in ("model2", "byte_kernel", "two_phase", "one_pass"):
+        d = line.get(key)
+        if d:
+            out[key] = {"value": d["value"], "kernel": d.get("kernel"),
+                        "roofline_frac": d["roofline"]["frac"]}
+    mlp = line.get("mlp")
+    if mlp:
+        out["mlp"] = {"train_step_us": mlp["train_step_us"],
+                      "forward_2624_us": mlp["forward_2624_us"],
+                      "gemm_hbm_frac": mlp["gemm"]["roofline"]["frac"]}
+    cfg = line.get("configs")
+    if cfg:
+        a = cfg["256x256_rho0.30_1024steps"]
+        b = cfg["4096x4096_rho0.20-0.50_seeds1-3_4096steps"]
+        out["configs"] = {"256x256_cell_updates_per_s": a["cell_updates_per_s"],
+                          "4096x4096_bitplane_cell_updates_per_s":
+                              b["bitplane_cell_updates_per_s"],
+                          "4096x4096_byte_cell_updates_per_s": b["byte_cell_updates_per_s"]}
+    return out
 
 
 def _ints(spec):
@@ -761,7 +804,7 @@ def main():
     ap.add_argument("--band", type=int, default=None, help="band rows (with --kernel tblock)")
     ap.add_argument("--lane-words", type=int, default=1, help="1 or 2 (with --band)")
     ap.add_argument("--no-ensemble", action="store_true")
-    ap.add_argument("--ensemble-steps", type=int, default=1024)
+    ap.add_argument("--ensemble-steps", type=int, default=10000)
     ap.add_argument("--ensemble-tiling", default=None,
                     help="K,BAND: explicit ensemble depth and band (default: autotuned)")
     ap.add_argument("--no-model2", action="store_true")

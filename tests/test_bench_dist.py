@@ -59,3 +59,29 @@ def test_single_rank_helpers():
     import bench
     assert bench.dist_max(3.0, 1) == 3.0
     assert bench.job_rate(1, 10.0, 2.0) == 5.0
+
+
+def test_summary_repeats_every_sub_measurement():
+    """The line's trailing summary carries the headline number of each
+    sub-measurement (a reader keeping only the end of the line sees them)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    rf = {"frac": 0.5}
+    line = {"value": 1.0, "roofline": {"frac": 0.6, "kernel": "k"}, "e2e": {"value": 0.9},
+            "cpu_baseline": {"value": 1e9},
+            "ensemble": {"value": 3.0, "unit": "lattice-steps/s", "steps": 10000,
+                         "roofline": rf, "cpu_oracle": {"value": 7.0}},
+            "model2": {"value": 2.0, "kernel": "m", "roofline": rf},
+            "byte_kernel": {"value": 4.0, "roofline": rf}, "two_phase": None,
+            "one_pass": {"value": 5.0, "roofline": rf},
+            "mlp": {"train_step_us": 170.0, "forward_2624_us": 60.0,
+                    "gemm": {"roofline": {"frac": 0.8}}},
+            "configs": {"256x256_rho0.30_1024steps": {"cell_updates_per_s": 1e11},
+                        "4096x4096_rho0.20-0.50_seeds1-3_4096steps": {
+                            "bitplane_cell_updates_per_s": 7e12,
+                            "byte_cell_updates_per_s": 7e11}}}
+    s = bench._summary(line)
+    assert s["ensemble"]["value"] == 3.0 and s["ensemble"]["cpu_oracle"] == 7.0
+    assert s["model2"]["value"] == 2.0 and s["one_pass"]["roofline_frac"] == 0.5
+    assert "two_phase" not in s and s["mlp"]["gemm_hbm_frac"] == 0.8
+    assert s["configs"]["4096x4096_bitplane_cell_updates_per_s"] == 7e12
