@@ -7,7 +7,7 @@ this package imports nothing from the product.
 
 `bml_oracle.c` is the plain serial byte-per-cell simulator (Marzolla 2018,
 Sec. 2 rules, Sec. 3 layout and double buffer, Sec. 4 row-parallel loop for
-the threaded mode), with Model II (Sec. 2) in `run_model`.  `mlp.py` is the fp64 reference for the surrogate
+the threaded mode), with Models II and III (Sec. 2) in `run_model`.  `mlp.py` is the fp64 reference for the surrogate
 network.  `features.py` holds the trace features and labels the surrogate
 is trained on.
 """
@@ -121,8 +121,9 @@ def run(g: np.ndarray, K: int, threads: int = 1):
 
 def run_model(g: np.ndarray, K: int, model: int, tie_seed: int = 0, t0: int = 0,
               threads: int = 1):
-    """Advance a copy of g by K steps of Model II (model=2, the only one
-    accepted); the first step has index t0 (it selects the tie-break bits).
+    """Advance a copy of g by K steps of Model II (model=2) or Model III
+    (model=3; a cell may then hold 3 = one LR and one TB vehicle); the first
+    step has index t0 (for Model II it selects the tie-break bits).
 
     Returns (lattice after K steps, moved_lr[K], moved_tb[K]) as int64."""
     g = np.ascontiguousarray(g, dtype=np.uint8).copy()

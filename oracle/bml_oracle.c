@@ -36,7 +36,7 @@
  *   cell = LR if u < t_lr, else TB if u - t_lr < t_tb, else EMPTY,
  *   t_x = floor(p_x * 2^64) clamped to 2^64 - 1.
  *
- * Model II: oracle_run_model below (reading stated there).
+ * Models II and III: oracle_run_model below (readings stated there).
  *
  * Threaded mode: the row loop of each phase may be split across OpenMP
  * threads exactly as Sec. 4 describes ("parallel for" over rows).  Every
@@ -283,22 +283,76 @@ static void model_step(const uint8_t *cur, uint8_t *next, int64_t M, int64_t N,
 }
 
 /*
- * Advance g by K steps of Model II (model = 2; no other model is accepted);
- * the first step has index t0 (it selects the tie-break bits).
- * Counts as in oracle_run.  Returns 0, -1 on bad arguments, -2 on no memory.
+ * Model III (Sec. 2: the same cell may contain both an LR and a TB
+ * vehicle).  The paper gives only that sentence; the reading here: every
+ * vehicle moves in one synchronous phase per step, from the state at its
+ * start; a vehicle moves iff its target cell (right for LR, below for TB,
+ * wrap-around) holds no vehicle at that time; an empty cell wanted by an LR
+ * and a TB vehicle receives both, and then holds one vehicle of each kind.
+ * A cell byte has bit 0 for an LR vehicle and bit 1 for a TB vehicle, so a
+ * doubly occupied cell is 3.  (With alternating phases, or with targets
+ * that need only be free of the vehicle's own kind, no cell could become
+ * doubly occupied or the two kinds would never interact.)
+ */
+static void model3_step(const uint8_t *cur, uint8_t *next, int64_t M, int64_t N,
+                        int threads, int64_t *mlr, int64_t *mtb)
+{
+    int64_t a = 0, b = 0;
+#pragma omp parallel for reduction(+ : a, b) num_threads(threads) schedule(static)
+    for (int64_t i = 0; i < M; i++) {
+        for (int64_t j = 0; j < N; j++) {
+            const uint8_t c = cur[i * N + j];
+            const uint8_t right = cur[i * N + (j + 1) % N];
+            const uint8_t below = cur[((i + 1) % M) * N + j];
+            const uint8_t left = cur[i * N + (j - 1 + N) % N];
+            const uint8_t above = cur[((i - 1 + M) % M) * N + j];
+            uint8_t out = 0;
+            /* the vehicles in this cell: each stays unless its target is empty */
+            if (c & LR) {
+                if (right == EMPTY) a++;
+                else out |= LR;
+            }
+            if (c & TB) {
+                if (below == EMPTY) b++;
+                else out |= TB;
+            }
+            /* an empty cell receives the LR vehicle on its left and the TB
+               vehicle above it, both of whose targets it is */
+            if (c == EMPTY) {
+                if (left & LR) out |= LR;
+                if (above & TB) out |= TB;
+            }
+            next[i * N + j] = out;
+        }
+    }
+    *mlr = a;
+    *mtb = b;
+}
+
+/*
+ * Advance g by K steps of Model II (model = 2) or Model III (model = 3); the
+ * first step has index t0 (for Model II it selects the tie-break bits).
+ * Counts as in oracle_run.  Returns 0, -1 on bad arguments (another model,
+ * or for Model III a cell byte above 3), -2 on no memory.
  */
 int oracle_run_model(uint8_t *g, int64_t M, int64_t N, int64_t K, int model,
                      uint64_t tie_seed, int64_t t0, int64_t *moved_lr,
                      int64_t *moved_tb, int threads)
 {
-    if (!g || M <= 0 || N <= 0 || K < 0 || t0 < 0 || model != 2)
+    if (!g || M <= 0 || N <= 0 || K < 0 || t0 < 0 || (model != 2 && model != 3))
         return -1;
+    if (model == 3)
+        for (int64_t q = 0; q < M * N; q++)
+            if (g[q] > (LR | TB)) return -1;
     if (threads < 1) threads = 1;
     uint8_t *tmp = (uint8_t *)malloc((size_t)(M * N));
     if (!tmp) return -2;
     for (int64_t t = 0; t < K; t++) {
         int64_t a, b;
-        model_step(g, tmp, M, N, model, tie_seed, t0 + t, threads, &a, &b);
+        if (model == 3)
+            model3_step(g, tmp, M, N, threads, &a, &b);
+        else
+            model_step(g, tmp, M, N, model, tie_seed, t0 + t, threads, &a, &b);
         memcpy(g, tmp, (size_t)(M * N));
         if (moved_lr) moved_lr[t] = a;
         if (moved_tb) moved_tb[t] = b;

@@ -55,9 +55,11 @@ def ensemble_params(count: int, seed: int = 1, lo: int = 64, hi: int = 2048,
 
 
 def parse_golden(path: str):
-    """Read a worked-example fixture: returns (shape, [(label, moved|None,
-    uint8 lattice)])."""
-    sym = {".": EMPTY, ">": LR, "v": TB}
+    """Read a worked-example fixture: returns (shape, [(label, moved,
+    uint8 lattice)]); moved is the count of a "moved n" state, the pair
+    (LR, TB) of an "lr a tb b" state, else None.  '+' marks a cell holding
+    one vehicle of each kind (byte 3)."""
+    sym = {".": EMPTY, ">": LR, "v": TB, "+": LR | TB}
     shape = None
     blocks = []
     cur = None
@@ -70,7 +72,12 @@ def parse_golden(path: str):
             if parts[0] == "shape":
                 shape = (int(parts[1]), int(parts[2]))
             elif parts[0] == "state":
-                moved = int(parts[3]) if len(parts) >= 4 and parts[2] == "moved" else None
+                if len(parts) >= 4 and parts[2] == "moved":
+                    moved = int(parts[3])
+                elif len(parts) >= 6 and parts[2] == "lr" and parts[4] == "tb":
+                    moved = (int(parts[3]), int(parts[5]))
+                else:
+                    moved = None
                 cur = [parts[1], moved, []]
                 blocks.append(cur)
             else:
