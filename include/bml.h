@@ -11,7 +11,8 @@
  * N x N lattices; this library takes any M x N.
  *
  * Lattice format at the boundary (Sec. 3): one byte per cell, values 0/1/2,
- * row-major, cell (i, j) at byte i*N + j, no padding.
+ * row-major, cell (i, j) at byte i*N + j, no padding (Model III, below,
+ * adds the value 3 for a cell holding one vehicle of each kind).
  *
  * Moved counts (not defined in the paper): for step t (1-based), moved_lr[t-1]
  * is the number of LR cars that moved in its horizontal phase and
@@ -195,19 +196,34 @@ int bml_get_tiling(const bml_sim *sim, int *block_k, int64_t *band_rows, int *la
  * (j mod 64) of the SplitMix64 output n = t*M*W + i*W + floor(j/64) + 1
  * from state tie_seed is 1 (W = ceil(N/64)).  Moved counts: LR and TB
  * vehicles that changed cell in the step.
+ *
+ * Model III (Sec. 2: the same cell may contain both an LR and a TB
+ * vehicle).  The paper gives only that sentence; the reading here: every
+ * vehicle moves in one synchronous phase per step, from the state at the
+ * start of the step, into its target cell if that cell holds no vehicle;
+ * an EMPTY cell wanted by both an LR and a TB vehicle receives both and
+ * then holds one of each.  At the boundary such a cell is the byte 3 (LR
+ * bit 0 plus TB bit 1): bml_read_lattice may return it and
+ * bml_write_lattice accepts it while the object runs Model III.  (This
+ * reading keeps flowing at densities where Model I jams; the paper states
+ * that Model III behaves like Model I.)
  * ---------------------------------------------------------------------- */
-#define BML_MODEL_I 1  /* the paper's model: H phase then V phase (default) */
-#define BML_MODEL_II 2 /* one synchronous phase, random tie-break */
+#define BML_MODEL_I 1   /* the paper's model: H phase then V phase (default) */
+#define BML_MODEL_II 2  /* one synchronous phase, random tie-break */
+#define BML_MODEL_III 3 /* one synchronous phase, a cell may hold one of each kind */
 
 /* Select the update rule for the following steps (the lattice and the
- * count history are kept).  Model II runs on the streaming bitplane kernel
- * (k steps per launch, one 64-cell word per lane, any N): the object must
- * have been created with BML_KERNEL_TBLOCK or BML_KERNEL_AUTO, otherwise
- * BML_EINVAL.  On a BML_KERNEL_AUTO object selecting a model autotunes the
- * tiling for it (cached per shape, model and device); a BML_KERNEL_TBLOCK
- * object keeps its tiling (bml_set_tiling_ex may change either).
- * Synchronises the object's stream.  BML_EINVAL for an
- * unknown model; the object is unchanged on failure. */
+ * count history are kept).  Models II and III run on the streaming
+ * bitplane kernels (k steps per launch; two words per lane on rows of full
+ * words, else one; any N): the object must have been created with
+ * BML_KERNEL_TBLOCK or BML_KERNEL_AUTO (and a TBLOCK object must have bands,
+ * band_rows >= 1), otherwise BML_EINVAL.  Leaving Model III while the
+ * lattice holds a doubly occupied cell gives BML_ESTATE.  On a
+ * BML_KERNEL_AUTO object selecting a model autotunes the tiling for it
+ * (cached per shape, model and device); a BML_KERNEL_TBLOCK object keeps its
+ * tiling (bml_set_tiling_ex may change either).  Synchronises the object's
+ * stream.  BML_EINVAL for an unknown model; the object is unchanged on
+ * failure. */
 int bml_set_model(bml_sim *sim, int model, uint64_t tie_seed);
 
 /* Current model and tie-break seed. */

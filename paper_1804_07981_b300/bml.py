@@ -39,6 +39,7 @@ BML_KERNEL_RESIDENT = 5
 
 BML_MODEL_I = 1
 BML_MODEL_II = 2
+BML_MODEL_III = 3
 
 KERNELS = {"auto": BML_KERNEL_AUTO, "byte": BML_KERNEL_BYTE, "bitplane": BML_KERNEL_BITPLANE,
            "fused": BML_KERNEL_FUSED, "tblock": BML_KERNEL_TBLOCK,

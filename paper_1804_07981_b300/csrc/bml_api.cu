@@ -195,7 +195,7 @@ int set_layout(bml_sim *s, bool pair) {
 int enqueue_steps(bml_sim *s, int64_t k, u64 *lr, u64 *tb, bool commit, int64_t t0 = 0) {
   const Geom &g = s->g;
   if (uses_planes(s->kernel)) {
-    const bool pair = s->model == BML_MODEL_I && s->lane_words == 2 && s->band_rows != 0 &&
+    const bool pair = s->model != BML_MODEL_II && s->lane_words == 2 && s->band_rows != 0 &&
                       s->kernel != BML_KERNEL_BITPLANE;
     int rc = set_layout(s, pair);
     if (rc) return rc;
@@ -219,6 +219,10 @@ int enqueue_steps(bml_sim *s, int64_t k, u64 *lr, u64 *tb, bool commit, int64_t 
     }
     return BML_OK;
   }
+  const bool m3 = s->model == BML_MODEL_III;
+  if (m3 && (s->kernel == BML_KERNEL_BYTE || s->kernel == BML_KERNEL_BITPLANE ||
+             s->lane_words == 0 || s->band_rows == 0))
+    return fail(BML_ESTATE, "Model III runs on the streaming kernels only");
   if (s->kernel == BML_KERNEL_BYTE) {
     uint8_t *c0 = (uint8_t *)s->bytes[0].ptr, *c1 = (uint8_t *)s->bytes[1].ptr;
     for (int64_t t = 0; t < k; ++t) {
@@ -267,10 +271,10 @@ int enqueue_steps(bml_sim *s, int64_t k, u64 *lr, u64 *tb, bool commit, int64_t 
     const int a = s->cur, b = 1 - s->cur;
     if (s->lane_words == 2)
       CUDA_TRY(launch_stream2(plane_L(s, a), plane_T(s, a), plane_L(s, b), plane_T(s, b), g, d,
-                              s->band_rows, lr + done, tb + done, s->st));
+                              s->band_rows, lr + done, tb + done, s->st, m3 ? 3 : 1));
     else
       CUDA_TRY(launch_stream(plane_L(s, a), plane_T(s, a), plane_L(s, b), plane_T(s, b), g, d,
-                             s->band_rows, lr + done, tb + done, s->st));
+                             s->band_rows, lr + done, tb + done, s->st, m3));
     if (commit) s->cur = b;
     done += d;
   }
@@ -315,12 +319,12 @@ int autotune(bml_sim *s) {
   // heights that make the tile count fill 1..4 whole waves of resident warps
   int sms = 148;
   CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const bool m2 = s->model == BML_MODEL_II;
+  const bool m2 = s->model == BML_MODEL_II, m1 = s->model == BML_MODEL_I;
   std::vector<Tiling> cands;
-  if (!m2) cands.push_back({1, 0, 1});  // Model II has no one-pass kernel
+  if (m1) cands.push_back({1, 0, 1});  // Models II and III have no one-pass kernel
   // the resident kernel, timed on 64-step launches (a call runs all its steps in one):
-  // the lattice in one block, or split over a cluster of 2, 4 or 8 blocks
-  if (!m2 && resident_applies(s->g)) {
+  // the lattice in one block, or split over a cluster of 2, 4 or 8 blocks (Model I)
+  if (m1 && resident_applies(s->g)) {
     for (int64_t blocks : {1, 2, 4, 8}) {
       if (blocks > s->g.M) break;
       cands.push_back({kTuneSteps, (s->g.M + blocks - 1) / blocks, 0});
@@ -358,7 +362,7 @@ int autotune(bml_sim *s) {
   const int saved_lw = s->lane_words;
   double best = 1e30;
   int best_k = 1, best_lw = 1;
-  int64_t best_b = m2 ? default_band(s->g) : 0;
+  int64_t best_b = m1 ? 0 : default_band(s->g);
   const double cells = (double)s->g.M * (double)s->g.N;
   const int reps = cells > 1e8 ? 3 : (cells > 1e6 ? 10 : 20);
   int rc = BML_OK;
@@ -581,8 +585,8 @@ extern "C" int bml_set_tiling(bml_sim *s, int block_k, int64_t band_rows) {
     return fail(BML_EINVAL, "the fused kernel runs one step per launch without bands");
   if (band_rows < 0 || band_rows > INT32_MAX || (band_rows == 0 && block_k != 1))
     return fail(BML_EINVAL, "bad band_rows (0 selects the direct one-pass kernel, depth 1)");
-  if (band_rows == 0 && s->model == BML_MODEL_II)
-    return fail(BML_EINVAL, "Model II has no one-pass kernel (band_rows >= 1)");
+  if (band_rows == 0 && s->model != BML_MODEL_I)
+    return fail(BML_EINVAL, "Models II and III have no one-pass kernel (band_rows >= 1)");
   s->block_k = block_k;
   s->band_rows = band_rows;
   s->lane_words = 1;
@@ -604,10 +608,24 @@ extern "C" int bml_set_resident_blocks(bml_sim *s, int blocks) {
 
 extern "C" int bml_set_model(bml_sim *s, int model, uint64_t tie_seed) {
   if (!s) return fail(BML_EINVAL, "sim is NULL");
-  if (model != BML_MODEL_I && model != BML_MODEL_II)
+  if (model != BML_MODEL_I && model != BML_MODEL_II && model != BML_MODEL_III)
     return fail(BML_EINVAL, "unknown model %d", model);
-  if (model == BML_MODEL_II && s->kernel != BML_KERNEL_TBLOCK && s->kernel != BML_KERNEL_AUTO)
-    return fail(BML_EINVAL, "Model II needs an object created with BML_KERNEL_TBLOCK or AUTO");
+  if (model != BML_MODEL_I && s->kernel != BML_KERNEL_TBLOCK && s->kernel != BML_KERNEL_AUTO)
+    return fail(BML_EINVAL, "Models II and III need an object created with BML_KERNEL_TBLOCK "
+                "or AUTO");
+  if (model != BML_MODEL_I && s->kernel == BML_KERNEL_TBLOCK && s->band_rows == 0)
+    return fail(BML_EINVAL, "Models II and III have no one-pass kernel (band_rows >= 1)");
+  if (s->model == BML_MODEL_III && model != BML_MODEL_III) {
+    // Models I and II have no doubly occupied cells
+    int *flag = (int *)s->flag.ptr;
+    int h = 0;
+    CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), s->st));
+    CUDA_TRY(launch_find_overlap(plane_L(s, s->cur), plane_T(s, s->cur), s->g, flag, s->st));
+    CUDA_TRY(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, s->st));
+    CUDA_TRY(cudaStreamSynchronize(s->st));
+    if (h)
+      return fail(BML_ESTATE, "the lattice holds doubly occupied cells (Model III only)");
+  }
   const int old_model = s->model, old_k = s->block_k, old_lw = s->lane_words;
   const int64_t old_b = s->band_rows;
   const u64 old_seed = s->tie_seed;
@@ -761,7 +779,8 @@ int write_impl(bml_sim *s, const uint8_t *in, cudaMemcpyKind kind) {
   if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(int), s->st);
   if (e == cudaSuccess) {
     if (uses_planes(s->kernel))
-      e = launch_pack(dst, plane_L(s, other), plane_T(s, other), g, bad, s->st);
+      e = launch_pack(dst, plane_L(s, other), plane_T(s, other), g, bad, s->st,
+                      s->model == BML_MODEL_III ? 3 : 2);
     else
       e = launch_check_bytes(dst, g, bad, s->st);
   }

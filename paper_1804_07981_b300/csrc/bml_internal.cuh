@@ -55,9 +55,13 @@ cudaError_t launch_init_planes(u64 *L, u64 *T, const Geom &g, u64 seed, u64 t_lr
                                u64 t_tb, cudaStream_t st);
 cudaError_t launch_init_bytes(uint8_t *c, const Geom &g, u64 seed, u64 t_lr, u64 t_tb,
                               cudaStream_t st);
-// bytes (pitch PB) -> planes; sets *bad (device int) if a byte is not 0/1/2.
+// bytes (pitch PB) -> planes; sets *bad (device int) if a byte is above
+// max_value (2; 3 where a cell may hold one vehicle of each kind).
 cudaError_t launch_pack(const uint8_t *c, u64 *L, u64 *T, const Geom &g, int *bad,
-                        cudaStream_t st);
+                        cudaStream_t st, int max_value = 2);
+// Sets *flag (device int) if some cell holds both an LR and a TB vehicle.
+cudaError_t launch_find_overlap(const u64 *L, const u64 *T, const Geom &g, int *flag,
+                                cudaStream_t st);
 // planes -> bytes (pitch PB).
 cudaError_t launch_unpack(const u64 *L, const u64 *T, uint8_t *c, const Geom &g,
                           cudaStream_t st);
@@ -92,10 +96,11 @@ int stream_occupancy(const Geom &g, int k, int *warps_per_block);
 
 // Streaming kernel: k full steps (k in 1, 2, 4, 8) from (Lin, Tin) to
 // (Lout, Tout); the counts of sub-step s are added to moved_lr[s],
-// moved_tb[s].  band_rows: rows per warp tile.
+// moved_tb[s].  band_rows: rows per warp tile.  model3: Model III steps
+// (one synchronous phase; a cell may hold one vehicle of each kind).
 cudaError_t launch_stream(const u64 *Lin, const u64 *Tin, u64 *Lout, u64 *Tout, const Geom &g,
                           int k, int64_t band_rows, u64 *moved_lr, u64 *moved_tb,
-                          cudaStream_t st);
+                          cudaStream_t st, bool model3 = false);
 
 // Model II streaming kernel (one synchronous phase, random tie-break of
 // contested cells; k in 1, 2, 4, 8): t0 = index of the launch's first step.
@@ -116,9 +121,10 @@ cudaError_t launch_resident(const u64 *Lin, const u64 *Tin, u64 *Lout, u64 *Tout
                             cudaStream_t st);
 
 // Two-words-per-lane streaming kernel (rows of full words, W even, W > 32);
-// model 1 (the paper's model) or 2 (Model II, with tie_seed and the index
-// t0 of the launch's first step).  Model 1 runs on the pair-interleaved
-// layout of the planes (see launch_pair_layout), Model II on the plain one.
+// model 1 (the paper's model), 2 (Model II, with tie_seed and the index t0
+// of the launch's first step) or 3 (Model III).  Models 1 and 3 run on the
+// pair-interleaved layout of the planes (see launch_pair_layout), Model II
+// on the plain one.
 bool stream2_applies(const Geom &g);
 int64_t stream2_strips(const Geom &g);
 int stream2_occupancy(int k, int model = 1);

@@ -79,7 +79,7 @@ __global__ void init_bytes_kernel(uint8_t *__restrict__ c, Geom g, u64 seed, u64
 // bytes -> planes.  One thread per word; reads the word's 64 bytes as up to
 // four 16-byte chunks that lie inside the row pitch.
 __global__ void pack_kernel(const uint8_t *__restrict__ c, u64 *__restrict__ L,
-                            u64 *__restrict__ T, Geom g, int *bad) {
+                            u64 *__restrict__ T, Geom g, int *bad, uint32_t max_value) {
   const int64_t total = g.M * g.P;
   int badl = 0;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
@@ -95,7 +95,7 @@ __global__ void pack_kernel(const uint8_t *__restrict__ c, u64 *__restrict__ L,
         const int64_t j = off + b;
         if (j >= g.N) break;
         const uint32_t x = (vv[b >> 2] >> (8 * (b & 3))) & 0xffu;
-        badl |= x > 2u;
+        badl |= x > max_value;
         l |= (u64)(x & 1u) << (16 * q + b);
         t |= (u64)((x >> 1) & 1u) << (16 * q + b);
       }
@@ -162,9 +162,25 @@ cudaError_t launch_init_bytes(uint8_t *c, const Geom &g, u64 seed, u64 t_lr, u64
   return cudaGetLastError();
 }
 
+// any word with a cell set in both planes raises the flag
+__global__ void find_overlap_kernel(const u64 *__restrict__ L, const u64 *__restrict__ T,
+                                    int64_t words, int *flag) {
+  int hit = 0;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < words;
+       q += (int64_t)gridDim.x * blockDim.x)
+    hit |= (L[q] & T[q]) != 0ull;
+  if (__any_sync(0xffffffffu, hit) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
+}
+
+cudaError_t launch_find_overlap(const u64 *L, const u64 *T, const Geom &g, int *flag,
+                                cudaStream_t st) {
+  find_overlap_kernel<<<grid_for(g.M * g.P, 256), 256, 0, st>>>(L, T, g.M * g.P, flag);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_pack(const uint8_t *c, u64 *L, u64 *T, const Geom &g, int *bad,
-                        cudaStream_t st) {
-  pack_kernel<<<grid_for(g.M * g.P, 256), 256, 0, st>>>(c, L, T, g, bad);
+                        cudaStream_t st, int max_value) {
+  pack_kernel<<<grid_for(g.M * g.P, 256), 256, 0, st>>>(c, L, T, g, bad, (uint32_t)max_value);
   return cudaGetLastError();
 }
 

@@ -72,7 +72,12 @@ __device__ __forceinline__ u64 mk64(uint32_t lo, uint32_t hi) {
 // the add carries nothing; the neighbour's higher bits land past the end,
 // where L is zero and Er is not read); the last cell sent to the left
 // neighbour is placed at bit 31 by two multiply-adds.
-template <bool FULL>
+//
+// M3 (Model III, one synchronous phase, a cell may hold one vehicle of each
+// kind): a TB vehicle moves iff the cell below held no vehicle at the start
+// of the step, so mvV reads the row's input L instead of Lh; the rest is
+// unchanged (an empty cell may then receive an LR and a TB vehicle).
+template <bool FULL, bool M3 = false>
 __device__ __forceinline__ void stage_step_pp(u64 &inL, u64 &inT, const u64 curT, const u64 curLh,
                                               const u64 prevMv, u64 &nT, u64 &nLh, u64 &nMv,
                                               const LaneWord &lw, u64 &mvIn, u64 &mvV) {
@@ -90,7 +95,7 @@ __device__ __forceinline__ void stage_step_pp(u64 &inL, u64 &inT, const u64 curT
   const u64 Ll = mk64(__funnelshift_l(rl, lo32(inL), 1), __funnelshift_l(lo32(inL), hi32(inL), 1));
   mvIn = Ll & E;
   nLh = (inL & ~Er) | mvIn;
-  mvV = curT & ~(nLh | inT);
+  mvV = curT & ~((M3 ? inL : nLh) | inT);
   nT = inT;
   nMv = mvV;
   inT = (curT & ~mvV) | prevMv;

@@ -29,6 +29,10 @@
 // so that the second row's early stages can overlap the first row's late
 // ones.
 //
+// MODEL = 3 runs Model III (one synchronous phase; a cell may hold one
+// vehicle of each kind) in the interleaved layout: the same stage as the
+// paper's model with the TB moves read from the state at the step's start.
+//
 // MODEL = 2 runs the Model II rule of model2_step.cu (one synchronous phase,
 // tie-break words from the step, row and word indices) on the same
 // structure, in the plain layout: per stage and row a lane draws the two tie-break words of its
@@ -73,6 +77,11 @@ struct StateI {
 // shifted one bit, the left lane's column 127 entering at bit 0) need
 // shifts: 4 funnel shifts per pair and stage instead of 8 in the plain
 // layout, 22 logic operations instead of 28.
+//
+// M3: Model III (one synchronous phase; a cell may hold one vehicle of each
+// kind): a TB vehicle moves iff the cell below held no vehicle at the start
+// of the step, so mV reads the row's input L instead of Lh.
+template <bool M3>
 __device__ __forceinline__ void stage_i(Quad &L, Quad &T, const StateI &st, StateI &nx,
                                         int src_l, int src_r, uint32_t &cnt, bool cnt_h,
                                         bool cnt_v) {
@@ -85,7 +94,7 @@ __device__ __forceinline__ void stage_i(Quad &L, Quad &T, const StateI &st, Stat
                    L[2] ^ mHb0 ^ mHa0, L[3] ^ mHb1 ^ mHa1};
   Quad mV;
 #pragma unroll
-  for (int h = 0; h < 4; ++h) mV[h] = st.T[h] & ~(Lh[h] | T[h]);
+  for (int h = 0; h < 4; ++h) mV[h] = st.T[h] & ~((M3 ? L[h] : Lh[h]) | T[h]);
   if (cnt_h) cnt += __popc(mHa0) + __popc(mHa1) + __popc(mHb0) + __popc(mHb1);
   if (cnt_v) cnt += (__popc(mV[0]) + __popc(mV[1]) + __popc(mV[2]) + __popc(mV[3])) << 16;
 #pragma unroll
@@ -210,7 +219,7 @@ __device__ __forceinline__ void run_stages(PairTile &t, int i, int x0, Quad &L, 
       L[0] = lo32(La), L[1] = hi32(La), L[2] = lo32(Lb), L[3] = hi32(Lb);
       T[0] = lo32(Ta), T[1] = hi32(Ta), T[2] = lo32(Tb), T[3] = hi32(Tb);
     } else {
-      stage_i(L, T, st[U][s], st[U ^ 1][s], t.src_l, t.src_r, cnt[s], ch, cv);
+      stage_i<MODEL == 3>(L, T, st[U][s], st[U ^ 1][s], t.src_l, t.src_r, cnt[s], ch, cv);
     }
   }
 }
@@ -499,6 +508,15 @@ cudaError_t launch_stream2(const u64 *Lin, const u64 *Tin, u64 *Lout, u64 *Tout,
                            cudaStream_t st, int model, u64 tie_seed, u64 t0) {
   if (!stream2_applies(g) || band_rows < 1 || band_rows > INT32_MAX || Tin - Lin != Tout - Lout)
     return cudaErrorInvalidValue;
+  if (model == 3) {
+    switch (k) {
+      case 1: return launch2_k<1, 3>(Lin, Tin, Lout, Tout, g, band_rows, moved_lr, moved_tb, 0, 0, st);
+      case 2: return launch2_k<2, 3>(Lin, Tin, Lout, Tout, g, band_rows, moved_lr, moved_tb, 0, 0, st);
+      case 4: return launch2_k<4, 3>(Lin, Tin, Lout, Tout, g, band_rows, moved_lr, moved_tb, 0, 0, st);
+      case 8: return launch2_k<8, 3>(Lin, Tin, Lout, Tout, g, band_rows, moved_lr, moved_tb, 0, 0, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   if (model == 2) {
     switch (k) {
       case 1: return launch2_k<1, 2>(Lin, Tin, Lout, Tout, g, band_rows, moved_lr, moved_tb, tie_seed, t0, st);

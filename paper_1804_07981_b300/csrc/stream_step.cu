@@ -79,14 +79,14 @@ struct Pipe {
 // One row through all K stages.  With PRED, stage s counts its moves only
 // for band rows (band-relative row i - K - s horizontally, the row above it
 // vertically).
-template <int K, bool FULL, bool PRED>
+template <int K, bool FULL, bool PRED, bool M3>
 __device__ __forceinline__ void row_through(u64 &inL, u64 &inT, const Pipe<K> &src, Pipe<K> &dst,
                                             const LaneWord &lw, int i, int B,
                                             uint32_t (&c_lr)[K], uint32_t (&c_tb)[K]) {
 #pragma unroll
   for (int s = 0; s < K; ++s) {
     u64 mvIn, mvV;
-    stage_step_pp<FULL>(inL, inT, src.curT[s], src.curLh[s], src.prevMv[s], dst.curT[s],
+    stage_step_pp<FULL, M3>(inL, inT, src.curT[s], src.curLh[s], src.prevMv[s], dst.curT[s],
                         dst.curLh[s], dst.prevMv[s], lw, mvIn, mvV);
     if (!PRED || (unsigned)(i - K - s) < (unsigned)B) c_lr[s] += popc64(mvIn);
     if (!PRED || (unsigned)(i - K - s - 1) < (unsigned)B) c_tb[s] += popc64(mvV);
@@ -94,7 +94,8 @@ __device__ __forceinline__ void row_through(u64 &inL, u64 &inT, const Pipe<K> &s
 }
 
 // RING: input rows through the shared-memory ring, else a register prefetch.
-template <int K, bool FULL, bool RING>
+// M3: Model III (see stage.cuh).
+template <int K, bool FULL, bool RING, bool M3>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, K >= 8 ? 3 : 4)
     stream_kernel(const u64 *__restrict__ Lin, const u64 *__restrict__ Tin,
                   u64 *__restrict__ Lout, u64 *__restrict__ Tout, Geom g, StripPlan sp,
@@ -237,10 +238,10 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, K >= 8 ? 3 : 4)
             }
           }
           if (steady)
-            row_through<K, FULL, false>(inL, inT, pp[u & 1], pp[(u & 1) ^ 1], lw, i, B, c_lr,
+            row_through<K, FULL, false, M3>(inL, inT, pp[u & 1], pp[(u & 1) ^ 1], lw, i, B, c_lr,
                                         c_tb);
           else
-            row_through<K, FULL, true>(inL, inT, pp[u & 1], pp[(u & 1) ^ 1], lw, i, B, c_lr,
+            row_through<K, FULL, true, M3>(inL, inT, pp[u & 1], pp[(u & 1) ^ 1], lw, i, B, c_lr,
                                        c_tb);
           // row i - 2K of the band leaves the last stage
           if ((steady || i >= 2 * K) && own) {
@@ -290,16 +291,16 @@ bool use_ring(const Geom &g) {
   return footprint > 0.5 * (double)l2_bytes;
 }
 
-template <int K, bool FULL, bool RING>
+template <int K, bool FULL, bool RING, bool M3>
 cudaError_t launch_kfr(const u64 *Lin, const u64 *Tin, u64 *Lout, u64 *Tout, const Geom &g,
                        const StripPlan &sp, int64_t band_rows, int64_t n_bands, int64_t blocks,
                        u64 *moved_lr, u64 *moved_tb, cudaStream_t st) {
-  return launch_pdl(stream_kernel<K, FULL, RING>, dim3((unsigned)blocks),
+  return launch_pdl(stream_kernel<K, FULL, RING, M3>, dim3((unsigned)blocks),
                     dim3(kWarpsPerBlock * 32), 0, st, Lin, Tin, Lout, Tout, g, sp,
                     (int)band_rows, (int)n_bands, moved_lr, moved_tb);
 }
 
-template <int K>
+template <int K, bool M3>
 cudaError_t launch_k(const u64 *Lin, const u64 *Tin, u64 *Lout, u64 *Tout, const Geom &g,
                      int64_t band_rows, u64 *moved_lr, u64 *moved_tb, cudaStream_t st) {
   const StripPlan sp = make_strip_plan(g, K);
@@ -309,22 +310,22 @@ cudaError_t launch_k(const u64 *Lin, const u64 *Tin, u64 *Lout, u64 *Tout, const
   const int64_t blocks = (tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
   const bool full = g.nb == 64, ring = use_ring(g);
   if (full && ring)
-    return launch_kfr<K, true, true>(Lin, Tin, Lout, Tout, g, sp, band_rows, n_bands, blocks,
+    return launch_kfr<K, true, true, M3>(Lin, Tin, Lout, Tout, g, sp, band_rows, n_bands, blocks,
                                      moved_lr, moved_tb, st);
   if (full)
-    return launch_kfr<K, true, false>(Lin, Tin, Lout, Tout, g, sp, band_rows, n_bands, blocks,
+    return launch_kfr<K, true, false, M3>(Lin, Tin, Lout, Tout, g, sp, band_rows, n_bands, blocks,
                                       moved_lr, moved_tb, st);
   if (ring)
-    return launch_kfr<K, false, true>(Lin, Tin, Lout, Tout, g, sp, band_rows, n_bands, blocks,
+    return launch_kfr<K, false, true, M3>(Lin, Tin, Lout, Tout, g, sp, band_rows, n_bands, blocks,
                                       moved_lr, moved_tb, st);
-  return launch_kfr<K, false, false>(Lin, Tin, Lout, Tout, g, sp, band_rows, n_bands, blocks,
+  return launch_kfr<K, false, false, M3>(Lin, Tin, Lout, Tout, g, sp, band_rows, n_bands, blocks,
                                      moved_lr, moved_tb, st);
 }
 
 template <int K, bool FULL, bool RING>
 int occupancy_of() {
   int blocks = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, stream_kernel<K, FULL, RING>,
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, stream_kernel<K, FULL, RING, false>,
                                                     kWarpsPerBlock * 32, 0) != cudaSuccess) {
     cudaGetLastError();
     return 1;
@@ -372,17 +373,26 @@ StripPlan make_strip_plan(const Geom &g, int k) {
   return sp;
 }
 
-cudaError_t launch_stream(const u64 *Lin, const u64 *Tin, u64 *Lout, u64 *Tout, const Geom &g,
-                          int k, int64_t band_rows, u64 *moved_lr, u64 *moved_tb,
-                          cudaStream_t st) {
-  if (band_rows < 1 || band_rows > INT32_MAX) return cudaErrorInvalidValue;
+template <bool M3>
+cudaError_t launch_stream_m(const u64 *Lin, const u64 *Tin, u64 *Lout, u64 *Tout, const Geom &g,
+                            int k, int64_t band_rows, u64 *moved_lr, u64 *moved_tb,
+                            cudaStream_t st) {
   switch (k) {
-    case 1: return launch_k<1>(Lin, Tin, Lout, Tout, g, band_rows, moved_lr, moved_tb, st);
-    case 2: return launch_k<2>(Lin, Tin, Lout, Tout, g, band_rows, moved_lr, moved_tb, st);
-    case 4: return launch_k<4>(Lin, Tin, Lout, Tout, g, band_rows, moved_lr, moved_tb, st);
-    case 8: return launch_k<8>(Lin, Tin, Lout, Tout, g, band_rows, moved_lr, moved_tb, st);
+    case 1: return launch_k<1, M3>(Lin, Tin, Lout, Tout, g, band_rows, moved_lr, moved_tb, st);
+    case 2: return launch_k<2, M3>(Lin, Tin, Lout, Tout, g, band_rows, moved_lr, moved_tb, st);
+    case 4: return launch_k<4, M3>(Lin, Tin, Lout, Tout, g, band_rows, moved_lr, moved_tb, st);
+    case 8: return launch_k<8, M3>(Lin, Tin, Lout, Tout, g, band_rows, moved_lr, moved_tb, st);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_stream(const u64 *Lin, const u64 *Tin, u64 *Lout, u64 *Tout, const Geom &g,
+                          int k, int64_t band_rows, u64 *moved_lr, u64 *moved_tb,
+                          cudaStream_t st, bool model3) {
+  if (band_rows < 1 || band_rows > INT32_MAX) return cudaErrorInvalidValue;
+  if (model3)
+    return launch_stream_m<true>(Lin, Tin, Lout, Tout, g, k, band_rows, moved_lr, moved_tb, st);
+  return launch_stream_m<false>(Lin, Tin, Lout, Tout, g, k, band_rows, moved_lr, moved_tb, st);
 }
 
 }  // namespace bml
