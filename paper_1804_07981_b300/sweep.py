@@ -26,6 +26,13 @@ Arms:
   nothing tells which of them will still jam.
 
 The exact arm judges the others: per-density mean velocity and jam fraction.
+It also judges the network itself (network_scores): the error of its
+velocity prediction v_hat and how often its jam probability is on the wrong
+side of 0.5 and of the allocator's threshold.  The answers of runs stopped
+at B0 are their measured window velocities, not v_hat: the measurement is
+the closer of the two (its error against the exact arm is reported beside
+v_hat's), so the velocity head is trained and scored as the network's
+velocity predictor, and the allocation reads only the jam head.
 """
 from __future__ import annotations
 
@@ -101,8 +108,11 @@ def exact_arm(runs, T_long, window, stream=None):
     return out, secs
 
 
-def surrogate_arm(runs, net, T_long, B0, window, tau, v_free=0.99, stream=None, use_net=True):
-    """Returns ((v, jam) answers, seconds, number of runs extended to T_long)."""
+def surrogate_arm(runs, net, T_long, B0, window, tau, v_free=0.99, stream=None, use_net=True,
+                  predictions=None):
+    """Returns ((v, jam) answers, seconds, number of runs extended to T_long).
+    predictions (a dict, optional) receives the network's own outputs per run:
+    "v_hat" (predicted steady-state velocity) and "p_jam"."""
     import torch
     M, N, seeds, plr, ptb, _ = runs
     t0 = time.perf_counter()
@@ -111,8 +121,11 @@ def surrogate_arm(runs, net, T_long, B0, window, tau, v_free=0.99, stream=None, 
     ens.step(PROBE)
     if use_net:
         X = ens.features(0, PROBE, POINTS)
-        z = net.forward(X)[:, 1]
-        p_jam = torch.sigmoid(z).cpu().numpy()
+        out = net.forward(X)
+        p_jam = torch.sigmoid(out[:, 1]).cpu().numpy()
+        if predictions is not None:
+            predictions["v_hat"] = out[:, 0].cpu().numpy().astype(np.float64)
+            predictions["p_jam"] = p_jam.astype(np.float64)
     ens.step(B0 - PROBE)
     v0, jam0 = (t.cpu().numpy().astype(np.float64) for t in ens.labels(window))
     jammed = jam0 > 0
@@ -122,6 +135,9 @@ def surrogate_arm(runs, net, T_long, B0, window, tau, v_free=0.99, stream=None, 
         extend = ~jammed
     v, jam = np.where(jammed, 0.0, v0), jam0.copy()
     idx = np.flatnonzero(extend)
+    if use_net and predictions is not None:
+        predictions["v_B0"] = v0
+        predictions["stopped"] = ~jammed & ~extend
     if idx.size:
         # the other runs stop here; the extended ones go on in the same ensemble
         ens.retire(np.flatnonzero(~extend))
@@ -187,6 +203,71 @@ def compare(runs, answer, exact):
             "run_jam_misclassified": float(np.mean(answer[1] != exact[1]))}
 
 
+# density bands of the network's score table (a band holds its lower bound)
+SCORE_BANDS = (0.25, 0.30, 0.35, 0.40, 0.45)
+# jam-probability bins of the calibration table
+CAL_BINS = (0.0, 0.01, 0.1, 0.5, 0.9, 0.99, 1.0)
+
+
+def network_scores(pred, exact, rho, tau, bands=SCORE_BANDS):
+    """The network's own accuracy against the exact runs to T_long: its
+    velocity prediction v_hat (absolute error, cars per step per car,
+    overall and per density band) and its jam probability (misclassified
+    runs at p = 0.5 with the false negatives and positives, the same at the
+    allocator's threshold tau, and a calibration table: per probability bin
+    the runs and the fraction that jammed)."""
+    v_hat, p = pred["v_hat"], pred["p_jam"]
+    v, jam = exact[0], exact[1] > 0
+    err = np.abs(v_hat - v)
+    out = {"runs": int(v.size), "v_mae": float(err.mean()), "v_max_abs_err": float(err.max()),
+           "v_mae_flowing": float(err[~jam].mean()) if (~jam).any() else None,
+           "v_mae_jammed": float(err[jam].mean()) if jam.any() else None}
+    per = []
+    edges = list(bands)
+    for lo, hi in zip(edges[:-1], edges[1:]):
+        last = hi == edges[-1]
+        sel = (rho >= lo - 1e-9) & ((rho <= hi + 1e-9) if last else (rho < hi - 1e-9))
+        if sel.any():
+            per.append({"rho": [lo, hi], "runs": int(sel.sum()), "v_mae": float(err[sel].mean()),
+                        "jam_fraction": float(jam[sel].mean()),
+                        "jam_misclassified": float(np.mean((p[sel] >= 0.5) != jam[sel]))})
+    out["per_density_band"] = per
+    # reference predictors that know the exact per-density outcome of the
+    # sweep itself (not available to an allocator): the per-density jam
+    # fraction thresholded at 1/2, and the per-density mean velocity; and
+    # the trivial one (the sweep's majority class, its mean velocity)
+    keys = np.unique(rho)
+    dens_jam_err = sum(min(jam[rho == k].mean(), 1 - jam[rho == k].mean()) * np.sum(rho == k)
+                       for k in keys) / rho.size
+    dens_v_err = sum(np.abs(v[rho == k] - v[rho == k].mean()).sum() for k in keys) / rho.size
+    out["reference_predictors"] = {
+        "jam_misclassified_per_density_fraction": float(dens_jam_err),
+        "jam_misclassified_majority": float(min(jam.mean(), 1 - jam.mean())),
+        "v_mae_per_density_mean": float(dens_v_err),
+        "v_mae_global_mean": float(np.abs(v - v.mean()).mean())}
+    if "stopped" in pred and pred["stopped"].any():
+        st = pred["stopped"]
+        # the runs the allocator stopped at B0: their answer (the measured
+        # window velocity) against the network's prediction
+        out["stopped_at_B0"] = {"runs": int(st.sum()),
+                                "answer_v_mae": float(np.mean(np.abs(pred["v_B0"][st] - v[st]))),
+                                "v_hat_mae": float(err[st].mean()),
+                                "jammed_later": int(np.sum(jam[st]))}
+    for name, thr in (("p0.5", 0.5), ("tau", tau)):
+        said = p >= thr
+        out["jam_" + name] = {"threshold": thr,
+                              "misclassified": float(np.mean(said != jam)),
+                              "false_negatives": int(np.sum(jam & ~said)),
+                              "false_positives": int(np.sum(~jam & said))}
+    cal = []
+    for lo, hi in zip(CAL_BINS[:-1], CAL_BINS[1:]):
+        sel = (p >= lo) & ((p <= hi) if hi == CAL_BINS[-1] else (p < hi))
+        cal.append({"p": [lo, hi], "runs": int(sel.sum()),
+                    "jammed": float(jam[sel].mean()) if sel.any() else None})
+    out["calibration"] = cal
+    return out
+
+
 def run(cfg: dict, stream=None) -> dict:
     """Train the surrogate, then run the three arms on one sweep; returns a
     summary dict (times in seconds)."""
@@ -200,8 +281,9 @@ def run(cfg: dict, stream=None) -> dict:
     t_train = time.perf_counter() - t0
     runs = sweep_runs(cfg["densities"], cfg["seeds"], cfg["L"])
     exact, t_exact = exact_arm(runs, cfg["T_long"], cfg["window"], stream)
+    pred = {}
     sur, t_sur, n_ext = surrogate_arm(runs, net, cfg["T_long"], cfg["B0"], cfg["window"],
-                                      cfg["tau"], cfg["v_free"], stream)
+                                      cfg["tau"], cfg["v_free"], stream, predictions=pred)
     base, t_base, n_base = surrogate_arm(runs, None, cfg["T_long"], cfg["B0"], cfg["window"],
                                          cfg["tau"], cfg["v_free"], stream, use_net=False)
     plain = None
@@ -209,11 +291,17 @@ def run(cfg: dict, stream=None) -> dict:
         est, info = plain_byte_estimate(runs, cfg["T_long"], every=1,
                                         sample_stride=cfg["plain_sample_stride"], stream=stream)
         plain = {"seconds_estimated": est, **info}
+    saved = t_exact - t_sur
     return {
         "plain_byte_per_lattice": plain,
         "config": cfg, "runs": int(runs[0].size),
         "training": {"seconds_data": t_data, "seconds_train": t_train,
-                     "loss_first": losses[0], "loss_last": float(np.mean(losses[-50:]))},
+                     "loss_first": losses[0], "loss_last": float(np.mean(losses[-50:])),
+                     # sweeps after which the one-time training has paid for itself
+                     # against the exact batched arm (None if no sweep saves time)
+                     "break_even_sweeps_vs_exact":
+                         (t_data + t_train) / saved if saved > 0 else None},
+        "network": network_scores(pred, exact, runs[5], cfg["tau"]),
         "exact": {"seconds": t_exact},
         "surrogate": {"seconds": t_sur, "extended_runs": n_ext, **compare(runs, sur, exact)},
         "no_surrogate": {"seconds": t_base, "extended_runs": n_base,
