@@ -216,6 +216,28 @@ def _oracle_ensemble_sample(budget_s: float, threads: int):
                       "extrapolated at the mean lattice size" % dt}
 
 
+def _cpu_ladder_sample(threads: int, N: int = 2048, steps: int = 64):
+    """The paper's CPU implementations (oracle/cpu_ladder.c: serial with
+    ghost cells, OpenMP, SIMD, OpenMP+SIMD, and a bit-packed OpenMP form) on
+    an N x N lattice at the Fig. 3 density 0.3, `steps` steps each (a bounded
+    sample of the paper's protocol; the full one: python -m oracle.ladder
+    --fig3).  Each result is checked against the oracle.  Reported baselines,
+    not targets."""
+    import oracle
+    from oracle import ladder
+    g0 = oracle.init(N, N, 1, 0.15, 0.15)
+    t0 = time.perf_counter()
+    want, _, _ = oracle.run(g0, steps, threads=1)
+    out = {"serial (oracle)": N * N * steps / (time.perf_counter() - t0)}
+    for form, name in sorted(ladder.FORMS.items()):
+        got, dt = ladder.run(form, g0, steps, threads)
+        assert np.array_equal(got, want), name
+        out[name] = N * N * steps / dt
+    return {"unit": "cell-updates/s", "cores": threads, "kind": "cpu implementations of the "
+            "paper (Secs. 3-5)", "sample": "%d x %d, density 0.3, %d steps" % (N, N, steps),
+            "value_by_form": out}
+
+
 def _oracle_1core_4096(budget_s: float):
     """The oracle on one core, one 4096 x 4096 run (density 0.35, seed 1),
     timed over whole 8-step runs for about `budget_s` seconds and scaled to the
@@ -718,6 +740,7 @@ def run_ours(args):
         if small is not None:
             small["4096x4096_rho0.20-0.50_seeds1-3_4096steps"]["oracle_1core"] = \
                 _oracle_1core_4096(4.0)
+        cpu["ladder"] = _cpu_ladder_sample(threads)
 
     if rank == 0:
         line = {
@@ -761,6 +784,8 @@ def _summary(line):
         out["e2e"] = line["e2e"]["value"]
     if line.get("cpu_baseline"):
         out["cpu_baseline"] = line["cpu_baseline"]["value"]
+        if line["cpu_baseline"].get("ladder"):
+            out["cpu_ladder"] = line["cpu_baseline"]["ladder"]["value_by_form"]
     ens = line.get("ensemble")
     if ens:
         out["ensemble"] = pick(ens, "value", "unit", "steps", "seconds", "temporal_depth",
