@@ -69,11 +69,16 @@ def run(form: int, g: np.ndarray, K: int, threads: int = 1):
     return g, secs.value
 
 
-def fig3(sizes=(1024, 2048, 4096), steps=1024, reps=5, threads=None, max_run_s=120.0):
+def fig3(sizes=(1024, 2048, 4096), steps=1024, reps=5, threads=None, max_run_s=30.0,
+         oracle_max_n=2048):
     """The Fig. 3 protocol: density 0.3 (p_lr = p_tb = 0.15, seeded
     placement, seed 1), N x N, `steps` steps, mean of `reps` runs per form
     and size.  A form whose first run takes longer than max_run_s is not
-    repeated at that size (its entry says how many runs it has)."""
+    repeated at that size (its entry says how many runs it has).  The
+    oracle (one core, several minutes per 4096^2 run) runs up to
+    oracle_max_n; above, its entry is its rate at the largest size run,
+    scaled to the cells (marked "extrapolated"), and the forms there are
+    checked against each other (the first form's lattice) instead."""
     import oracle
     threads = threads or os.cpu_count() or 1
     out = {"density": 0.3, "steps": steps, "threads": threads, "seconds": {}}
@@ -83,6 +88,14 @@ def fig3(sizes=(1024, 2048, 4096), steps=1024, reps=5, threads=None, max_run_s=1
         row = {}
         for form in [0] + sorted(FORMS):
             times = []
+            if form == 0 and N > oracle_max_n:
+                prev = out["seconds"].get(str(max(n for n in sizes if n <= oracle_max_n)))
+                if prev:
+                    rate = prev["serial (oracle)"]["cell_updates_per_s"]
+                    row["serial (oracle)"] = {"mean_s": N * N * steps / rate, "runs": 0,
+                                              "cell_updates_per_s": rate,
+                                              "extrapolated": True}
+                continue
             for r in range(reps):
                 if form == 0:  # the oracle: serial, modulo indexing (Sec. 3)
                     t0 = time.perf_counter()
