@@ -186,18 +186,17 @@ __device__ __forceinline__ void ens_store(EnsCursor &c, u64 L, u64 T) {
 // The K stages on one input row i (already read); A selects the state set
 // the row reads.  GUARD: a stage's row may lie outside the band.
 template <int K, bool GUARD, int A>
-__device__ __forceinline__ void ens_stages(u64 &inL, u64 &inT, u64 (&curT)[2][K],
-                                           u64 (&curLh)[2][K], u64 (&prevMv)[2][K],
-                                           uint32_t (&c_lr)[K], uint32_t (&c_tb)[K],
-                                           const LaneWord &lw, int i, int len) {
+__device__ __forceinline__ void ens_stages(uint32_t (&L)[2], uint32_t (&T)[2],
+                                           StageH (&st)[2][K], uint32_t (&c_lr)[K],
+                                           uint32_t (&c_tb)[K], const LaneWord &lw, int i,
+                                           int len) {
   constexpr int B = A ^ 1;
 #pragma unroll
   for (int s = 0; s < K; ++s) {
-    u64 mvIn, mvV;
-    stage_step_pp<false>(inL, inT, curT[A][s], curLh[A][s], prevMv[A][s], curT[B][s],
-                         curLh[B][s], prevMv[B][s], lw, mvIn, mvV);
-    if (!GUARD || (unsigned)(i - K - s) < (unsigned)len) c_lr[s] += popc64(mvIn);
-    if (!GUARD || (unsigned)(i - K - s - 1) < (unsigned)len) c_tb[s] += popc64(mvV);
+    uint32_t mvIn, mvV;
+    stage_step_h<false>(L, T, st[A][s], st[B][s], lw, mvIn, mvV);
+    if (!GUARD || (unsigned)(i - K - s) < (unsigned)len) c_lr[s] += mvIn;
+    if (!GUARD || (unsigned)(i - K - s - 1) < (unsigned)len) c_tb[s] += mvV;
   }
 }
 
@@ -262,12 +261,11 @@ __device__ void process_tile(const EnsParams &p, int t, long long step0, int par
   const int half = wi & 1;
 
   // two state sets, alternated row by row, so no value is copied
-  u64 curT[2][K], curLh[2][K], prevMv[2][K];
+  StageH st[2][K];
   uint32_t c_lr[K], c_tb[K];
 #pragma unroll
   for (int s = 0; s < K; ++s) {
-    curT[0][s] = curLh[0][s] = prevMv[0][s] = 0;
-    curT[1][s] = curLh[1][s] = prevMv[1][s] = 0;
+    st[0][s] = st[1][s] = StageH{};
     c_lr[s] = c_tb[s] = 0;
   }
 
@@ -287,8 +285,9 @@ __device__ void process_tile(const EnsParams &p, int t, long long step0, int par
     cp_async_wait<kEnsAhead>();  // row i has landed (this lane's own copies)
     u64 inL, inT;
     ring_read(ring, i & (kEnsRing - 1), lane, half, inL, inT);
-    ens_stages<K, true, A>(inL, inT, curT, curLh, prevMv, c_lr, c_tb, lw, i, len);
-    if (on && i >= 2 * K && i - 2 * K < len) ens_store(cur, inL, inT);
+    uint32_t L[2] = {lo32(inL), hi32(inL)}, T[2] = {lo32(inT), hi32(inT)};
+    ens_stages<K, true, A>(L, T, st, c_lr, c_tb, lw, i, len);
+    if (on && i >= 2 * K && i - 2 * K < len) ens_store(cur, mk64(L[0], L[1]), mk64(T[0], T[1]));
   };
   using A0 = std::integral_constant<int, 0>;
   using A1 = std::integral_constant<int, 1>;
@@ -311,14 +310,16 @@ __device__ void process_tile(const EnsParams &p, int t, long long step0, int par
       ens_fetch(cur, ring, (i + kEnsAhead + 1) & (kEnsRing - 1), lane);
     cp_async_commit();
     cp_async_wait<kEnsAhead>();  // rows i and i + 1 have landed
-    u64 L0, T0, L1, T1;
-    ring_read(ring, i & (kEnsRing - 1), lane, half, L0, T0);
-    ring_read(ring, (i + 1) & (kEnsRing - 1), lane, half, L1, T1);
-    ens_stages<K, false, 0>(L0, T0, curT, curLh, prevMv, c_lr, c_tb, lw, i, len);
-    ens_stages<K, false, 1>(L1, T1, curT, curLh, prevMv, c_lr, c_tb, lw, i + 1, len);
+    u64 a0, b0, a1, b1;
+    ring_read(ring, i & (kEnsRing - 1), lane, half, a0, b0);
+    ring_read(ring, (i + 1) & (kEnsRing - 1), lane, half, a1, b1);
+    uint32_t L0[2] = {lo32(a0), hi32(a0)}, T0[2] = {lo32(b0), hi32(b0)};
+    uint32_t L1[2] = {lo32(a1), hi32(a1)}, T1[2] = {lo32(b1), hi32(b1)};
+    ens_stages<K, false, 0>(L0, T0, st, c_lr, c_tb, lw, i, len);
+    ens_stages<K, false, 1>(L1, T1, st, c_lr, c_tb, lw, i + 1, len);
     if (on) {
-      ens_store(cur, L0, T0);
-      ens_store(cur, L1, T1);
+      ens_store(cur, mk64(L0[0], L0[1]), mk64(T0[0], T0[1]));
+      ens_store(cur, mk64(L1[0], L1[1]), mk64(T1[0], T1[1]));
     }
   }
   for (; i < n_max; i += 2) {

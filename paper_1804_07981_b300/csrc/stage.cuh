@@ -102,6 +102,49 @@ __device__ __forceinline__ void stage_step_pp(u64 &inL, u64 &inT, const u64 curT
   inL = curLh;
 }
 
+// The same stage with every value as two 32-bit halves (index 0: bits
+// 0-31, 1: bits 32-63); the state is T_{x-1}, Lh_{x-1}, mvV_{x-2} as halves.
+// Halves need no 64-bit register pairs, which saves the compiler copies.
+struct StageH {
+  uint32_t T[2], Lh[2], M[2];
+};
+
+template <bool FULL, bool M3 = false>
+__device__ __forceinline__ void stage_step_h(uint32_t (&L)[2], uint32_t (&T)[2], const StageH &st,
+                                             StageH &nx, const LaneWord &lw, uint32_t &mvIn,
+                                             uint32_t &mvV) {
+  const uint32_t E0 = FULL ? ~(L[0] | T[0]) : (~(L[0] | T[0]) & lo32(lw.valid));
+  const uint32_t E1 = FULL ? ~(L[1] | T[1]) : (~(L[1] | T[1]) & hi32(lw.valid));
+  const uint32_t send_l = FULL ? L[1] : L[1] * lw.mul_hi + L[0] * lw.mul_lo;
+  const uint32_t rl = __shfl_sync(BML_FULL_MASK, send_l, lw.src_l);
+  const uint32_t rr = __shfl_sync(BML_FULL_MASK, E0, lw.src_r);
+  uint32_t Er0, Er1;
+  if (FULL) {
+    Er0 = __funnelshift_r(E0, E1, 1);
+    Er1 = __funnelshift_r(E1, rr, 1);
+  } else {
+    Er0 = __funnelshift_r(E0, E1, 1) + rr * lw.ins_lo;
+    Er1 = (E1 >> 1) + rr * lw.ins_hi;
+  }
+  const uint32_t in0 = __funnelshift_l(rl, L[0], 1) & E0;
+  const uint32_t in1 = __funnelshift_l(L[0], L[1], 1) & E1;
+  const uint32_t Lh0 = (L[0] & ~Er0) | in0, Lh1 = (L[1] & ~Er1) | in1;
+  const uint32_t mv0 = st.T[0] & ~((M3 ? L[0] : Lh0) | T[0]);
+  const uint32_t mv1 = st.T[1] & ~((M3 ? L[1] : Lh1) | T[1]);
+  mvIn = __popc(in0) + __popc(in1);
+  mvV = __popc(mv0) + __popc(mv1);
+  nx.T[0] = T[0];
+  nx.T[1] = T[1];
+  nx.Lh[0] = Lh0;
+  nx.Lh[1] = Lh1;
+  nx.M[0] = mv0;
+  nx.M[1] = mv1;
+  T[0] = (st.T[0] & ~mv0) | st.M[0];
+  T[1] = (st.T[1] & ~mv1) | st.M[1];
+  L[0] = st.Lh[0];
+  L[1] = st.Lh[1];
+}
+
 // Input-row ring of a warp in shared memory, [slot][plane][lane], 16 bytes
 // per lane and plane.  A lane copies (cp.async, through L2) the aligned
 // 16-byte pair of words that holds its own word (rows start 16-byte aligned:

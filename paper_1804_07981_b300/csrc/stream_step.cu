@@ -73,23 +73,22 @@ struct RingGeom {
 
 template <int K>
 struct Pipe {
-  u64 curT[K], curLh[K], prevMv[K];
+  StageH st[K];
 };
 
 // One row through all K stages.  With PRED, stage s counts its moves only
 // for band rows (band-relative row i - K - s horizontally, the row above it
 // vertically).
 template <int K, bool FULL, bool PRED, bool M3>
-__device__ __forceinline__ void row_through(u64 &inL, u64 &inT, const Pipe<K> &src, Pipe<K> &dst,
-                                            const LaneWord &lw, int i, int B,
+__device__ __forceinline__ void row_through(uint32_t (&L)[2], uint32_t (&T)[2], const Pipe<K> &src,
+                                            Pipe<K> &dst, const LaneWord &lw, int i, int B,
                                             uint32_t (&c_lr)[K], uint32_t (&c_tb)[K]) {
 #pragma unroll
   for (int s = 0; s < K; ++s) {
-    u64 mvIn, mvV;
-    stage_step_pp<FULL, M3>(inL, inT, src.curT[s], src.curLh[s], src.prevMv[s], dst.curT[s],
-                        dst.curLh[s], dst.prevMv[s], lw, mvIn, mvV);
-    if (!PRED || (unsigned)(i - K - s) < (unsigned)B) c_lr[s] += popc64(mvIn);
-    if (!PRED || (unsigned)(i - K - s - 1) < (unsigned)B) c_tb[s] += popc64(mvV);
+    uint32_t mvIn, mvV;
+    stage_step_h<FULL, M3>(L, T, src.st[s], dst.st[s], lw, mvIn, mvV);
+    if (!PRED || (unsigned)(i - K - s) < (unsigned)B) c_lr[s] += mvIn;
+    if (!PRED || (unsigned)(i - K - s - 1) < (unsigned)B) c_tb[s] += mvV;
   }
 }
 
@@ -166,10 +165,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, K >= 8 ? 3 : 4)
 
     Pipe<K> pp[2];  // state sets, alternated row by row (P is even)
 #pragma unroll
-    for (int s = 0; s < K; ++s) {
-      pp[0].curT[s] = pp[0].curLh[s] = pp[0].prevMv[s] = 0;
-      pp[1].curT[s] = pp[1].curLh[s] = pp[1].prevMv[s] = 0;
-    }
+    for (int s = 0; s < K; ++s) pp[0].st[s] = pp[1].st[s] = StageH{};
 
     auto advance = [&]() {
       if (++ld_row == M) {
@@ -237,17 +233,21 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, K >= 8 ? 3 : 4)
               advance();
             }
           }
+          uint32_t L2[2] = {lo32(inL), hi32(inL)}, T2[2] = {lo32(inT), hi32(inT)};
           if (steady)
-            row_through<K, FULL, false, M3>(inL, inT, pp[u & 1], pp[(u & 1) ^ 1], lw, i, B, c_lr,
-                                        c_tb);
+            row_through<K, FULL, false, M3>(L2, T2, pp[u & 1], pp[(u & 1) ^ 1], lw, i, B, c_lr,
+                                            c_tb);
           else
-            row_through<K, FULL, true, M3>(inL, inT, pp[u & 1], pp[(u & 1) ^ 1], lw, i, B, c_lr,
-                                       c_tb);
-          // row i - 2K of the band leaves the last stage
-          if ((steady || i >= 2 * K) && own) {
-            const size_t off = (size_t)(i - 2 * K) * pitch;
-            __stcs(Lo + off, inL);
-            __stcs(To + off, inT);
+            row_through<K, FULL, true, M3>(L2, T2, pp[u & 1], pp[(u & 1) ^ 1], lw, i, B, c_lr,
+                                           c_tb);
+          // row i - 2K of the band leaves the last stage (rows in order)
+          if (steady || i >= 2 * K) {
+            if (own) {
+              __stcs(Lo, mk64(L2[0], L2[1]));
+              __stcs(To, mk64(T2[0], T2[1]));
+            }
+            Lo += pitch;
+            To += pitch;
           }
         }
       }
