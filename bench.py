@@ -16,7 +16,8 @@ collective.
 Sub-measurements on the same JSON line: "ensemble" (4096 lattices, the
 batched API, the workload's full 10^4 steps timed; with "cpu_oracle", the
 oracle on all host cores on a subset of the lattices, extrapolated), "model2" (the Sec. 2 Model II variant on the bench lattice,
-tie-break seed = placement seed, 1024 steps; --no-model2 skips it),
+tie-break seed = placement seed, 1024 steps; --no-model2 skips it and "model3"),
+"model3" (the Model III reading on the bench lattice, 1024 steps),
 "byte_kernel" (the plain byte-per-cell form on the bench lattice, 16 steps,
 against the HBM peak), "two_phase" (the two-phase bitplane form, a horizontal and
 a vertical kernel per step, 64 steps, against the HBM peak), "one_pass" (one full step
@@ -296,15 +297,15 @@ def _ensemble_bench(bml, torch, stream, steps, seed_base=1, tiling=None, sm_mhz=
                         "LR fraction ~ U[0.3,0.7], seeds 1..4096"}
 
 
-def _model2_bench(bml, torch, stream, M, N, steps, sm_mhz, seed=1, tiling=None):
-    """Model II on the bench lattice (same placement), autotuned, `steps`
-    steps timed with CUDA events after a warm-up; the counts of the timed
-    steps are checked for plausibility."""
+def _model2_bench(bml, torch, stream, M, N, steps, sm_mhz, seed=1, tiling=None, model=2):
+    """Model II (model=2) or Model III (model=3) on the bench lattice (same
+    placement), autotuned, `steps` steps timed with CUDA events after a
+    warm-up; the counts of the timed steps are checked for plausibility."""
     # explicit tiling: a TBLOCK object (no autotuning launches); else AUTO
     kernel, bk = ("tblock", tiling[0]) if tiling else ("auto", 0)
     with bml.Lattice(M, N, seed=seed, density=DENSITY, kernel=kernel, block_k=bk,
                      stream=stream, reserve_steps=steps + 64) as sim:
-        sim.set_model(bml.BML_MODEL_II, seed)
+        sim.set_model(bml.BML_MODEL_II if model == 2 else bml.BML_MODEL_III, seed)
         if tiling:
             sim.set_tiling(*tiling)
         k, band, lw = sim.tiling
@@ -320,18 +321,25 @@ def _model2_bench(bml, torch, stream, M, N, steps, sm_mhz, seed=1, tiling=None):
         cells = M * N
         assert (tot >= 0).all() and (tot <= cells).all()
     launches = (steps + k - 1) // k
-    ops = MODEL2_ALU_OPS_PER_CELL_STEP * cells * steps
+    # Model III's step is the paper's model's with the vertical moves read
+    # from the step's start: the same operation count
+    per = MODEL2_ALU_OPS_PER_CELL_STEP if model == 2 else ALU_OPS_PER_CELL_STEP
+    ops = per * cells * steps
     achieved = ops / (ms / 1e3) / 1e12
     peak = SMS * ALU_LANES_PER_SM_CLK * sm_mhz * 1e6 / 1e12
+    if model == 2:
+        kname = ("stream2_kernel<%d, Model II>" if lw == 2 else "model2_kernel<%d>") % k
+    else:
+        kname = ("stream2_kernel<%d, Model III>" if lw == 2 else "stream_kernel<%d, Model III>") % k
     return {"metric": "cell-updates/s", "value": cells * steps / (ms / 1e3),
             "unit": "cell-updates/s", "steps": steps, "seconds": ms / 1e3,
-            "workload": workload_name(M, N) + "_model2_tie1",
-            "kernel": ("stream2_kernel<%d, Model II>" if lw == 2 else "model2_kernel<%d>") % k,
+            "workload": workload_name(M, N) + ("_model2_tie1" if model == 2 else "_model3"),
+            "kernel": kname,
             "temporal_depth": k, "band_rows": band, "lane_words": lw,
             "gpu_launches": launches,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                          "frac": achieved / peak, "traffic": None,
-                         "ops_per_cell_step": MODEL2_ALU_OPS_PER_CELL_STEP}}
+                         "ops_per_cell_step": per}}
 
 
 def _timed_steps(torch, stream, sim, steps):
@@ -721,13 +729,16 @@ def run_ours(args):
     if not args.no_mlp and world == 1:
         mlp = _mlp_bench(bml, torch, stream, hbm_peak, gemm_rows=args.mlp_gemm_rows)
 
-    m2 = None
+    m2 = m3 = None
     if not args.no_model2:
         m2 = _model2_bench(bml, torch, stream, M, N, args.model2_steps,
                            (clk or {}).get("sm_mhz") or SM_MAX_MHZ, seed=1 + rank,
                            tiling=_ints(args.model2_tiling))
         m2_max = max_over_ranks(m2["seconds"])
         m2["value"] = job_rate(world, M * N * m2["steps"], m2_max)
+        m3 = _model2_bench(bml, torch, stream, M, N, args.model2_steps,
+                           (clk or {}).get("sm_mhz") or SM_MAX_MHZ, seed=1 + rank, model=3)
+        m3["value"] = job_rate(world, M * N * m3["steps"], max_over_ranks(m3["seconds"]))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -758,7 +769,7 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (2 x 256 MB bitplanes)",
                        "parallelism": "replicas x%d" % world},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "ensemble": ens,
-            "model2": m2, "byte_kernel": byte, "two_phase": two, "one_pass": one,
+            "model2": m2, "model3": m3, "byte_kernel": byte, "two_phase": two, "one_pass": one,
             "configs": small,
             "mlp": mlp,
             "gpu_launches": gpu_launches, "clocks": clk,
@@ -793,7 +804,7 @@ def _summary(line):
         out["ensemble"]["roofline_frac"] = ens["roofline"]["frac"]
         if ens.get("cpu_oracle"):
             out["ensemble"]["cpu_oracle"] = ens["cpu_oracle"]["value"]
-    for key in ("model2", "byte_kernel", "two_phase", "one_pass"):
+    for key in ("model2", "model3", "byte_kernel", "two_phase", "one_pass"):
         d = line.get(key)
         if d:
             out[key] = {"value": d["value"], "kernel": d.get("kernel"),

@@ -387,6 +387,47 @@ def test_two_words_per_lane_tall_bands_count_exactly(lib, band):
         oracle_counts_equal(sim.moved_counts(), mlr, mtb)
 
 
+def test_pair_layout_conversions_between_kernels(lib):
+    """The two-words-per-lane kernel keeps its planes column-interleaved; the
+    object converts them whenever the next kernel (one word per lane, the
+    Model II pair kernel), a read or a device read needs the plain order.
+    Switching tilings, models and reads between calls in every order gives
+    the oracle's lattice and counts at every point."""
+    import torch
+    M, N = 70, 4096
+    g0 = random_lattice(M, N, 99, 0.17, 0.19)
+    plan = [("pair", 8, 5), ("one", 4, 3), ("pair", 1, 2), ("read", 0, 0), ("pair", 8, 9),
+            ("m2pair", 4, 6), ("pair", 2, 7), ("devread", 0, 0), ("one", 8, 8), ("pair", 4, 4)]
+    want, done = g0, 0
+    lrs, tbs = [], []
+    with make(lib, M, N, "tblock", 8) as sim:
+        sim.write(g0)
+        for what, k, n in plan:
+            if what == "read":
+                np.testing.assert_array_equal(sim.read(), want)
+                continue
+            if what == "devread":
+                d = torch.empty(M * N, dtype=torch.uint8, device="cuda")
+                lib.bml_read_lattice_device(sim.handle, d.data_ptr())
+                np.testing.assert_array_equal(d.cpu().numpy().reshape(M, N), want)
+                continue
+            if what == "m2pair":
+                sim.set_model(lib.BML_MODEL_II, 5)
+                sim.set_tiling(k, 16, lane_words=2)
+                want, a, b = oracle.run_model(want, n, 2, tie_seed=5, t0=done)
+                sim.step(n)
+                sim.set_model(lib.BML_MODEL_I)
+            else:
+                sim.set_tiling(k, 16, lane_words=2 if what == "pair" else 1)
+                want, a, b = oracle.run(want, n)
+                sim.step(n)
+            done += n
+            lrs.append(a)
+            tbs.append(b)
+            np.testing.assert_array_equal(sim.read(), want, err_msg=str((what, k, n)))
+        oracle_counts_equal(sim.moved_counts(), np.concatenate(lrs), np.concatenate(tbs))
+
+
 def test_two_words_per_lane_rejected_where_it_does_not_apply(lib):
     with make(lib, 16, 100, "tblock", 2) as sim:       # N % 64 != 0
         with pytest.raises(lib.BMLError):
