@@ -21,6 +21,38 @@ __device__ __forceinline__ int word_top(int64_t w, const Geom &g) {
   return w == g.W - 1 ? g.nb - 1 : 63;
 }
 
+__device__ __forceinline__ uint32_t lo32(u64 x) { return (uint32_t)x; }
+__device__ __forceinline__ uint32_t hi32(u64 x) { return (uint32_t)(x >> 32); }
+__device__ __forceinline__ u64 mk64(uint32_t lo, uint32_t hi) {
+  return (u64)lo | ((u64)hi << 32);
+}
+
+// One three-input logic instruction (PTX lop3.b32): bit i of the result is
+// bit (a_i b_i c_i) of the truth table LUT, whose operand patterns are
+// a = 0xF0, b = 0xCC, c = 0xAA.  The stage rules are written with it, one
+// instruction per rule line and 32-bit half: left to the compiler, algebraic
+// rewriting (L ^ (L & ~X) into L & X, for one) makes operands shared between
+// lines, and a line that then needs four inputs costs two instructions (26
+// instead of 18 logic instructions per pair-stage of the pair kernel).
+template <unsigned LUT>
+__device__ __forceinline__ uint32_t lop3(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d;
+  asm("lop3.b32 %0, %1, %2, %3, %4;" : "=r"(d) : "r"(a), "r"(b), "r"(c), "n"(LUT));
+  return d;
+}
+template <unsigned LUT>
+__device__ __forceinline__ u64 lop3(u64 a, u64 b, u64 c) {
+  return mk64(lop3<LUT>(lo32(a), lo32(b), lo32(c)), lop3<LUT>(hi32(a), hi32(b), hi32(c)));
+}
+constexpr unsigned kNor = 0x03;       // ~(a | b)          (c unused)
+constexpr unsigned kNorAnd = 0x02;    // ~(a | b) & c
+constexpr unsigned kAnd = 0xC0;       // a & b             (c unused)
+constexpr unsigned kAndNor = 0x10;    // a & ~(b | c)
+constexpr unsigned kXor3 = 0x96;      // a ^ b ^ c
+constexpr unsigned kAndNotOr = 0xBA;  // (a & ~b) | c
+constexpr unsigned kAndOrNot = 0xB0;  // a & (~b | c)
+constexpr unsigned kAndNand = 0x70;   // a & ~(b & c)
+
 // Programmatic dependent launch: a kernel launched with launch_pdl may start
 // (and run its set-up) while the previous kernel on the stream finishes;
 // pdl_wait() returns once that kernel has completed and its memory writes are

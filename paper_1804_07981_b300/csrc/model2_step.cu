@@ -44,14 +44,24 @@ __device__ __forceinline__ void stage_m2(u64 &inL, u64 &inT, const u64 curT, con
                                          const u64 prevIn, u64 &nT, u64 &nL, u64 &nIn,
                                          const LaneWord &lw, const u64 coin, u64 &mvH,
                                          u64 &mvV) {
-  const u64 E = FULL ? ~(inL | inT) : (~(inL | inT) & lw.valid);
   // the left neighbour's last cell, moved to bit 31 of the shuffled half
   const uint32_t send_l = FULL ? hi32(inL) : ((lw.top_hi ? hi32(inL) : lo32(inL)) << lw.top_sh);
   const uint32_t rl = __shfl_sync(BML_FULL_MASK, send_l, lw.src_l);
   const u64 fromL =
       mk64(__funnelshift_l(rl, lo32(inL), 1), __funnelshift_l(lo32(inL), hi32(inL), 1));
-  const u64 inLR = E & fromL & (~curT | coin);
-  const u64 inTB = E & curT & ~(fromL & coin);
+  // entering LR: empty, LR on the left, and no TB above or the coin says LR;
+  // entering TB: empty, TB above, and no LR on the left or the coin says TB
+  const u64 wantLR = lop3<kAndOrNot>(fromL, curT, coin);
+  const u64 wantTB = lop3<kAndNand>(curT, fromL, coin);
+  u64 inLR, inTB;
+  if (FULL) {
+    inLR = lop3<kNorAnd>(inL, inT, wantLR);
+    inTB = lop3<kNorAnd>(inL, inT, wantTB);
+  } else {
+    const u64 E = lop3<kNorAnd>(inL, inT, lw.valid);
+    inLR = lop3<kAnd>(E, wantLR, 0ull);
+    inTB = lop3<kAnd>(E, wantTB, 0ull);
+  }
   // bit 0 of the right neighbour's inLR enters at this word's last cell
   const uint32_t rr = __shfl_sync(BML_FULL_MASK, lo32(inLR), lw.src_r);
   if (FULL) {
@@ -63,9 +73,9 @@ __device__ __forceinline__ void stage_m2(u64 &inL, u64 &inT, const u64 curT, con
   }
   mvV = inTB;
   nT = inT;
-  nL = (inL & ~mvH) | inLR;
+  nL = lop3<kAndNotOr>(inL, mvH, inLR);
   nIn = inTB;
-  inT = (curT & ~inTB) | prevIn;
+  inT = lop3<kAndNotOr>(curT, inTB, prevIn);
   inL = curL;
 }
 

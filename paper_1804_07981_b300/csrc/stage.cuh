@@ -46,15 +46,11 @@ __device__ __forceinline__ void lane_word_bits(LaneWord &lw, bool on, bool last,
   lw.top_sh = 31 - (top & 31);
 }
 
-__device__ __forceinline__ uint32_t lo32(u64 x) { return (uint32_t)x; }
-__device__ __forceinline__ uint32_t hi32(u64 x) { return (uint32_t)(x >> 32); }
-__device__ __forceinline__ u64 mk64(uint32_t lo, uint32_t hi) {
-  return (u64)lo | ((u64)hi << 32);
-}
-
-// Stage state: T_{x-1}, Lh_{x-1}, mvV_{x-2}.  Consumes row x (inL, inT) of
-// its input state, replaces them with row x-1 of the next state, and returns
-// the row's moved-car masks.  The state is read from one set and written to
+// Stage state: T_{x-1}, Lh_{x-1}, mvV_{x-2}, every value as two 32-bit
+// halves (index 0: bits 0-31, 1: bits 32-63; halves need no 64-bit register
+// pairs, which saves the compiler copies).  Consumes row x (L, T) of its
+// input state, replaces them with row x-1 of the next state, and returns the
+// row's moved-car counts.  The state is read from one set and written to
 // another (callers alternate two sets from row to row, so no value is
 // copied).  FULL: every word of the row holds 64 cells.
 //
@@ -63,7 +59,8 @@ __device__ __forceinline__ u64 mk64(uint32_t lo, uint32_t hi) {
 // an LR car enters), Lh = (L & ~Er) | in (cars that stay, plus cars that
 // enter).  Every moving car enters exactly one cell, so the row's LR move
 // count is the popcount of `in` (returned as mvIn).  The left shuffle needs
-// only L, so both shuffles issue at the start of the stage.
+// only L, so both shuffles issue at the start of the stage.  Each rule line is
+// one lop3 per half.
 //
 // Words with fewer cells (the last word of a row whose N is not a multiple of
 // 64): E is masked to the valid cells, so `in` never sets a cell past the
@@ -77,34 +74,6 @@ __device__ __forceinline__ u64 mk64(uint32_t lo, uint32_t hi) {
 // kind): a TB vehicle moves iff the cell below held no vehicle at the start
 // of the step, so mvV reads the row's input L instead of Lh; the rest is
 // unchanged (an empty cell may then receive an LR and a TB vehicle).
-template <bool FULL, bool M3 = false>
-__device__ __forceinline__ void stage_step_pp(u64 &inL, u64 &inT, const u64 curT, const u64 curLh,
-                                              const u64 prevMv, u64 &nT, u64 &nLh, u64 &nMv,
-                                              const LaneWord &lw, u64 &mvIn, u64 &mvV) {
-  const u64 E = FULL ? ~(inL | inT) : (~(inL | inT) & lw.valid);
-  const uint32_t send_l = FULL ? hi32(inL) : hi32(inL) * lw.mul_hi + lo32(inL) * lw.mul_lo;
-  const uint32_t rl = __shfl_sync(BML_FULL_MASK, send_l, lw.src_l);
-  const uint32_t rr = __shfl_sync(BML_FULL_MASK, lo32(E), lw.src_r);
-  u64 Er;
-  if (FULL) {
-    Er = mk64(__funnelshift_r(lo32(E), hi32(E), 1), __funnelshift_r(hi32(E), rr, 1));
-  } else {
-    Er = mk64(__funnelshift_r(lo32(E), hi32(E), 1) + rr * lw.ins_lo,
-              (hi32(E) >> 1) + rr * lw.ins_hi);
-  }
-  const u64 Ll = mk64(__funnelshift_l(rl, lo32(inL), 1), __funnelshift_l(lo32(inL), hi32(inL), 1));
-  mvIn = Ll & E;
-  nLh = (inL & ~Er) | mvIn;
-  mvV = curT & ~((M3 ? inL : nLh) | inT);
-  nT = inT;
-  nMv = mvV;
-  inT = (curT & ~mvV) | prevMv;
-  inL = curLh;
-}
-
-// The same stage with every value as two 32-bit halves (index 0: bits
-// 0-31, 1: bits 32-63); the state is T_{x-1}, Lh_{x-1}, mvV_{x-2} as halves.
-// Halves need no 64-bit register pairs, which saves the compiler copies.
 struct StageH {
   uint32_t T[2], Lh[2], M[2];
 };
@@ -113,8 +82,10 @@ template <bool FULL, bool M3 = false>
 __device__ __forceinline__ void stage_step_h(uint32_t (&L)[2], uint32_t (&T)[2], const StageH &st,
                                              StageH &nx, const LaneWord &lw, uint32_t &mvIn,
                                              uint32_t &mvV) {
-  const uint32_t E0 = FULL ? ~(L[0] | T[0]) : (~(L[0] | T[0]) & lo32(lw.valid));
-  const uint32_t E1 = FULL ? ~(L[1] | T[1]) : (~(L[1] | T[1]) & hi32(lw.valid));
+  const uint32_t E0 =
+      FULL ? lop3<kNor>(L[0], T[0], 0u) : lop3<kNorAnd>(L[0], T[0], lo32(lw.valid));
+  const uint32_t E1 =
+      FULL ? lop3<kNor>(L[1], T[1], 0u) : lop3<kNorAnd>(L[1], T[1], hi32(lw.valid));
   const uint32_t send_l = FULL ? L[1] : L[1] * lw.mul_hi + L[0] * lw.mul_lo;
   const uint32_t rl = __shfl_sync(BML_FULL_MASK, send_l, lw.src_l);
   const uint32_t rr = __shfl_sync(BML_FULL_MASK, E0, lw.src_r);
@@ -126,11 +97,11 @@ __device__ __forceinline__ void stage_step_h(uint32_t (&L)[2], uint32_t (&T)[2],
     Er0 = __funnelshift_r(E0, E1, 1) + rr * lw.ins_lo;
     Er1 = (E1 >> 1) + rr * lw.ins_hi;
   }
-  const uint32_t in0 = __funnelshift_l(rl, L[0], 1) & E0;
-  const uint32_t in1 = __funnelshift_l(L[0], L[1], 1) & E1;
-  const uint32_t Lh0 = (L[0] & ~Er0) | in0, Lh1 = (L[1] & ~Er1) | in1;
-  const uint32_t mv0 = st.T[0] & ~((M3 ? L[0] : Lh0) | T[0]);
-  const uint32_t mv1 = st.T[1] & ~((M3 ? L[1] : Lh1) | T[1]);
+  const uint32_t in0 = lop3<kAnd>(__funnelshift_l(rl, L[0], 1), E0, 0u);
+  const uint32_t in1 = lop3<kAnd>(__funnelshift_l(L[0], L[1], 1), E1, 0u);
+  const uint32_t Lh0 = lop3<kAndNotOr>(L[0], Er0, in0), Lh1 = lop3<kAndNotOr>(L[1], Er1, in1);
+  const uint32_t mv0 = lop3<kAndNor>(st.T[0], M3 ? L[0] : Lh0, T[0]);
+  const uint32_t mv1 = lop3<kAndNor>(st.T[1], M3 ? L[1] : Lh1, T[1]);
   mvIn = __popc(in0) + __popc(in1);
   mvV = __popc(mv0) + __popc(mv1);
   nx.T[0] = T[0];
@@ -139,8 +110,8 @@ __device__ __forceinline__ void stage_step_h(uint32_t (&L)[2], uint32_t (&T)[2],
   nx.Lh[1] = Lh1;
   nx.M[0] = mv0;
   nx.M[1] = mv1;
-  T[0] = (st.T[0] & ~mv0) | st.M[0];
-  T[1] = (st.T[1] & ~mv1) | st.M[1];
+  T[0] = lop3<kAndNotOr>(st.T[0], mv0, st.M[0]);
+  T[1] = lop3<kAndNotOr>(st.T[1], mv1, st.M[1]);
   L[0] = st.Lh[0];
   L[1] = st.Lh[1];
 }

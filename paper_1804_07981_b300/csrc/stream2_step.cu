@@ -76,7 +76,8 @@ struct StateI {
 // lane's column 0 entering at bit 63) and the even cells' entering cars (mHb
 // shifted one bit, the left lane's column 127 entering at bit 0) need
 // shifts: 4 funnel shifts per pair and stage instead of 8 in the plain
-// layout, 22 logic operations instead of 28.
+// layout, 22 logic operations instead of 28.  Every rule line is one lop3
+// per half (18 of the 22), so the count holds in the compiled kernel.
 //
 // M3: Model III (one synchronous phase; a cell may hold one vehicle of each
 // kind): a TB vehicle moves iff the cell below held no vehicle at the start
@@ -85,16 +86,17 @@ template <bool M3>
 __device__ __forceinline__ void stage_i(Quad &L, Quad &T, const StateI &st, StateI &nx,
                                         int src_l, int src_r, uint32_t &cnt, bool cnt_h,
                                         bool cnt_v) {
-  const uint32_t Ea0 = ~(L[0] | T[0]), Ea1 = ~(L[1] | T[1]);
+  const uint32_t Ea0 = lop3<kNor>(L[0], T[0], 0u), Ea1 = lop3<kNor>(L[1], T[1], 0u);
   const uint32_t rr = __shfl_sync(BML_FULL_MASK, Ea0, src_r);
-  const uint32_t mHa0 = L[0] & ~(L[2] | T[2]), mHa1 = L[1] & ~(L[3] | T[3]);
-  const uint32_t mHb0 = L[2] & fsr(Ea0, Ea1), mHb1 = L[3] & fsr(Ea1, rr);
+  const uint32_t mHa0 = lop3<kAndNor>(L[0], L[2], T[2]), mHa1 = lop3<kAndNor>(L[1], L[3], T[3]);
+  const uint32_t mHb0 = lop3<kAnd>(L[2], fsr(Ea0, Ea1), 0u),
+                 mHb1 = lop3<kAnd>(L[3], fsr(Ea1, rr), 0u);
   const uint32_t rl = __shfl_sync(BML_FULL_MASK, mHb1, src_l);
-  const Quad Lh = {L[0] ^ mHa0 ^ fsl(rl, mHb0), L[1] ^ mHa1 ^ fsl(mHb0, mHb1),
-                   L[2] ^ mHb0 ^ mHa0, L[3] ^ mHb1 ^ mHa1};
+  const Quad Lh = {lop3<kXor3>(L[0], mHa0, fsl(rl, mHb0)), lop3<kXor3>(L[1], mHa1, fsl(mHb0, mHb1)),
+                   lop3<kXor3>(L[2], mHb0, mHa0), lop3<kXor3>(L[3], mHb1, mHa1)};
   Quad mV;
 #pragma unroll
-  for (int h = 0; h < 4; ++h) mV[h] = st.T[h] & ~((M3 ? L[h] : Lh[h]) | T[h]);
+  for (int h = 0; h < 4; ++h) mV[h] = lop3<kAndNor>(st.T[h], M3 ? L[h] : Lh[h], T[h]);
   if (cnt_h) cnt += __popc(mHa0) + __popc(mHa1) + __popc(mHb0) + __popc(mHb1);
   if (cnt_v) cnt += (__popc(mV[0]) + __popc(mV[1]) + __popc(mV[2]) + __popc(mV[3])) << 16;
 #pragma unroll
@@ -102,7 +104,7 @@ __device__ __forceinline__ void stage_i(Quad &L, Quad &T, const StateI &st, Stat
     nx.T[h] = T[h];
     nx.L[h] = Lh[h];
     nx.M[h] = mV[h];
-    T[h] = (st.T[h] & ~mV[h]) | st.M[h];
+    T[h] = lop3<kAndNotOr>(st.T[h], mV[h], st.M[h]);
     L[h] = st.L[h];
   }
 }
@@ -116,22 +118,25 @@ struct StateII {
 __device__ __forceinline__ void stage_ii(u64 &La, u64 &Lb, u64 &Ta, u64 &Tb, const StateII &st,
                                          StateII &nx, int src_l, int src_r, uint32_t &cnt,
                                          bool cnt_h, bool cnt_v, u64 coinA, u64 coinB) {
-  const u64 Ea = ~(La | Ta), Eb = ~(Lb | Tb);
   const uint32_t rl = __shfl_sync(BML_FULL_MASK, hi32(Lb), src_l);
   const u64 fLa = mk64(fsl(rl, lo32(La)), fsl(lo32(La), hi32(La)));
   const u64 fLb = mk64(fsl(hi32(La), lo32(Lb)), fsl(lo32(Lb), hi32(Lb)));
-  const u64 iLa = Ea & fLa & (~st.Ta | coinA), iLb = Eb & fLb & (~st.Tb | coinB);
-  const u64 iTa = Ea & st.Ta & ~(fLa & coinA), iTb = Eb & st.Tb & ~(fLb & coinB);
+  // entering LR: empty, LR on the left, and no TB above or the coin says LR;
+  // entering TB: empty, TB above, and no LR on the left or the coin says TB
+  const u64 iLa = lop3<kNorAnd>(La, Ta, lop3<kAndOrNot>(fLa, st.Ta, coinA)),
+            iLb = lop3<kNorAnd>(Lb, Tb, lop3<kAndOrNot>(fLb, st.Tb, coinB));
+  const u64 iTa = lop3<kNorAnd>(La, Ta, lop3<kAndNand>(st.Ta, fLa, coinA)),
+            iTb = lop3<kNorAnd>(Lb, Tb, lop3<kAndNand>(st.Tb, fLb, coinB));
   const uint32_t rr = __shfl_sync(BML_FULL_MASK, lo32(iLa), src_r);
   const u64 mHa = mk64(fsr(lo32(iLa), hi32(iLa)), fsr(hi32(iLa), lo32(iLb)));
   const u64 mHb = mk64(fsr(lo32(iLb), hi32(iLb)), fsr(hi32(iLb), rr));
-  const u64 oTa = (st.Ta & ~iTa) | st.Ma, oTb = (st.Tb & ~iTb) | st.Mb;
+  const u64 oTa = lop3<kAndNotOr>(st.Ta, iTa, st.Ma), oTb = lop3<kAndNotOr>(st.Tb, iTb, st.Mb);
   if (cnt_h) cnt += popc64(mHa) + popc64(mHb);
   if (cnt_v) cnt += (popc64(iTa) + popc64(iTb)) << 16;
   nx.Ta = Ta;
   nx.Tb = Tb;
-  nx.La = (La & ~mHa) | iLa;
-  nx.Lb = (Lb & ~mHb) | iLb;
+  nx.La = lop3<kAndNotOr>(La, mHa, iLa);
+  nx.Lb = lop3<kAndNotOr>(Lb, mHb, iLb);
   nx.Ma = iTa;
   nx.Mb = iTb;
   La = st.La;
