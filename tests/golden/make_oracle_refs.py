@@ -9,10 +9,13 @@ count traces (moved_lr then moved_tb, int64 little-endian), plus a few plain
 numbers for diagnostics.
 
     python tests/golden/make_oracle_refs.py [4096] [windows] [ensemble]
+                                            [ensemble512] [ensemble256]
 
-With no argument all three files are written.  On 8 host threads the 4096^2
-runs take about 30 minutes, the windows about 2 and the ensemble subset
-about 20.
+With no argument all five files are written.  On 8 host threads the 4096^2
+runs take about 30 minutes, the windows about 2, the 32-lattice ensemble
+subset about 20, all 4096 lattices for 512 steps about 2 hours and the
+256-lattice subset for 10^4 steps about 2.5 hours (one single-threaded
+oracle run per lattice, as many processes as host threads).
 
 - oracle_4096_runs.json: the single-lattice workload 4096 x 4096, densities
   0.20, 0.35, 0.50 split evenly between LR and TB, seeds 1-3, 4096 steps,
@@ -31,6 +34,12 @@ about 20.
   placement seed l + 1), one at each of 32 evenly spaced quantiles of the
   cell count, run for the full 10^4 steps; with the first step index at
   which no car moved (-1 if none).
+- oracle_ensemble_all_512.json: every lattice of that workload for 512
+  steps, each recorded by the first 32 hex digits of the SHA-256 of its
+  final lattice followed by its count traces (moved_lr then moved_tb, int64
+  little-endian).
+- oracle_ensemble_256.json: the seeded 256-lattice subset l = 0, 16, 32, ...
+  of that workload for the full 10^4 steps, full records as above.
 """
 from __future__ import annotations
 
@@ -144,14 +153,74 @@ def ensemble_subset(path):
         json.dump(out, f, indent=1)
 
 
+def lattice_digest(g, lr, tb) -> str:
+    h = hashlib.sha256(np.ascontiguousarray(g).tobytes())
+    h.update(np.concatenate([lr.astype("<i8"), tb.astype("<i8")]).tobytes())
+    return h.hexdigest()[:32]
+
+
+def _ens_run(args):
+    """One ensemble lattice through the oracle (a worker process)."""
+    M, N, seed, p_lr, p_tb, K = args
+    g0 = oracle.init(M, N, seed, p_lr, p_tb)
+    return oracle.run(g0, K, threads=1)
+
+
+def _ens_pool_runs(p, idx, K, reduce):
+    import multiprocessing as mp
+    jobs = [(int(p["M"][l]), int(p["N"][l]), int(p["seed"][l]), float(p["p_lr"][l]),
+             float(p["p_tb"][l]), K) for l in idx]
+    # largest first, so the pool ends evenly
+    order = sorted(range(len(jobs)), key=lambda k: -jobs[k][0] * jobs[k][1])
+    out = [None] * len(jobs)
+    tic = time.time()
+    with mp.get_context("spawn").Pool(THREADS) as pool:
+        for n, (k, res) in enumerate(zip(order, pool.imap(_ens_run, [jobs[k] for k in order]))):
+            out[k] = reduce(*res)
+            if n % 256 == 255:
+                print("%d of %d lattices: %.0f s" % (n + 1, len(jobs), time.time() - tic),
+                      flush=True)
+    return out
+
+
+def ensemble_all_512(path):
+    p = ensemble_params(4096, seed=1)
+    K = 512
+    recs = _ens_pool_runs(p, range(4096), K,
+                          lambda g, lr, tb: (lattice_digest(g, lr, tb), int(lr.sum()),
+                                             int(tb.sum())))
+    out = {"workload": "ensemble_params(4096, seed=1)", "steps": K,
+           "lr_sum": sum(r[1] for r in recs), "tb_sum": sum(r[2] for r in recs),
+           "digests": [r[0] for r in recs]}
+    with open(path, "w") as f:
+        json.dump(out, f, indent=0)
+
+
+def ensemble_256(path):
+    p = ensemble_params(4096, seed=1)
+    idx = list(range(0, 4096, 16))
+    recs = _ens_pool_runs(p, idx, ENS_STEPS, record)
+    out = {"workload": "ensemble_params(4096, seed=1)", "steps": ENS_STEPS, "lattices": []}
+    for l, r in zip(idx, recs):
+        rec = {"index": l, "M": int(p["M"][l]), "N": int(p["N"][l])}
+        rec.update(r)
+        out["lattices"].append(rec)
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1)
+
+
 def main(argv):
-    which = set(argv) or {"4096", "windows", "ensemble"}
+    which = set(argv) or {"4096", "windows", "ensemble", "ensemble512", "ensemble256"}
     if "windows" in which:
         windows_32768(os.path.join(HERE, "oracle_32768_windows.json"))
     if "ensemble" in which:
         ensemble_subset(os.path.join(HERE, "oracle_ensemble_subset.json"))
     if "4096" in which:
         runs_4096(os.path.join(HERE, "oracle_4096_runs.json"))
+    if "ensemble512" in which:
+        ensemble_all_512(os.path.join(HERE, "oracle_ensemble_all_512.json"))
+    if "ensemble256" in which:
+        ensemble_256(os.path.join(HERE, "oracle_ensemble_256.json"))
 
 
 if __name__ == "__main__":
