@@ -76,9 +76,14 @@ ALU_LANES_PER_SM_CLK = 64  # integer ALU pipe: 2 warp instructions per clock per
 SM_MAX_MHZ = 2032.0
 # DRAM bytes (read + write, as counted by ncu for one launch) per cell, from
 # the captures summarised in profiles/ (32768 x 32768, the kernels as they are
-# now); scaled by the cell count of the run.  A kernel without an entry (or
+# now), keyed by kernel and band rows (the captured tiling); scaled by the
+# cell count of the run.  A kernel or tiling without an entry (or a kernel
 # changed since its capture) reports traffic null.
-TRAFFIC_PER_CELL = {"stream2_kernel<8>": 0.4698, "stream2_kernel<1>": 0.4525}
+TRAFFIC_PER_CELL = {("stream2_kernel<8>", 251): 0.4698, ("stream2_kernel<1>", 16): 0.4525,
+                    ("stream2_kernel<4, Model II>", 167): 0.4664}
+# the ensemble kernel per cell and chunk of 8 steps (bands of 448 rows: one
+# launch of 8 chunks captured, 20.77 GB over 4.55e9 cells)
+ENS_TRAFFIC_PER_CELL_CHUNK = {(8, 448): 0.5706}
 
 
 def _peaks():
@@ -291,7 +296,11 @@ def _ensemble_bench(bml, torch, stream, steps, seed_base=1, tiling=None, sm_mhz=
             "cell_updates_per_s": cu, "cells": cells,
             "roofline": {"bound": "alu", "kernel": "ens_kernel<%d>" % k, "achieved": ops,
                          "peak": peak, "unit": "Tops/s", "frac": ops / peak,
-                         "ops_per_cell_step": ALU_OPS_PER_CELL_STEP},
+                         "ops_per_cell_step": ALU_OPS_PER_CELL_STEP,
+                         "traffic_per_chunk": (ENS_TRAFFIC_PER_CELL_CHUNK[(k, band)] * cells
+                                               if (k, band) in ENS_TRAFFIC_PER_CELL_CHUNK
+                                               else None),
+                         "chunk_steps": k},
             "temporal_depth": k, "band_rows": band, "graph": graphs,
             "workload": "4096 lattices, M,N ~ U{64..2048}, rho ~ U[0.1,0.6], "
                         "LR fraction ~ U[0.3,0.7], seeds 1..4096"}
@@ -338,7 +347,9 @@ def _model2_bench(bml, torch, stream, M, N, steps, sm_mhz, seed=1, tiling=None, 
             "temporal_depth": k, "band_rows": band, "lane_words": lw,
             "gpu_launches": launches,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak,
+                         "traffic": (TRAFFIC_PER_CELL[(kname, band)] * cells
+                                     if (kname, band) in TRAFFIC_PER_CELL else None),
                          "ops_per_cell_step": per}}
 
 
@@ -402,7 +413,7 @@ def _one_pass_bench(bml, torch, stream, M, N, steps, hbm_peak, seed=1):
     cells = M * N
     gbs = BYTES_PER_CELL_STEP * cells * steps / (ms / 1e3) / 1e9
     kname = "stream2_kernel<1>" if lw == 2 else "stream_kernel<1>"
-    traffic = TRAFFIC_PER_CELL.get(kname)
+    traffic = TRAFFIC_PER_CELL.get((kname, 16))
     return {"metric": "cell-updates/s", "value": cells * steps / (ms / 1e3),
             "unit": "cell-updates/s", "steps": steps, "seconds": ms / 1e3,
             "kernel": kname, "temporal_depth": 1, "band_rows": 16, "lane_words": lw,
@@ -634,7 +645,7 @@ def run_ours(args):
     launch_ms = ms / (K * launches_per_step)
     cell_steps_per_launch = cells * depth
     effective = BYTES_PER_CELL_STEP * cells * lattice_steps / (ms / 1e3) / 1e9
-    traffic = TRAFFIC_PER_CELL.get(kname)
+    traffic = TRAFFIC_PER_CELL.get((kname, band_rows))
     if depth >= 2:
         # bit logic with k steps per DRAM pass: bound by the integer ALU pipe
         ops = ALU_OPS_PER_CELL_STEP * cell_steps_per_launch
