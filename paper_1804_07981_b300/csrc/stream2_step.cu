@@ -97,7 +97,11 @@ __device__ __forceinline__ void stage_i(Quad &L, Quad &T, const StateI &st, Stat
   Quad mV;
 #pragma unroll
   for (int h = 0; h < 4; ++h) mV[h] = lop3<kAndNor>(st.T[h], M3 ? L[h] : Lh[h], T[h]);
-  if (cnt_h) cnt += __popc(mHa0) + __popc(mHa1) + __popc(mHb0) + __popc(mHb1);
+  // a car cannot move while the cell to its right holds a car, so the cars of
+  // columns 2i and 2i + 1 never both move: mHa and mHb share no bit, and one
+  // popcount per half pair counts both (the popcounts' pipe, not the logic,
+  // was the busiest unit before)
+  if (cnt_h) cnt += __popc(mHa0 | mHb0) + __popc(mHa1 | mHb1);
   if (cnt_v) cnt += (__popc(mV[0]) + __popc(mV[1]) + __popc(mV[2]) + __popc(mV[3])) << 16;
 #pragma unroll
   for (int h = 0; h < 4; ++h) {
