@@ -169,6 +169,25 @@ def test_conservation_and_bounds(M, N, rho, seed):
         cur = nxt
 
 
+@pytest.mark.parametrize("M,N,rho,seed", [(16, 64, 0.3, 1), (9, 65, 0.5, 2), (33, 130, 0.7, 3),
+                                          (5, 2, 0.6, 4)])
+def test_horizontally_adjacent_cars_never_both_move(M, N, rho, seed):
+    """A car cannot move while the cell to its right holds a car, so in the
+    horizontal phase the cars of columns j and j + 1 (mod N) never both
+    move (the GPU kernels count the two interleaved move masks of a column
+    pair with one popcount because of this)."""
+    cur = random_lattice(M, N, seed, rho / 2, rho / 2)
+    total = 0
+    for _ in range(8):
+        h, moved = oracle.phase(cur, 0)
+        mv = (cur == LR) & (h != LR)  # the cars that left their cell
+        assert int(mv.sum()) == moved
+        assert not (mv & np.roll(mv, -1, axis=1)).any()
+        total += moved
+        cur, _ = oracle.phase(h, 1)
+    assert total > 0
+
+
 @pytest.mark.parametrize("M,N", [(12, 63), (9, 64), (10, 65), (6, 127), (5, 129), (3, 2047)])
 def test_translation_equivariance(M, N):
     g = random_lattice(M, N, M * 1000 + N, 0.2, 0.2)
