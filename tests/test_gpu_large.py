@@ -5,8 +5,9 @@ written by tests/golden/make_oracle_refs.py, which runs only the oracle and
 records each final lattice and count trace by its SHA-256): all nine
 4096^2 x 4096-step runs through both the byte-per-cell and the bit-packed
 kernels, the 32768^2 lattice after 1024 steps through eight (2t + 33)^2
-windows in the benchmark's launch configuration, and 32 lattices of the
-ensemble workload for the full 10^4 steps.  Beside them: oracle runs on
+windows in the benchmark's launch configuration, 32 lattices of the
+ensemble workload for the full 10^4 steps, and every lattice of that
+workload for 512 steps.  Beside them: oracle runs on
 sampled windows computed here, exact cross-checks between independent GPU
 paths, and properties that hold at any size."""
 import hashlib
@@ -35,6 +36,14 @@ def _digest(a):
 
 def _count_digest(lr, tb):
     return _digest(np.concatenate([np.asarray(lr).astype("<i8"), np.asarray(tb).astype("<i8")]))
+
+
+def _lattice_digest(g, lr, tb):
+    """First 32 hex digits of the SHA-256 of a final lattice followed by its
+    count traces (the oracle_ensemble_all_512.json record)."""
+    h = hashlib.sha256(np.ascontiguousarray(g).tobytes())
+    h.update(np.concatenate([np.asarray(lr).astype("<i8"), np.asarray(tb).astype("<i8")]).tobytes())
+    return h.hexdigest()[:32]
 
 
 @pytest.mark.parametrize("kernel", ["byte", "auto"])
@@ -277,20 +286,26 @@ def _byte_runs(lib, M, N, seeds, plr, ptb, K):
     return outs, np.stack(lrs), np.stack(tbs)
 
 
-def test_ensemble_workload_all_lattices_512_steps_against_byte_kernel(lib):
+def test_ensemble_workload_all_lattices_512_steps_against_oracle(lib):
     """The batched-ensemble workload (4096 lattices, M, N uniform on
     {64..2048}, density in [0.1, 0.6], LR fraction in [0.3, 0.7]), autotuned
-    as the bench runs it, 512 steps: every lattice and every count equals the
-    lattice run alone through the byte-per-cell kernels (an independent GPU
-    path)."""
+    as the bench runs it, 512 steps: every lattice's final state and count
+    traces equal the oracle's (tests/golden/oracle_ensemble_all_512.json),
+    and also the lattice run alone through the byte-per-cell kernels (an
+    independent GPU path)."""
     from paper_1804_07981_b300.inputs import ensemble_params
+    ref = _golden("oracle_ensemble_all_512.json")
     p = ensemble_params(4096, seed=1)
-    K = 512
+    K = ref["steps"]
+    assert K == 512 and len(ref["digests"]) == 4096
     with lib.Ensemble(p["M"], p["N"], p["seed"], p["p_lr"], p["p_tb"],
                       reserve_steps=K) as ens:
         ens.step(K)
         got = ens.read_all()
         lr, tb = ens.traces()
+    bad = [l for l in range(4096) if _lattice_digest(got[l], lr[l], tb[l]) != ref["digests"][l]]
+    assert not bad, "lattices differing from the oracle: %s" % bad[:16]
+    assert int(lr.sum()) == ref["lr_sum"] and int(tb.sum()) == ref["tb_sum"]
     want, wlr, wtb = _byte_runs(lib, p["M"], p["N"], p["seed"], p["p_lr"], p["p_tb"], K)
     for l in range(len(want)):
         assert np.array_equal(got[l], want[l]), l

@@ -1,7 +1,7 @@
 """The stored full-length oracle results (tests/golden/oracle_*.json) are
 what the committed script computes from the oracle: their layout is
-checked, and the cheapest record (the smallest lattice of the ensemble
-subset, 10^4 steps) is recomputed here from the oracle alone."""
+checked, and the cheapest records (the smallest lattice of each ensemble
+file) are recomputed here from the oracle alone."""
 import importlib.util
 import json
 import os
@@ -43,6 +43,9 @@ def test_golden_files_cover_the_workloads():
     mod = _script()
     p = ensemble_params(4096, seed=1)
     assert [r["index"] for r in ens["lattices"]] == mod.ensemble_subset_indices(p)
+    all512 = _load("oracle_ensemble_all_512.json")
+    assert all512["steps"] == 512 and len(all512["digests"]) == 4096
+    assert all(len(d) == 32 and int(d, 16) >= 0 for d in all512["digests"])
 
 
 def test_smallest_ensemble_record_recomputes_from_the_oracle():
@@ -58,3 +61,18 @@ def test_smallest_ensemble_record_recomputes_from_the_oracle():
     for key, val in got.items():
         assert rec[key] == val, key
     assert isinstance(rec["first_zero_step"], int) and np.all(lr >= 0)
+
+
+def test_smallest_records_of_the_whole_ensemble_files_recompute():
+    """The three smallest lattices of the 512-step file, recomputed from the
+    oracle."""
+    mod = _script()
+    p = ensemble_params(4096, seed=1)
+    cells = p["M"].astype(np.int64) * p["N"].astype(np.int64)
+    all512 = _load("oracle_ensemble_all_512.json")
+    for l in np.argsort(cells, kind="stable")[:3]:
+        l = int(l)
+        g0 = oracle.init(int(p["M"][l]), int(p["N"][l]), int(p["seed"][l]),
+                         float(p["p_lr"][l]), float(p["p_tb"][l]))
+        g, lr, tb = oracle.run(g0, 512)
+        assert mod.lattice_digest(g, lr, tb) == all512["digests"][l], l
