@@ -8,11 +8,12 @@ the SHA-256 of its final lattice (M*N bytes, row-major, 0/1/2) and of its
 count traces (moved_lr then moved_tb, int64 little-endian), plus a few plain
 numbers for diagnostics.
 
-    python tests/golden/make_oracle_refs.py [4096] [windows] [ensemble]
+    python tests/golden/make_oracle_refs.py [4096] [windows] [windows4096] [ensemble]
                                             [ensemble512] [ensemble256]
 
-With no argument all five files are written.  On 8 host threads the 4096^2
-runs take about 30 minutes, the windows about 2, the 32-lattice ensemble
+With no argument all six files are written.  On 8 host threads the 4096^2
+runs take about 30 minutes, the t = 1024 windows about 2 (the four t = 4096
+windows about an hour), the 32-lattice ensemble
 subset about 20, all 4096 lattices for 512 steps about 2 hours and the
 256-lattice subset for 10^4 steps about 2.5 hours (one single-threaded
 oracle run per lattice, as many processes as host threads).
@@ -28,6 +29,8 @@ oracle run per lattice, as many processes as host threads).
   (2t + 33) x (2t + 33) window of the initial lattice, wrapped as its own
   torus, gives the exact state of the window's 33 x 33 centre.  Eight
   windows; the first straddles both wrap seams.
+- oracle_32768_windows_4096.json: the same lattice after t = 4096 steps,
+  four (2t + 33) x (2t + 33) windows (the first across both seams).
 - oracle_ensemble_subset.json: 32 lattices of the batched-ensemble workload
   (4096 lattices, M, N uniform on {64..2048}, density uniform on [0.1, 0.6],
   LR fraction uniform on [0.3, 0.7], numpy PCG64 seed 1; lattice l uses
@@ -100,21 +103,21 @@ WINDOW_T = 1024
 WINDOW_CORE = 33
 
 
-def window_corners(M, N):
-    rng = np.random.Generator(np.random.PCG64(1024))
-    corners = rng.integers(0, M, size=(8, 2))
-    half = WINDOW_T + WINDOW_CORE // 2
+def window_corners(M, N, t=WINDOW_T, count=8):
+    rng = np.random.Generator(np.random.PCG64(t))
+    corners = rng.integers(0, M, size=(count, 2))
+    half = t + WINDOW_CORE // 2
     corners[0] = [M - half, N - half]  # the centre sits on both wrap seams
     return [(int(i), int(j)) for i, j in corners]
 
 
-def windows_32768(path):
+def windows_32768(path, t=WINDOW_T, count=8):
     M = N = 32768
-    t, c = WINDOW_T, WINDOW_CORE
+    c = WINDOW_CORE
     S = 2 * t + c
     out = {"M": M, "N": N, "rho": 0.38, "seed": 1, "steps": t, "window": S, "centre": c,
            "windows": []}
-    for i0, j0 in window_corners(M, N):
+    for i0, j0 in window_corners(M, N, t, count):
         tic = time.time()
         w = oracle.init_window(i0, j0, S, S, M, N, 1, 0.19, 0.19)
         w_t, _, _ = oracle.run(w, t, threads=THREADS)
@@ -210,9 +213,12 @@ def ensemble_256(path):
 
 
 def main(argv):
-    which = set(argv) or {"4096", "windows", "ensemble", "ensemble512", "ensemble256"}
+    which = set(argv) or {"4096", "windows", "windows4096", "ensemble", "ensemble512",
+                          "ensemble256"}
     if "windows" in which:
         windows_32768(os.path.join(HERE, "oracle_32768_windows.json"))
+    if "windows4096" in which:
+        windows_32768(os.path.join(HERE, "oracle_32768_windows_4096.json"), t=4096, count=4)
     if "ensemble" in which:
         ensemble_subset(os.path.join(HERE, "oracle_ensemble_subset.json"))
     if "4096" in which:
