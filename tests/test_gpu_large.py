@@ -5,7 +5,8 @@ written by tests/golden/make_oracle_refs.py, which runs only the oracle and
 records each final lattice and count trace by its SHA-256): all nine
 4096^2 x 4096-step runs through both the byte-per-cell and the bit-packed
 kernels, the 32768^2 lattice after 1024 steps through eight (2t + 33)^2
-windows in the benchmark's launch configuration, 32 lattices of the
+windows in the benchmark's launch configuration and after 4096 steps through
+four, 32 lattices of the
 ensemble workload for the full 10^4 steps, and every lattice of that
 workload for 512 steps.  Beside them: oracle runs on
 sampled windows computed here, exact cross-checks between independent GPU
@@ -81,6 +82,24 @@ def test_32768_windows_after_1024_steps_against_oracle(lib, config):
         sim.step(t)
         got = sim.read()
     assert len(ref["windows"]) == 8
+    for w in ref["windows"]:
+        rows = (np.arange(t, t + c) + w["i0"]) % M
+        cols = (np.arange(t, t + c) + w["j0"]) % N
+        want = np.array([[int(ch) for ch in r] for r in w["centre_rows"]], dtype=np.uint8)
+        np.testing.assert_array_equal(got[np.ix_(rows, cols)], want, err_msg=str(w["i0"]))
+
+
+def test_32768_windows_after_4096_steps_against_oracle(lib):
+    """32768 x 32768, density 0.38, seed 1, 4096 steps, autotuned as the
+    benchmark runs it: the 33 x 33 centres of four (2t + 33)^2 windows (t =
+    4096), one across both wrap seams, equal the oracle's run of each window
+    as its own torus."""
+    ref = _golden("oracle_32768_windows_4096.json")
+    M, N, t, c = ref["M"], ref["N"], ref["steps"], ref["centre"]
+    assert t == 4096 and len(ref["windows"]) == 4
+    with lib.Lattice(M, N, seed=ref["seed"], density=ref["rho"], reserve_steps=t) as sim:
+        sim.step(t)
+        got = sim.read()
     for w in ref["windows"]:
         rows = (np.arange(t, t + c) + w["i0"]) % M
         cols = (np.arange(t, t + c) + w["j0"]) % N

@@ -39,6 +39,12 @@ def test_golden_files_cover_the_workloads():
     assert w0["i0"] + t < M <= w0["i0"] + t + c - 1 and w0["j0"] + t < M <= w0["j0"] + t + c - 1
     for w in win["windows"]:
         assert len(w["centre_rows"]) == c and all(len(r) == c for r in w["centre_rows"])
+    w4 = _load("oracle_32768_windows_4096.json")
+    t4 = w4["steps"]
+    assert (t4, w4["centre"], w4["window"]) == (4096, 33, 2 * 4096 + 33)
+    assert len(w4["windows"]) == 4
+    v0 = w4["windows"][0]
+    assert v0["i0"] + t4 < M <= v0["i0"] + t4 + c - 1 and v0["j0"] + t4 < M <= v0["j0"] + t4 + c - 1
     ens = _load("oracle_ensemble_subset.json")
     mod = _script()
     p = ensemble_params(4096, seed=1)
