@@ -123,20 +123,21 @@ cudaError_t launch_resident(const u64 *Lin, const u64 *Tin, u64 *Lout, u64 *Tout
 // Two-words-per-lane streaming kernel (rows of full words, W even, W > 32);
 // model 1 (the paper's model), 2 (Model II, with tie_seed and the index t0
 // of the launch's first step) or 3 (Model III).  Models 1 and 3 run on the
-// pair-interleaved layout of the planes (see launch_pair_layout), Model II
-// on the plain one.
+// interleaved layout of the planes (see launch_pair_layout), Model II on the
+// plain one.  stream2_bands_for_tiles: the largest band count whose warp
+// tiles number at most `tiles`.
 bool stream2_applies(const Geom &g);
-int64_t stream2_strips(const Geom &g);
+int64_t stream2_bands_for_tiles(const Geom &g, int64_t tiles);
 int stream2_occupancy(int k, int model = 1);
 cudaError_t launch_stream2(const u64 *Lin, const u64 *Tin, u64 *Lout, u64 *Tout, const Geom &g,
                            int k, int64_t band_rows, u64 *moved_lr, u64 *moved_tb,
                            cudaStream_t st, int model = 1, u64 tie_seed = 0, u64 t0 = 0);
 
-// Pair-interleaved layout (rows of full words, W even): in every aligned
-// word pair (2p, 2p+1) of a row, word 2p holds the even columns of the
-// pair's 128 (bit i = column 128p + 2i) and word 2p+1 the odd ones (bit i =
-// column 128p + 2i + 1).  Converts both planes in place between the plain
-// layout and this one (to_pair: plain -> interleaved).
+// Interleaved layout (rows of full words, W even): word w of a row holds
+// its 64 columns' even ones in its low half (bit i = column 64w + 2i) and
+// the odd ones in its high half (bit 32 + i = column 64w + 2i + 1).
+// Converts both planes in place between the plain layout and this one
+// (to_pair: plain -> interleaved).
 cudaError_t launch_pair_layout(u64 *L, u64 *T, const Geom &g, bool to_pair, cudaStream_t st);
 
 // Launch `kern` with programmatic stream serialization: it may be scheduled

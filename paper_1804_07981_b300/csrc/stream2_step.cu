@@ -3,17 +3,26 @@
 //
 // Same pipeline as stream_step.cu (k stages in registers, the Sec. 2 rules
 // per stage, the TB cars entering a row being the previous row's TB move
-// mask), but lane l of a warp holds one aligned pair of ring words: pair
-// first-1+l of the W/2 pairs of the row (W even), read and written with
-// 128-bit accesses.  For the paper's model the planes are kept in the
-// pair-interleaved layout (launch_pair_layout: the pair's even columns in
-// its first word, the odd columns in its second), so that a cell's right
-// neighbour is mostly the same bit of the other word and the horizontal rule
-// needs half the shifts of the plain layout; lanes 0 and owned+1 hold halo
-// pairs (a 128-column cone), lanes 1..owned are stored and counted (up to 30
-// pairs per warp).  Per stage and row a lane makes two 32-bit shuffles for
-// two words: the right lane's low half of E (even columns) and the left
-// lane's high half of the odd columns' LR move mask.
+// mask), but a lane holds one aligned pair of ring words (128 columns), read
+// and written with 128-bit accesses.  For the paper's model the planes are
+// kept in the interleaved layout (launch_pair_layout: every word's even
+// columns in its low half, its odd columns in its high half), so that a
+// cell's right neighbour is mostly the same bit of the other half and the
+// horizontal rule needs half the shifts of the plain layout.  Per stage and
+// row a lane makes two 32-bit shuffles for two words: the right lane's even
+// columns of E and the left lane's odd columns of the LR move mask.
+//
+// Lane groups.  A row of WP <= 32 pairs is one cyclic group of WP lanes (the
+// whole ring, no halo).  Wider rows are cut into segments of 31 pairs and a
+// remainder segment; a segment's group is its lanes plus one halo lane that
+// holds the first 64 columns right of the segment (its low word) and the
+// last 64 columns left of it (its high word), and the group's shuffles are
+// cyclic.  The halo lane's two words are not neighbours in the lattice, but
+// a wrong neighbour changes a cell only after as many steps as the cell is
+// columns away from it (one per step), so at depth k < 33 the columns next
+// to the segment stay exact.  Remainder groups of several bands share a
+// warp (up to 32 lanes), so a row of 256 pairs costs 8 + 1/3 warp tiles per
+// band instead of 9 with a halo lane on each side of 30 pairs.
 //
 // Moved-car counts: one 32-bit register per stage and lane holds the LR moves
 // in its low 16 bits and the TB moves in its high 16 bits (a lane moves at
@@ -22,8 +31,9 @@
 // rows.  This keeps the depth-8 kernel within 255 registers without spills.
 //
 // Input rows reach the warp through a ring of kRing row slots in shared
-// memory, filled kAhead rows ahead with cp.async (16 bytes per lane and
-// plane); a slot is refilled at least two rows after it was last read.  The
+// memory, filled kAhead rows ahead with cp.async (the lane's two words as two
+// 8-byte copies per plane, so that the halo lane can take them from two
+// pairs); a slot is refilled at least two rows after it was last read.  The
 // prefetch holds no registers and its wait is explicit.  In the steady part
 // of a band two rows are read from the ring before either runs its stages,
 // so that the second row's early stages can overlap the first row's late
@@ -56,9 +66,13 @@ static_assert(kAhead + 1 <= kRing - 2 && (kRing & (kRing - 1)) == 0, "ring layou
 __device__ __forceinline__ uint32_t fsr(uint32_t lo, uint32_t hi) { return __funnelshift_r(lo, hi, 1); }
 __device__ __forceinline__ uint32_t fsl(uint32_t lo, uint32_t hi) { return __funnelshift_l(lo, hi, 1); }
 
-// A lane's two words as four 32-bit halves: a.lo, a.hi, b.lo, b.hi.  Model I
-// keeps every value of a stage as separate 32-bit halves (no 64-bit register
-// pairs to form), which measured 3-7% faster than the same logic on u64.
+// A lane's 128 columns as four 32-bit halves: a.lo, a.hi, b.lo, b.hi, where
+// a is the pair's 64 even columns (bit i = column 2i of the pair's 128) and b
+// its 64 odd columns.  In the interleaved layout a.lo and b.lo are the low
+// and high halves of the pair's first word, a.hi and b.hi those of its
+// second.  Model I keeps every value of a stage as separate 32-bit halves (no
+// 64-bit register pairs to form), which measured 3-7% faster than the same
+// logic on u64.
 typedef uint32_t Quad[4];
 
 // Stage state of the paper's model: T_{x-1}, Lh_{x-1}, mvV_{x-2} (halves).
@@ -66,10 +80,8 @@ struct StateI {
   Quad T, L, M;
 };
 
-// One Model I stage on the lane's pair in the column-interleaved layout
-// (word a holds the pair's even columns, bit i = column 2i of the pair's
-// 128; word b the odd ones, bit i = column 2i + 1); see stage.cuh for the
-// rule.  The right neighbour of even column 2i is odd column 2i + 1, the
+// One Model I stage on the lane's 128 columns (a: even columns, b: odd
+// columns; see Quad); see stage.cuh for the rule.  The right neighbour of even column 2i is odd column 2i + 1, the
 // same bit of b, so the even cells' move mask needs no shift:
 // mHa = La & ~(Lb | Tb), and the cars entering the odd cells are exactly
 // mHa.  Only the odd cells' right neighbours (a shifted one bit, the right
@@ -167,30 +179,41 @@ __device__ __forceinline__ void flush_counts(uint32_t (&cnt)[K], bool own, int l
   }
 }
 
+// Store a lane's pair (the inverse of read_row's order).
+template <int MODEL>
 __device__ __forceinline__ void st_quad(u64 *p, const Quad &v) {
-  __stcs(reinterpret_cast<uint4 *>(p), make_uint4(v[0], v[1], v[2], v[3]));
+  __stcs(reinterpret_cast<uint4 *>(p), MODEL == 2 ? make_uint4(v[0], v[1], v[2], v[3])
+                                                  : make_uint4(v[0], v[2], v[1], v[3]));
 }
 
-// Per-warp constants and running positions of a tile.
+// Per-lane constants and running positions of a tile.
 struct PairTile {
-  const u64 *Lin, *Tin;  // this lane's pair in row 0 of the input planes
-  const u64 *fL;         // this lane's pair in the next row to fetch (L plane)
-  int64_t dT;            // T plane minus L plane, in words (input and output)
-  u64 *sL;               // this lane's pair in the next row to store (L plane)
-  size_t pitch;          // row pitch in words
-  int ld_row, M;         // lattice row of the next row to fetch
-  int wa;              // first word of this lane's pair
-  int r0, B, n_in;     // band start, band rows, input rows (B + 2K)
+  const u64 *Lin;  // this lane's first word in row 0 of the input L plane
+  const u64 *fL;   // this lane's first word in the next row to fetch (L plane)
+  int64_t dT;      // T plane minus L plane, in words (input and output)
+  int64_t dH;      // this lane's second word minus its first (1, except the halo lane)
+  u64 *sL;         // this lane's pair in the next row to store (L plane)
+  size_t pitch;    // row pitch in words
+  int ld_row, M;   // lattice row of the next row to fetch
+  int wa;          // first word of this lane's (owned) pair
+  int r0, B, n_in; // band start, band rows, input rows (B + 2K); B = 0 off a band
   int src_l, src_r;
   bool own;
   u64 W64, MW, nbase, tie_seed;  // Model II tie-break counters
   int x0;                        // lattice row of the current input row (Model II)
 };
 
-// Fetch the next input row into ring slot `slot` (one commit group).
+// Fetch the next input row into ring slot `slot` (one commit group): the
+// lane's two words as two 8-byte copies per plane (the halo lane's come from
+// two different pairs).
 __device__ __forceinline__ void fetch_row(PairTile &t, RingSlot *ring, int lane, int slot) {
-  cp_async16(&ring[slot][0][lane], t.fL);
-  cp_async16(&ring[slot][1][lane], t.fL + t.dT);
+  u64 *dL = reinterpret_cast<u64 *>(&ring[slot][0][lane]);
+  u64 *dT = reinterpret_cast<u64 *>(&ring[slot][1][lane]);
+  const u64 *fT = t.fL + t.dT;
+  cp_async8(dL, t.fL);
+  cp_async8(dL + 1, t.fL + t.dH);
+  cp_async8(dT, fT);
+  cp_async8(dT + 1, fT + t.dH);
   if (++t.ld_row == t.M) {
     t.ld_row = 0;
     t.fL = t.Lin;
@@ -199,12 +222,20 @@ __device__ __forceinline__ void fetch_row(PairTile &t, RingSlot *ring, int lane,
   }
 }
 
-// Ring slot of input row i as four halves per plane.
+// Ring slot of input row i as four halves per plane: in memory order for
+// Model II (plain layout: first word, second word), as (a.lo, a.hi, b.lo,
+// b.hi) for the interleaved layout (see Quad).
+template <int MODEL>
 __device__ __forceinline__ void read_row(const RingSlot *ring, int lane, int i, Quad &L, Quad &T) {
   const uint4 vL = *reinterpret_cast<const uint4 *>(&ring[i & (kRing - 1)][0][lane]);
   const uint4 vT = *reinterpret_cast<const uint4 *>(&ring[i & (kRing - 1)][1][lane]);
-  L[0] = vL.x, L[1] = vL.y, L[2] = vL.z, L[3] = vL.w;
-  T[0] = vT.x, T[1] = vT.y, T[2] = vT.z, T[3] = vT.w;
+  if (MODEL == 2) {
+    L[0] = vL.x, L[1] = vL.y, L[2] = vL.z, L[3] = vL.w;
+    T[0] = vT.x, T[1] = vT.y, T[2] = vT.z, T[3] = vT.w;
+  } else {
+    L[0] = vL.x, L[1] = vL.z, L[2] = vL.y, L[3] = vL.w;
+    T[0] = vT.x, T[1] = vT.z, T[2] = vT.y, T[3] = vT.w;
+  }
 }
 
 // Input row i (already in registers) through the K stages; U selects the
@@ -224,7 +255,7 @@ __device__ __forceinline__ void run_stages(PairTile &t, int i, int x0, Quad &L, 
       u64 La = mk64(L[0], L[1]), Lb = mk64(L[2], L[3]), Ta = mk64(T[0], T[1]),
           Tb = mk64(T[2], T[3]);
       stage_ii(La, Lb, Ta, Tb, st[U][s], st[U ^ 1][s], t.src_l, t.src_r, cnt[s], ch, cv,
-               splitmix64_at(t.tie_seed, n), splitmix64_at(t.tie_seed, n + 1));
+               splitmix64_at(t.tie_seed, n), splitmix64_at(t.tie_seed, n + (u64)t.dH));
       L[0] = lo32(La), L[1] = hi32(La), L[2] = lo32(Lb), L[3] = hi32(Lb);
       T[0] = lo32(Ta), T[1] = hi32(Ta), T[2] = lo32(Tb), T[3] = hi32(Tb);
     } else {
@@ -233,34 +264,40 @@ __device__ __forceinline__ void run_stages(PairTile &t, int i, int x0, Quad &L, 
   }
 }
 
-// Store the next emitted row (band rows in order).
-__device__ __forceinline__ void store_row(PairTile &t, const Quad &L, const Quad &T) {
-  if (t.own) {
-    st_quad(t.sL, L);
-    st_quad(t.sL + t.dT, T);
+// Store the next emitted row (band rows in order); `in_band`: the row lies
+// in the lane's band.
+template <int MODEL>
+__device__ __forceinline__ void store_row(PairTile &t, const Quad &L, const Quad &T,
+                                          bool in_band = true) {
+  if (t.own && in_band) {
+    st_quad<MODEL>(t.sL, L);
+    st_quad<MODEL>(t.sL + t.dT, T);
   }
   t.sL += t.pitch;
 }
 
-// One input row near the band's ends (pipeline fill and drain): rows past
-// the input are skipped, stages whose row lies outside the band are not
-// counted, and nothing is stored before row 2K.
+// One input row near the band's ends (pipeline fill and drain), run by the
+// whole warp while any of its lanes has input rows left (the bands of a
+// warp's lane groups may differ in height): a lane fetches only its own input
+// rows, stages whose row lies outside the lane's band are not counted, and a
+// lane stores only rows of its band, from row 2K on (lanes past their input
+// run on stale slots and keep nothing).
 template <int K, int MODEL, int U, typename ST>
 __device__ __forceinline__ void guarded_row(PairTile &t, RingSlot *ring, int lane, int i,
                                             ST (&st)[2][K], uint32_t (&cnt)[K]) {
-  if (i >= t.n_in) return;
   if (i + kAhead < t.n_in) fetch_row(t, ring, lane, (i + kAhead) & (kRing - 1));
   cp_async_commit();
   cp_async_wait<kAhead>();  // row i has landed
   Quad L, T;
-  read_row(ring, lane, i, L, T);
+  read_row<MODEL>(ring, lane, i, L, T);
   run_stages<K, MODEL, true, U>(t, i, t.x0, L, T, st, cnt);
   if (++t.x0 == t.M) t.x0 = 0;
-  if (i >= 2 * K) store_row(t, L, T);
+  if (i >= 2 * K) store_row<MODEL>(t, L, T, i - 2 * K < t.B);
 }
 
-// One input row of the band's steady part (below B + K): every stage's row
-// lies in the band and the emitted row is stored.
+// One input row of the band's steady part (below the smallest B + K of the
+// warp's lanes): every stage's row lies in the lane's band and the emitted
+// row is stored.
 template <int K, int MODEL, int U, typename ST>
 __device__ __forceinline__ void steady_row1(PairTile &t, RingSlot *ring, int lane, int i,
                                             ST (&st)[2][K], uint32_t (&cnt)[K]) {
@@ -268,13 +305,14 @@ __device__ __forceinline__ void steady_row1(PairTile &t, RingSlot *ring, int lan
   cp_async_commit();
   cp_async_wait<kAhead>();  // row i has landed
   Quad L, T;
-  read_row(ring, lane, i, L, T);
+  read_row<MODEL>(ring, lane, i, L, T);
   run_stages<K, MODEL, false, U>(t, i, t.x0, L, T, st, cnt);
   if (++t.x0 == t.M) t.x0 = 0;
-  store_row(t, L, T);
+  store_row<MODEL>(t, L, T);
 }
 
-// Two input rows i, i + 1 of the band's steady part (both below B + K):
+// Two input rows i, i + 1 of the band's steady part (both below the
+// smallest B + K of the warp's lanes):
 // every stage's row lies in the band and both emitted rows are stored.  Both
 // rows are fetched from the ring before any stage runs, so the stages of row
 // i + 1 can overlap the later stages of row i (no memory operation of row i
@@ -297,24 +335,39 @@ __device__ __forceinline__ void steady_rows(PairTile &t, RingSlot *ring, int lan
   cp_async_commit();
   cp_async_wait<kAhead>();  // rows i and i + 1 have landed
   Quad L0, T0, L1, T1;
-  read_row(ring, lane, i, L0, T0);
-  read_row(ring, lane, i + 1, L1, T1);
+  read_row<MODEL>(ring, lane, i, L0, T0);
+  read_row<MODEL>(ring, lane, i + 1, L1, T1);
   const int x0 = t.x0;
   int x1 = x0 + 1;
   if (x1 == t.M) x1 = 0;
   run_stages<K, MODEL, false, 0>(t, i, x0, L0, T0, st, cnt);
   run_stages<K, MODEL, false, 1>(t, i + 1, x1, L1, T1, st, cnt);
   t.x0 = x1 + 1 == t.M ? 0 : x1 + 1;
-  store_row(t, L0, T0);
-  store_row(t, L1, T1);
+  store_row<MODEL>(t, L0, T0);
+  store_row<MODEL>(t, L1, T1);
 }
+
+// Tile plan of a launch (see the lane groups above): tiles [0, full_tiles)
+// are one full segment of one band each (tile = band * n_full + segment);
+// the rest hold gpw remainder groups each, of consecutive bands.
+struct PairPlan {
+  int n_full;      // segments of kSegOwn owned pairs (groups of 32 lanes)
+  int rem_own;     // owned pairs of the remainder segment (0: none)
+  int rem_g;       // lanes of a remainder group
+  int rem_halo;    // 1: remainder groups have a halo lane; 0: a group is the whole row ring
+  int gpw;         // remainder groups per warp tile
+  int band_rows, n_bands;
+  int full_tiles, n_tiles;
+};
+
+constexpr int kSegOwn = 31;  // owned pairs of a full segment (plus one halo lane)
 
 template <int K, int MODEL>
 __global__ void __launch_bounds__(kWarps2 * 32, K >= 8 ? 2 : 3)
     stream2_kernel(const u64 *__restrict__ Lin, const u64 *__restrict__ Tin,
-                   u64 *__restrict__ Lout, u64 *__restrict__ Tout, Geom g, int n_strips,
-                   int base, int rem, int band_rows, int n_bands, u64 *__restrict__ moved_lr,
-                   u64 *__restrict__ moved_tb, u64 tie_seed, u64 t0) {
+                   u64 *__restrict__ Lout, u64 *__restrict__ Tout, Geom g, PairPlan pp,
+                   u64 *__restrict__ moved_lr, u64 *__restrict__ moved_tb, u64 tie_seed,
+                   u64 t0) {
   using ST = typename std::conditional<MODEL == 2, StateII, StateI>::type;
   __shared__ unsigned long long s_cnt[2 * K];
   __shared__ __align__(16) ulonglong2 s_ring[kWarps2][kRing][2][32];  // [warp][slot][plane][lane]
@@ -328,21 +381,50 @@ __global__ void __launch_bounds__(kWarps2 * 32, K >= 8 ? 2 : 3)
   for (int s = 0; s < K; ++s) cnt[s] = 0;
   bool own = false;
 
-  if (tile < n_strips * n_bands) {
-    const int strip = tile % n_strips, band = tile / n_strips;
-    const int owned = base + (strip < rem ? 1 : 0);  // pairs
-    const int first = strip * base + (strip < rem ? strip : rem);
+  if (tile < pp.n_tiles) {
+    // this lane's group: its band, first owned pair, owned pairs, lanes,
+    // position and first lane in the warp, halo lane or not
+    int band, first, n_own, gs, gl, gbase, halo;
+    bool on = true;
+    if (tile < pp.full_tiles) {
+      band = tile / pp.n_full;
+      first = (tile - band * pp.n_full) * kSegOwn;
+      n_own = kSegOwn;
+      gs = 32;
+      gl = lane;
+      gbase = 0;
+      halo = 1;
+    } else {
+      const int grp = lane / pp.rem_g;
+      band = (tile - pp.full_tiles) * pp.gpw + grp;
+      first = pp.n_full * kSegOwn;
+      n_own = pp.rem_own;
+      gs = pp.rem_g;
+      gbase = grp * gs;
+      gl = lane - gbase;
+      halo = pp.rem_halo;
+      on = grp < pp.gpw && band < pp.n_bands;
+    }
     const int WP = (int)(g.W / 2);
-    int pw = (first - 1 + lane) % WP;
-    if (pw < 0) pw += WP;
+    // the pairs whose first and second words this lane holds (the halo lane:
+    // the first word of the pair right of the segment and the second word of
+    // the pair left of it); lanes in no group take pair 0 of band 0 and keep
+    // nothing
+    int p_lo = first + gl - halo, p_hi = p_lo;
+    if (halo && gl == 0) {
+      p_lo = first + n_own;
+      if (p_lo >= WP) p_lo -= WP;
+      p_hi = first > 0 ? first - 1 : WP - 1;
+    }
+    if (!on) band = p_lo = p_hi = 0;
     PairTile t;
-    t.wa = 2 * pw;
-    own = lane >= 1 && lane <= owned;
+    t.wa = 2 * p_lo;
+    own = on && !(halo && gl == 0);
     t.own = own;
-    t.src_l = lane > 0 ? lane - 1 : 0;
-    t.src_r = lane < 31 ? lane + 1 : 31;
-    t.r0 = band * band_rows;
-    t.B = t.r0 + band_rows < g.M ? band_rows : (int)g.M - t.r0;
+    t.src_l = on ? gbase + (gl == 0 ? gs - 1 : gl - 1) : lane;
+    t.src_r = on ? gbase + (gl == gs - 1 ? 0 : gl + 1) : lane;
+    t.r0 = band * pp.band_rows;
+    t.B = !on ? 0 : (t.r0 + pp.band_rows < g.M ? pp.band_rows : (int)g.M - t.r0);
     t.n_in = t.B + 2 * K;
     t.M = (int)g.M;
     t.ld_row = (t.r0 - K) % t.M;
@@ -350,8 +432,8 @@ __global__ void __launch_bounds__(kWarps2 * 32, K >= 8 ? 2 : 3)
     t.pitch = (size_t)g.P;
     // the T planes follow the L planes at the same distance in both buffers
     t.dT = Tin - Lin;
+    t.dH = (int64_t)(2 * p_hi + 1) - 2 * p_lo;
     t.Lin = Lin + t.wa;
-    t.Tin = Tin + t.wa;
     t.fL = t.Lin + (size_t)t.ld_row * t.pitch;
     t.sL = Lout + (size_t)t.r0 * t.pitch + t.wa;
     // Model II tie-break counters: n = t*M*W + x*W + w + 1 for word w of row x
@@ -360,6 +442,10 @@ __global__ void __launch_bounds__(kWarps2 * 32, K >= 8 ? 2 : 3)
     t.nbase = t0 * t.MW + (u64)t.wa + 1;
     t.tie_seed = tie_seed;
     t.x0 = t.ld_row;  // lattice row of input row i (stage 0)
+    // rows of the warp: the steady part ends at the smallest band's end, the
+    // drain at the tallest band's input
+    const int minB = (int)__reduce_min_sync(BML_FULL_MASK, on ? (unsigned)t.B : 0x7fffffffu);
+    const int n_max = (int)__reduce_max_sync(BML_FULL_MASK, (unsigned)t.B) + 2 * K;
 
     ST st[2][K];  // state sets, alternated row by row
 #pragma unroll
@@ -372,24 +458,24 @@ __global__ void __launch_bounds__(kWarps2 * 32, K >= 8 ? 2 : 3)
       if (u < t.n_in) fetch_row(t, ring, lane, u);
       cp_async_commit();
     }
-    // rows [0, 2K): the pipeline fills (guarded); rows [2K, B + K): every
-    // stage's row lies in the band and a row is emitted (unguarded, two rows
-    // a turn); the rest: the pipeline drains (guarded).  Counts are flushed
-    // every 256 rows (a 16-bit field holds at most 511 rows of moves).
+    // rows [0, 2K): the pipeline fills (guarded); rows [2K, minB + K): every
+    // stage's row lies in every lane's band and a row is emitted (unguarded,
+    // two rows a turn); the rest: the pipeline drains (guarded).  Counts are
+    // flushed every 256 rows (a 16-bit field holds at most 511 rows of moves).
     int i = 0;
     for (; i < 2 * K; i += 2) {
       guarded_row<K, MODEL, 0>(t, ring, lane, i, st, cnt);
       guarded_row<K, MODEL, 1>(t, ring, lane, i + 1, st, cnt);
     }
-    const int steady_end = t.B + K;
+    const int steady_end = minB + K;
     for (; i + 2 <= steady_end; i += 2) {
       if ((i & 255) == 0) flush_counts<K>(cnt, own, lane, s_cnt);
       steady_rows<K, MODEL>(t, ring, lane, i, st, cnt);
     }
-    for (; i < t.n_in; i += 2) {
+    for (; i < n_max; i += 2) {
       if ((i & 255) == 0) flush_counts<K>(cnt, own, lane, s_cnt);
       guarded_row<K, MODEL, 0>(t, ring, lane, i, st, cnt);
-      guarded_row<K, MODEL, 1>(t, ring, lane, i + 1, st, cnt);
+      if (i + 1 < n_max) guarded_row<K, MODEL, 1>(t, ring, lane, i + 1, st, cnt);
     }
   }
   pdl_release();  // this block's lattice work is done
@@ -403,20 +489,42 @@ __global__ void __launch_bounds__(kWarps2 * 32, K >= 8 ? 2 : 3)
   }
 }
 
+// The tile plan for bands of band_rows rows (see PairPlan); false if the
+// tile count does not fit an int.
+bool pair_plan(const Geom &g, int64_t band_rows, PairPlan &pp) {
+  const int64_t WP = g.W / 2;
+  const int64_t n_bands = (g.M + band_rows - 1) / band_rows;
+  if (WP <= 32) {  // the whole row ring in one group
+    pp.n_full = 0;
+    pp.rem_own = (int)WP;
+    pp.rem_g = (int)WP;
+    pp.rem_halo = 0;
+  } else {
+    pp.n_full = (int)(WP / kSegOwn);
+    pp.rem_own = (int)(WP % kSegOwn);
+    pp.rem_g = pp.rem_own + 1;
+    pp.rem_halo = 1;
+  }
+  pp.gpw = pp.rem_own ? 32 / pp.rem_g : 1;
+  const int64_t full = pp.n_full * n_bands;
+  const int64_t tiles = full + (pp.rem_own ? (n_bands + pp.gpw - 1) / pp.gpw : 0);
+  if (tiles > INT32_MAX - kWarps2 || band_rows > INT32_MAX) return false;
+  pp.band_rows = (int)band_rows;
+  pp.n_bands = (int)n_bands;
+  pp.full_tiles = (int)full;
+  pp.n_tiles = (int)tiles;
+  return true;
+}
+
 template <int K, int MODEL>
 cudaError_t launch2_k(const u64 *Lin, const u64 *Tin, u64 *Lout, u64 *Tout, const Geom &g,
                       int64_t band_rows, u64 *moved_lr, u64 *moved_tb, u64 tie_seed, u64 t0,
                       cudaStream_t st) {
-  const int64_t WP = g.W / 2;
-  const int64_t n_strips = (WP + 29) / 30;
-  const int base = (int)(WP / n_strips), rem = (int)(WP % n_strips);
-  const int64_t n_bands = (g.M + band_rows - 1) / band_rows;
-  const int64_t tiles = n_strips * n_bands;
-  if (tiles > INT32_MAX - kWarps2) return cudaErrorInvalidValue;
-  const int64_t blocks = (tiles + kWarps2 - 1) / kWarps2;
+  PairPlan pp;
+  if (!pair_plan(g, band_rows, pp)) return cudaErrorInvalidValue;
+  const int64_t blocks = ((int64_t)pp.n_tiles + kWarps2 - 1) / kWarps2;
   return launch_pdl(stream2_kernel<K, MODEL>, dim3((unsigned)blocks), dim3(kWarps2 * 32), 0, st,
-                    Lin, Tin, Lout, Tout, g, (int)n_strips, base, rem, (int)band_rows,
-                    (int)n_bands, moved_lr, moved_tb, tie_seed, t0);
+                    Lin, Tin, Lout, Tout, g, pp, moved_lr, moved_tb, tie_seed, t0);
 }
 
 template <int K, int MODEL>
@@ -452,9 +560,10 @@ __device__ __forceinline__ u64 shuffle64(u64 x) {
   return delta_swap(x, 0x2222222222222222ull, 1);
 }
 
-// In place, every aligned word pair (A, B) of both planes (columns
-// 128p .. 128p + 127 of a row): plain -> interleaved (to_pair) sets
-// a = even columns, b = odd columns; interleaved -> plain undoes it.
+// In place, every word of both planes: plain -> interleaved (to_pair) puts
+// the word's even columns in its low half and its odd columns in its high
+// half; interleaved -> plain undoes it.
+// One thread per aligned word pair (16-byte accesses) of either plane.
 __global__ void pair_layout_kernel(u64 *__restrict__ L, u64 *__restrict__ T, int64_t pairs,
                                    int to_pair) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < 2 * pairs;
@@ -462,14 +571,8 @@ __global__ void pair_layout_kernel(u64 *__restrict__ L, u64 *__restrict__ T, int
     u64 *p = (q < pairs ? L : T) + 2 * (q < pairs ? q : q - pairs);
     const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(p);
     ulonglong2 o;
-    if (to_pair) {
-      const u64 ua = unshuffle64(v.x), ub = unshuffle64(v.y);
-      o.x = (ua & 0xFFFFFFFFull) | (ub << 32);
-      o.y = (ua >> 32) | (ub & 0xFFFFFFFF00000000ull);
-    } else {
-      o.x = shuffle64((v.x & 0xFFFFFFFFull) | (v.y << 32));
-      o.y = shuffle64((v.x >> 32) | (v.y & 0xFFFFFFFF00000000ull));
-    }
+    o.x = to_pair ? unshuffle64(v.x) : shuffle64(v.x);
+    o.y = to_pair ? unshuffle64(v.y) : shuffle64(v.y);
     *reinterpret_cast<ulonglong2 *>(p) = o;
   }
 }
@@ -493,7 +596,18 @@ cudaError_t launch_pair_layout(u64 *L, u64 *T, const Geom &g, bool to_pair, cuda
 
 bool stream2_applies(const Geom &g) { return g.nb == 64 && g.W % 2 == 0 && g.W > 32; }
 
-int64_t stream2_strips(const Geom &g) { return (g.W / 2 + 29) / 30; }
+int64_t stream2_bands_for_tiles(const Geom &g, int64_t tiles) {
+  // tiles(n) = n_full * n + ceil(n / gpw) grows with n: the largest n that fits
+  PairPlan pp;
+  if (!pair_plan(g, g.M, pp)) return 0;
+  int64_t lo = 0, hi = g.M;
+  while (lo < hi) {
+    const int64_t n = (lo + hi + 1) / 2;
+    const int64_t t = (int64_t)pp.n_full * n + (pp.rem_own ? (n + pp.gpw - 1) / pp.gpw : 0);
+    if (t <= tiles) lo = n; else hi = n - 1;
+  }
+  return lo;
+}
 
 int stream2_occupancy(int k, int model) {
   if (model == 2) {

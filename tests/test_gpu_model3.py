@@ -55,7 +55,8 @@ def test_model3_every_depth_matches_oracle(lib, M, N):
             assert sim.model[0] == lib.BML_MODEL_III
 
 
-@pytest.mark.parametrize("M,N", [(100, 4096), (77, 6144), (40, 32768), (5, 4224)])
+@pytest.mark.parametrize("M,N", [(100, 4096), (77, 6144), (40, 32768), (5, 4224),
+                                 (60, 128 * 63), (50, 128 * 17), (40, 128 * 62)])
 def test_model3_two_words_per_lane_matches_oracle(lib, M, N):
     """The two-words-per-lane kernel (column-interleaved pairs) at every
     depth and ragged bands."""

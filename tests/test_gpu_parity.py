@@ -367,6 +367,34 @@ def test_two_words_per_lane_tilings_match_oracle(lib, M, N):
             oracle_counts_equal(sim.moved_counts(), mlr, mtb)
 
 
+# Row widths in pairs of words (128 columns) that exercise every lane-group
+# form of the two-words-per-lane kernel: the whole row ring in one cyclic
+# group (17, 31, 32 pairs), full segments of 31 pairs with no remainder (62),
+# a remainder group of one pair (63: 16 such groups share a warp), of two (33)
+# and of eight pairs (256 would be the bench row; 39 and 93 are narrower).
+PAIR_WIDTHS = [17, 31, 32, 33, 39, 62, 63, 93]
+
+
+@pytest.mark.parametrize("pairs", PAIR_WIDTHS)
+def test_two_words_per_lane_lane_groups_match_oracle(lib, pairs):
+    """Every lane-group form of the two-words-per-lane kernel, with bands of
+    different heights in one warp (a short last band packed beside full ones)
+    and a lattice shorter than one band: lattice and every count against
+    the oracle."""
+    N = 128 * pairs
+    for M, bands in [(100, [(8, 7), (8, 33), (4, 45), (2, 99), (1, 100)]), (3, [(8, 16)])]:
+        g0 = random_lattice(M, N, 7 * pairs + M, 0.19, 0.19)
+        K = 19
+        want, mlr, mtb = oracle.run(g0, K)
+        for k, band in bands:
+            with make(lib, M, N, "tblock", k) as sim:
+                sim.set_tiling(k, band, lane_words=2)
+                sim.write(g0)
+                sim.step(K)
+                np.testing.assert_array_equal(sim.read(), want, err_msg=str((M, k, band)))
+                oracle_counts_equal(sim.moved_counts(), mlr, mtb)
+
+
 @pytest.mark.parametrize("band", [300, 700, 12000])
 def test_two_words_per_lane_tall_bands_count_exactly(lib, band):
     """Bands taller than the 16-bit per-lane count fields can hold without a
