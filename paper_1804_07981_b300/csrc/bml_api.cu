@@ -342,7 +342,7 @@ int autotune(bml_sim *s) {
       const int64_t resident = (int64_t)sms * per_sm * wpb;
       const int64_t strips = lw == 2 ? 0 : make_strip_plan(s->g, k).n_strips;
       for (int waves = 1; waves <= 4; ++waves) {
-        const int64_t nb = lw == 2 ? stream2_bands_for_tiles(s->g, resident * waves)
+        const int64_t nb = lw == 2 ? stream2_bands_for_tiles(s->g, k, resident * waves)
                                    : resident * waves / strips;
         if (nb >= 1) bands.push_back((s->g.M + nb - 1) / nb);
       }

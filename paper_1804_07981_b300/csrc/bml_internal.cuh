@@ -125,9 +125,9 @@ cudaError_t launch_resident(const u64 *Lin, const u64 *Tin, u64 *Lout, u64 *Tout
 // of the launch's first step) or 3 (Model III).  Models 1 and 3 run on the
 // interleaved layout of the planes (see launch_pair_layout), Model II on the
 // plain one.  stream2_bands_for_tiles: the largest band count whose warp
-// tiles number at most `tiles`.
+// tiles number at most `tiles` at depth k.
 bool stream2_applies(const Geom &g);
-int64_t stream2_bands_for_tiles(const Geom &g, int64_t tiles);
+int64_t stream2_bands_for_tiles(const Geom &g, int k, int64_t tiles);
 int stream2_occupancy(int k, int model = 1);
 cudaError_t launch_stream2(const u64 *Lin, const u64 *Tin, u64 *Lout, u64 *Tout, const Geom &g,
                            int k, int64_t band_rows, u64 *moved_lr, u64 *moved_tb,

@@ -22,7 +22,9 @@
 // columns away from it (one per step), so at depth k < 33 the columns next
 // to the segment stay exact.  Remainder groups of several bands share a
 // warp (up to 32 lanes), so a row of 256 pairs costs 8 + 1/3 warp tiles per
-// band instead of 9 with a halo lane on each side of 30 pairs.
+// band instead of 9 with a halo lane on each side of 30 pairs.  At depth 1
+// (bound by HBM) rows of more than 32 pairs keep that strip form instead:
+// see PairPlan.
 //
 // Moved-car counts: one 32-bit register per stage and lane holds the LR moves
 // in its low 16 bits and the TB moves in its high 16 bits (a lane moves at
@@ -31,9 +33,8 @@
 // rows.  This keeps the depth-8 kernel within 255 registers without spills.
 //
 // Input rows reach the warp through a ring of kRing row slots in shared
-// memory, filled kAhead rows ahead with cp.async (the lane's two words as two
-// 8-byte copies per plane, so that the halo lane can take them from two
-// pairs); a slot is refilled at least two rows after it was last read.  The
+// memory, filled kAhead rows ahead with cp.async (see fetch_row); a slot is
+// refilled at least two rows after it was last read.  The
 // prefetch holds no registers and its wait is explicit.  In the steady part
 // of a band two rows are read from the ring before either runs its stages,
 // so that the second row's early stages can overlap the first row's late
@@ -192,6 +193,7 @@ struct PairTile {
   const u64 *fL;   // this lane's first word in the next row to fetch (L plane)
   int64_t dT;      // T plane minus L plane, in words (input and output)
   int64_t dH;      // this lane's second word minus its first (1, except the halo lane)
+  bool split;      // the tile has a two-sided halo lane: 8-byte copies (warp-uniform)
   u64 *sL;         // this lane's pair in the next row to store (L plane)
   size_t pitch;    // row pitch in words
   int ld_row, M;   // lattice row of the next row to fetch
@@ -203,17 +205,24 @@ struct PairTile {
   int x0;                        // lattice row of the current input row (Model II)
 };
 
-// Fetch the next input row into ring slot `slot` (one commit group): the
-// lane's two words as two 8-byte copies per plane (the halo lane's come from
-// two different pairs).
+// Fetch the next input row into ring slot `slot` (one commit group).  In a
+// tile with a two-sided halo lane every lane makes two 8-byte copies per
+// plane (the halo lane's words come from two pairs; copies chosen per lane
+// made the warp diverge on every row and measured 3% slower at depth 8),
+// otherwise one 16-byte copy per plane.
 __device__ __forceinline__ void fetch_row(PairTile &t, RingSlot *ring, int lane, int slot) {
   u64 *dL = reinterpret_cast<u64 *>(&ring[slot][0][lane]);
   u64 *dT = reinterpret_cast<u64 *>(&ring[slot][1][lane]);
   const u64 *fT = t.fL + t.dT;
-  cp_async8(dL, t.fL);
-  cp_async8(dL + 1, t.fL + t.dH);
-  cp_async8(dT, fT);
-  cp_async8(dT + 1, fT + t.dH);
+  if (t.split) {
+    cp_async8(dL, t.fL);
+    cp_async8(dL + 1, t.fL + t.dH);
+    cp_async8(dT, fT);
+    cp_async8(dT + 1, fT + t.dH);
+  } else {
+    cp_async16(dL, t.fL);
+    cp_async16(dT, fT);
+  }
   if (++t.ld_row == t.M) {
     t.ld_row = 0;
     t.fL = t.Lin;
@@ -347,9 +356,18 @@ __device__ __forceinline__ void steady_rows(PairTile &t, RingSlot *ring, int lan
   store_row<MODEL>(t, L1, T1);
 }
 
-// Tile plan of a launch (see the lane groups above): tiles [0, full_tiles)
-// are one full segment of one band each (tile = band * n_full + segment);
-// the rest hold gpw remainder groups each, of consecutive bands.
+// Tile plan of a launch (see the lane groups above).  Bands come in runs of
+// gpw: a run's tiles are its bands' full segments (band-major), then one
+// tile with the run's remainder groups, so that a remainder group runs near
+// the full segments of its band (their halo rows are then still in L2 when a
+// launch takes several waves).
+//
+// two_sided (depth 1 on rows of more than 32 pairs): strips of up to 30
+// pairs with a whole-pair halo lane on each side and one 16-byte copy per
+// plane for every lane (tile = band * n_strips + strip).  At depth 1 the
+// launch is bound by HBM, not by the logic, and this form reads the planes
+// at 97% of the copy peak against 77% with the 8-byte copies of the
+// two-sided halo lane (90% with 16-byte copies off the halo lane).
 struct PairPlan {
   int n_full;      // segments of kSegOwn owned pairs (groups of 32 lanes)
   int rem_own;     // owned pairs of the remainder segment (0: none)
@@ -357,7 +375,10 @@ struct PairPlan {
   int rem_halo;    // 1: remainder groups have a halo lane; 0: a group is the whole row ring
   int gpw;         // remainder groups per warp tile
   int band_rows, n_bands;
-  int full_tiles, n_tiles;
+  int per_run;     // tiles of a run of gpw bands: gpw * n_full, plus 1 with a remainder
+  int n_tiles;
+  int two_sided;   // the strip form below
+  int n_strips, s_base, s_rem;  // strips; owned pairs: s_base, one more in the first s_rem
 };
 
 constexpr int kSegOwn = 31;  // owned pairs of a full segment (plus one halo lane)
@@ -384,45 +405,68 @@ __global__ void __launch_bounds__(kWarps2 * 32, K >= 8 ? 2 : 3)
   if (tile < pp.n_tiles) {
     // this lane's group: its band, first owned pair, owned pairs, lanes,
     // position and first lane in the warp, halo lane or not
-    int band, first, n_own, gs, gl, gbase, halo;
-    bool on = true;
-    if (tile < pp.full_tiles) {
-      band = tile / pp.n_full;
-      first = (tile - band * pp.n_full) * kSegOwn;
-      n_own = kSegOwn;
-      gs = 32;
-      gl = lane;
-      gbase = 0;
-      halo = 1;
-    } else {
-      const int grp = lane / pp.rem_g;
-      band = (tile - pp.full_tiles) * pp.gpw + grp;
-      first = pp.n_full * kSegOwn;
-      n_own = pp.rem_own;
-      gs = pp.rem_g;
-      gbase = grp * gs;
-      gl = lane - gbase;
-      halo = pp.rem_halo;
-      on = grp < pp.gpw && band < pp.n_bands;
-    }
     const int WP = (int)(g.W / 2);
-    // the pairs whose first and second words this lane holds (the halo lane:
-    // the first word of the pair right of the segment and the second word of
-    // the pair left of it); lanes in no group take pair 0 of band 0 and keep
-    // nothing
-    int p_lo = first + gl - halo, p_hi = p_lo;
-    if (halo && gl == 0) {
-      p_lo = first + n_own;
-      if (p_lo >= WP) p_lo -= WP;
-      p_hi = first > 0 ? first - 1 : WP - 1;
-    }
-    if (!on) band = p_lo = p_hi = 0;
+    int band, p_lo, p_hi;
+    bool on = true, halo_lane = false;
     PairTile t;
+    if (pp.two_sided) {
+      // a strip of up to 30 pairs, its halo lanes 0 and owned + 1 (whole pairs)
+      const int strip = tile % pp.n_strips;
+      band = tile / pp.n_strips;
+      const int owned = pp.s_base + (strip < pp.s_rem ? 1 : 0);
+      const int first = strip * pp.s_base + (strip < pp.s_rem ? strip : pp.s_rem);
+      p_lo = (first - 1 + lane) % WP;
+      if (p_lo < 0) p_lo += WP;
+      p_hi = p_lo;
+      own = lane >= 1 && lane <= owned;
+      t.src_l = lane > 0 ? lane - 1 : 0;
+      t.src_r = lane < 31 ? lane + 1 : 31;
+      t.split = false;
+    } else {
+      int first, n_own, gs, gl, gbase, halo;
+      const int run = tile / pp.per_run, r = tile - run * pp.per_run;
+      const int b0 = run * pp.gpw;
+      const int run_bands = pp.n_bands - b0 < pp.gpw ? pp.n_bands - b0 : pp.gpw;
+      if (r < run_bands * pp.n_full) {  // a full segment
+        const int bi = r / pp.n_full;
+        band = b0 + bi;
+        first = (r - bi * pp.n_full) * kSegOwn;
+        n_own = kSegOwn;
+        gs = 32;
+        gl = lane;
+        gbase = 0;
+        halo = 1;
+      } else {  // the run's remainder groups, one band each
+        const int grp = lane / pp.rem_g;
+        band = b0 + grp;
+        first = pp.n_full * kSegOwn;
+        n_own = pp.rem_own;
+        gs = pp.rem_g;
+        gbase = grp * gs;
+        gl = lane - gbase;
+        halo = pp.rem_halo;
+        on = grp < run_bands;
+      }
+      // the pairs whose first and second words this lane holds (the halo lane:
+      // the first word of the pair right of the segment and the second word of
+      // the pair left of it); lanes in no group take pair 0 of band 0 and keep
+      // nothing
+      p_lo = first + gl - halo;
+      p_hi = p_lo;
+      halo_lane = halo && gl == 0;
+      if (halo_lane) {
+        p_lo = first + n_own;
+        if (p_lo >= WP) p_lo -= WP;
+        p_hi = first > 0 ? first - 1 : WP - 1;
+      }
+      if (!on) band = p_lo = p_hi = 0;
+      own = on && !halo_lane;
+      t.src_l = on ? gbase + (gl == 0 ? gs - 1 : gl - 1) : lane;
+      t.src_r = on ? gbase + (gl == gs - 1 ? 0 : gl + 1) : lane;
+      t.split = halo != 0;  // the same for every lane of the tile
+    }
     t.wa = 2 * p_lo;
-    own = on && !(halo && gl == 0);
     t.own = own;
-    t.src_l = on ? gbase + (gl == 0 ? gs - 1 : gl - 1) : lane;
-    t.src_r = on ? gbase + (gl == gs - 1 ? 0 : gl + 1) : lane;
     t.r0 = band * pp.band_rows;
     t.B = !on ? 0 : (t.r0 + pp.band_rows < g.M ? pp.band_rows : (int)g.M - t.r0);
     t.n_in = t.B + 2 * K;
@@ -489,29 +533,38 @@ __global__ void __launch_bounds__(kWarps2 * 32, K >= 8 ? 2 : 3)
   }
 }
 
-// The tile plan for bands of band_rows rows (see PairPlan); false if the
-// tile count does not fit an int.
-bool pair_plan(const Geom &g, int64_t band_rows, PairPlan &pp) {
+// The tile plan for depth k and bands of band_rows rows (see PairPlan);
+// false if the tile count does not fit an int.
+bool pair_plan(const Geom &g, int k, int64_t band_rows, PairPlan &pp) {
   const int64_t WP = g.W / 2;
   const int64_t n_bands = (g.M + band_rows - 1) / band_rows;
-  if (WP <= 32) {  // the whole row ring in one group
-    pp.n_full = 0;
-    pp.rem_own = (int)WP;
-    pp.rem_g = (int)WP;
-    pp.rem_halo = 0;
+  pp = PairPlan{};
+  int64_t tiles;
+  if (k == 1 && WP > 32) {
+    pp.two_sided = 1;
+    pp.n_strips = (int)((WP + 29) / 30);
+    pp.s_base = (int)(WP / pp.n_strips);
+    pp.s_rem = (int)(WP % pp.n_strips);
+    tiles = (int64_t)pp.n_strips * n_bands;
   } else {
-    pp.n_full = (int)(WP / kSegOwn);
-    pp.rem_own = (int)(WP % kSegOwn);
-    pp.rem_g = pp.rem_own + 1;
-    pp.rem_halo = 1;
+    if (WP <= 32) {  // the whole row ring in one group
+      pp.n_full = 0;
+      pp.rem_own = (int)WP;
+      pp.rem_g = (int)WP;
+      pp.rem_halo = 0;
+    } else {
+      pp.n_full = (int)(WP / kSegOwn);
+      pp.rem_own = (int)(WP % kSegOwn);
+      pp.rem_g = pp.rem_own + 1;
+      pp.rem_halo = 1;
+    }
+    pp.gpw = pp.rem_own ? 32 / pp.rem_g : 1;
+    pp.per_run = pp.gpw * pp.n_full + (pp.rem_own ? 1 : 0);
+    tiles = pp.n_full * n_bands + (pp.rem_own ? (n_bands + pp.gpw - 1) / pp.gpw : 0);
   }
-  pp.gpw = pp.rem_own ? 32 / pp.rem_g : 1;
-  const int64_t full = pp.n_full * n_bands;
-  const int64_t tiles = full + (pp.rem_own ? (n_bands + pp.gpw - 1) / pp.gpw : 0);
   if (tiles > INT32_MAX - kWarps2 || band_rows > INT32_MAX) return false;
   pp.band_rows = (int)band_rows;
   pp.n_bands = (int)n_bands;
-  pp.full_tiles = (int)full;
   pp.n_tiles = (int)tiles;
   return true;
 }
@@ -521,7 +574,7 @@ cudaError_t launch2_k(const u64 *Lin, const u64 *Tin, u64 *Lout, u64 *Tout, cons
                       int64_t band_rows, u64 *moved_lr, u64 *moved_tb, u64 tie_seed, u64 t0,
                       cudaStream_t st) {
   PairPlan pp;
-  if (!pair_plan(g, band_rows, pp)) return cudaErrorInvalidValue;
+  if (!pair_plan(g, K, band_rows, pp)) return cudaErrorInvalidValue;
   const int64_t blocks = ((int64_t)pp.n_tiles + kWarps2 - 1) / kWarps2;
   return launch_pdl(stream2_kernel<K, MODEL>, dim3((unsigned)blocks), dim3(kWarps2 * 32), 0, st,
                     Lin, Tin, Lout, Tout, g, pp, moved_lr, moved_tb, tie_seed, t0);
@@ -596,14 +649,16 @@ cudaError_t launch_pair_layout(u64 *L, u64 *T, const Geom &g, bool to_pair, cuda
 
 bool stream2_applies(const Geom &g) { return g.nb == 64 && g.W % 2 == 0 && g.W > 32; }
 
-int64_t stream2_bands_for_tiles(const Geom &g, int64_t tiles) {
-  // tiles(n) = n_full * n + ceil(n / gpw) grows with n: the largest n that fits
+int64_t stream2_bands_for_tiles(const Geom &g, int k, int64_t tiles) {
+  // the tile count grows with the band count n: the largest n that fits
   PairPlan pp;
-  if (!pair_plan(g, g.M, pp)) return 0;
+  if (!pair_plan(g, k, g.M, pp)) return 0;
   int64_t lo = 0, hi = g.M;
   while (lo < hi) {
     const int64_t n = (lo + hi + 1) / 2;
-    const int64_t t = (int64_t)pp.n_full * n + (pp.rem_own ? (n + pp.gpw - 1) / pp.gpw : 0);
+    const int64_t t = pp.two_sided ? (int64_t)pp.n_strips * n
+                                   : (int64_t)pp.n_full * n +
+                                         (pp.rem_own ? (n + pp.gpw - 1) / pp.gpw : 0);
     if (t <= tiles) lo = n; else hi = n - 1;
   }
   return lo;

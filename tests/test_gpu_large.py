@@ -67,18 +67,21 @@ def test_4096_nine_full_runs_against_oracle(lib, kernel):
         assert _digest(g) == r["lattice_sha256"], what
 
 
-@pytest.mark.parametrize("config", ["auto", "depth 8, 251-row bands, two words per lane"])
+@pytest.mark.parametrize("config", ["auto", (8, 231, 2), (8, 251, 2)],
+                         ids=["auto", "depth8-band231-pairs", "depth8-band251-pairs"])
 def test_32768_windows_after_1024_steps_against_oracle(lib, config):
     """32768 x 32768, density 0.38, seed 1, 1024 steps in the benchmark's
-    launch configuration (autotuned, and the tiling it picks on a B300 given
-    explicitly): the 33 x 33 centres of eight (2t + 33)^2 windows, one across
-    both wrap seams, equal the oracle's run of each window as its own torus."""
+    launch configuration (autotuned, and the tiling it picks on a B300 --
+    depth 8, 231-row bands, two words per lane -- given explicitly; 251-row
+    bands as another band height): the 33 x 33 centres of eight
+    (2t + 33)^2 windows, one across both wrap seams, equal the oracle's run
+    of each window as its own torus."""
     ref = _golden("oracle_32768_windows.json")
     M, N, t, c = ref["M"], ref["N"], ref["steps"], ref["centre"]
     kw = {} if config == "auto" else {"kernel": "tblock", "block_k": 8}
     with lib.Lattice(M, N, seed=ref["seed"], density=ref["rho"], reserve_steps=t, **kw) as sim:
         if config != "auto":
-            sim.set_tiling(8, 251, lane_words=2)
+            sim.set_tiling(*config[:2], lane_words=config[2])
         sim.step(t)
         got = sim.read()
     assert len(ref["windows"]) == 8
@@ -244,7 +247,7 @@ def test_32768_one_pass_and_depth_8_agree_and_match_windows(lib):
     sampled 33 x 33 windows match the oracle (8 steps at a time)."""
     M = N = 32768
     out = []
-    for k, band in ((1, 16), (8, 251)):
+    for k, band in ((1, 16), (8, 231)):
         with lib.Lattice(M, N, seed=1, density=0.38, kernel="tblock", block_k=k) as sim:
             sim.set_tiling(k, band, lane_words=2)
             sim.step(8)
@@ -272,12 +275,12 @@ def test_32768_full_job_byte_kernel_agrees(lib):
     """The benchmark's full job, 32768 x 32768, density 0.38, seed 1, 10^4
     steps: the byte-per-cell kernels (an independent GPU path: one byte per
     cell, one kernel per phase) and the bit-packed kernel in the bench's
-    launch configuration (depth 8, 251-row bands, two words per lane) end
+    launch configuration (depth 8, 231-row bands, two words per lane) end
     with the same lattice and the same count at every step."""
     M = N = 32768
     K = 10000
     out = []
-    for kernel, tiling in (("byte", None), ("tblock", (8, 251, 2))):
+    for kernel, tiling in (("byte", None), ("tblock", (8, 231, 2))):
         with lib.Lattice(M, N, seed=1, density=0.38, kernel=kernel,
                          block_k=8 if tiling else 0, reserve_steps=K) as sim:
             if tiling:
