@@ -93,7 +93,7 @@ struct bml_sim {
   DevBuf planes[2];  // each: L then T, M*P words apiece
   DevBuf bytes[2];
   int cur = 0;
-  bool pair_layout = false;  // planes[cur] in the pair-interleaved layout (else plain)
+  bool pair_layout = false;  // planes[cur] in the interleaved layout (else plain)
   DevBuf counts;  // cap u64 LR counts, then cap u64 TB counts
   int64_t cap = 0;
   int64_t steps_done = 0;
@@ -181,8 +181,8 @@ int grow_counts(bml_sim *s, int64_t need) {
 }
 
 // Bring the current planes into the layout the next kernel reads: the
-// pair-interleaved one for the two-words-per-lane Model I kernel, the plain
-// one for every other kernel and for unpacking (one in-place pass).
+// interleaved one for the two-words-per-lane kernel of Models I and III, the
+// plain one for every other kernel and for unpacking (one in-place pass).
 int set_layout(bml_sim *s, bool pair) {
   if (s->pair_layout == pair) return BML_OK;
   CUDA_TRY(launch_pair_layout(plane_L(s, s->cur), plane_T(s, s->cur), s->g, pair, s->st));

@@ -58,7 +58,7 @@ def test_model3_every_depth_matches_oracle(lib, M, N):
 @pytest.mark.parametrize("M,N", [(100, 4096), (77, 6144), (40, 32768), (5, 4224),
                                  (60, 128 * 63), (50, 128 * 17), (40, 128 * 62)])
 def test_model3_two_words_per_lane_matches_oracle(lib, M, N):
-    """The two-words-per-lane kernel (column-interleaved pairs) at every
+    """The two-words-per-lane kernel (interleaved layout) at every
     depth and ragged bands."""
     g0 = with_doubles(random_lattice(M, N, 5 * M + N, 0.25, 0.25), N)
     K = 21

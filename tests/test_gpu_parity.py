@@ -416,7 +416,7 @@ def test_two_words_per_lane_tall_bands_count_exactly(lib, band):
 
 
 def test_pair_layout_conversions_between_kernels(lib):
-    """The two-words-per-lane kernel keeps its planes column-interleaved; the
+    """The two-words-per-lane kernel keeps its planes interleaved; the
     object converts them whenever the next kernel (one word per lane, the
     Model II pair kernel), a read or a device read needs the plain order.
     Switching tilings, models and reads between calls in every order gives
