@@ -30,6 +30,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <vector>
 
 #include <cuda.h>  // CUtensorMap and its enums (the encoder is fetched at run time)
@@ -557,25 +558,35 @@ int mfail(int code, const char *fmt, ...) {
                    __LINE__);                                                               \
   } while (0)
 
-bool g_attr_done = false;
+// Set-up shared by all calls, under g_setup_mu: the tensor-map encoder
+// (fetched from the driver once per process) and, per device, whether the
+// GEMM kernel's dynamic shared-memory limit has been raised there.
+constexpr int kMaxDevices = 64;
+std::mutex g_setup_mu;
+bool g_attr_done[kMaxDevices] = {};
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
 // Tensor map of a K-major bf16 matrix (rows x K, ld elements between rows)
 // with a box of 64 elements of K x box_rows rows, 128-byte swizzle.
 cudaError_t kmajor_map(CUtensorMap *map, const bf16 *p, int rows, int K, int ld, int box_rows) {
-  if (!g_encode) {
-    void *fn = nullptr;
-    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
-    const cudaError_t e =
-        cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
-    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
-    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_setup_mu);
+    if (!g_encode) {
+      void *fn = nullptr;
+      cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+      const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                             cudaEnableDefault, &q);
+      if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+      g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    encode = g_encode;
   }
   const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
   const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
   const cuuint32_t box[2] = {(cuuint32_t)kKC, (cuuint32_t)box_rows};
   const cuuint32_t elem[2] = {1, 1};
-  const CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16 *>(p), dims,
+  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16 *>(p), dims,
                               strides, box, elem, CU_TENSOR_MAP_INTERLEAVE_NONE,
                               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -585,11 +596,19 @@ cudaError_t kmajor_map(CUtensorMap *map, const bf16 *p, int rows, int K, int ld,
 // A: M rows x K (lda), B: N rows x K (ldb); 16-byte aligned, lda, ldb % 8 == 0.
 cudaError_t launch_gemm(const bf16 *A, int lda, const bf16 *B, int ldb, int M, int N, int K,
                         const Epi &epi, cudaStream_t st) {
-  if (!g_attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(umma_gemm_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+  {
+    // the shared-memory limit is raised once on every device the GEMM runs on
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    g_attr_done = true;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_setup_mu);
+    if (!g_attr_done[dev]) {
+      e = cudaFuncSetAttribute(umma_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               kMaxSmem);
+      if (e != cudaSuccess) return e;
+      g_attr_done[dev] = true;
+    }
   }
   if (M < 1 || N < 16 || N > 128 || N % 16 || K < 16 || K % 16 || lda % 8 || ldb % 8 ||
       (uintptr_t)A % 16 || (uintptr_t)B % 16)
