@@ -201,6 +201,33 @@ def test_translation_equivariance(M, N):
         np.testing.assert_array_equal(stb, btb)
 
 
+@pytest.mark.parametrize("K", [1, 2, 4, 8])
+def test_light_cone_of_a_false_junction(K):
+    """A cell's state after K steps depends only on the cells within K
+    columns of it (Sec. 2: a car moves at most one cell per phase, and a
+    cell's phase reads only its neighbours).  So a row ring assembled from
+    pieces of the lattice that are not neighbours -- 64 columns right of a
+    strip of 128-column pairs, then 64 columns left of it, then the strip,
+    as the two-words-per-lane kernel's halo lane holds them -- gives every
+    strip cell exactly after K <= 8 steps.  The cone is exactly K columns:
+    pieces K columns wide still give the strip exactly, pieces K - 1
+    columns wide do not (on this lattice)."""
+    M, P = 48, 12                      # rows; the lattice is P pairs of 128 columns wide
+    g = random_lattice(M, 128 * P, 17 + K, 0.19, 0.19)
+    want, _, _ = oracle.run(g, K)
+    first, n_own = 3, 5                # the strip: pairs 3..7
+    right = np.arange(64) + 128 * (first + n_own)
+    left = np.arange(64, 128) + 128 * (first - 1)
+    strip = np.arange(128 * first, 128 * (first + n_own))
+    cols = np.concatenate([right, left, strip])
+    got, _, _ = oracle.run(np.ascontiguousarray(g[:, cols]), K)
+    np.testing.assert_array_equal(got[:, 128:], want[:, strip])
+    for w, exact in ((K, True), (K - 1, False)):
+        ring = np.concatenate([right[:w], left[64 - w:], strip])
+        out, _, _ = oracle.run(np.ascontiguousarray(g[:, ring]), K)
+        assert np.array_equal(out[:, 2 * w:], want[:, strip]) == exact, w
+
+
 def _swap_kinds(g):
     out = g.copy()
     out[g == LR] = TB
