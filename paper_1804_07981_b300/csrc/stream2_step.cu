@@ -15,12 +15,13 @@
 // Lane groups.  A row of WP <= 32 pairs is one cyclic group of WP lanes (the
 // whole ring, no halo).  Wider rows are cut into segments of 31 pairs and a
 // remainder segment; a segment's group is its lanes plus one halo lane that
-// holds the first 64 columns right of the segment (its low word) and the
-// last 64 columns left of it (its high word), and the group's shuffles are
+// holds the first 64 columns right of the segment (its first word) and the
+// last 64 columns left of it (its second word), and the group's shuffles are
 // cyclic.  The halo lane's two words are not neighbours in the lattice, but
-// a wrong neighbour changes a cell only after as many steps as the cell is
-// columns away from it (one per step), so at depth k < 33 the columns next
-// to the segment stay exact.  Remainder groups of several bands share a
+// a cell d columns away from a wrong neighbour is still exact after d steps
+// (a car moves one cell per phase and a phase reads only neighbours), so the
+// segment's cells, 64 columns from that junction, stay exact at every depth
+// the kernel runs (k <= 8).  Remainder groups of several bands share a
 // warp (up to 32 lanes), so a row of 256 pairs costs 8 + 1/3 warp tiles per
 // band instead of 9 with a halo lane on each side of 30 pairs.  At depth 1
 // (bound by HBM) rows of more than 32 pairs keep that strip form instead:
