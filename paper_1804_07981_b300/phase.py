@@ -185,12 +185,14 @@ def fig1(prefix: str, N: int = 256, densities=(0.25, 0.32, 0.38), steps: int = 4
 
 
 # single_tiling: the 4096^2 runs go six at a time, so each takes a share of
-# the GPU; bands of 64 rows at depth 8 (one word per lane) beat the tiling
-# autotuned for a lattice alone (band 16) by 21% on this workload.
+# the GPU; two words per lane at depth 8 with bands of 32 rows (a 4096-column
+# row is one cyclic group of 32 lanes) beat the tiling autotuned for a lattice
+# alone (depth 4, band 16) by 12% and one word per lane with 64-row bands by
+# 27% on six concurrent lattices.
 FULL = {"sizes": [256, 512, 1024, 2048, 4096],
         "densities": [round(0.20 + 0.01 * i, 2) for i in range(31)],
         "seeds": 32, "single_seeds": 8, "T": 100000, "window": 1024,
-        "single_tiling": (8, 64, 1)}
+        "single_tiling": (8, 32, 2)}
 
 SMALL = {"sizes": [64, 128, 256], "densities": [round(0.20 + 0.04 * i, 2) for i in range(8)],
          "seeds": 8, "single_seeds": 4, "T": 8192, "window": 256}

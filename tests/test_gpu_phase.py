@@ -16,7 +16,7 @@ def oracle_runs(N, densities, seeds, T, window):
     for r in densities:
         for s in range(1, seeds + 1):
             g0 = oracle.init(N, N, s, r / 2, r / 2)
-            _, lr, tb = oracle.run(g0, T)
+            _, lr, tb = oracle.run(g0, T, threads=os.cpu_count() or 1)
             tot = lr + tb
             cars = int(np.count_nonzero(g0))
             rho.append(r)
@@ -40,15 +40,13 @@ def test_phase_runs_match_oracle(lib):
         np.testing.assert_allclose(got[1], want[1], rtol=1e-12, atol=0)
         np.testing.assert_array_equal(got[2], want[2])
         if N > 64:
-            # the same runs with a given tiling for the concurrent lattices,
-            # the shipped one of the full diagram included (depth 8, 64-row
-            # bands: a 96-row lattice is cut into two bands)
-            for tiling in [(8, 16, 1), tuple(phase.FULL["single_tiling"])]:
-                got = phase._runs_single(N, dens, seeds, T, window, None, chunk=300,
-                                         tiling=tiling)
-                np.testing.assert_array_equal(got[0], want[0])
-                np.testing.assert_allclose(got[1], want[1], rtol=1e-12, atol=0)
-                np.testing.assert_array_equal(got[2], want[2])
+            # the same runs with a given tiling for the concurrent lattices
+            # (depth 8, 16-row bands, one word per lane)
+            got = phase._runs_single(N, dens, seeds, T, window, None, chunk=300,
+                                     tiling=(8, 16, 1))
+            np.testing.assert_array_equal(got[0], want[0])
+            np.testing.assert_allclose(got[1], want[1], rtol=1e-12, atol=0)
+            np.testing.assert_array_equal(got[2], want[2])
     curves = phase.phase_diagram([32, 96], dens, 4, T, window, ensemble_max_n=64,
                                  single_seeds=2)
     for N, S in [(32, 4), (96, 2)]:
@@ -58,6 +56,22 @@ def test_phase_runs_match_oracle(lib):
             assert c["runs"][i] == S
             assert c["jam_frac"][i] == jam[rho == r].mean()
             assert abs(c["v_mean"][i] - v[rho == r].mean()) < 1e-12
+
+
+def test_phase_runs_in_the_shipped_tiling_match_oracle(lib):
+    """The full diagram's tiling for its concurrent single lattices (two
+    words per lane, depth 8, 32-row bands) on the smallest square lattice it
+    applies to, 2176 x 2176 (17 word pairs per row, one cyclic lane group
+    like a 4096-column row): velocities and jam flags equal the oracle's."""
+    from paper_1804_07981_b300 import phase
+    tiling = tuple(phase.FULL["single_tiling"])
+    assert tiling[2] == 2
+    N, dens, seeds, T, window = 2176, [0.3, 0.5], 1, 192, 64
+    want = oracle_runs(N, dens, seeds, T, window)
+    got = phase._runs_single(N, dens, seeds, T, window, None, chunk=100, tiling=tiling)
+    np.testing.assert_array_equal(got[0], want[0])
+    np.testing.assert_allclose(got[1], want[1], rtol=1e-12, atol=0)
+    np.testing.assert_array_equal(got[2], want[2])
 
 
 def test_fig1_lattices_match_oracle(lib, tmp_path):
