@@ -15,7 +15,7 @@ With no argument all six files are written.  On 8 host threads the 4096^2
 runs take about 30 minutes, the t = 1024 windows about 2 (the four t = 4096
 windows about an hour), the 32-lattice ensemble
 subset about 20, all 4096 lattices for 512 steps about 2 hours and the
-256-lattice subset for 10^4 steps about 2.5 hours (one single-threaded
+256-lattice subset for 10^4 steps about 80 minutes (one single-threaded
 oracle run per lattice, as many processes as host threads).
 
 - oracle_4096_runs.json: the single-lattice workload 4096 x 4096, densities

@@ -6,9 +6,9 @@ records each final lattice and count trace by its SHA-256): all nine
 4096^2 x 4096-step runs through both the byte-per-cell and the bit-packed
 kernels, the 32768^2 lattice after 1024 steps through eight (2t + 33)^2
 windows in the benchmark's launch configuration and after 4096 steps through
-four, 32 lattices of the
-ensemble workload for the full 10^4 steps, and every lattice of that
-workload for 512 steps.  Beside them: oracle runs on
+four, 32 lattices of the ensemble workload at its size quantiles and the
+seeded 256-lattice subset (every 16th) for the full 10^4 steps, and every
+lattice of that workload for 512 steps.  Beside them: oracle runs on
 sampled windows computed here, exact cross-checks between independent GPU
 paths, and properties that hold at any size."""
 import hashlib
@@ -110,18 +110,23 @@ def test_32768_windows_after_4096_steps_against_oracle(lib):
         np.testing.assert_array_equal(got[np.ix_(rows, cols)], want, err_msg=str(w["i0"]))
 
 
-def test_ensemble_workload_32_lattices_full_10000_steps_against_oracle(lib):
+def test_ensemble_workload_full_10000_steps_against_oracle(lib):
     """The batched-ensemble workload (4096 lattices), autotuned as the
-    benchmark runs it, 10^4 steps: 32 lattices spread over the range of
-    sizes (N mod 64 != 0 included) end with the oracle's lattice and count
-    trace, and the jam steps of the early-exit ensemble equal the oracle's
-    first step with no move."""
+    benchmark runs it, 10^4 steps, with and without the jam early exit: 32
+    lattices spread over the range of sizes and the seeded 256-lattice
+    subset (every 16th; N mod 64 != 0 included) end with the oracle's
+    lattice and count trace, and the jam steps of the early-exit ensemble
+    equal the oracle's first step with no move."""
     from paper_1804_07981_b300.inputs import ensemble_params
-    ref = _golden("oracle_ensemble_subset.json")
-    K = ref["steps"]
+    sub = _golden("oracle_ensemble_subset.json")
+    every16 = _golden("oracle_ensemble_256.json")
+    K = sub["steps"]
+    assert every16["steps"] == K == 10000
     p = ensemble_params(4096, seed=1)
-    recs = ref["lattices"]
-    assert len(recs) == 32 and any(r["N"] % 64 for r in recs)
+    recs = sub["lattices"] + every16["lattices"]
+    assert len(sub["lattices"]) == 32 and len(every16["lattices"]) == 256
+    assert [r["index"] for r in every16["lattices"]] == list(range(0, 4096, 16))
+    assert any(r["N"] % 64 for r in recs)
     for flags in (0, lib.BML_ENS_EARLY_EXIT):
         with lib.Ensemble(p["M"], p["N"], p["seed"], p["p_lr"], p["p_tb"], flags=flags,
                           reserve_steps=K) as ens:

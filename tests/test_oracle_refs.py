@@ -52,6 +52,11 @@ def test_golden_files_cover_the_workloads():
     all512 = _load("oracle_ensemble_all_512.json")
     assert all512["steps"] == 512 and len(all512["digests"]) == 4096
     assert all(len(d) == 32 and int(d, 16) >= 0 for d in all512["digests"])
+    e256 = _load("oracle_ensemble_256.json")
+    assert e256["steps"] == 10000
+    assert [r["index"] for r in e256["lattices"]] == list(range(0, 4096, 16))
+    assert all((r["M"], r["N"]) == (int(p["M"][r["index"]]), int(p["N"][r["index"]]))
+               for r in e256["lattices"])
 
 
 def test_smallest_ensemble_record_recomputes_from_the_oracle():
@@ -67,6 +72,22 @@ def test_smallest_ensemble_record_recomputes_from_the_oracle():
     for key, val in got.items():
         assert rec[key] == val, key
     assert isinstance(rec["first_zero_step"], int) and np.all(lr >= 0)
+
+
+def test_smallest_record_of_the_256_lattice_file_recomputes():
+    """The smallest lattice of the seeded 256-lattice subset (10^4 steps),
+    recomputed from the oracle."""
+    mod = _script()
+    e256 = _load("oracle_ensemble_256.json")
+    rec = min(e256["lattices"], key=lambda r: r["M"] * r["N"])
+    p = ensemble_params(4096, seed=1)
+    l = rec["index"]
+    g0 = oracle.init(rec["M"], rec["N"], int(p["seed"][l]), float(p["p_lr"][l]),
+                     float(p["p_tb"][l]))
+    g, lr, tb = oracle.run(g0, e256["steps"], threads=os.cpu_count() or 1)
+    got = mod.record(g, lr, tb)
+    for key, val in got.items():
+        assert rec[key] == val, key
 
 
 def test_smallest_records_of_the_whole_ensemble_files_recompute():
