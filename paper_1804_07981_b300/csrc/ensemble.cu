@@ -3,16 +3,18 @@
 // from a CUDA graph).
 //
 // Layout.  Every lattice has two bitplane buffers (ping-pong), each L then T,
-// M x P words (P = W rounded up to even), in one device pool.  Per-lattice
-// moved-count traces are [lattice][step] int64 arrays (LR and TB).
+// M x P words (P = W rounded up to even), in one device pool; within a word
+// the even columns sit in the low half and the odd ones in the high half
+// (ens_bit).  Per-lattice moved-count traces are [lattice][step] int64
+// arrays (LR and TB).
 //
 // Tiles.  Every lattice row fits one warp (N <= 2048, W <= 32 words).  A
 // lattice is cut into row bands; a warp tile packs bands of any word widths
 // side by side (first fit over the bands sorted by length; a band of W words
 // takes W consecutive lanes, one whole periodic row), so narrow lattices do
 // not leave lanes idle.  Each band streams through the same k-stage register
-// pipeline as the single-lattice streaming kernel (the stage math is
-// shared), with k-row halos read modulo M.  Tiles are ordered longest first
+// pipeline as the single-lattice streaming kernel (the rule of stage.cuh,
+// here on interleaved words: stage_step_x), with k-row halos read modulo M.  Tiles are ordered longest first
 // and warps draw them from a dispenser (one atomic per tile), so the work is
 // spread by longest-processing-time-first list scheduling; the band height
 // is chosen on the host by a model of that schedule and confirmed by timing.
@@ -183,18 +185,92 @@ __device__ __forceinline__ void ens_store(EnsCursor &c, u64 L, u64 T) {
   c.Lo += c.pitch;
 }
 
+// Interleaved word layout of the ensemble's planes: column 64w + b of a row
+// is bit ens_bit(b) of word w, the word's even columns in its low half and
+// its odd columns in its high half (so a cell's right neighbour is mostly
+// the same bit of the other half, and the stage needs half the shifts).
+__host__ __device__ __forceinline__ int ens_bit(int b) { return (b >> 1) | ((b & 1) << 5); }
+
+// Per-lane constants of the interleaved stage; half a = even columns (low
+// 32 bits), half b = odd columns (high 32 bits).  A word with n cells (64
+// except a row's last word) has ne = ceil(n/2) even and no = floor(n/2) odd
+// cells.  The right neighbour of its last cell is the right lane's column 0,
+// inserted by a multiply-add: for n odd the last cell is even (a bit no), the
+// neighbour's E enters the even cells' right-neighbour word at bit no
+// (ins_a); for n even it is odd (b bit no - 1, bit 31 of a full word) and
+// enters at bit no - 1 of the odd cells' one (ins_b).  The last cell sent
+// to the left lane's neighbour is placed at bit 31 by a * mul_a + b * mul_b.
+struct LaneWordX {
+  uint32_t va, vb;        // valid cells of each half (0 for a lane that is off)
+  uint32_t ins_a, ins_b;  // bit that receives the right neighbour's column 0
+  uint32_t mul_a, mul_b;
+  int src_l, src_r;       // lanes holding the left / right neighbour words
+};
+
+__device__ __forceinline__ void lane_word_bits_x(LaneWordX &lw, bool on, bool last, int nb) {
+  const int n = last ? nb : 64;
+  const int ne = (n + 1) >> 1, no = n >> 1;
+  lw.va = on ? (ne >= 32 ? ~0u : (1u << ne) - 1u) : 0u;
+  lw.vb = on ? (no >= 32 ? ~0u : (1u << no) - 1u) : 0u;
+  lw.ins_a = (n & 1) ? 1u << no : 0u;
+  lw.ins_b = (n & 1) ? 0u : 1u << (no - 1);
+  lw.mul_a = (n & 1) ? 1u << (31 - no) : 0u;
+  lw.mul_b = (n & 1) ? 0u : 1u << (32 - no);
+}
+
+// One stage (the rule of stage.cuh, "who enters" form) on a word in the
+// interleaved layout; L, T: {a, b}.  Even cell 2i: right neighbour odd cell
+// 2i + 1 (b bit i), left neighbour odd cell 2i - 1 (b bit i - 1, the left
+// word's last cell for i = 0).  Odd cell 2i + 1: right neighbour even cell
+// 2i + 2 (a bit i + 1, the right word's column 0 for the last one), left
+// neighbour even cell 2i (a bit i).  So the cars entering the odd cells are
+// La & Eb with no shift, and only Er_b and the cars entering the even cells
+// need a shift: 2 shifts per word instead of 4.  A car never enters an even
+// and the odd cell right of it in the same step (the even cell would have to
+// be empty and hold the leaving car), so one popcount of in_a | in_b counts
+// the LR moves.
+__device__ __forceinline__ void stage_step_x(uint32_t (&L)[2], uint32_t (&T)[2], const StageH &st,
+                                             StageH &nx, const LaneWordX &lw, uint32_t &mvIn,
+                                             uint32_t &mvV) {
+  const uint32_t Ea = lop3<kNorAnd>(L[0], T[0], lw.va);
+  const uint32_t Eb = lop3<kNorAnd>(L[1], T[1], lw.vb);
+  const uint32_t send_l = L[1] * lw.mul_b + L[0] * lw.mul_a;
+  const uint32_t rl = __shfl_sync(BML_FULL_MASK, send_l, lw.src_l);
+  const uint32_t rr = __shfl_sync(BML_FULL_MASK, Ea, lw.src_r);
+  // the right neighbours' E (no carry: the inserted bit is past the valid ones)
+  const uint32_t Era = Eb + rr * lw.ins_a;
+  const uint32_t Erb = (Ea >> 1) + rr * lw.ins_b;
+  const uint32_t ina = lop3<kAnd>(__funnelshift_l(rl, L[1], 1), Ea, 0u);
+  const uint32_t inb = lop3<kAnd>(L[0], Eb, 0u);
+  const uint32_t Lha = lop3<kAndNotOr>(L[0], Era, ina), Lhb = lop3<kAndNotOr>(L[1], Erb, inb);
+  const uint32_t mva = lop3<kAndNor>(st.T[0], Lha, T[0]);
+  const uint32_t mvb = lop3<kAndNor>(st.T[1], Lhb, T[1]);
+  mvIn = __popc(ina | inb);
+  mvV = __popc(mva) + __popc(mvb);
+  nx.T[0] = T[0];
+  nx.T[1] = T[1];
+  nx.Lh[0] = Lha;
+  nx.Lh[1] = Lhb;
+  nx.M[0] = mva;
+  nx.M[1] = mvb;
+  T[0] = lop3<kAndNotOr>(st.T[0], mva, st.M[0]);
+  T[1] = lop3<kAndNotOr>(st.T[1], mvb, st.M[1]);
+  L[0] = st.Lh[0];
+  L[1] = st.Lh[1];
+}
+
 // The K stages on one input row i (already read); A selects the state set
 // the row reads.  GUARD: a stage's row may lie outside the band.
 template <int K, bool GUARD, int A>
 __device__ __forceinline__ void ens_stages(uint32_t (&L)[2], uint32_t (&T)[2],
                                            StageH (&st)[2][K], uint32_t (&c_lr)[K],
-                                           uint32_t (&c_tb)[K], const LaneWord &lw, int i,
+                                           uint32_t (&c_tb)[K], const LaneWordX &lw, int i,
                                            int len) {
   constexpr int B = A ^ 1;
 #pragma unroll
   for (int s = 0; s < K; ++s) {
     uint32_t mvIn, mvV;
-    stage_step_h<false>(L, T, st[A][s], st[B][s], lw, mvIn, mvV);
+    stage_step_x(L, T, st[A][s], st[B][s], lw, mvIn, mvV);
     if (!GUARD || (unsigned)(i - K - s) < (unsigned)len) c_lr[s] += mvIn;
     if (!GUARD || (unsigned)(i - K - s - 1) < (unsigned)len) c_tb[s] += mvV;
   }
@@ -233,14 +309,14 @@ __device__ void process_tile(const EnsParams &p, int t, long long step0, int par
   }
   if (!__any_sync(BML_FULL_MASK, on)) return;
 
-  LaneWord lw;
+  LaneWordX lw;
   if (on) {
     lw.src_l = gr.lane0 + (wi == 0 ? W - 1 : wi - 1);
     lw.src_r = gr.lane0 + (wi == W - 1 ? 0 : wi + 1);
   } else {
     lw.src_l = lw.src_r = lane;
   }
-  lane_word_bits(lw, on, on && wi == L.W - 1, on ? L.nb : 64, on ? L.tail : ~0ull);
+  lane_word_bits_x(lw, on, on && wi == L.W - 1, on ? L.nb : 64);
 
   const int M = on ? L.M : 1;
   const size_t pitch = on ? (size_t)L.P : 0;
@@ -428,9 +504,9 @@ __global__ void ens_init_kernel(const EnsLattice *lat, int count, const u64 *see
         for (int b = 0; b < nbits; ++b) {
           const u64 u = sm64_at(seed[l], base + (u64)b);
           if (u < t_lr[l])
-            lv |= 1ull << b;
+            lv |= 1ull << ens_bit(b);
           else if (u - t_lr[l] < t_tb[l])
-            tv |= 1ull << b;
+            tv |= 1ull << ens_bit(b);
         }
       }
       Lp[idx] = lv;
@@ -457,8 +533,8 @@ __global__ void ens_pack_kernel(const EnsLattice *lat, int count, const long lon
         for (int b = 0; b < nbits; ++b) {
           const uint32_t x = row[b];
           badl |= x > 2u;
-          lv |= (u64)(x & 1u) << b;
-          tv |= (u64)((x >> 1) & 1u) << b;
+          lv |= (u64)(x & 1u) << ens_bit(b);
+          tv |= (u64)((x >> 1) & 1u) << ens_bit(b);
         }
       }
       if (pool) {
@@ -483,7 +559,7 @@ __global__ void ens_unpack_kernel(const EnsLattice *lat, int count, const long l
     for (long long idx = threadIdx.x; idx < cells; idx += blockDim.x) {
       const int i = (int)(idx / L.N), j = (int)(idx - (long long)i * L.N);
       const long long wi = (long long)i * L.P + (j >> 6);
-      const int b = j & 63;
+      const int b = ens_bit(j & 63);
       dst[idx] = (uint8_t)(((Lp[wi] >> b) & 1ull) | (((Tp[wi] >> b) & 1ull) << 1));
     }
   }
@@ -500,7 +576,7 @@ __global__ void ens_unpack_one_kernel(const EnsLattice *lat, int l, const int *b
        idx += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(idx / L.N), j = (int)(idx - (long long)i * L.N);
     const long long wi = (long long)i * L.P + (j >> 6);
-    const int b = j & 63;
+    const int b = ens_bit(j & 63);
     dst[idx] = (uint8_t)(((Lp[wi] >> b) & 1ull) | (((Tp[wi] >> b) & 1ull) << 1));
   }
 }
