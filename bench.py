@@ -82,8 +82,8 @@ SM_MAX_MHZ = 2032.0
 TRAFFIC_PER_CELL = {("stream2_kernel<8>", 231): 0.4719, ("stream2_kernel<1>", 16): 0.4520,
                     ("stream2_kernel<4, Model II>", 154): 0.4671}
 # the ensemble kernel per cell and chunk of 8 steps (bands of 448 rows: one
-# launch of 8 chunks captured, 20.77 GB over 4.55e9 cells)
-ENS_TRAFFIC_PER_CELL_CHUNK = {(8, 448): 0.5706}
+# launch of 8 chunks captured, 20.78 GB over 4.55e9 cells)
+ENS_TRAFFIC_PER_CELL_CHUNK = {(8, 448): 0.5710}
 
 
 def _peaks():
