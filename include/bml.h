@@ -378,9 +378,10 @@ typedef struct bml_ens bml_ens;
                                  counts are 0 and their lattice stays as it is,
                                  exactly as the automaton would evolve        */
 #define BML_ENS_NO_GRAPH 2u   /* launch directly instead of replaying graphs  */
-#define BML_ENS_TEST_STALL 4u /* test hook: the grid barrier waits for one
-                                 block more than exists and gives up after
-                                 20 ms; bml_ensemble_step returns
+#define BML_ENS_TEST_STALL 4u /* test hook: the first wait between chunks
+                                 waits for one band more than its lattice
+                                 has and gives up after 20 ms (a call of at
+                                 least two chunks); bml_ensemble_step returns
                                  BML_ETIMEOUT and the ensemble becomes
                                  unusable (BML_ESTATE afterwards)             */
 

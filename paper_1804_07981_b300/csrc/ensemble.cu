@@ -19,13 +19,19 @@
 // spread by longest-processing-time-first list scheduling; the band height
 // is chosen on the host by a model of that schedule and confirmed by timing.
 //
-// Chunks.  One launch runs n chunks of k steps; between chunks every block
-// meets at a grid barrier whose waits are bounded by %globaltimer (on expiry
-// the kernel sets an error flag and returns; the host reports BML_ETIMEOUT).
-// The launch is cooperative, so all blocks are co-resident.  Data written in
-// one chunk is read by other blocks in the next, so lattice words move
-// through L2 only (cp.async.cg into a per-warp shared-memory ring, st.cg),
-// never through L1 or the non-coherent read-only path.
+// Chunks.  One launch runs n chunks of k steps.  There is no grid-wide
+// barrier between chunks: a tile of chunk c waits only until every band of
+// its own lattices has finished chunk c - 1 (a per-lattice count of finished
+// bands, released by each band after its stores; the waits are bounded by
+// %globaltimer, on expiry the kernel sets an error flag and returns and the
+// host reports BML_ETIMEOUT).  The tiles of a chunk are all handed out
+// before those of the next, so the warps a tile waits for are running.  A
+// barrier made every warp wait for the slowest tile of the whole chunk
+// (about 6% of the warps' time in stalls at the barrier, plus the idle tail
+// of every chunk).  Data written in one chunk is read by other blocks in the
+// next, so lattice words move through L2 only (cp.async.cg into a per-warp
+// shared-memory ring, st.cg), never through L1 or the non-coherent
+// read-only path.
 //
 // Jam early exit (optional).  A step in which no car moves leaves the lattice
 // unchanged, so every later step does too (an absorbing fixed point).  At the
@@ -75,9 +81,7 @@ struct EnsCtrl {
   long long steps;       // steps completed
   long long last_depth;  // depth of the last chunk run (for jam checks)
   int parity;            // buffer holding the state of lattices not frozen
-  int err;               // set by a barrier that timed out
-  unsigned bar_count;
-  unsigned bar_gen;
+  int err;               // set by a wait between chunks that timed out
   unsigned tile_next;    // tile dispenser (0 between launches)
 };
 
@@ -95,7 +99,9 @@ struct EnsParams {
   EnsCtrl *ctrl;
   int commit;          // 0: tuning launch, counts go to scratch, nothing frozen
   int early_exit;
-  unsigned bar_target; // blocks expected at the barrier
+  const unsigned *lat_groups;  // bands (groups) of every lattice in the tile plan
+  unsigned *lat_done;  // bands of every lattice finished in this launch (0 at its start)
+  unsigned stall_extra;  // test hook: 1 makes the first wait between chunks never end
   long long timeout_ns;
   u64 *scratch;        // tuning counts
 };
@@ -110,42 +116,29 @@ __device__ __forceinline__ long long globaltimer_ns() {
   return (long long)t;
 }
 
-// Grid-wide barrier with a bounded wait.  Returns false if this or another
-// block gave up (the error flag is set).
-__device__ bool grid_barrier(EnsCtrl *ctrl, unsigned target, long long timeout_ns) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    volatile unsigned *gen = &ctrl->bar_gen;
-    volatile int *err = &ctrl->err;
-    const unsigned g0 = *gen;
-    __threadfence();
-    const unsigned arrived = atomicAdd(&ctrl->bar_count, 1u) + 1u;
-    if (arrived == target) {
-      atomicExch(&ctrl->bar_count, 0u);
-      __threadfence();
-      atomicAdd(&ctrl->bar_gen, 1u);
-    } else {
-      const long long t0 = globaltimer_ns();
-      while (*gen == g0) {
-        if (*err) {
-          ok = 0;
-          break;
-        }
-        if (globaltimer_ns() - t0 > timeout_ns) {
-          atomicExch(&ctrl->err, 1);
-          ok = 0;
-          break;
-        }
-        __nanosleep(200);
-      }
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *q) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(q) : "memory");
+  return v;
+}
+
+// Wait until lattice l's count of finished bands reaches `target`, bounded by
+// p.timeout_ns; on expiry (or when another wait gave up) the error flag is
+// set and false is returned.
+__device__ bool wait_lattice(const EnsParams &p, int l, unsigned target) {
+  const unsigned *cnt = p.lat_done + l;
+  if (ld_acquire_u32(cnt) >= target) return true;
+  volatile int *err = &p.ctrl->err;
+  const long long t0 = globaltimer_ns();
+  while (ld_acquire_u32(cnt) < target) {
+    if (*err) return false;
+    if (globaltimer_ns() - t0 > p.timeout_ns) {
+      atomicExch(&p.ctrl->err, 1);
+      return false;
     }
-    __threadfence();
-    s_ok = ok;
+    __nanosleep(64);
   }
-  __syncthreads();
-  return s_ok != 0;
+  return true;
 }
 
 // Input rows reach a warp through a ring of kEnsRing row slots in shared
@@ -432,41 +425,63 @@ __device__ void process_tile(const EnsParams &p, int t, long long step0, int par
 template <int K>
 __global__ void __launch_bounds__(kEnsWarps * 32, K >= 8 ? 3 : 4) ens_kernel(EnsParams p) {
   __shared__ __align__(16) EnsRing s_ring[kEnsWarps];
-  const int lane = threadIdx.x & 31;
+  __shared__ unsigned s_ticket[kEnsWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwarps = gridDim.x * kEnsWarps;
   const long long base = __ldcg(&p.ctrl->steps);
   const long long last_depth = __ldcg(&p.ctrl->last_depth);
   const int par0 = *(volatile int *)&p.ctrl->parity;
-  // Every warp draws tickets until it gets one past the chunk's last tile, so
-  // chunk c draws exactly n_tiles + nwarps tickets: [c * stride, (c+1) * stride).
-  // The draw of the launch's last ticket resets the dispenser for the next
-  // launch (no later draw exists).
-  // (the host keeps n_chunks * stride below 2^32)
-  const unsigned stride = (unsigned)p.n_tiles + (unsigned)nwarps;
-  const unsigned last_ticket = stride * (unsigned)p.n_chunks - 1u;
-  for (int c = 0; c < p.n_chunks; ++c) {
+  // Ticket v is tile v % n_tiles of chunk v / n_tiles: every tile of a chunk
+  // is drawn before any tile of the next one, and tiles are ordered longest
+  // first (longest-processing-time-first list scheduling within a chunk).
+  // Every warp draws until it gets a ticket past the last tile, so a launch
+  // draws n_chunks * n_tiles + nwarps tickets; the draw of the last one
+  // resets the dispenser for the next launch (no later draw exists).  (The
+  // host keeps that count below 2^32.)
+  const unsigned total = (unsigned)p.n_tiles * (unsigned)p.n_chunks;
+  const unsigned last_ticket = total + (unsigned)nwarps - 1u;
+  for (;;) {
+    if (lane == 0) {
+      const unsigned v = atomicAdd(&p.ctrl->tile_next, 1u);
+      if (v == last_ticket) atomicExch(&p.ctrl->tile_next, 0u);
+      s_ticket[warp] = v;
+    }
+    __syncwarp();
+    const unsigned v = s_ticket[warp];
+    __syncwarp();
+    if (v >= total) break;
+    const int c = (int)(v / (unsigned)p.n_tiles);
+    const int t = (int)(v - (unsigned)c * (unsigned)p.n_tiles);
     const long long step0 = base + (long long)c * K;
     const int par = (par0 + c) & 1;
     const long long prev_depth = c == 0 ? last_depth : K;
-    // dynamic assignment: a warp takes the next tile (tiles are ordered
-    // longest first, so this is longest-processing-time-first list
-    // scheduling) until the dispenser passes the last tile
-    const unsigned cbase = (unsigned)c * stride;
-    for (;;) {
-      __shared__ unsigned s_ticket[kEnsWarps];
-      if (lane == 0) {
-        const unsigned v = atomicAdd(&p.ctrl->tile_next, 1u);
-        if (v == last_ticket) atomicExch(&p.ctrl->tile_next, 0u);
-        s_ticket[threadIdx.x >> 5] = v;
-      }
-      __syncwarp();
-      const unsigned t = s_ticket[threadIdx.x >> 5] - cbase;
-      __syncwarp();
-      if (t >= (unsigned)p.n_tiles) break;
-      process_tile<K>(p, (int)t, step0, par, prev_depth, lane, s_ring[threadIdx.x >> 5]);
+    // A band of chunk c reads its lattice's rows written in chunk c - 1 (its
+    // own and k rows of each neighbour band) and overwrites the buffer chunk
+    // c - 1 read; the jam check reads the lattice's counts of chunk c - 1.
+    // So before its tile runs, the lane leading each of the tile's bands
+    // waits until every band of that lattice has finished chunk c - 1 (a
+    // count of finished bands, released after their stores).  Tiles of
+    // chunk c - 1 were all drawn before this one, by warps that are running
+    // them, so every wait ends (within the time bound, else an error).
+    const EnsTile &tile = p.tiles[t];
+    const int grp = tile.lane_grp[lane];
+    int lat = -1;
+    if (grp != 0xff) {
+      const EnsGroup g = p.groups[tile.first_group + grp];
+      if (g.lane0 == lane) lat = g.lat;
     }
-    if (c + 1 < p.n_chunks) {
-      if (!grid_barrier(p.ctrl, p.bar_target, p.timeout_ns)) return;
+    if (c > 0) {
+      const bool ok =
+          lat < 0 || wait_lattice(p, lat, p.lat_groups[lat] * (unsigned)c + p.stall_extra);
+      if (!__all_sync(BML_FULL_MASK, ok)) return;
+    }
+    process_tile<K>(p, t, step0, par, prev_depth, lane, s_ring[warp]);
+    // the tile's rows and counts are written: each band leader publishes
+    // (the warp's stores are ordered before the leader's fence and atomic)
+    __syncwarp();
+    if (lat >= 0) {
+      __threadfence();
+      atomicAdd(p.lat_done + lat, 1u);
     }
   }
 }
@@ -774,6 +789,9 @@ struct bml_ens {
   std::vector<long long> byte_off;
   long long total_bytes = 0;
   EnsCtrl *ctrl = nullptr;
+  unsigned *lat_groups = nullptr;  // bands of every lattice in the current tile plan
+  unsigned *lat_done = nullptr;    // bands finished per lattice, cleared before each launch
+  unsigned max_groups = 1;         // most bands of one lattice
   u64 *scratch = nullptr;
   int *flag = nullptr;
   int grid[4] = {0, 0, 0, 0};  // persistent grid per depth index (k = 1, 2, 4, 8)
@@ -807,6 +825,8 @@ void ens_free(bml_ens *e) {
   cudaFree(e->buf_of);
   cudaFree(e->byte_off_d);
   cudaFree(e->ctrl);
+  cudaFree(e->lat_groups);
+  cudaFree(e->lat_done);
   cudaFree(e->scratch);
   cudaFree(e->flag);
 }
@@ -936,6 +956,12 @@ int upload_tiles(bml_ens *e, const TilePlan &plan, int64_t band) {
                         cudaMemcpyHostToDevice, e->st));
   ECUDA(cudaMemcpyAsync(e->d_groups, groups.data(), groups.size() * sizeof(EnsGroup),
                         cudaMemcpyHostToDevice, e->st));
+  // bands per lattice: what a wait between chunks counts to
+  std::vector<unsigned> per((size_t)e->count, 0u);
+  for (const EnsGroup &g : groups) ++per[(size_t)g.lat];
+  e->max_groups = std::max(1u, *std::max_element(per.begin(), per.end()));
+  ECUDA(cudaMemcpyAsync(e->lat_groups, per.data(), per.size() * sizeof(unsigned),
+                        cudaMemcpyHostToDevice, e->st));
   ECUDA(cudaStreamSynchronize(e->st));
   e->n_tiles = (int)tiles.size();
   e->band_rows = band;
@@ -965,6 +991,9 @@ EnsParams make_params(bml_ens *e, int n_chunks, int commit) {
   p.ctrl = e->ctrl;
   p.commit = commit;
   p.early_exit = commit && (e->flags & BML_ENS_EARLY_EXIT) ? 1 : 0;
+  p.lat_groups = e->lat_groups;
+  p.lat_done = e->lat_done;
+  p.stall_extra = (e->flags & BML_ENS_TEST_STALL) ? 1u : 0u;
   p.timeout_ns = e->timeout_ns;
   p.scratch = e->scratch;
   return p;
@@ -988,7 +1017,7 @@ int enqueue_ens(bml_ens *e, int k, int n_chunks, int commit) {
   if (n_chunks <= 0) return BML_OK;
   EnsParams p = make_params(e, n_chunks, commit);
   const int grid = grid_for(e, k);
-  p.bar_target = (unsigned)grid + ((e->flags & BML_ENS_TEST_STALL) ? 1u : 0u);
+  ECUDA(cudaMemsetAsync(e->lat_done, 0, (size_t)e->count * sizeof(unsigned), e->st));
   cudaError_t rc;
   switch (k) {
     case 1: rc = launch_ens<1>(p, grid, e->st); break;
@@ -1009,9 +1038,12 @@ int enqueue_steps_ens(bml_ens *e, int64_t k) {
   const int64_t full = k / e->block_k;
   int64_t left = k - full * e->block_k;
   int64_t done = 0;
-  // one launch draws n_chunks * (n_tiles + warps) 32-bit tickets
+  // one launch draws n_chunks * n_tiles + warps 32-bit tickets, and a
+  // lattice's count of finished bands reaches n_chunks * its bands
   const int64_t per_chunk = (int64_t)e->n_tiles + 4ll * grid_for(e, e->block_k);
-  const int64_t max_chunks = std::max<int64_t>(1, std::min<int64_t>(1 << 20, 0xffffffffll / per_chunk));
+  const int64_t max_chunks = std::max<int64_t>(
+      1, std::min<int64_t>({1 << 20, 0xffffffffll / per_chunk,
+                            (0xffffffffll - 1) / (int64_t)e->max_groups}));
   while (done < full) {
     const int n = (int)std::min<int64_t>(full - done, max_chunks);
     int rc = enqueue_ens(e, e->block_k, n, 1);
@@ -1055,8 +1087,8 @@ int check_err(bml_ens *e) {
   ECUDA(cudaStreamSynchronize(e->st));
   if (c.err) {
     e->failed = true;
-    return efail(BML_ETIMEOUT, "a grid barrier of the ensemble kernel timed out; the ensemble "
-                 "state is undefined");
+    return efail(BML_ETIMEOUT, "a wait between chunks of the ensemble kernel timed out; the "
+                 "ensemble state is undefined");
   }
   return BML_OK;
 }
@@ -1274,6 +1306,8 @@ extern "C" int bml_ensemble_create_ex(int64_t count, const int64_t *M, const int
   ETRY(cudaMalloc(&e->buf_of, count * sizeof(int)));
   ETRY(cudaMalloc(&e->byte_off_d, count * sizeof(long long)));
   ETRY(cudaMalloc(&e->ctrl, sizeof(EnsCtrl)));
+  ETRY(cudaMalloc(&e->lat_groups, count * sizeof(unsigned)));
+  ETRY(cudaMalloc(&e->lat_done, count * sizeof(unsigned)));
   ETRY(cudaMalloc(&e->scratch, 16 * sizeof(u64)));
   ETRY(cudaMalloc(&e->flag, 256));
   ETRY(cudaMalloc(&d_seed, count * 8));
@@ -1337,7 +1371,7 @@ extern "C" void bml_ensemble_destroy(bml_ens *e) {
 
 extern "C" int bml_ensemble_step(bml_ens *e, int64_t k) {
   if (!e) return efail(BML_EINVAL, "ensemble is NULL");
-  if (e->failed) return efail(BML_ESTATE, "ensemble failed earlier (barrier timeout)");
+  if (e->failed) return efail(BML_ESTATE, "ensemble failed earlier (a wait between chunks timed out)");
   if (k < 0) return efail(BML_EINVAL, "k < 0");
   if (k == 0) return BML_OK;
   int rc = grow_traces(e, e->steps_done + k);
@@ -1428,7 +1462,7 @@ extern "C" int bml_ensemble_plan(int64_t count, const int64_t *M, const int64_t 
 extern "C" int bml_ensemble_retire(bml_ens *e, int64_t n, const int64_t *lattices) {
   if (!e || (n > 0 && !lattices)) return efail(BML_EINVAL, "NULL argument");
   if (n < 0 || n > INT32_MAX) return efail(BML_EINVAL, "n outside [0, 2^31)");
-  if (e->failed) return efail(BML_ESTATE, "ensemble failed earlier (barrier timeout)");
+  if (e->failed) return efail(BML_ESTATE, "ensemble failed earlier (a wait between chunks timed out)");
   for (int64_t i = 0; i < n; ++i)
     if (lattices[i] < 0 || lattices[i] >= e->count)
       return efail(BML_EINVAL, "lattice index %lld out of range", (long long)lattices[i]);
@@ -1563,7 +1597,7 @@ extern "C" int bml_ensemble_read_lattice(bml_ens *e, int64_t lattice, uint8_t *o
 
 extern "C" int bml_ensemble_write_lattices(bml_ens *e, const uint8_t *in) {
   if (!e || !in) return efail(BML_EINVAL, "NULL argument");
-  if (e->failed) return efail(BML_ESTATE, "ensemble failed earlier (barrier timeout)");
+  if (e->failed) return efail(BML_ESTATE, "ensemble failed earlier (a wait between chunks timed out)");
   uint8_t *d = nullptr;
   ECUDA(cudaMalloc(&d, (size_t)std::max<long long>(1, e->total_bytes)));
   int hbad = 0;

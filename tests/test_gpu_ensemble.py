@@ -173,15 +173,15 @@ def test_ensemble_write_rejects_bad_values(lib):
 
 
 def test_ensemble_barrier_timeout_is_reported(lib):
-    """A grid barrier that can never complete (test hook: it waits for one
-    block more than the grid has) gives up after its time limit; the call
-    reports BML_ETIMEOUT, the ensemble refuses further work, and the GPU
-    context stays usable."""
+    """A wait between chunks that can never complete (test hook: it waits
+    for one band more than its lattice has) gives up after its time limit;
+    the call reports BML_ETIMEOUT, the ensemble refuses further work, and
+    the GPU context stays usable."""
     M, N, seeds, plr, ptb = mixed_shapes(8, 5)
     with lib.Ensemble(M, N, seeds, plr, ptb, block_k=2, band_rows=16,
                       flags=lib.BML_ENS_TEST_STALL | lib.BML_ENS_NO_GRAPH) as ens:
         with pytest.raises(lib.BMLError) as e:
-            ens.step(8)  # four chunks: three barriers
+            ens.step(8)  # four chunks: waits before the last three
         assert e.value.code == lib.BML_ETIMEOUT
         with pytest.raises(lib.BMLError) as e:
             ens.step(2)
