@@ -446,11 +446,14 @@ int bml_ensemble_labels(bml_ens *ens, int64_t window, float *d_v, float *d_jam);
 /* The ensemble's tile plan for lattices M[l] x N[l] (host arrays of count
  * entries) at target band height `band`, computed on the host without any
  * CUDA call: *out_tiles = warp tiles; *out_score = the autotuner's predicted
- * chunk cost in rows per warp at depth `depth` on `warps` warps (mean tile
- * rows per warp plus the makespan of the longest-first assignment, each tile
- * costing its longest band plus 2 * depth halo rows); out_rows (NULL or
- * count entries) = rows of each lattice covered by the plan's bands (M[l]
- * when every row is in exactly one band).  BML_EINVAL on bad arguments. */
+ * cost of a launch of 32 chunks of depth `depth` on `warps` warps, in rows
+ * per warp: each tile costs its longest band plus 2 * depth halo rows, a
+ * chunk costs the larger of the mean tile rows per warp and 1.2 times the
+ * longest tile, and the makespan of the longest-first assignment beyond the
+ * mean is added once (32 * max(mean, 1.2 * longest) + makespan - mean);
+ * out_rows (NULL or count entries) = rows of each lattice covered by the
+ * plan's bands (M[l] when every row is in exactly one band).  BML_EINVAL on
+ * bad arguments. */
 int bml_ensemble_plan(int64_t count, const int64_t *M, const int64_t *N, int64_t band, int depth,
                       int warps, int64_t *out_tiles, double *out_score, int64_t *out_rows);
 

@@ -97,7 +97,8 @@ struct EnsParams {
   long long *frozen;   // first zero-move step of a frozen lattice, else -1
   int *frozen_buf;     // buffer index holding a frozen lattice
   EnsCtrl *ctrl;
-  int commit;          // 0: tuning launch, counts go to scratch, nothing frozen
+  int commit;          // 0: tuning launch: every chunk reads the current buffer, counts
+                       // go to scratch, nothing frozen
   int early_exit;
   const unsigned *lat_groups;  // bands (groups) of every lattice in the tile plan
   unsigned *lat_done;  // bands of every lattice finished in this launch (0 at its start)
@@ -453,7 +454,9 @@ __global__ void __launch_bounds__(kEnsWarps * 32, K >= 8 ? 3 : 4) ens_kernel(Ens
     const int c = (int)(v / (unsigned)p.n_tiles);
     const int t = (int)(v - (unsigned)c * (unsigned)p.n_tiles);
     const long long step0 = base + (long long)c * K;
-    const int par = (par0 + c) & 1;
+    // a tuning launch (not committed) runs every chunk from the current
+    // buffer into the other one, so the lattices' state is left as it was
+    const int par = p.commit ? (par0 + c) & 1 : par0;
     const long long prev_depth = c == 0 ? last_depth : K;
     // A band of chunk c reads its lattice's rows written in chunk c - 1 (its
     // own and k rows of each neighbour band) and overwrites the buffer chunk
@@ -921,26 +924,35 @@ void plan_tiles(const bml_ens *e, int64_t band, TilePlan &plan) {
                    [](const EnsTile &a, const EnsTile &b) { return a.max_len > b.max_len; });
 }
 
-// Predicted time of one chunk of depth k for a plan, in rows per warp: a tile
-// costs its longest band plus the 2k halo rows; the score is the mean work
-// per warp plus the makespan of the kernel's longest-first assignment to
-// `warps` warps (list scheduling, simulated).  Measured chunk times of
-// mixed ensembles follow the sum of the two closely (a warp that runs alone
-// at the end of a chunk is faster than one among a full SM, so neither term
-// alone fits).
+// Predicted time of a launch of kTuneChunks chunks of depth k for a plan, in
+// rows per warp.  A tile costs its longest band plus the 2k halo rows.  With
+// no barrier between chunks a chunk costs the mean work per warp (total /
+// warps), unless one lattice's longest band comes close: a lattice's chunk c
+// waits for all of its bands' chunk c - 1, so the longest tile bounds a
+// chunk from below (counted with a margin of 1.2: near the mean that chain
+// already makes the time vary from run to run); the makespan of the
+// longest-first assignment (list scheduling, simulated) beyond the mean is
+// paid once, at the launch's end.
+// On the bench ensemble (4096 lattices, depth 8) the measured times follow
+// it: bands of 336 / 448 / 576 / 768 / 1024 rows, mean 1379 / 1363 / 1357 /
+// 1359 / 1348 rows per warp, longest tile 519 / 687 / 879 / 1167 / 1551,
+// 1.063 / 1.054 / 1.041 / 1.043 / 1.128 s for 10^4 steps.
+constexpr int kTuneChunks = 32;
 double plan_score(const TilePlan &plan, int k, int warps) {
   if (plan.tiles.empty() || warps < 1) return 0.0;
   std::vector<long long> heap((size_t)warps, 0);  // min-heap of warp finish times
-  long long total = 0, makespan = 0;
+  long long total = 0, makespan = 0, longest = 0;
   for (const EnsTile &t : plan.tiles) {
     const long long c = (long long)t.max_len + 2ll * k;
     total += c;
+    longest = std::max(longest, c);
     std::pop_heap(heap.begin(), heap.end(), std::greater<long long>());
     heap.back() += c;
     makespan = std::max(makespan, heap.back());
     std::push_heap(heap.begin(), heap.end(), std::greater<long long>());
   }
-  return (double)total / warps + (double)makespan;
+  const double mean = (double)total / warps;
+  return kTuneChunks * std::max(mean, 1.2 * (double)longest) + ((double)makespan - mean);
 }
 
 int upload_tiles(bml_ens *e, const TilePlan &plan, int64_t band) {
@@ -1096,7 +1108,9 @@ int check_err(bml_ens *e) {
 // Autotune (depth, band).  Every band height from 32 to 1024 rows in steps of
 // 16 (and powers of two up to the tallest lattice) is planned on the host
 // and scored for depth 8 (plan_score); the four best distinct plans are
-// timed at depth 8 and the best-scored one also at depths 1, 2 and 4.
+// timed at depth 8 and the best-scored one also at depths 1, 2 and 4, each
+// on launches of kTuneChunks chunks (as long calls run them: the end-of-launch
+// tail is paid once, not once per chunk).
 int autotune_ens(bml_ens *e) {
   int max_m = 1;
   for (const EnsLattice &l : e->lat) max_m = std::max(max_m, l.M);
@@ -1146,10 +1160,10 @@ int autotune_ens(bml_ens *e) {
       if ((rc = build_tiles(e, band))) break;
       built = band;
     }
-    if ((rc = enqueue_ens(e, k, 1, 0))) break;  // warm-up, not committed
+    if ((rc = enqueue_ens(e, k, kTuneChunks, 0))) break;  // warm-up, not committed
     cudaEventRecord(a, e->st);
-    const int reps = 3;
-    for (int r = 0; r < reps && !rc; ++r) rc = enqueue_ens(e, k, 1, 0);
+    const int reps = 2;
+    for (int r = 0; r < reps && !rc; ++r) rc = enqueue_ens(e, k, kTuneChunks, 0);
     cudaEventRecord(b, e->st);
     if (rc) break;
     if (cudaEventSynchronize(b) != cudaSuccess) {
@@ -1158,7 +1172,7 @@ int autotune_ens(bml_ens *e) {
     }
     float ms = 0;
     cudaEventElapsedTime(&ms, a, b);
-    const double per = ms / (reps * k);
+    const double per = ms / ((double)reps * kTuneChunks * k);
     if (per < best) {
       best = per;
       best_k = k;

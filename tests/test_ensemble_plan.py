@@ -3,7 +3,9 @@ row of every lattice lies in exactly one band, and the plan and its score
 equal a plain Python restatement of the planning rules (bands of round(M /
 band) near-equal rows, first fit of the bands sorted longest first into
 32-lane warps that close at 7/8 of their longest band, tiles ordered longest
-first, longest-first list scheduling of tile costs max_len + 2 * depth)."""
+first, tile costs max_len + 2 * depth; the score of a launch of 32 chunks:
+32 * max(mean cost per warp, 1.2 * longest tile) plus the makespan of
+longest-first list scheduling beyond the mean)."""
 import heapq
 import math
 
@@ -50,7 +52,8 @@ def restated_plan(M, N, band, depth, warps):
         f = heapq.heappop(heap) + c
         makespan = max(makespan, f)
         heapq.heappush(heap, f)
-    return len(tiles), sum(costs) / warps + makespan
+    mean = sum(costs) / warps
+    return len(tiles), 32 * max(mean, 1.2 * costs[0]) + (makespan - mean)
 
 
 @pytest.mark.parametrize("band", [16, 64, 448, 5000])
