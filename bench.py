@@ -81,9 +81,10 @@ SM_MAX_MHZ = 2032.0
 # changed since its capture) reports traffic null.
 TRAFFIC_PER_CELL = {("stream2_kernel<8>", 231): 0.4719, ("stream2_kernel<1>", 16): 0.4520,
                     ("stream2_kernel<4, Model II>", 154): 0.4671}
-# the ensemble kernel per cell and chunk of 8 steps (bands of 448 rows: one
-# launch of 8 chunks captured, 20.78 GB over 4.55e9 cells)
-ENS_TRAFFIC_PER_CELL_CHUNK = {(8, 448): 0.5710}
+# the ensemble kernel per cell and chunk of 8 steps (bands of 608 rows, the
+# autotuner's pick on a B300: one launch of 8 chunks captured, 20.69 GB over
+# 4.55e9 cells)
+ENS_TRAFFIC_PER_CELL_CHUNK = {(8, 608): 0.5686}
 
 
 def _peaks():
