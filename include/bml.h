@@ -459,8 +459,10 @@ int bml_ensemble_plan(int64_t count, const int64_t *M, const int64_t *N, int64_t
 
 /* Stop advancing the n listed lattices (host array of indices; repeats and
  * lattices already retired or jammed are allowed): from the next step on
- * they keep their current state, their per-step counts are 0 and their
- * tiles cost the kernel nothing, while the other lattices go on.  Their jam
+ * they keep their current state, their per-step counts are 0 and they leave
+ * the tile plan, while the other lattices go on; the tiles are planned again
+ * for the lattices that go on (with the band height given at creation, else
+ * the one the autotuner's plan score prefers for them).  Their jam
  * steps and labels are computed over the steps before the retirement.  For
  * budget allocation: runs that have had their budget stop, the others
  * continue in the same ensemble.  bml_ensemble_write_lattices makes every

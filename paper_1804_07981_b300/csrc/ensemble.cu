@@ -785,6 +785,8 @@ struct bml_ens {
   long long cap = 0;
   long long *frozen = nullptr;
   long long *retired = nullptr;  // step at which a lattice was retired, else -1
+  std::vector<char> unplanned;   // lattices left out of the tile plan (retired); empty: none
+  bool band_fixed = false;       // band height given at creation (kept when re-planning)
   long long *cars = nullptr;
   int *frozen_buf = nullptr;
   int *buf_of = nullptr;
@@ -851,6 +853,7 @@ void plan_tiles(const bml_ens *e, int64_t band, TilePlan &plan) {
   };
   std::vector<Band> all;
   for (int l = 0; l < e->count; ++l) {
+    if (!e->unplanned.empty() && e->unplanned[(size_t)l]) continue;  // retired: no tiles
     const int M = e->lat[l].M;
     int64_t nb = (int64_t)std::llround((double)M / (double)band);
     if (nb < 1) nb = 1;
@@ -987,6 +990,45 @@ int build_tiles(bml_ens *e, int64_t band) {
   return upload_tiles(e, plan, band);
 }
 
+// Candidate band heights of the planner: 32 to 1024 rows in steps of 16,
+// then powers of two up to the tallest lattice.
+std::vector<int64_t> band_candidates(const bml_ens *e) {
+  int max_m = 1;
+  for (const EnsLattice &l : e->lat) max_m = std::max(max_m, l.M);
+  std::vector<int64_t> bands;
+  for (int64_t b = 32; b <= 1024; b += 16) bands.push_back(b);
+  for (int64_t b = 2048; b / 2 < max_m; b *= 2) bands.push_back(b);
+  return bands;
+}
+
+double plan_score(const TilePlan &plan, int k, int warps);
+int grid_for(bml_ens *e, int k);
+
+// New tile plan for the lattices still in it (after a retirement), at the
+// current depth, with the band height given at creation, else the one of the
+// best plan score (host only; no timing: the lattices' state must not move).
+int replan_ens(bml_ens *e) {
+  if (e->band_fixed) return build_tiles(e, e->band_rows);
+  const int k = e->block_k;
+  const int warps = grid_for(e, k) * kEnsWarps;
+  double best = 1e300;
+  int64_t best_b = e->band_rows;
+  TilePlan plan;
+  for (int64_t b : band_candidates(e)) {
+    plan_tiles(e, b, plan);
+    if (plan.tiles.empty()) {
+      best_b = b;
+      break;
+    }
+    const double sc = plan_score(plan, k, warps);
+    if (sc < best) {
+      best = sc;
+      best_b = b;
+    }
+  }
+  return build_tiles(e, best_b);
+}
+
 EnsParams make_params(bml_ens *e, int n_chunks, int commit) {
   EnsParams p{};
   p.lat = e->d_lat;
@@ -1027,6 +1069,13 @@ int grid_for(bml_ens *e, int k) {
 // Enqueue one persistent launch of n_chunks chunks of depth k.
 int enqueue_ens(bml_ens *e, int k, int n_chunks, int commit) {
   if (n_chunks <= 0) return BML_OK;
+  if (e->n_tiles == 0) {  // every lattice retired: nothing moves, the steps still count
+    if (commit) {
+      ens_advance_kernel<<<1, 32, 0, e->st>>>(e->ctrl, n_chunks, k);
+      ECUDA(cudaGetLastError());
+    }
+    return BML_OK;
+  }
   EnsParams p = make_params(e, n_chunks, commit);
   const int grid = grid_for(e, k);
   ECUDA(cudaMemsetAsync(e->lat_done, 0, (size_t)e->count * sizeof(unsigned), e->st));
@@ -1112,11 +1161,7 @@ int check_err(bml_ens *e) {
 // on launches of kTuneChunks chunks (as long calls run them: the end-of-launch
 // tail is paid once, not once per chunk).
 int autotune_ens(bml_ens *e) {
-  int max_m = 1;
-  for (const EnsLattice &l : e->lat) max_m = std::max(max_m, l.M);
-  std::vector<int64_t> bands;
-  for (int64_t b = 32; b <= 1024; b += 16) bands.push_back(b);
-  for (int64_t b = 2048; b / 2 < max_m; b *= 2) bands.push_back(b);
+  const std::vector<int64_t> bands = band_candidates(e);
   const int warps8 = grid_for(e, 8) * kEnsWarps;
   struct Cand {
     double score;
@@ -1357,6 +1402,7 @@ extern "C" int bml_ensemble_create_ex(int64_t count, const int64_t *M, const int
     if ((rc = tune_or_reuse(e))) goto fail_;
   } else {
     e->block_k = block_k;
+    e->band_fixed = true;
     if ((rc = build_tiles(e, band_rows))) goto fail_;
   }
   *out = e;
@@ -1494,7 +1540,14 @@ extern "C" int bml_ensemble_retire(bml_ens *e, int64_t n, const int64_t *lattice
   if (r == cudaSuccess) r = cudaStreamSynchronize(e->st);
   cudaFree(d);
   if (r != cudaSuccess) return efail(BML_ECUDA, "retire: %s", cudaGetErrorString(r));
-  return check_err(e);
+  int rc = check_err(e);
+  if (rc) return rc;
+  // the retired lattices leave the tile plan, and the band height is chosen
+  // again for the lattices that go on (fewer lattices: shorter bands keep the
+  // warps busy)
+  if (e->unplanned.empty()) e->unplanned.assign((size_t)e->count, 0);
+  for (int64_t i = 0; i < n; ++i) e->unplanned[(size_t)lattices[i]] = 1;
+  return replan_ens(e);
 }
 
 extern "C" int bml_ensemble_get_config(const bml_ens *e, int *block_k, int64_t *band_rows,
@@ -1652,6 +1705,10 @@ extern "C" int bml_ensemble_write_lattices(bml_ens *e, const uint8_t *in) {
   cudaFree(d);
   if (r != cudaSuccess) return efail(BML_ECUDA, "write lattices: %s", cudaGetErrorString(r));
   if (hbad) return efail(BML_EINVAL, "a lattice holds a value other than 0, 1, 2");
+  if (!e->unplanned.empty()) {  // no lattice is retired any more: plan them all again
+    e->unplanned.clear();
+    return replan_ens(e);
+  }
   return BML_OK;
 }
 
