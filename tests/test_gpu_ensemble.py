@@ -1,5 +1,7 @@
 """GPU parity of the batched ensemble against the CPU oracle (per lattice),
 through the C ABI."""
+import os
+
 import numpy as np
 import pytest
 
@@ -265,6 +267,43 @@ def test_ensemble_retire_stops_lattices_and_others_continue(lib, early_exit):
             np.testing.assert_array_equal(got[l], w2[l])
             np.testing.assert_array_equal(lr[l], l2[l])
             np.testing.assert_array_equal(tb[l], t2[l])
+
+
+def test_ensemble_retire_plans_the_tiles_again(lib):
+    """An autotuned ensemble of 1024 lattices of 1024 x 1024 (bands of a few
+    hundred rows): retiring all but 6 plans the tiles again for those 6 with
+    shorter bands (more tiles for the warps), and they go on exactly as the
+    oracle's runs; retired lattices keep their state.  An ensemble with its
+    band height given at creation keeps it."""
+    count, M, N, K1, K2 = 1024, 1024, 1024, 24, 40
+    rho = np.linspace(0.15, 0.45, count)
+    seeds = np.arange(1, count + 1, dtype=np.uint64)
+    keep = np.array([3, 170, 400, 401, 777, 1023])
+    gone = np.setdiff1d(np.arange(count), keep)
+    Ms, Ns = np.full(count, M), np.full(count, N)
+    with lib.Ensemble(Ms, Ns, seeds, rho / 2, rho / 2, reserve_steps=K1 + K2) as ens:
+        ens.step(K1)
+        k0, band0, _ = ens.config
+        mid = {int(l): ens.read(int(l)) for l in gone[::97]}
+        ens.retire(gone)
+        k1, band1, _ = ens.config
+        ens.step(K2)
+        for l, g in mid.items():
+            np.testing.assert_array_equal(ens.read(l), g)
+        got = {int(l): ens.read(int(l)) for l in keep}
+        lr, tb = ens.traces()
+    assert k1 == k0 and band1 < band0, (band0, band1)
+    for l in keep:
+        g0 = oracle.init(M, N, int(seeds[l]), rho[l] / 2, rho[l] / 2)
+        want, wlr, wtb = oracle.run(g0, K1 + K2, threads=os.cpu_count() or 1)
+        np.testing.assert_array_equal(got[int(l)], want)
+        np.testing.assert_array_equal(lr[l], wlr)
+        np.testing.assert_array_equal(tb[l], wtb)
+    with lib.Ensemble(Ms[:8], Ns[:8], seeds[:8], rho[:8] / 2, rho[:8] / 2, block_k=4,
+                      band_rows=128) as ens:
+        ens.step(8)
+        ens.retire(np.arange(6))
+        assert ens.config[:2] == (4, 128)
 
 
 @pytest.mark.parametrize("block_k,band", [(1, 16), (4, 64), (8, 21), (0, 0)])
