@@ -724,6 +724,10 @@ int ens_occupancy() {
   return b > 0 ? b : 1;
 }
 
+// The grid is one resident wave (SMs x blocks per SM); the launch is
+// cooperative so that it fails rather than run part of the grid later.  The
+// waits between chunks do not rely on that: a tile waits only for tiles that
+// running warps have already drawn.
 template <int K>
 cudaError_t launch_ens(const EnsParams &p, int grid, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
